@@ -1,0 +1,185 @@
+"""Plain CPU oracle for exact Density Peaks Clustering (test infrastructure).
+
+This package is TEST INFRASTRUCTURE.  Only the tests, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import it.  The CUDA library never
+does, and the two share no code, headers or helpers.
+
+The arithmetic lives in ``dpc_oracle.c`` (plain C, built with
+``-ffp-contract=off``); this module only compiles it and marshals numpy arrays.
+Every routine evaluates the paper's definitions directly (Section 3,
+Definitions 1-5): O(n^2) for full arrays, O(n) per selected point for the
+sampled forms used on large point sets.
+
+Points are ``(n, d)`` C-contiguous numpy arrays of ``int32`` or ``float32``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dpc_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+I32 = 0
+F32 = 1
+
+# planted deviations, used only by tests that show a pin catches a mistake
+VAR_EXCLUSIVE = 1
+VAR_NO_SELF = 2
+VAR_TIE_LARGER_ID = 4
+VAR_DIST_TIE_LARGER = 8
+VAR_SQRT_COMPARE = 16
+VAR_DROP_LAST_DIM = 32
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into ``oracle/_liboracle.so``."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-pthread", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        i64, i32, dbl, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+        lib.orc_density.argtypes = [vp, i32, i64, i32, dbl, vp, i64, i32, i32, vp]
+        lib.orc_dependent.argtypes = [vp, i32, i64, i32, vp, ctypes.c_int32, i32, i32, vp, vp]
+        lib.orc_dependent_at.argtypes = [vp, i32, i64, i32, dbl, vp, i64, i64, i32, i32, vp, vp, vp, vp]
+        lib.orc_cluster.argtypes = [i64, vp, vp, vp, ctypes.c_int32, ctypes.c_int32, dbl, vp]
+        lib.orc_kth_sqdist.argtypes = [vp, i32, i64, i32, vp, i64, i32, i32, vp]
+        lib.orc_threads.argtypes = [i32]
+        for f in (lib.orc_density, lib.orc_dependent, lib.orc_dependent_at, lib.orc_cluster,
+                  lib.orc_kth_sqdist, lib.orc_threads):
+            f.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _points(pts):
+    pts = np.asarray(pts)
+    if pts.ndim == 1:
+        pts = pts[:, None]
+    if pts.dtype == np.int32:
+        dtype = I32
+    elif pts.dtype == np.float32:
+        dtype = F32
+    else:
+        raise TypeError("points must be int32 or float32, got %s" % pts.dtype)
+    pts = np.ascontiguousarray(pts)
+    return pts, dtype, pts.shape[0], pts.shape[1]
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def threads(requested: int = 0) -> int:
+    """Number of worker threads the oracle uses for `requested` (0 = all cores)."""
+    return _load().orc_threads(requested)
+
+
+def density(pts, d_cut: float, idx=None, variant: int = 0, nthreads: int = 0) -> np.ndarray:
+    """rho (Definition 1) of every point, or of the points ``idx`` only."""
+    pts, dtype, n, d = _points(pts)
+    if idx is not None:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        m = idx.shape[0]
+    else:
+        m = n
+    out = np.zeros(m, dtype=np.int32)
+    if n == 0 or m == 0:
+        return out
+    rc = _load().orc_density(_ptr(pts), dtype, n, d, float(d_cut), _ptr(idx), m, variant, nthreads, _ptr(out))
+    if rc:
+        raise RuntimeError("orc_density failed: %d" % rc)
+    return out
+
+
+def dependent(pts, rho, rho_skip: int = 0, variant: int = 0, nthreads: int = 0):
+    """(lambda, delta) of every point from a full rho array (Definitions 2-3)."""
+    pts, dtype, n, d = _points(pts)
+    rho = np.ascontiguousarray(rho, dtype=np.int32)
+    assert rho.shape == (n,)
+    lam = np.zeros(n, dtype=np.int32)
+    delta = np.zeros(n, dtype=np.float64)
+    if n == 0:
+        return lam, delta
+    rc = _load().orc_dependent(_ptr(pts), dtype, n, d, _ptr(rho), int(rho_skip), variant, nthreads,
+                               _ptr(lam), _ptr(delta))
+    if rc:
+        raise RuntimeError("orc_dependent failed: %d" % rc)
+    return lam, delta
+
+
+def dependent_at(pts, d_cut: float, idx, max_checks: int = 64, variant: int = 0, nthreads: int = 0):
+    """(lambda, delta, rho, resolved) of the points ``idx``, with densities
+    computed on demand; see ``orc_dependent_at``.  ``resolved[t]`` is False when
+    more than ``max_checks`` nearer points had to be examined."""
+    pts, dtype, n, d = _points(pts)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    m = idx.shape[0]
+    lam = np.zeros(m, dtype=np.int32)
+    delta = np.zeros(m, dtype=np.float64)
+    rho = np.zeros(m, dtype=np.int32)
+    status = np.zeros(m, dtype=np.int8)
+    if m == 0:
+        return lam, delta, rho, status.astype(bool)
+    rc = _load().orc_dependent_at(_ptr(pts), dtype, n, d, float(d_cut), _ptr(idx), m, int(max_checks),
+                                  variant, nthreads, _ptr(lam), _ptr(delta), _ptr(rho), _ptr(status))
+    if rc:
+        raise RuntimeError("orc_dependent_at failed: %d" % rc)
+    return lam, delta, rho, status.astype(bool)
+
+
+def cluster(rho, lam, delta, rho_noise: int, rho_min: int, delta_min: float) -> np.ndarray:
+    """Labels (Definitions 4-5 and the assignment rule)."""
+    rho = np.ascontiguousarray(rho, dtype=np.int32)
+    lam = np.ascontiguousarray(lam, dtype=np.int32)
+    delta = np.ascontiguousarray(delta, dtype=np.float64)
+    n = rho.shape[0]
+    out = np.zeros(n, dtype=np.int32)
+    if n == 0:
+        return out
+    rc = _load().orc_cluster(n, _ptr(rho), _ptr(lam), _ptr(delta), int(rho_noise), int(rho_min),
+                             float(delta_min), _ptr(out))
+    if rc:
+        raise RuntimeError("orc_cluster: dependent pointers do not form a valid forest (%d)" % rc)
+    return out
+
+
+def kth_sqdist(pts, idx, k: int, nthreads: int = 0) -> np.ndarray:
+    """k-th smallest squared distance from each point ``idx`` (self counted first)."""
+    pts, dtype, n, d = _points(pts)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.zeros(idx.shape[0], dtype=np.float64)
+    if idx.shape[0] == 0:
+        return out
+    rc = _load().orc_kth_sqdist(_ptr(pts), dtype, n, d, _ptr(idx), idx.shape[0], int(k), nthreads, _ptr(out))
+    if rc:
+        raise RuntimeError("orc_kth_sqdist failed: %d" % rc)
+    return out
+
+
+def run(pts, d_cut: float, rho_noise: int, rho_min: int, delta_min: float, rho_skip: int = 0,
+        nthreads: int = 0):
+    """Full DPC on a small point set: returns dict(rho, lam, delta, label)."""
+    rho = density(pts, d_cut, nthreads=nthreads)
+    lam, delta = dependent(pts, rho, rho_skip=rho_skip, nthreads=nthreads)
+    label = cluster(rho, lam, delta, rho_noise, rho_min, delta_min)
+    return {"rho": rho, "lam": lam, "delta": delta, "label": label}
