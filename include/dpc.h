@@ -1,0 +1,183 @@
+/*
+ * dpc.h -- C ABI of the GB300 exact Density Peaks Clustering library.
+ *
+ * What is computed (Huang, Yu, Shun, "Faster Parallel Exact Density Peaks
+ * Clustering", Section 3):
+ *   rho_i     Definition 1: the number of points j with D(x_i, x_j) <= d_cut,
+ *             the point itself included.
+ *   lambda_i  Definition 2: the nearest point of strictly higher density;
+ *             density ties are broken by id (the smaller id is higher), distance
+ *             ties go to the smaller id.  -1 for the highest point.
+ *   delta_i   Definition 3: D(x_i, lambda_i); +inf for the highest point.
+ *   label_i   Definitions 4-5 and the assignment rule after them: noise
+ *             (rho < rho_noise) gets -1; a center (not noise, and either no
+ *             dependent point or rho >= rho_min and delta >= delta_min) gets its
+ *             own id; every other point gets its dependent point's label.
+ *
+ * Distances are exact: int32 inputs use the exact integer squared distance;
+ * float32 inputs use the binary64 value
+ *     s = (((t_0*t_0) + t_1*t_1) + ...),  t_k = (double)x_ik - (double)x_jk,
+ * each operation rounded to nearest, no fused multiply-add.  The density
+ * predicate is s <= fl64(d_cut*d_cut); delta = sqrt(s) rounded to nearest.
+ * The fast paths filter in float32 with a proven error band and re-evaluate
+ * every undecided pair in binary64, so all outputs are identical to that
+ * definition whatever precision mode is chosen.
+ *
+ * Conventions shared by every entry point:
+ *   - Points are row-major [n][d], d in 1..8, int32 or float32.  int32
+ *     coordinates must satisfy |x| <= 2^24, float32 ones must be finite with
+ *     |x| <= 2^60 (so every squared distance is exact in binary64 for integers
+ *     and representable in float32); otherwise the call fails with
+ *     DPC_ERR_DATA (reported when DPC_FLAG_SYNC_CHECK is set, or by
+ *     dpc_last_status).
+ *   - Ids are 0-based and local to each instance of a batch.
+ *   - Unless stated otherwise pointers to points and results are DEVICE
+ *     pointers owned by the caller; the library never frees them.  The
+ *     library owns an internal workspace per (device, stream), grown on
+ *     demand with cudaMalloc and freed by dpc_release().  The first call at a
+ *     given size therefore allocates; later calls of the same or smaller size
+ *     do not.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = the legacy default stream).  Calls on different streams use
+ *     different workspaces and may overlap.
+ *   - Return value: DPC_OK or a negative dpc_status.  Argument errors are
+ *     detected on the host before any work is queued; nothing is written to
+ *     the outputs then.  Errors found on the device (bad coordinates, a
+ *     bounded wait that expired) are recorded in a per-workspace status word:
+ *     with DPC_FLAG_SYNC_CHECK the call synchronizes the stream and returns
+ *     that status; otherwise dpc_last_status() returns it later.
+ *   - There is no CPU fallback: without a usable CUDA device every compute
+ *     entry point returns DPC_ERR_CUDA.
+ */
+#ifndef DPC_H
+#define DPC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DPC_OK = 0,
+  DPC_ERR_ARG = -1,         /* invalid argument (detected on the host)         */
+  DPC_ERR_CUDA = -2,        /* a CUDA call failed or no device is available    */
+  DPC_ERR_OOM = -3,         /* workspace allocation failed                     */
+  DPC_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up              */
+  DPC_ERR_OVERFLOW = -5,    /* an instance has 2^31 or more points             */
+  DPC_ERR_UNSUPPORTED = -6, /* valid request this build does not implement     */
+  DPC_ERR_DATA = -7         /* coordinates out of the supported range / NaN, or
+                               dependent pointers that do not form a forest    */
+} dpc_status;
+
+/* coordinate types */
+enum { DPC_I32 = 0, DPC_F32 = 1 };
+
+/* precision modes (flags & DPC_PREC_MASK).  Both give identical results. */
+enum {
+  DPC_PREC_FP64 = 0,     /* every distance evaluated in binary64              */
+  DPC_PREC_FP32_CERT = 1 /* float32 filter + binary64 recheck of the band     */
+};
+#define DPC_PREC_MASK 0xFu
+#define DPC_FLAG_SYNC_CHECK (1u << 8) /* synchronize and return the device status */
+
+/* A batch of independent point sets packed back to back.  n_inst = 1 for a
+ * single point set.  All arrays are HOST arrays read during the call only. */
+typedef struct {
+  int32_t n_inst;
+  const int64_t* pt_offset;    /* [n_inst+1]: instance i owns points
+                                  [pt_offset[i], pt_offset[i+1]) of the packed
+                                  result arrays; pt_offset[0] = 0              */
+  const int64_t* coord_offset; /* [n_inst]: element offset of instance i's
+                                  first coordinate in `pts`; NULL means
+                                  pt_offset[i] * dim[i]                        */
+  const int32_t* dim;          /* [n_inst]: d of each instance, 1..8           */
+  int32_t n_dcut;              /* cutoffs per instance (a sweep), >= 1         */
+  const double* d_cut;         /* [n_inst * n_dcut], finite and >= 0; entry
+                                  i*n_dcut + k is cutoff k of instance i       */
+} dpc_batch;
+
+/* Labelling thresholds of one (instance, cutoff) pair (Definitions 4-5). */
+typedef struct {
+  int32_t rho_noise; /* rho < rho_noise -> noise                               */
+  int32_t rho_min;   /* centers need rho >= rho_min ...                        */
+  double delta_min;  /* ... and delta >= delta_min                             */
+} dpc_params;
+
+/* Densities (Definition 1) for every cutoff of every instance.
+ *   pts   device, packed coordinates (see dpc_batch), int32 or float32 (dtype)
+ *   rho   device, int32 [n_dcut][N], N = pt_offset[n_inst]; rho[k*N + p] is
+ *         the density of packed point p under that instance's cutoff k. */
+int dpc_density(const void* pts, int dtype, const dpc_batch* b, int32_t* rho, uint32_t flags,
+                void* stream);
+
+/* Dependent points and distances (Definitions 2-3) for cutoff `dcut_index`,
+ * given the densities of that cutoff.
+ *   rho       device, int32 [N], as written by dpc_density for that cutoff
+ *   rho_skip  points with rho < rho_skip are skipped (lambda -1, delta NaN),
+ *             as the paper skips noise points (Algorithm 1); 0 = none
+ *   lambda    device, int32 [N], instance-local id of the dependent point or -1
+ *   delta     device, double [N]; +inf for the highest point of an instance
+ * The cutoff is used only to size the search grid; the results depend on
+ * (pts, rho) alone. */
+int dpc_dependent(const void* pts, int dtype, const dpc_batch* b, int32_t dcut_index,
+                  const int32_t* rho, int32_t rho_skip, int32_t* lambda, double* delta,
+                  uint32_t flags, void* stream);
+
+/* Labels (Definitions 4-5 and the assignment rule) for cutoff `dcut_index`.
+ *   params  host, [n_inst * n_dcut] thresholds (entry i*n_dcut + dcut_index is
+ *           used for instance i)
+ *   rho, lambda, delta  device, [N], as produced by the two calls above
+ *   label   device, int32 [N]: instance-local id of the cluster center, or -1
+ * lambda must form a forest within each instance (as dpc_dependent writes
+ * it); a chain that does not end within ceil(log2 N)+2 pointer-jumping rounds
+ * is reported as DPC_ERR_DATA. */
+int dpc_cluster(const dpc_batch* b, int32_t dcut_index, const dpc_params* params,
+                const int32_t* rho, const int32_t* lambda, const double* delta, int32_t* label,
+                uint32_t flags, void* stream);
+
+/* The whole pipeline for every cutoff: one binning per instance, then for each
+ * cutoff density, dependent points and labels.
+ *   params                   host, [n_inst * n_dcut] thresholds
+ *   rho, lambda, delta, label  device, [n_dcut][N] each (cutoff-major) */
+int dpc_run(const void* pts, int dtype, const dpc_batch* b, const dpc_params* params,
+            int32_t* rho, int32_t* lambda, double* delta, int32_t* label, uint32_t flags,
+            void* stream);
+
+/* dpc_run on HOST buffers: copies the points to the device, runs, copies the
+ * four results back and synchronizes `stream` before returning.  Host buffers
+ * that are page-locked copy faster.  Same layouts as dpc_run. */
+int dpc_run_host(const void* pts_host, int dtype, const dpc_batch* b, const dpc_params* params,
+                 int32_t* rho_host, int32_t* lambda_host, double* delta_host,
+                 int32_t* label_host, uint32_t flags, void* stream);
+
+/* Counters from the last call on `stream` (synchronizes the stream). */
+typedef struct {
+  int64_t band_pairs;     /* density pairs re-evaluated in binary64          */
+  int64_t far_queries;    /* dependent queries not settled by the grid block */
+  int64_t exact_rescans;  /* dependent queries whose float32 winner was
+                             ambiguous and were re-ranked in binary64        */
+  int64_t occupied_cells; /* occupied grid cells of the last cutoff          */
+  int32_t grid_level;     /* level of the density grid of the last cutoff    */
+  int32_t bits_per_axis;  /* Morton bits per gridded axis of the last binning */
+} dpc_stats;
+int dpc_get_stats(void* stream, dpc_stats* out);
+
+/* Device-side status of the last call on `stream` (synchronizes it). */
+int dpc_last_status(void* stream);
+
+/* Short description of a status code (static storage). */
+const char* dpc_strerror(int status);
+
+/* Library version, e.g. "0.1.0". */
+const char* dpc_version(void);
+
+/* Free every workspace of every device and stream.  Must not overlap with
+ * running calls. */
+void dpc_release(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPC_H */

@@ -1,0 +1,302 @@
+"""Python binding of the GB300 exact Density Peaks Clustering library.
+
+A thin ctypes layer over ``libdpc.so`` (declared in ``include/dpc.h``): it
+only marshals arguments.  Every step of the computation runs in the library's
+CUDA kernels; PyTorch provides device memory and the current stream.  There is
+no CPU fallback: if the library is not built, or no CUDA device is present,
+every compute call raises.
+
+The functions carry the C names:
+
+* ``dpc_density(pts, batch, ...)``            -> rho      [n_dcut, N] int32
+* ``dpc_dependent(pts, batch, k, rho, ...)``  -> (lambda [N] int32, delta [N] float64)
+* ``dpc_cluster(batch, k, params, rho, lambda, delta)`` -> label [N] int32
+* ``dpc_run(pts, batch, params, ...)``        -> dict of [n_dcut, N] tensors
+* ``dpc_run_host(pts_host, batch, params, ...)`` -> dict of host tensors
+
+``Batch.single(n, d, d_cut)`` describes one point set; ``Batch.packed`` a batch.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdpc.so")
+
+DPC_OK = 0
+DPC_ERR_ARG = -1
+DPC_ERR_CUDA = -2
+DPC_ERR_OOM = -3
+DPC_ERR_TIMEOUT = -4
+DPC_ERR_OVERFLOW = -5
+DPC_ERR_UNSUPPORTED = -6
+DPC_ERR_DATA = -7
+
+DPC_I32 = 0
+DPC_F32 = 1
+PREC = {"fp64": 0, "fp32": 1}
+DPC_FLAG_SYNC_CHECK = 1 << 8
+
+EXPORTS = ["dpc_density", "dpc_dependent", "dpc_cluster", "dpc_run", "dpc_run_host", "dpc_get_stats",
+           "dpc_last_status", "dpc_strerror", "dpc_version", "dpc_release"]
+
+
+class DpcError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__("%s failed: %s (%d)" % (what, strerror(code), code))
+        self.code = code
+
+
+class _Batch(ctypes.Structure):
+    _fields_ = [("n_inst", ctypes.c_int32), ("pt_offset", ctypes.POINTER(ctypes.c_int64)),
+                ("coord_offset", ctypes.POINTER(ctypes.c_int64)), ("dim", ctypes.POINTER(ctypes.c_int32)),
+                ("n_dcut", ctypes.c_int32), ("d_cut", ctypes.POINTER(ctypes.c_double))]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("rho_noise", ctypes.c_int32), ("rho_min", ctypes.c_int32), ("delta_min", ctypes.c_double)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("band_pairs", ctypes.c_int64), ("far_queries", ctypes.c_int64),
+                ("exact_rescans", ctypes.c_int64), ("occupied_cells", ctypes.c_int64),
+                ("grid_level", ctypes.c_int32), ("bits_per_axis", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load ``libdpc.so``; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libdpc.so is not built (%s); run `python -c \"import __graft_entry__ as g; "
+                           "g.build()\"`" % path)
+    lib = ctypes.CDLL(path)
+    vp, i32, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32
+    bp = ctypes.POINTER(_Batch)
+    pp = ctypes.POINTER(_Params)
+    lib.dpc_density.argtypes = [vp, ctypes.c_int, bp, vp, u32, vp]
+    lib.dpc_dependent.argtypes = [vp, ctypes.c_int, bp, i32, vp, i32, vp, vp, u32, vp]
+    lib.dpc_cluster.argtypes = [bp, i32, pp, vp, vp, vp, vp, u32, vp]
+    lib.dpc_run.argtypes = [vp, ctypes.c_int, bp, pp, vp, vp, vp, vp, u32, vp]
+    lib.dpc_run_host.argtypes = [vp, ctypes.c_int, bp, pp, vp, vp, vp, vp, u32, vp]
+    lib.dpc_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
+    lib.dpc_last_status.argtypes = [vp]
+    lib.dpc_strerror.argtypes = [ctypes.c_int]
+    lib.dpc_strerror.restype = ctypes.c_char_p
+    lib.dpc_version.restype = ctypes.c_char_p
+    lib.dpc_release.restype = None
+    for f in ("dpc_density", "dpc_dependent", "dpc_cluster", "dpc_run", "dpc_run_host", "dpc_get_stats",
+              "dpc_last_status"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().dpc_strerror(code).decode()
+    except RuntimeError:
+        return "status %d" % code
+
+
+def version() -> str:
+    return load().dpc_version().decode()
+
+
+def release() -> None:
+    load().dpc_release()
+
+
+# ---------------------------------------------------------------------------
+# argument marshalling
+
+
+class Batch:
+    """Host-side batch descriptor (``dpc_batch``)."""
+
+    def __init__(self, pt_offset: Sequence[int], dims: Sequence[int], d_cut, coord_offset=None):
+        n_inst = len(dims)
+        assert len(pt_offset) == n_inst + 1
+        cuts = [[float(c) for c in (row if isinstance(row, (list, tuple)) else [row])] for row in d_cut]
+        assert len(cuts) == n_inst and len({len(r) for r in cuts}) == 1
+        self.n_inst = n_inst
+        self.n_dcut = len(cuts[0])
+        self.N = int(pt_offset[-1])
+        self.dims = [int(d) for d in dims]
+        self.pt_offset = [int(x) for x in pt_offset]
+        self._po = (ctypes.c_int64 * (n_inst + 1))(*self.pt_offset)
+        self._dim = (ctypes.c_int32 * n_inst)(*self.dims)
+        self._dc = (ctypes.c_double * (n_inst * self.n_dcut))(*[c for r in cuts for c in r])
+        self._co = (ctypes.c_int64 * n_inst)(*[int(x) for x in coord_offset]) if coord_offset is not None else None
+        self.c = _Batch(n_inst, self._po, self._co, self._dim, self.n_dcut, self._dc)
+
+    @classmethod
+    def single(cls, n: int, d: int, d_cut) -> "Batch":
+        cuts = list(d_cut) if isinstance(d_cut, (list, tuple)) else [d_cut]
+        return cls([0, n], [d], [cuts])
+
+    @classmethod
+    def packed(cls, sizes: Sequence[int], dims: Sequence[int], d_cut) -> "Batch":
+        po = [0]
+        co = []
+        c = 0
+        for n, d in zip(sizes, dims):
+            co.append(c)
+            c += n * d
+            po.append(po[-1] + n)
+        return cls(po, dims, d_cut, coord_offset=co)
+
+    @property
+    def ptr(self):
+        return ctypes.byref(self.c)
+
+
+def make_params(batch: Batch, rho_noise, rho_min, delta_min):
+    """``dpc_params`` array [n_inst * n_dcut]; scalars broadcast, lists per cutoff
+    (length n_dcut) or per (instance, cutoff) (length n_inst * n_dcut)."""
+    m = batch.n_inst * batch.n_dcut
+
+    def expand(v):
+        if isinstance(v, (list, tuple)):
+            if len(v) == m:
+                return list(v)
+            if len(v) == batch.n_dcut:
+                return list(v) * batch.n_inst
+            raise ValueError("threshold list length %d" % len(v))
+        return [v] * m
+    rn, rm, dm = expand(rho_noise), expand(rho_min), expand(delta_min)
+    arr = (_Params * m)(*[_Params(int(rn[i]), int(rm[i]), float(dm[i])) for i in range(m)])
+    return arr
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.int32:
+        return DPC_I32
+    if t.dtype == torch.float32:
+        return DPC_F32
+    raise TypeError("points must be int32 or float32, got %s" % t.dtype)
+
+
+def _dev(t: torch.Tensor, name: str):
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _flags(precision: str, sync: bool) -> int:
+    return PREC[precision] | (DPC_FLAG_SYNC_CHECK if sync else 0)
+
+
+def _check(rc: int, what: str):
+    if rc != DPC_OK:
+        raise DpcError(rc, what)
+
+
+def dpc_density(pts: torch.Tensor, batch: Batch, precision: str = "fp32", sync: bool = False,
+                stream=None, out: torch.Tensor | None = None) -> torch.Tensor:
+    lib = load()
+    rho = out if out is not None else torch.empty((batch.n_dcut, batch.N), dtype=torch.int32, device=pts.device)
+    _check(lib.dpc_density(_dev(pts, "pts"), _dtype_code(pts), batch.ptr, _dev(rho, "rho"), _flags(precision, sync),
+                           _stream(stream)), "dpc_density")
+    return rho
+
+
+def dpc_dependent(pts: torch.Tensor, batch: Batch, dcut_index: int, rho: torch.Tensor, rho_skip: int = 0,
+                  precision: str = "fp32", sync: bool = False, stream=None):
+    lib = load()
+    if rho.dtype != torch.int32 or rho.numel() != batch.N:
+        raise ValueError("rho must be int32 [N]")
+    lam = torch.empty(batch.N, dtype=torch.int32, device=pts.device)
+    delta = torch.empty(batch.N, dtype=torch.float64, device=pts.device)
+    _check(lib.dpc_dependent(_dev(pts, "pts"), _dtype_code(pts), batch.ptr, int(dcut_index), _dev(rho, "rho"),
+                             int(rho_skip), _dev(lam, "lambda"), _dev(delta, "delta"), _flags(precision, sync),
+                             _stream(stream)), "dpc_dependent")
+    return lam, delta
+
+
+def dpc_cluster(batch: Batch, dcut_index: int, params, rho: torch.Tensor, lam: torch.Tensor, delta: torch.Tensor,
+                sync: bool = False, stream=None) -> torch.Tensor:
+    lib = load()
+    label = torch.empty(batch.N, dtype=torch.int32, device=rho.device)
+    _check(lib.dpc_cluster(batch.ptr, int(dcut_index), params, _dev(rho, "rho"), _dev(lam, "lambda"),
+                           _dev(delta, "delta"), _dev(label, "label"), DPC_FLAG_SYNC_CHECK if sync else 0,
+                           _stream(stream)), "dpc_cluster")
+    return label
+
+
+def dpc_run(pts: torch.Tensor, batch: Batch, params, precision: str = "fp32", sync: bool = False, stream=None,
+            out: dict | None = None) -> dict:
+    lib = load()
+    shape = (batch.n_dcut, batch.N)
+    if out is None:
+        out = {"rho": torch.empty(shape, dtype=torch.int32, device=pts.device),
+               "lam": torch.empty(shape, dtype=torch.int32, device=pts.device),
+               "delta": torch.empty(shape, dtype=torch.float64, device=pts.device),
+               "label": torch.empty(shape, dtype=torch.int32, device=pts.device)}
+    _check(lib.dpc_run(_dev(pts, "pts"), _dtype_code(pts), batch.ptr, params, _dev(out["rho"], "rho"),
+                       _dev(out["lam"], "lambda"), _dev(out["delta"], "delta"), _dev(out["label"], "label"),
+                       _flags(precision, sync), _stream(stream)), "dpc_run")
+    return out
+
+
+def dpc_run_host(pts: torch.Tensor, batch: Batch, params, precision: str = "fp32", stream=None,
+                 out: dict | None = None) -> dict:
+    """Host-buffer form: `pts` and the results are CPU tensors (pin them for
+    faster copies); the call returns after the results are on the host."""
+    lib = load()
+    if pts.is_cuda or not pts.is_contiguous():
+        raise ValueError("pts must be a contiguous CPU tensor")
+    shape = (batch.n_dcut, batch.N)
+    if out is None:
+        out = {"rho": torch.empty(shape, dtype=torch.int32), "lam": torch.empty(shape, dtype=torch.int32),
+               "delta": torch.empty(shape, dtype=torch.float64), "label": torch.empty(shape, dtype=torch.int32)}
+
+    def hp(t):
+        return ctypes.c_void_p(t.data_ptr())
+    _check(lib.dpc_run_host(hp(pts), _dtype_code(pts), batch.ptr, params, hp(out["rho"]), hp(out["lam"]),
+                            hp(out["delta"]), hp(out["label"]), _flags(precision, True), _stream(stream)),
+           "dpc_run_host")
+    return out
+
+
+def dpc_get_stats(stream=None) -> dict:
+    lib = load()
+    s = _Stats()
+    _check(lib.dpc_get_stats(_stream(stream), ctypes.byref(s)), "dpc_get_stats")
+    return {f: getattr(s, f) for f, _ in _Stats._fields_}
+
+
+def dpc_last_status(stream=None) -> int:
+    return load().dpc_last_status(_stream(stream))
+
+
+# ---------------------------------------------------------------------------
+# convenience
+
+
+def run(pts: torch.Tensor, d_cut, rho_noise, rho_min, delta_min, precision: str = "fp32", sync: bool = True,
+        stream=None) -> dict:
+    """DPC of one point set ``pts`` [n, d] (CUDA, int32/float32) for one or more cutoffs."""
+    if pts.dim() == 1:
+        pts = pts.reshape(-1, 1)
+    n, d = pts.shape
+    cuts = list(d_cut) if isinstance(d_cut, (list, tuple)) else [d_cut]
+    batch = Batch.single(n, d, cuts)
+    params = make_params(batch, rho_noise, rho_min, delta_min)
+    return dpc_run(pts.contiguous(), batch, params, precision=precision, sync=sync, stream=stream)
+

@@ -1,0 +1,257 @@
+// dpc_device.cuh -- device-side data structures and helpers shared by the
+// kernels of the exact DPC library (sm_103a).
+//
+// Layout in HBM for one instance of n points (see the kernels for who writes
+// what):
+//   codes      u64[n]   Morton code of the fine grid cell of each point
+//   spts       float[n][DP] points in Morton order, zero padded to DP = 2/4/8
+//   skey       u64[n]   order key of each sorted point, (rho << 32) | ~id
+//   hash       u64[T] keys + uint2[T] (start, end) of each occupied cell of
+//              the density grid level, open addressing, T a power of two
+//   tree       Node[n-1] binary radix tree over the sorted codes
+//
+// The grid: a fine uniform grid of 2^B cells per gridded axis (the first
+// g = min(d, 3) coordinates) covers the bounding box; a point's fine index is
+// floor((x - org) / f).  Level k of the grid merges 2^k fine cells per axis;
+// since the Morton code interleaves the axes, every level-k cell is the
+// contiguous run of sorted points sharing code >> (g*k).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dpc {
+
+constexpr int kMaxDim = 8;
+constexpr int kMaxBits = 21;              // fine-grid bits per axis (see choose_bits)
+constexpr uint64_t kEmpty = ~0ull;        // empty hash slot (codes are < 2^63)
+constexpr uint32_t kLeafBit = 0x80000000u;
+
+// status bits recorded on the device
+enum : int {
+  kStatusBadCoord = 1,   // NaN/Inf or out-of-range coordinate
+  kStatusHashFull = 2,   // hash probe limit reached (cannot happen at load <= 1/2)
+  kStatusStack = 4,      // tree traversal stack overflow
+  kStatusCycle = 8,      // dependent pointers did not converge to roots
+  kStatusIndex = 16      // an internal index failed its bounds check (a bug)
+};
+
+// Per-instance grid geometry, written by the setup kernel from the bounding box.
+struct GridGeom {
+  double org[3];     // bounding-box minimum of the gridded axes
+  double f;          // fine cell side
+  double inv_f;      // 1 / f
+  float f2;          // f*f rounded down (for lower bounds)
+  int g;             // gridded axes
+  int B;             // fine-grid bits per axis
+  int nbits;         // g * B
+  int npass;         // 8-bit radix passes needed to sort nbits-bit codes
+  int* status;       // the workspace's device status word (kStatus* bits)
+  uint32_t bbox_ord[6];  // ordered-uint min (0..2) and max (3..5) accumulators
+};
+
+// Per (instance, cutoff) parameters.  Fields marked [host] are filled before
+// the launch; the others by the setup kernels.
+struct CutGeom {
+  double dc;          // d_cut                                           [host]
+  double dc2;         // fl64(d_cut * d_cut): the density predicate      [host]
+  float t_in;         // float32 filter: s32 <= t_in  => s64 <= dc2      [host]
+  float t_out;        // float32 filter: s32 >  t_out => s64 >  dc2      [host]
+  float band_mul;     // float32 ambiguity band: s_b > s_a*band_mul+band_add
+  float band_add;     //   => s64_b > s64_a                              [host]
+  int k;              // grid level of the density / near-dependent search
+  int R;              // neighbourhood radius in level-k cells
+  float prune_fine;   // density: a cell whose squared lower bound, in fine
+                      //   units, exceeds this holds no point within d_cut
+  float far32;        // dependent: a float32 winner band below this is
+  double far64;       //   settled by the (2R+1)^g block (float / double forms)
+  uint32_t m;         // occupied level-k cells
+  uint32_t hmask;     // hash table size - 1
+};
+
+// Counters for dpc_get_stats.
+struct Counters {
+  unsigned long long band_pairs;
+  unsigned long long far_queries;
+  unsigned long long exact_rescans;
+  unsigned int queue_n;   // dependent far-query queue length
+  unsigned int pad;
+};
+
+// One internal node of the binary radix tree over sorted Morton codes.
+struct __align__(16) Node {
+  uint32_t left, right;   // child index; kLeafBit marks a leaf (sorted point)
+  unsigned long long maxkey;  // largest order key in the subtree (per cutoff)
+  unsigned long long code;    // code of the first leaf of the node's range
+  uint32_t plen;          // length of the common code prefix, <= nbits
+  uint32_t parent;        // parent internal node (root: itself)
+};
+
+// ---------------------------------------------------------------------------
+// Morton codes: axis a's bit b sits at position g*b + a.
+
+__host__ __device__ __forceinline__ uint64_t spread2(uint64_t x) {  // 32 -> 64 bits
+  x &= 0xffffffffull;
+  x = (x | (x << 16)) & 0x0000ffff0000ffffull;
+  x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
+  x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  x = (x | (x << 1)) & 0x5555555555555555ull;
+  return x;
+}
+__host__ __device__ __forceinline__ uint32_t compact2(uint64_t x) {
+  x &= 0x5555555555555555ull;
+  x = (x | (x >> 1)) & 0x3333333333333333ull;
+  x = (x | (x >> 2)) & 0x0f0f0f0f0f0f0f0full;
+  x = (x | (x >> 4)) & 0x00ff00ff00ff00ffull;
+  x = (x | (x >> 8)) & 0x0000ffff0000ffffull;
+  x = (x | (x >> 16)) & 0x00000000ffffffffull;
+  return (uint32_t)x;
+}
+__host__ __device__ __forceinline__ uint64_t spread3(uint64_t x) {  // 21 -> 63 bits
+  x &= 0x1fffffull;
+  x = (x | (x << 32)) & 0x001f00000000ffffull;
+  x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+__host__ __device__ __forceinline__ uint32_t compact3(uint64_t x) {
+  x &= 0x1249249249249249ull;
+  x = (x | (x >> 2)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x >> 4)) & 0x100f00f00f00f00full;
+  x = (x | (x >> 8)) & 0x001f0000ff0000ffull;
+  x = (x | (x >> 16)) & 0x001f00000000ffffull;
+  x = (x | (x >> 32)) & 0x00000000001fffffull;
+  return (uint32_t)x;
+}
+
+template <int G>
+__host__ __device__ __forceinline__ uint64_t morton(const uint32_t* c) {
+  if constexpr (G == 1) return c[0];
+  else if constexpr (G == 2) return spread2(c[0]) | (spread2(c[1]) << 1);
+  else return spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
+}
+template <int G>
+__host__ __device__ __forceinline__ void unmorton(uint64_t code, uint32_t* c) {
+  if constexpr (G == 1) c[0] = (uint32_t)code;
+  else if constexpr (G == 2) { c[0] = compact2(code); c[1] = compact2(code >> 1); }
+  else { c[0] = compact3(code); c[1] = compact3(code >> 1); c[2] = compact3(code >> 2); }
+}
+
+// ---------------------------------------------------------------------------
+// Open-addressing hash of occupied cells: key = level-k Morton code.
+
+__device__ __forceinline__ uint32_t hash_slot(uint64_t key, uint32_t mask) {
+  key ^= key >> 33;
+  key *= 0xff51afd7ed558ccdull;
+  key ^= key >> 33;
+  key *= 0xc4ceb9fe1a85ec53ull;
+  key ^= key >> 33;
+  return (uint32_t)key & mask;
+}
+
+// Returns (start, end) of the cell's sorted-point run, or (0, 0) if empty.
+__device__ __forceinline__ uint2 hash_find(const unsigned long long* __restrict__ keys,
+                                           const uint2* __restrict__ vals, uint32_t mask,
+                                           uint64_t key) {
+  uint32_t h = hash_slot(key, mask);
+  for (uint32_t probe = 0; probe <= mask; ++probe) {
+    unsigned long long k = __ldg(keys + h);
+    if (k == key) return __ldg(vals + h);
+    if (k == kEmpty) break;
+    h = (h + 1) & mask;
+  }
+  return make_uint2(0u, 0u);
+}
+
+// A cell run clipped to [0, n): the hash only holds runs of this instance, so
+// the clip never changes a valid run; it keeps a corrupted one in bounds.
+__device__ __forceinline__ uint2 clip_run(uint2 r, uint32_t n) {
+  r.y = r.y < n ? r.y : n;
+  r.x = r.x < r.y ? r.x : r.y;
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Distances.
+
+// Point coordinates padded to DP floats (DP = 2, 4 or 8).
+template <int DP>
+struct Pt {
+  float x[DP];
+};
+
+template <int DP>
+__device__ __forceinline__ Pt<DP> load_pt(const float* __restrict__ spts, uint32_t i) {
+  Pt<DP> p;
+  if constexpr (DP == 2) {
+    float2 v = __ldg(reinterpret_cast<const float2*>(spts) + i);
+    p.x[0] = v.x; p.x[1] = v.y;
+  } else if constexpr (DP == 4) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(spts) + i);
+    p.x[0] = v.x; p.x[1] = v.y; p.x[2] = v.z; p.x[3] = v.w;
+  } else {
+    const float4* q = reinterpret_cast<const float4*>(spts) + 2 * (size_t)i;
+    float4 a = __ldg(q), b = __ldg(q + 1);
+    p.x[0] = a.x; p.x[1] = a.y; p.x[2] = a.z; p.x[3] = a.w;
+    p.x[4] = b.x; p.x[5] = b.y; p.x[6] = b.z; p.x[7] = b.w;
+  }
+  return p;
+}
+
+// float32 filter value: any evaluation order, contraction allowed; its error
+// against the exact squared distance is covered by the bands in CutGeom.
+template <int DP>
+__device__ __forceinline__ float dist32(const Pt<DP>& a, const Pt<DP>& b) {
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < DP; ++k) {
+    float t = a.x[k] - b.x[k];
+    s = fmaf(t, t, s);
+  }
+  return s;
+}
+
+// The canonical binary64 squared distance: t_k = x_k - y_k, s = ((t0*t0 + t1*t1) + ...)
+// in increasing k, each step rounded to nearest, never contracted.  Padding
+// coordinates are zero and add exactly 0.
+template <int DP>
+__device__ __forceinline__ double dist64(const Pt<DP>& a, const Pt<DP>& b) {
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < DP; ++k) {
+    double t = __dsub_rn((double)a.x[k], (double)b.x[k]);
+    s = __dadd_rn(s, __dmul_rn(t, t));
+  }
+  return s;
+}
+
+// Order key: larger = higher in the total order (density, then smaller id).
+__device__ __forceinline__ unsigned long long order_key(int32_t rho, uint32_t id) {
+  return ((unsigned long long)(uint32_t)rho << 32) | (unsigned long long)(0xffffffffu - id);
+}
+__device__ __forceinline__ uint32_t key_id(unsigned long long key) {
+  return 0xffffffffu - (uint32_t)key;
+}
+
+// Ordered-uint encoding of floats (monotone), for atomic min/max.
+__device__ __forceinline__ uint32_t float_ord(float x) {
+  uint32_t u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__host__ __device__ __forceinline__ float ord_float(uint32_t u) {
+  uint32_t v = (u & 0x80000000u) ? (u & 0x7fffffffu) : ~u;
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(v);
+#else
+  float f;
+  __builtin_memcpy(&f, &v, 4);
+  return f;
+#endif
+}
+
+__device__ __forceinline__ void set_status(int* status, int bits) { atomicOr(status, bits); }
+
+}  // namespace dpc

@@ -1,0 +1,222 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle,
+element by element, on seeded inputs that span many grid cells and tiles,
+plus the edge cases the method has.  Both precision modes must give the
+oracle's exact output (see _gpu_util for the tolerance: none)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2305_11335_gb300 as dpc
+import workloads as W
+from _gpu_util import assert_same, bits, gpu_run, parity
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+@pytest.mark.parametrize("name", ["hand_example_1d.json", "hand_example_2d.json"])
+@pytest.mark.parametrize("dtype,scale", [(np.int32, 1.0), (np.float32, 0.25)])
+def test_hand_examples(name, dtype, scale):
+    with open(os.path.join(GOLDEN, name)) as f:
+        g = json.load(f)
+    pts = np.ascontiguousarray((np.array(g["points"], np.float64) * scale).astype(dtype))
+    got = gpu_run(pts, [g["d_cut"] * scale], g["rho_noise"], g["rho_min"], g["delta_min"] * scale)
+    assert got["rho"][0].tolist() == g["rho"]
+    assert got["lam"][0].tolist() == g["lambda"]
+    want = [math.inf if v == "inf" else v * scale for v in g["delta"]]
+    assert got["delta"][0].tolist() == want
+    assert got["label"][0].tolist() == g["label"]
+
+
+@pytest.mark.parametrize("dim,k", [(1, 40), (2, 23), (3, 9)])
+def test_lattices(dim, k):
+    pts = W.lattice(k, dim, 1)
+    parity(pts, [1.0, math.sqrt(2.0), np.nextafter(1.0, 0.0), 2.0], rho_noise=1, rho_min=2, delta_min=1.5)
+
+
+def test_line_deep_chain():
+    pts = W.line(5000, np.int32)
+    parity(pts, [1.0, 3.0], rho_noise=1, rho_min=1, delta_min=10.0)
+
+
+@pytest.mark.parametrize("n,d", [(17, 3), (300, 8), (1, 2), (2, 5)])
+def test_all_equal_and_tiny(n, d):
+    pts = W.all_equal(n, d)
+    parity(pts, [0.0, 1.0], rho_noise=1, rho_min=1, delta_min=0.5)
+
+
+def test_zero_and_huge_cutoff():
+    pts = W.random_blobs(2000, 2, 31, dtype=np.float32, dup_frac=0.05)
+    parity(pts, [0.0, 1e-6, 50.0], rho_noise=1, rho_min=2, delta_min=0.05)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 7, 8])
+@pytest.mark.parametrize("dtype", [np.float32, np.int32])
+def test_random_blobs(d, dtype):
+    n = 6000 if d <= 3 else 3000
+    scale = 2000.0 if dtype == np.int32 else 1.0
+    pts = W.random_blobs(n, d, 100 + d, dtype=dtype, scale=scale, dup_frac=0.02)
+    dc = 0.03 * scale * (1.0 + 0.6 * (d - 1))
+    parity(pts, [dc, 1.5 * dc], rho_noise=3, rho_min=8, delta_min=4 * dc)
+
+
+def test_c1_full():
+    w = W.c1()
+    parity(w.pts, w.d_cut, w.rho_noise[0], w.rho_min[0], w.delta_min[0])
+
+
+def test_boundary_band():
+    """Pairs at exactly d_cut and one float step either side: the float32
+    filter cannot decide them, the binary64 recheck must."""
+    rng = np.random.default_rng(5)
+    base = rng.random((400, 3)) * 10.0
+    dc = 0.37
+    u = rng.standard_normal((400, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    partner = base + dc * u
+    pts = np.concatenate([base, partner]).astype(np.float32)
+    # nudge partners by single float steps in random directions
+    k = rng.integers(-2, 3, (400, 3))
+    for s in range(3):
+        pts[400:, s] = np.array([np.nextafter(np.float32(v), np.float32(np.sign(t) * np.inf)) if t else v
+                                 for v, t in zip(pts[400:, s], k[:, s])], np.float32)
+    parity(pts, [dc], rho_noise=1, rho_min=2, delta_min=1.0)
+
+
+def test_large_offset_cancellation():
+    """Coordinates near 1e5 with tiny spreads: float32 differences cancel."""
+    rng = np.random.default_rng(9)
+    pts = (1e5 + rng.random((3000, 2)) * 0.5).astype(np.float32)
+    parity(pts, [0.01, 0.003], rho_noise=1, rho_min=2, delta_min=0.05)
+
+
+def test_equidistant_ties_int():
+    """Integer points on a coarse lattice with random duplicates: many exact
+    distance ties, decided by the smaller id."""
+    rng = np.random.default_rng(3)
+    pts = rng.integers(0, 40, (5000, 2)).astype(np.int32)
+    parity(pts, [1.0, 2.0, 2.5], rho_noise=2, rho_min=4, delta_min=3.0)
+
+
+def test_batched_equals_single():
+    sizes = [500, 1, 0, 2500, 1200]
+    dims = [2, 3, 2, 5, 1]
+    insts = [W.random_blobs(n, d, 200 + i) if n else np.zeros((0, d), np.float32)
+             for i, (n, d) in enumerate(zip(sizes, dims))]
+    cuts = [[0.02 * (1 + 0.5 * (d - 1)), 0.04 * (1 + 0.5 * (d - 1))] for d in dims]
+    batch = dpc.Batch.packed(sizes, dims, cuts)
+    flat = torch.from_numpy(np.concatenate([p.reshape(-1) for p in insts]).astype(np.float32)).cuda()
+    params = dpc.make_params(batch, 2, 3, [0.1] * (len(sizes) * 2))
+    out = dpc.dpc_run(flat, batch, params, sync=True)
+    out = {k: v.cpu().numpy() for k, v in out.items()}
+    for i, p in enumerate(insts):
+        lo, hi = batch.pt_offset[i], batch.pt_offset[i + 1]
+        for c in range(2):
+            ref = oracle.run(p, cuts[i][c], 2, 3, 0.1)
+            assert_same({k: v[c, lo:hi] for k, v in out.items()}, ref, "inst %d cut %d" % (i, c))
+
+
+def test_split_entry_points_match_run():
+    pts = W.random_blobs(4000, 3, 77)
+    dc = 0.05
+    t = torch.from_numpy(pts).cuda()
+    batch = dpc.Batch.single(4000, 3, [dc])
+    params = dpc.make_params(batch, 3, 6, 0.2)
+    rho = dpc.dpc_density(t, batch, sync=True)
+    lam, delta = dpc.dpc_dependent(t, batch, 0, rho[0].contiguous(), sync=True)
+    label = dpc.dpc_cluster(batch, 0, params, rho[0].contiguous(), lam, delta, sync=True)
+    ref = oracle.run(pts, dc, 3, 6, 0.2)
+    assert_same({"rho": rho[0].cpu().numpy(), "lam": lam.cpu().numpy(), "delta": delta.cpu().numpy(),
+                 "label": label.cpu().numpy()}, ref)
+
+
+def test_dependent_accepts_any_rho():
+    """dpc_dependent is a function of (points, rho): feed it densities that
+    are not those of any cutoff (seeded random), with a noise skip."""
+    pts = W.random_blobs(3000, 2, 55)
+    rng = np.random.default_rng(1)
+    rho = rng.integers(1, 12, 3000).astype(np.int32)
+    t = torch.from_numpy(pts).cuda()
+    batch = dpc.Batch.single(3000, 2, [0.02])
+    for prec in ("fp32", "fp64"):
+        lam, delta = dpc.dpc_dependent(t, batch, 0, torch.from_numpy(rho).cuda(), rho_skip=3, precision=prec,
+                                       sync=True)
+        rl, rd = oracle.dependent(pts, rho, rho_skip=3)
+        assert np.array_equal(lam.cpu().numpy(), rl)
+        assert np.array_equal(bits(delta.cpu().numpy()), bits(rd))
+
+
+def test_cluster_on_generated_forest():
+    """dpc_cluster on a seeded random forest (lambda pointing to higher ids
+    in a random order) with thresholds that create noise and centers."""
+    rng = np.random.default_rng(8)
+    n = 20000
+    order = rng.permutation(n)           # order[0] is the highest point
+    rank = np.empty(n, np.int64)
+    rank[order] = np.arange(n)
+    rho = (n - rank).astype(np.int32) // 50 + 1
+    lam = np.full(n, -1, np.int32)
+    for r in range(1, n):
+        lam[order[r]] = order[rng.integers(max(0, r - 40), r)]
+    delta = rng.random(n) * 10.0
+    delta[order[0]] = np.inf
+    ref = oracle.cluster(rho, lam, delta, 20, 60, 8.5)
+    batch = dpc.Batch.single(n, 2, [1.0])
+    params = dpc.make_params(batch, 20, 60, 8.5)
+    got = dpc.dpc_cluster(batch, 0, params, torch.from_numpy(rho).cuda(), torch.from_numpy(lam).cuda(),
+                          torch.from_numpy(delta).cuda(), sync=True)
+    assert np.array_equal(got.cpu().numpy(), ref)
+
+
+def test_bad_coordinates_reported():
+    pts = W.random_blobs(100, 2, 4)
+    pts[17, 1] = np.nan
+    with pytest.raises(dpc.DpcError) as e:
+        gpu_run(pts, [0.1], 1, 1, 1.0)
+    assert e.value.code == dpc.DPC_ERR_DATA
+    ip = W.random_blobs(100, 2, 4, dtype=np.int32, scale=100.0)
+    ip[3, 0] = (1 << 24) + 1
+    with pytest.raises(dpc.DpcError) as e:
+        gpu_run(ip, [5.0], 1, 1, 1.0)
+    assert e.value.code == dpc.DPC_ERR_DATA
+    # the library recovers: a valid call afterwards succeeds
+    parity(W.random_blobs(300, 2, 4), [0.05], precisions=("fp32",))
+
+
+def test_repeat_runs_identical():
+    pts = W.random_blobs(20000, 3, 66)
+    outs = [gpu_run(pts, [0.04], 3, 6, 0.2) for _ in range(3)]
+    for o in outs[1:]:
+        for k in o:
+            assert np.array_equal(o[k].view(np.uint8), outs[0][k].view(np.uint8))
+
+
+def test_run_host_matches_device():
+    pts = W.random_blobs(5000, 2, 12)
+    batch = dpc.Batch.single(5000, 2, [0.02, 0.03])
+    params = dpc.make_params(batch, 2, 4, 0.1)
+    host = dpc.dpc_run_host(torch.from_numpy(pts).pin_memory(), batch, params)
+    dev = dpc.dpc_run(torch.from_numpy(pts).cuda(), batch, params, sync=True)
+    for k in host:
+        assert np.array_equal(host[k].numpy().view(np.uint8), dev[k].cpu().numpy().view(np.uint8))
+
+
+def test_stats():
+    pts = W.random_blobs(20000, 2, 67)
+    gpu_run(pts, [0.01], 2, 4, 0.1)
+    s = dpc.dpc_get_stats()
+    assert s["occupied_cells"] > 0 and s["bits_per_axis"] >= 1
+    assert 0 < s["far_queries"] < 20000
