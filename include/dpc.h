@@ -79,7 +79,9 @@ enum {
   DPC_PREC_FP32_CERT = 1 /* float32 filter + binary64 recheck of the band     */
 };
 #define DPC_PREC_MASK 0xFu
-#define DPC_FLAG_SYNC_CHECK (1u << 8) /* synchronize and return the device status */
+#define DPC_FLAG_SYNC_CHECK (1u << 8)  /* synchronize and return the device status */
+#define DPC_FLAG_PHASE_TIMES (1u << 9) /* record CUDA events around every phase
+                                          (read with dpc_get_phase_times)      */
 
 /* A batch of independent point sets packed back to back.  n_inst = 1 for a
  * single point set.  All arrays are HOST arrays read during the call only. */
@@ -160,8 +162,31 @@ typedef struct {
   int64_t occupied_cells; /* occupied grid cells of the last cutoff          */
   int32_t grid_level;     /* level of the density grid of the last cutoff    */
   int32_t bits_per_axis;  /* Morton bits per gridded axis of the last binning */
+  int64_t kernel_launches;/* kernels the last call enqueued                  */
 } dpc_stats;
 int dpc_get_stats(void* stream, dpc_stats* out);
+
+/* Phases of a call, for DPC_FLAG_PHASE_TIMES. */
+enum {
+  DPC_PHASE_BIN = 0,      /* bbox, grid setup, Morton codes, radix sort, gather */
+  DPC_PHASE_TREE = 1,     /* radix tree over the sorted points                 */
+  DPC_PHASE_CELLS = 2,    /* occupied cells of the density level + hash        */
+  DPC_PHASE_DENSITY = 3,  /* the density kernel (one launch per cutoff)        */
+  DPC_PHASE_MAXKEY = 4,   /* subtree maximum keys                              */
+  DPC_PHASE_NEAR = 5,     /* dependent points, grid-block phase (one launch)   */
+  DPC_PHASE_FAR = 6,      /* dependent points, tree phase (one launch)         */
+  DPC_PHASE_LABELS = 7,   /* labels                                            */
+  DPC_NUM_PHASES = 8
+};
+/* Milliseconds spent in each phase by the last call on `stream` that set
+ * DPC_FLAG_PHASE_TIMES, summed over its instances and cutoffs, measured with
+ * CUDA events on that stream; launches[p] is the number of times phase p ran.
+ * Synchronizes the stream. */
+typedef struct {
+  double ms[DPC_NUM_PHASES];
+  int64_t launches[DPC_NUM_PHASES];
+} dpc_phase_times;
+int dpc_get_phase_times(void* stream, dpc_phase_times* out);
 
 /* Device-side status of the last call on `stream` (synchronizes it). */
 int dpc_last_status(void* stream);

@@ -42,7 +42,7 @@ PREC = {"fp64": 0, "fp32": 1}
 DPC_FLAG_SYNC_CHECK = 1 << 8
 
 EXPORTS = ["dpc_density", "dpc_dependent", "dpc_cluster", "dpc_run", "dpc_run_host", "dpc_get_stats",
-           "dpc_last_status", "dpc_strerror", "dpc_version", "dpc_release"]
+           "dpc_get_phase_times", "dpc_last_status", "dpc_strerror", "dpc_version", "dpc_release"]
 
 
 class DpcError(RuntimeError):
@@ -64,7 +64,16 @@ class _Params(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [("band_pairs", ctypes.c_int64), ("far_queries", ctypes.c_int64),
                 ("exact_rescans", ctypes.c_int64), ("occupied_cells", ctypes.c_int64),
-                ("grid_level", ctypes.c_int32), ("bits_per_axis", ctypes.c_int32)]
+                ("grid_level", ctypes.c_int32), ("bits_per_axis", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+PHASES = ["bin", "tree", "cells", "density", "maxkey", "near", "far", "labels"]
+DPC_FLAG_PHASE_TIMES = 1 << 9
+
+
+class _PhaseTimes(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * len(PHASES)), ("launches", ctypes.c_int64 * len(PHASES))]
 
 
 _lib = None
@@ -88,6 +97,8 @@ def load(path: str = LIB_PATH):
     lib.dpc_run.argtypes = [vp, ctypes.c_int, bp, pp, vp, vp, vp, vp, u32, vp]
     lib.dpc_run_host.argtypes = [vp, ctypes.c_int, bp, pp, vp, vp, vp, vp, u32, vp]
     lib.dpc_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
+    lib.dpc_get_phase_times.argtypes = [vp, ctypes.POINTER(_PhaseTimes)]
+    lib.dpc_get_phase_times.restype = ctypes.c_int
     lib.dpc_last_status.argtypes = [vp]
     lib.dpc_strerror.argtypes = [ctypes.c_int]
     lib.dpc_strerror.restype = ctypes.c_char_p
@@ -240,7 +251,7 @@ def dpc_cluster(batch: Batch, dcut_index: int, params, rho: torch.Tensor, lam: t
 
 
 def dpc_run(pts: torch.Tensor, batch: Batch, params, precision: str = "fp32", sync: bool = False, stream=None,
-            out: dict | None = None) -> dict:
+            out: dict | None = None, phase_times: bool = False) -> dict:
     lib = load()
     shape = (batch.n_dcut, batch.N)
     if out is None:
@@ -250,7 +261,8 @@ def dpc_run(pts: torch.Tensor, batch: Batch, params, precision: str = "fp32", sy
                "label": torch.empty(shape, dtype=torch.int32, device=pts.device)}
     _check(lib.dpc_run(_dev(pts, "pts"), _dtype_code(pts), batch.ptr, params, _dev(out["rho"], "rho"),
                        _dev(out["lam"], "lambda"), _dev(out["delta"], "delta"), _dev(out["label"], "label"),
-                       _flags(precision, sync), _stream(stream)), "dpc_run")
+                       _flags(precision, sync) | (DPC_FLAG_PHASE_TIMES if phase_times else 0), _stream(stream)),
+           "dpc_run")
     return out
 
 
@@ -279,6 +291,14 @@ def dpc_get_stats(stream=None) -> dict:
     s = _Stats()
     _check(lib.dpc_get_stats(_stream(stream), ctypes.byref(s)), "dpc_get_stats")
     return {f: getattr(s, f) for f, _ in _Stats._fields_}
+
+
+def dpc_get_phase_times(stream=None) -> dict:
+    """{phase: (milliseconds, launches)} of the last call made with phase times."""
+    lib = load()
+    t = _PhaseTimes()
+    _check(lib.dpc_get_phase_times(_stream(stream), ctypes.byref(t)), "dpc_get_phase_times")
+    return {p: (t.ms[i], t.launches[i]) for i, p in enumerate(PHASES)}
 
 
 def dpc_last_status(stream=None) -> int:

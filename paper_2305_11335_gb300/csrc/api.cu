@@ -22,6 +22,9 @@
 #include "internal.h"
 
 namespace dpc {
+
+long long g_kernel_launches = 0;
+
 namespace {
 
 constexpr size_t kAlign = 256;
@@ -70,8 +73,40 @@ struct Workspace {
 
   int last_level = 0;     // for dpc_get_stats
   int last_ncut_used = 0;
+  long long launches_last = 0;
+
+  // phase timing (DPC_FLAG_PHASE_TIMES)
+  struct PhaseRec {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<PhaseRec> recs;
+
+  cudaEvent_t take_event() {
+    if (ev_used == ev_pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      ev_pool.push_back(e);
+    }
+    return ev_pool[ev_used++];
+  }
+
+  void begin_call(uint32_t flags) {
+    timing = (flags & DPC_FLAG_PHASE_TIMES) != 0;
+    recs.clear();
+    ev_used = 0;
+    g_kernel_launches = 0;
+  }
+  void end_call() { launches_last = g_kernel_launches; }
 
   void release() {
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    ev_pool.clear();
+    ev_used = 0;
+    recs.clear();
     if (base) cudaFree(base);
     if (io) cudaFree(io);
     base = nullptr;
@@ -168,6 +203,26 @@ struct Workspace {
   }
 };
 
+// Records CUDA events around one phase when the call asked for phase times.
+struct Phase {
+  Workspace* w;
+  int ph;
+  cudaEvent_t a = nullptr;
+  Phase(Workspace* w_, int ph_) : w(w_), ph(ph_) {
+    if (w->timing) {
+      a = w->take_event();
+      cudaEventRecord(a, w->stream);
+    }
+  }
+  ~Phase() {
+    if (w->timing) {
+      cudaEvent_t b = w->take_event();
+      cudaEventRecord(b, w->stream);
+      w->recs.push_back({ph, a, b});
+    }
+  }
+};
+
 std::mutex g_mu;
 std::map<std::pair<int, cudaStream_t>, Workspace*> g_ws;
 
@@ -234,7 +289,7 @@ int check_batch(const dpc_batch* b, std::vector<Inst>* insts, uint64_t* total) {
 int check_flags(uint32_t flags) {
   const uint32_t prec = flags & DPC_PREC_MASK;
   if (prec != DPC_PREC_FP64 && prec != DPC_PREC_FP32_CERT) return DPC_ERR_UNSUPPORTED;
-  if (flags & ~(DPC_PREC_MASK | DPC_FLAG_SYNC_CHECK)) return DPC_ERR_ARG;
+  if (flags & ~(DPC_PREC_MASK | DPC_FLAG_SYNC_CHECK | DPC_FLAG_PHASE_TIMES)) return DPC_ERR_ARG;
   return DPC_OK;
 }
 
@@ -249,6 +304,7 @@ int status_to_code(int s) {
 }
 
 int finish(Workspace* w, uint32_t flags) {
+  w->end_call();
   if (cudaGetLastError() != cudaSuccess) return DPC_ERR_CUDA;
   if (flags & DPC_FLAG_SYNC_CHECK) {
     if (cudaStreamSynchronize(w->stream) != cudaSuccess) {
@@ -275,6 +331,7 @@ void bin_instance(Workspace* w, const void* pts, int dtype, const Inst& in,
   const int d = in.d, g = g_of(d), dp = dp_of(d);
   const size_t esz = 4;
   const void* p = (const char*)pts + in.coord_off * esz;
+  Phase ph(w, DPC_PHASE_BIN);
   launch_geom_init(w->geom, w->status, g, st);
   launch_bbox(p, dtype, n, d, g, w->geom, st);
   launch_setup(w->geom, w->cuts, cuts.data(), (int)cuts.size(), st);
@@ -306,11 +363,43 @@ void dependent_step(Workspace* w, const Inst& in, CutGeom* cut, int32_t rho_skip
   cudaStream_t st = w->stream;
   const uint32_t n = (uint32_t)in.n;
   const int d = in.d, g = g_of(d), dp = dp_of(d);
-  launch_tree_maxkey(w->skey, n, w->nodes, w->leaf_parent, w->visit, st);
-  launch_dep_near(dp, g, fp64, w->spts, w->scode, w->skey, n, rho_skip, w->geom, cut, w->hkeys,
-                  w->hvals, lambda, delta, queue_of(w), w->ctr, st);
-  launch_dep_far(dp, g, fp64, w->spts, w->skey, n, w->geom, cut, w->nodes, queue_of(w), lambda,
-                 delta, w->ctr, n, st);
+  {
+    Phase ph(w, DPC_PHASE_MAXKEY);
+    launch_tree_maxkey(w->skey, n, w->nodes, w->leaf_parent, w->visit, st);
+  }
+  {
+    Phase ph(w, DPC_PHASE_NEAR);
+    launch_dep_near(dp, g, fp64, w->spts, w->scode, w->skey, n, rho_skip, w->geom, cut, w->hkeys,
+                    w->hvals, lambda, delta, queue_of(w), w->ctr, st);
+  }
+  {
+    Phase ph(w, DPC_PHASE_FAR);
+    launch_dep_far(dp, g, fp64, w->spts, w->skey, n, w->geom, cut, w->nodes, queue_of(w), lambda,
+                   delta, w->ctr, n, st);
+  }
+}
+
+void cells_step(Workspace* w, uint32_t n, CutGeom* cut) {
+  Phase ph(w, DPC_PHASE_CELLS);
+  launch_cells(w->scode, n, w->geom, cut, w->hkeys, w->hvals, w->hcap, w->stream);
+}
+
+void density_step(Workspace* w, const Inst& in, CutGeom* cut, bool fp64, int32_t* rho) {
+  Phase ph(w, DPC_PHASE_DENSITY);
+  launch_density(dp_of(in.d), g_of(in.d), fp64, w->spts, w->scode, w->sid, (uint32_t)in.n, w->geom,
+                 cut, w->hkeys, w->hvals, rho, w->skey, w->ctr, w->stream);
+}
+
+void tree_step(Workspace* w, uint32_t n) {
+  Phase ph(w, DPC_PHASE_TREE);
+  launch_tree_build(w->scode, n, w->geom, w->nodes, w->leaf_parent, w->stream);
+}
+
+void labels_step(Workspace* w, uint32_t n, const dpc_params& P, const int32_t* rho,
+                 const int32_t* lambda, const double* delta, int32_t* label) {
+  Phase ph(w, DPC_PHASE_LABELS);
+  launch_labels(rho, lambda, delta, n, P.rho_noise, P.rho_min, P.delta_min, label, w->flags,
+                w->geom, w->stream);
 }
 
 uint64_t max_n(const std::vector<Inst>& v) {
@@ -319,7 +408,8 @@ uint64_t max_n(const std::vector<Inst>& v) {
   return m;
 }
 
-void reset_call(Workspace* w) {
+void reset_call(Workspace* w, uint32_t flags) {
+  w->begin_call(flags);
   cudaMemsetAsync(w->status, 0, sizeof(int), w->stream);
   cudaMemsetAsync(w->ctr, 0, sizeof(Counters), w->stream);
 }
@@ -360,7 +450,7 @@ int dpc_density(const void* pts, int dtype, const dpc_batch* b, int32_t* rho, ui
   if ((rc = get_workspace((cudaStream_t)stream, &w))) return rc;
   std::lock_guard<std::mutex> lk(g_mu);
   if ((rc = w->reserve(max_n(insts), b->n_dcut))) return rc;
-  reset_call(w);
+  reset_call(w, flags);
   const bool fp64 = (flags & DPC_PREC_MASK) == DPC_PREC_FP64;
   for (int i = 0; i < b->n_inst; ++i) {
     const Inst& in = insts[i];
@@ -369,10 +459,8 @@ int dpc_density(const void* pts, int dtype, const dpc_batch* b, int32_t* rho, ui
     std::vector<CutHost> cuts = host_cuts(b, i, dp);
     bin_instance(w, pts, dtype, in, cuts);
     for (int c = 0; c < b->n_dcut; ++c) {
-      launch_cells(w->scode, (uint32_t)in.n, w->geom, w->cuts + c, w->hkeys, w->hvals, w->hcap, w->stream);
-      launch_density(dp, g_of(in.d), fp64, w->spts, w->scode, w->sid, (uint32_t)in.n, w->geom,
-                     w->cuts + c, w->hkeys, w->hvals, rho + (size_t)c * N + in.pt_off, w->skey,
-                     w->ctr, w->stream);
+      cells_step(w, (uint32_t)in.n, w->cuts + c);
+      density_step(w, in, w->cuts + c, fp64, rho + (size_t)c * N + in.pt_off);
     }
     w->last_ncut_used = b->n_dcut;
   }
@@ -394,7 +482,7 @@ int dpc_dependent(const void* pts, int dtype, const dpc_batch* b, int32_t dcut_i
   if ((rc = get_workspace((cudaStream_t)stream, &w))) return rc;
   std::lock_guard<std::mutex> lk(g_mu);
   if ((rc = w->reserve(max_n(insts), 1))) return rc;
-  reset_call(w);
+  reset_call(w, flags);
   const bool fp64 = (flags & DPC_PREC_MASK) == DPC_PREC_FP64;
   for (int i = 0; i < b->n_inst; ++i) {
     const Inst& in = insts[i];
@@ -402,8 +490,8 @@ int dpc_dependent(const void* pts, int dtype, const dpc_batch* b, int32_t dcut_i
     const int dp = dp_of(in.d);
     std::vector<CutHost> cuts = host_cuts(b, i, dp, dcut_index);
     bin_instance(w, pts, dtype, in, cuts);
-    launch_tree_build(w->scode, (uint32_t)in.n, w->geom, w->nodes, w->leaf_parent, w->stream);
-    launch_cells(w->scode, (uint32_t)in.n, w->geom, w->cuts, w->hkeys, w->hvals, w->hcap, w->stream);
+    tree_step(w, (uint32_t)in.n);
+    cells_step(w, (uint32_t)in.n, w->cuts);
     launch_keys_from_rho(rho + in.pt_off, w->sid, (uint32_t)in.n, w->skey, w->stream);
     dependent_step(w, in, w->cuts, rho_skip, fp64, lambda + in.pt_off, delta + in.pt_off);
     w->last_ncut_used = 1;
@@ -418,7 +506,7 @@ int dpc_cluster(const dpc_batch* b, int32_t dcut_index, const dpc_params* params
   uint64_t N = 0;
   int rc = check_batch(b, &insts, &N);
   if (rc) return rc;
-  if (flags & ~(DPC_PREC_MASK | DPC_FLAG_SYNC_CHECK)) return DPC_ERR_ARG;
+  if (flags & ~(DPC_PREC_MASK | DPC_FLAG_SYNC_CHECK | DPC_FLAG_PHASE_TIMES)) return DPC_ERR_ARG;
   if (dcut_index < 0 || dcut_index >= b->n_dcut || !params) return DPC_ERR_ARG;
   if (N > 0 && (!rho || !lambda || !delta || !label)) return DPC_ERR_ARG;
   for (int i = 0; i < b->n_inst; ++i)
@@ -427,15 +515,14 @@ int dpc_cluster(const dpc_batch* b, int32_t dcut_index, const dpc_params* params
   if ((rc = get_workspace((cudaStream_t)stream, &w))) return rc;
   std::lock_guard<std::mutex> lk(g_mu);
   if ((rc = w->reserve(max_n(insts), 1))) return rc;
-  reset_call(w);
+  reset_call(w, flags);
   for (int i = 0; i < b->n_inst; ++i) {
     const Inst& in = insts[i];
     if (in.n == 0) continue;
     const dpc_params& P = params[(size_t)i * b->n_dcut + dcut_index];
     launch_geom_init(w->geom, w->status, g_of(in.d), w->stream);
-    launch_labels(rho + in.pt_off, lambda + in.pt_off, delta + in.pt_off, (uint32_t)in.n,
-                  P.rho_noise, P.rho_min, P.delta_min, label + in.pt_off, w->flags, w->geom,
-                  w->stream);
+    labels_step(w, (uint32_t)in.n, P, rho + in.pt_off, lambda + in.pt_off, delta + in.pt_off,
+                label + in.pt_off);
   }
   return finish(w, flags);
 }
@@ -445,25 +532,22 @@ static int run_device(Workspace* w, const void* pts, int dtype, const dpc_batch*
                       int32_t* rho, int32_t* lambda, double* delta, int32_t* label,
                       uint32_t flags) {
   const bool fp64 = (flags & DPC_PREC_MASK) == DPC_PREC_FP64;
-  reset_call(w);
+  reset_call(w, flags);
   for (int i = 0; i < b->n_inst; ++i) {
     const Inst& in = insts[i];
     if (in.n == 0) continue;
     const uint32_t n = (uint32_t)in.n;
-    const int dp = dp_of(in.d), g = g_of(in.d);
+    const int dp = dp_of(in.d);
     std::vector<CutHost> cuts = host_cuts(b, i, dp);
     bin_instance(w, pts, dtype, in, cuts);
-    launch_tree_build(w->scode, n, w->geom, w->nodes, w->leaf_parent, w->stream);
+    tree_step(w, n);
     for (int c = 0; c < b->n_dcut; ++c) {
       const size_t o = (size_t)c * N + in.pt_off;
       CutGeom* cut = w->cuts + c;
-      launch_cells(w->scode, n, w->geom, cut, w->hkeys, w->hvals, w->hcap, w->stream);
-      launch_density(dp, g, fp64, w->spts, w->scode, w->sid, n, w->geom, cut, w->hkeys, w->hvals,
-                     rho + o, w->skey, w->ctr, w->stream);
+      cells_step(w, n, cut);
+      density_step(w, in, cut, fp64, rho + o);
       dependent_step(w, in, cut, 0, fp64, lambda + o, delta + o);
-      const dpc_params& P = params[(size_t)i * b->n_dcut + c];
-      launch_labels(rho + o, lambda + o, delta + o, n, P.rho_noise, P.rho_min, P.delta_min,
-                    label + o, w->flags, w->geom, w->stream);
+      labels_step(w, n, params[(size_t)i * b->n_dcut + c], rho + o, lambda + o, delta + o, label + o);
     }
     w->last_ncut_used = b->n_dcut;
   }
@@ -562,6 +646,7 @@ int dpc_get_stats(void* stream, dpc_stats* out) {
   out->far_queries = (int64_t)c.far_queries;
   out->exact_rescans = (int64_t)c.exact_rescans;
   out->bits_per_axis = g.B;
+  out->kernel_launches = w->launches_last;
   if (w->last_ncut_used > 0) {
     CutGeom cg;
     cudaMemcpy(&cg, w->cuts + (w->last_ncut_used - 1), sizeof(cg), cudaMemcpyDeviceToHost);
@@ -569,6 +654,29 @@ int dpc_get_stats(void* stream, dpc_stats* out) {
     out->grid_level = cg.k;
   }
   return cudaGetLastError() == cudaSuccess ? DPC_OK : DPC_ERR_CUDA;
+}
+
+int dpc_get_phase_times(void* stream, dpc_phase_times* out) {
+  if (!out) return DPC_ERR_ARG;
+  Workspace* w = nullptr;
+  int rc = get_workspace((cudaStream_t)stream, &w);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lk(g_mu);
+  std::memset(out, 0, sizeof(*out));
+  if (cudaStreamSynchronize(w->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return DPC_ERR_CUDA;
+  }
+  for (const auto& r : w->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+      cudaGetLastError();
+      return DPC_ERR_CUDA;
+    }
+    out->ms[r.phase] += ms;
+    out->launches[r.phase] += 1;
+  }
+  return DPC_OK;
 }
 
 int dpc_last_status(void* stream) {

@@ -315,6 +315,7 @@ CutHost make_cut_host(double d_cut, int dp) {
 
 void launch_geom_init(GridGeom* geom, int* status, int g, cudaStream_t st) {
   k_geom_init<<<1, 1, 0, st>>>(geom, status, g);
+  count_launches(1);
 }
 
 void launch_bbox(const void* pts, int dtype, uint32_t n, int d, int g, GridGeom* geom,
@@ -325,6 +326,7 @@ void launch_bbox(const void* pts, int dtype, uint32_t n, int d, int g, GridGeom*
     k_bbox<int32_t><<<grid, kThreads, 0, st>>>((const int32_t*)pts, n, d, g, geom);
   else
     k_bbox<float><<<grid, kThreads, 0, st>>>((const float*)pts, n, d, g, geom);
+  count_launches(1);
 }
 
 void launch_setup(GridGeom* geom, CutGeom* cuts, const CutHost* host_cuts, int ncut,
@@ -337,7 +339,9 @@ void launch_setup(GridGeom* geom, CutGeom* cuts, const CutHost* host_cuts, int n
     int m = ncut - c0 < kCutChunk ? ncut - c0 : kCutChunk;
     for (int c = 0; c < m; ++c) a.h[c] = host_cuts[c0 + c];
     k_setup_cuts<<<1, 32, 0, st>>>(geom, cuts + c0, m, a);
+    count_launches(1);
   }
+  count_launches(1);
 }
 
 template <typename T>
@@ -348,6 +352,7 @@ static void codes_t(const T* pts, uint32_t n, int d, const GridGeom* geom,
   if (g == 1) k_codes<T, 1><<<grid, kThreads, 0, st>>>(pts, n, d, geom, codes, ids);
   else if (g == 2) k_codes<T, 2><<<grid, kThreads, 0, st>>>(pts, n, d, geom, codes, ids);
   else k_codes<T, 3><<<grid, kThreads, 0, st>>>(pts, n, d, geom, codes, ids);
+  count_launches(1);
 }
 
 void launch_codes(const void* pts, int dtype, uint32_t n, int d, const GridGeom* geom,
@@ -366,6 +371,7 @@ static void gather_t(const T* pts, uint32_t n, int d, int dp, const GridGeom* ge
   if (dp == 2) k_gather<T, 2><<<grid, kThreads, 0, st>>>(pts, n, d, geom, ca, cb, ia, ib, spts, scode, sid);
   else if (dp == 4) k_gather<T, 4><<<grid, kThreads, 0, st>>>(pts, n, d, geom, ca, cb, ia, ib, spts, scode, sid);
   else k_gather<T, 8><<<grid, kThreads, 0, st>>>(pts, n, d, geom, ca, cb, ia, ib, spts, scode, sid);
+  count_launches(1);
 }
 
 void launch_gather(const void* pts, int dtype, uint32_t n, int d, int dp, const GridGeom* geom,
@@ -387,6 +393,7 @@ void launch_cells(const unsigned long long* scode, uint32_t n, const GridGeom* g
   k_hash_size<<<1, 1, 0, st>>>(cut, hcap);
   k_hash_clear<<<grid_for(hcap), kThreads, 0, st>>>(hkeys, cut);
   k_hash_insert<<<grid, kThreads, 0, st>>>(scode, n, geom, cut, hkeys, hvals);
+  count_launches(4);
 }
 
 }  // namespace dpc

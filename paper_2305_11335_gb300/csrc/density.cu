@@ -124,6 +124,7 @@ void density_dg(bool fp64, const float* spts, const unsigned long long* scode, c
   else
     k_density<DP, G, false><<<grid, kThreads, 0, st>>>(spts, scode, sid, n, geom, cut, hkeys, hvals,
                                                        rho_out, skey, ctr);
+  count_launches(1);
 }
 
 }  // namespace
@@ -143,6 +144,7 @@ void launch_keys_from_rho(const int32_t* rho, const uint32_t* sid, uint32_t n,
                           unsigned long long* skey, cudaStream_t st) {
   if (n == 0) return;
   k_keys_from_rho<<<grid_for(n), kThreads, 0, st>>>(rho, sid, n, skey);
+  count_launches(1);
 }
 
 }  // namespace dpc

@@ -436,6 +436,7 @@ void launch_dep_near(int dp, int g, bool fp64, const float* spts, const unsigned
   else if (g == 2) near_dg<2, 2>(fp64, spts, scode, skey, n, rho_skip, geom, cut, hkeys, hvals, lambda, delta, q, ctr, st);
   else if (dp == 4) near_dg<4, 3>(fp64, spts, scode, skey, n, rho_skip, geom, cut, hkeys, hvals, lambda, delta, q, ctr, st);
   else near_dg<8, 3>(fp64, spts, scode, skey, n, rho_skip, geom, cut, hkeys, hvals, lambda, delta, q, ctr, st);
+  count_launches(1);
 }
 
 void launch_dep_far(int dp, int g, bool fp64, const float* spts, const unsigned long long* skey,
@@ -448,6 +449,7 @@ void launch_dep_far(int dp, int g, bool fp64, const float* spts, const unsigned 
   else if (dp == 4) far_dg<4, 3>(fp64, spts, skey, n, geom, cut, nodes, q, lambda, delta, ctr, qcap, st);
   else far_dg<8, 3>(fp64, spts, skey, n, geom, cut, nodes, q, lambda, delta, ctr, qcap, st);
   k_far_count<<<1, 1, 0, st>>>(ctr);
+  count_launches(2);
 }
 
 }  // namespace dpc

@@ -8,6 +8,11 @@
 
 namespace dpc {
 
+// Kernels enqueued by the current call (the entry points hold the library
+// lock while enqueueing, so a plain counter suffices).
+extern long long g_kernel_launches;
+inline void count_launches(int k) { g_kernel_launches += k; }
+
 // Host-computed constants of one cutoff (the [host] fields of CutGeom).
 struct CutHost {
   double dc, dc2;

@@ -82,6 +82,7 @@ void launch_labels(const int32_t* rho, const int32_t* lambda, const double* delt
                                           label, flags);
   for (int r = 1; r <= rounds; ++r) k_label_jump<<<grid, kThreads, 0, st>>>(label, n, flags, r);
   k_label_check<<<1, 1, 0, st>>>(flags, rounds, geom);
+  count_launches(rounds + 2);
 }
 
 }  // namespace dpc

@@ -223,6 +223,7 @@ void launch_sort(unsigned long long* codes_a, unsigned long long* codes_b, uint3
     k_rs_scatter<<<nt, kRsThreads, sizeof(ScatterSmem), st>>>(kb[i], vb[i], kb[o], vb[o], n, pass,
                                                               geom, hist, nt);
   }
+  count_launches(3 * kMaxPasses);
 }
 
 }  // namespace dpc

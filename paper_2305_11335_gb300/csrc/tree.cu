@@ -111,6 +111,7 @@ void launch_tree_build(const unsigned long long* scode, uint32_t n, const GridGe
   if (n < 2) return;
   k_tree_build<<<grid_for(n - 1), kThreads, 0, st>>>(scode, n, geom, nodes, leaf_parent);
   k_root_parent<<<1, 1, 0, st>>>(nodes);
+  count_launches(2);
 }
 
 void launch_tree_maxkey(const unsigned long long* skey, uint32_t n, Node* nodes,
@@ -118,6 +119,7 @@ void launch_tree_maxkey(const unsigned long long* skey, uint32_t n, Node* nodes,
   if (n < 2) return;
   cudaMemsetAsync(visit, 0, sizeof(uint32_t) * (n - 1), st);
   k_tree_maxkey<<<grid_for(n), kThreads, 0, st>>>(skey, n, nodes, leaf_parent, visit);
+  count_launches(1);
 }
 
 }  // namespace dpc
