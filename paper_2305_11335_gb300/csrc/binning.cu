@@ -59,7 +59,7 @@ __global__ void k_bbox(const T* __restrict__ pts, uint32_t n, int d, int g, Grid
         if (k == a) { mn[k] = fminf(mn[k], x); mx[k] = fmaxf(mx[k], x); }
     }
   }
-  // warp reduce, then one atomic per warp
+  // warp reduce, block reduce through shared memory, one atomic per block
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -67,22 +67,37 @@ __global__ void k_bbox(const T* __restrict__ pts, uint32_t n, int d, int g, Grid
       mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], o));
     }
   }
-  bad = __any_sync(0xffffffffu, bad);
-  if ((threadIdx.x & 31) == 0) {
+  __shared__ float s_mn[32][3], s_mx[32][3];
+  __shared__ int s_bad;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { s_mn[w][k] = mn[k]; s_mx[w][k] = mx[k]; }
+  }
+  if (bad) s_bad = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
     for (int k = 0; k < g; ++k) {
-      if (mn[k] <= mx[k]) {
-        atomicMin(&geom->bbox_ord[k], float_ord(mn[k]));
-        atomicMax(&geom->bbox_ord[3 + k], float_ord(mx[k]));
+      float a = s_mn[0][k], b = s_mx[0][k];
+      for (int j = 1; j < nw; ++j) { a = fminf(a, s_mn[j][k]); b = fmaxf(b, s_mx[j][k]); }
+      if (a <= b) {
+        atomicMin(&geom->bbox_ord[k], float_ord(a));
+        atomicMax(&geom->bbox_ord[3 + k], float_ord(b));
       }
     }
-    if (bad) set_status(geom->status, kStatusBadCoord);
+    if (s_bad) set_status(geom->status, kStatusBadCoord);
   }
 }
 
 // Grid geometry from the bounding box.
 //
-// Fine grid: B bits per axis, about 3 bits finer than the smallest cutoff, at
-// most kMaxBits so that fine-unit coordinates are exact to 1/8 cell in float32.
+// Fine grid: the fine cell is 1/8 of the smallest cutoff (times 1 + 2^-20),
+// so the level-3 cell is just wider than d_cut and the 3^g block around it
+// holds every point within d_cut with the least volume a cell grid allows.
+// At most kMaxBits bits per axis keep fine-unit coordinates exact to 1/8 cell
+// in float32; a wider bounding box gets a coarser fine cell instead.
 // A point's fine index c = floor((x - org) * inv_f) is within 1e-9 cells of the
 // exact real value, so its real position lies in [c - 0.5, c + 1.5) fine units;
 // every bound below is derived from that interval.
@@ -106,13 +121,15 @@ __global__ void k_setup_geom(GridGeom* geom, double dcmin) {
     B = 1;
     f = 1.0;
   } else {
-    if (dcmin > 0.0) {
-      double r = ceil(log2(E / dcmin));
-      B = (int)fmin(fmax(r + 3.0, 1.0), (double)kMaxBits);
+    const double f_fit = dcmin * (1.0 + 0x1p-20) * 0.125;
+    if (f_fit > 0.0 && E / f_fit < ldexp(1.0, kMaxBits) * (1.0 - 0x1p-20)) {
+      f = f_fit;
+      B = 1;
+      while (ldexp(f, B) <= E * (1.0 + 0x1p-30)) ++B;  // E / f < 2^B with margin
     } else {
       B = kMaxBits;
+      f = ldexp(E, -B) * (1.0 + 0x1p-20);
     }
-    f = ldexp(E, -B) * (1.0 + 0x1p-20);
   }
   geom->B = B;
   geom->f = f;
@@ -142,11 +159,32 @@ __global__ void k_setup_cuts(const GridGeom* __restrict__ geom, CutGeom* cuts, i
   C.band_mul = a.h[c].band_mul;
   C.band_add = a.h[c].band_add;
   // Two points within d_cut differ by at most D fine indices on each axis.
-  double Dd = floor(C.dc * geom->inv_f * (1.0 + 1e-9) + 1e-6) + 1.0;
-  int k = 0;
-  while (k < B && ldexp(1.0, k) < Dd) ++k;
-  int R = (int)ceil(Dd / ldexp(1.0, k));
-  if (R < 1) R = 1;
+  // Choose the level k and block radius R (R * 2^k >= D).  R = 1 (the 3^g
+  // block of cells at least d_cut wide) unless a larger R on finer cells
+  // shrinks the block side by more than 20%, which pays for its extra cell
+  // lookups (it happens when d_cut falls just above a power-of-two multiple
+  // of the fine cell, e.g. the larger cutoffs of a sweep).
+  const double Dd = floor(C.dc * geom->inv_f * (1.0 + 1e-9) + 1e-6) + 1.0;
+  const int g = geom->g;
+  const int rmax = g == 3 ? 2 : 3;  // (2R+1)^g <= 125 cells
+  int k = B, R = 1;
+  double best = INFINITY;
+  for (int r = 1; r <= rmax; ++r) {
+    int kk = 0;
+    while (kk < B && ldexp((double)r, kk) < Dd) ++kk;
+    const int rr = (int)fmax(1.0, ceil(Dd / ldexp(1.0, kk)));
+    if (rr > rmax) continue;
+    const double side = (2.0 * rr + 1.0) * ldexp(1.0, kk);
+    if (side < (best < INFINITY ? 0.8 * best : INFINITY)) {
+      best = side;
+      k = kk;
+      R = rr;
+    }
+  }
+  if (!(best < INFINITY)) {  // the cutoff exceeds the whole box: one cell
+    k = B;
+    R = 1;
+  }
   C.k = k;
   C.R = R;
   // density prune: squared lower bound in fine units vs d_cut^2 / f^2

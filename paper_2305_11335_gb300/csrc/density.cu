@@ -1,24 +1,27 @@
 // density.cu -- rho_i = |{j : D(x_i, x_j) <= d_cut}| (Definition 1).
 //
-// One thread per point, points taken in Morton order so a warp covers a
-// compact patch of space and its neighbour cells are shared in L1.  Each
-// thread visits the (2R+1)^g level-k cells around its own (R = 1 when the
-// cell side is at least d_cut), skips cells whose conservative lower bound
-// already exceeds d_cut (the subtree pruning idea of Section 6.1 applied to
-// grid cells), and counts the points of the others:
+// A warp owns 32 consecutive Morton-sorted points.  For each level-k cell
+// they fall into, the warp looks up the (2R+1)^g cells of the cell's block in
+// parallel, stages their points in shared memory (in windows of kCap), and
+// counts, 4 queries at a time with 8 lanes per query:
 //   FP32_CERT: s32 <= t_in counts, s32 > t_out does not, anything between is
 //              re-evaluated with the canonical binary64 distance (rare: the
 //              band is about 1e-6 of d_cut^2 wide);
 //   FP64:      every pair is evaluated in binary64.
 // Both give exactly the binary64 count.  The kernel also writes the order key
 // of every sorted point, (rho << 32) | ~id.
+#include "block.cuh"
 #include "internal.h"
 
 namespace dpc {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kWarps = 4;
+constexpr int kThreads = kWarps * 32;
+
+template <int DP>
+constexpr int density_cap() { return DP == 8 ? 256 : 512; }
 
 template <int DP, int G, bool F64>
 __global__ void __launch_bounds__(kThreads)
@@ -27,73 +30,87 @@ k_density(const float* __restrict__ spts, const unsigned long long* __restrict__
           const CutGeom* __restrict__ cut, const unsigned long long* __restrict__ hkeys,
           const uint2* __restrict__ hvals, int32_t* __restrict__ rho_out,
           unsigned long long* __restrict__ skey, Counters* ctr) {
+  constexpr int kCap = density_cap<DP>();
+  __shared__ __align__(16) float smem[kWarps * kCap * DP];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  float* wpts = smem + wib * kCap * DP;
+
   const int k = cut->k;
   const int R = cut->R;
-  const int W = 2 * R + 1;
   const int shift = G * k;
   const int cmax = (1 << (geom->B - k)) - 1;
-  const float cell_fine = (float)(1u << k);
   const double dc2 = cut->dc2;
   const float t_in = cut->t_in, t_out = cut->t_out;
-  const float prune = cut->prune_fine;
   const uint32_t hmask = cut->hmask;
-  const double inv_f = geom->inv_f;
-  double org[G];
-#pragma unroll
-  for (int a = 0; a < G; ++a) org[a] = geom->org[a];
-  int ncell = 1;
-  for (int a = 0; a < G; ++a) ncell *= W;
+  const int sub = lane & 7;     // lane within its query group
+  const int grp = lane >> 3;    // query group 0..3
 
   unsigned long long band = 0;
-  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const Pt<DP> q = load_pt<DP>(spts, p);
-    float u[G];
+  const uint32_t nchunk = (n + 31) / 32;
+  for (uint32_t ch = blockIdx.x * kWarps + wib; ch < nchunk; ch += gridDim.x * kWarps) {
+    const uint32_t p0 = ch * 32;
+    const uint32_t p = p0 + lane;
+    const bool valid = p < n;
+    Pt<DP> me;
 #pragma unroll
-    for (int a = 0; a < G; ++a) u[a] = (float)(((double)q.x[a] - org[a]) * inv_f);
-    uint32_t c0[G];
-    unmorton<G>(scode[p] >> shift, c0);
+    for (int a = 0; a < DP; ++a) me.x[a] = 0.f;
+    if (valid) me = load_pt<DP>(spts, p);
+    const unsigned long long mycell = valid ? (scode[p] >> shift) : ~0ull;
+    const int nvalid = (int)min(32u, n - p0);
     int32_t count = 0;
-    for (int o = 0; o < ncell; ++o) {
-      int rem = o;
-      uint32_t c[G];
-      float lb2 = 0.f;
-      bool inside = true;
+    int s = 0;
+    while (s < nvalid) {
+      const unsigned long long cell = __shfl_sync(kFull, mycell, s);
+      const int e = s + __popc(__ballot_sync(kFull, mycell == cell));
+      uint32_t c0[G];
+      unmorton<G>(cell, c0);
+      BlockRuns br;
+      lookup_block<G>(c0, R, cmax, hkeys, hvals, hmask, n, lane, br);
+      for (uint32_t w0 = 0; w0 < br.total; w0 += kCap) {
+        const uint32_t T = min((uint32_t)kCap, br.total - w0);
+        __syncwarp();
+        stage_window<DP, false>(br, w0, kCap, spts, nullptr, wpts, nullptr, nullptr, lane);
+        __syncwarp();
+        for (int qb = s; qb < e; qb += 4) {
+          const int qi = qb + grp;
+          const Pt<DP> q = shfl_pt<DP>(me, qi < e ? qi : s);
+          int32_t c = 0;
+          for (uint32_t t = sub; t < T; t += 8) {
+            const Pt<DP> x = window_pt<DP>(wpts, t);
+            if constexpr (F64) {
+              c += dist64<DP>(q, x) <= dc2;
+            } else {
+              const float s32 = dist32<DP>(q, x);
+              if (s32 <= t_in) {
+                ++c;
+              } else if (s32 <= t_out) {
+                ++band;
+                c += dist64<DP>(q, x) <= dc2;
+              }
+            }
+          }
+          c += __shfl_xor_sync(kFull, c, 4);
+          c += __shfl_xor_sync(kFull, c, 2);
+          c += __shfl_xor_sync(kFull, c, 1);
 #pragma unroll
-      for (int a = 0; a < G; ++a) {
-        const int off = rem % W - R;
-        rem /= W;
-        const int ca = (int)c0[a] + off;
-        inside &= (ca >= 0) & (ca <= cmax);
-        c[a] = (uint32_t)ca;
-        const float lo = (float)ca * cell_fine;
-        const float hi = lo + cell_fine - 1.f;
-        const float l = fmaxf(fmaxf(lo - 1.f - u[a], u[a] - hi - 2.f), 0.f);
-        lb2 = fmaf(l, l, lb2);
-      }
-      if (!inside || lb2 > prune) continue;
-      const uint2 run = clip_run(hash_find(hkeys, hvals, hmask, morton<G>(c)), n);
-      for (uint32_t t = run.x; t < run.y; ++t) {
-        const Pt<DP> x = load_pt<DP>(spts, t);
-        if constexpr (F64) {
-          count += dist64<DP>(q, x) <= dc2;
-        } else {
-          const float s = dist32<DP>(q, x);
-          if (s <= t_in) {
-            ++count;
-          } else if (s <= t_out) {
-            ++band;
-            count += dist64<DP>(q, x) <= dc2;
+          for (int g = 0; g < 4; ++g) {
+            const int v = __shfl_sync(kFull, c, g * 8);
+            if (lane == qb + g && qb + g < e) count += v;
           }
         }
       }
+      s = e;
     }
-    const uint32_t id = sid[p];
-    rho_out[id] = count;
-    skey[p] = order_key(count, id);
+    if (valid) {
+      const uint32_t id = sid[p];
+      rho_out[id] = count;
+      skey[p] = order_key(count, id);
+    }
   }
   if constexpr (!F64) {
-    for (int o = 16; o > 0; o >>= 1) band += __shfl_xor_sync(0xffffffffu, band, o);
-    if ((threadIdx.x & 31) == 0 && band) atomicAdd(&ctr->band_pairs, band);
+    for (int o = 16; o > 0; o >>= 1) band += __shfl_xor_sync(kFull, band, o);
+    if (lane == 0 && band) atomicAdd(&ctr->band_pairs, band);
   }
 }
 
@@ -105,10 +122,10 @@ __global__ void k_keys_from_rho(const int32_t* __restrict__ rho, const uint32_t*
   }
 }
 
-inline unsigned grid_for(uint64_t n) {
-  uint64_t b = (n + kThreads - 1) / kThreads;
+inline unsigned grid_for(uint64_t items, int per_block, unsigned cap) {
+  uint64_t b = (items + per_block - 1) / per_block;
   if (b < 1) b = 1;
-  if (b > 152u * 64u) b = 152u * 64u;
+  if (b > cap) b = cap;
   return (unsigned)b;
 }
 
@@ -117,7 +134,7 @@ void density_dg(bool fp64, const float* spts, const unsigned long long* scode, c
                 uint32_t n, const GridGeom* geom, const CutGeom* cut,
                 const unsigned long long* hkeys, const uint2* hvals, int32_t* rho_out,
                 unsigned long long* skey, Counters* ctr, cudaStream_t st) {
-  const unsigned grid = grid_for(n);
+  const unsigned grid = grid_for((n + 31) / 32, kWarps, 152u * 64u);
   if (fp64)
     k_density<DP, G, true><<<grid, kThreads, 0, st>>>(spts, scode, sid, n, geom, cut, hkeys, hvals,
                                                       rho_out, skey, ctr);
@@ -143,7 +160,7 @@ void launch_density(int dp, int g, bool fp64, const float* spts, const unsigned 
 void launch_keys_from_rho(const int32_t* rho, const uint32_t* sid, uint32_t n,
                           unsigned long long* skey, cudaStream_t st) {
   if (n == 0) return;
-  k_keys_from_rho<<<grid_for(n), kThreads, 0, st>>>(rho, sid, n, skey);
+  k_keys_from_rho<<<grid_for(n, 256, 152u * 16u), 256, 0, st>>>(rho, sid, n, skey);
   count_launches(1);
 }
 

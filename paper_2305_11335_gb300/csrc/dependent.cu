@@ -4,14 +4,17 @@
 // The paper runs one priority nearest-neighbour query per point in parallel
 // (Algorithm 1) on a priority search kd-tree.  Here each query runs in two
 // phases:
-//   near  scan the (2R+1)^g grid block around the point (the same cells the
-//         density used).  If the best candidate is closer than anything
-//         outside the block can be, the query is settled; this holds for most
-//         points, since a point's dependent point is usually within d_cut.
-//   far   the remaining queries (local density maxima, isolated points) walk
-//         the radix tree (tree.cu) depth first, nearer child first, skipping
-//         subtrees whose largest key is not above the query's key or whose
-//         box is farther than the best candidate so far (Section 4.1.2).
+//   near  the grid block around the point's cell (the cells the density
+//         used), scanned warp-cooperatively from shared memory.  If the best
+//         candidate is closer than anything outside the block can be, and no
+//         other candidate is within the float32 error band of it, the query
+//         is settled; this holds for most points, since a point's dependent
+//         point is usually within d_cut.
+//   far   the remaining queries (local density maxima, isolated points, near
+//         ties) walk the radix tree (tree.cu) depth first, nearer child
+//         first, skipping subtrees whose largest key is not above the query's
+//         key or whose box is farther than the best candidate so far (the
+//         pruning of Section 4.1.2).
 //
 // Exactness.  Candidates are compared on their float32 distance s32; the
 // winner of the binary64 order (s64, id) -- the write-min of Section 3.2 --
@@ -24,14 +27,18 @@
 #include <cmath>
 #include <type_traits>
 
+#include "block.cuh"
 #include "internal.h"
 
 namespace dpc {
 
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kFarThreads = 128;
 constexpr int kStack = 128;
+constexpr int kNearWarps = 4;
+constexpr int kNearThreads = kNearWarps * 32;
+constexpr int kNearCap = 256;
 
 __device__ __forceinline__ float band_of(float s, float mul, float add) {
   return __fadd_ru(__fmul_ru(s, mul), add);
@@ -45,15 +52,16 @@ __device__ __forceinline__ bool beyond(float lbs, float bound) {
   return lbs > __fadd_ru(bound, kPruneAbs);
 }
 
-// Running minimum of (s, id) plus the second smallest s.
+// Running minimum of (s, id), the second smallest s, and the sorted position
+// of the minimum.
 template <typename S>
 struct Best {
   S s1, s2;
   uint32_t o1;   // id of the best
   uint32_t t1;   // sorted position of the best
-  __device__ __forceinline__ void init(S inf) {
-    s1 = inf;
-    s2 = inf;
+  __device__ __forceinline__ void init() {
+    s1 = (S)INFINITY;
+    s2 = (S)INFINITY;
     o1 = 0xffffffffu;
     t1 = 0xffffffffu;
   }
@@ -66,6 +74,24 @@ struct Best {
     } else if (s < s2) {
       s2 = s;
     }
+  }
+  // union with another candidate set's summary
+  __device__ __forceinline__ void merge(S bs1, uint32_t bo1, S bs2, uint32_t bt1) {
+    if (bs1 < s1 || (bs1 == s1 && bo1 < o1)) {
+      s2 = s1 < bs2 ? s1 : bs2;
+      s1 = bs1;
+      o1 = bo1;
+      t1 = bt1;
+    } else {
+      s2 = s2 < bs1 ? s2 : bs1;
+    }
+  }
+  __device__ __forceinline__ void merge_xor(int mask) {
+    const S bs1 = __shfl_xor_sync(kFull, s1, mask);
+    const uint32_t bo1 = __shfl_xor_sync(kFull, o1, mask);
+    const S bs2 = __shfl_xor_sync(kFull, s2, mask);
+    const uint32_t bt1 = __shfl_xor_sync(kFull, t1, mask);
+    merge(bs1, bo1, bs2, bt1);
   }
 };
 
@@ -96,136 +122,129 @@ __device__ __forceinline__ float lb_axis(float lo, float hi, float u) {
 // near phase
 
 template <int DP, int G, bool F64>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kNearThreads)
 k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict__ scode,
            const unsigned long long* __restrict__ skey, uint32_t n, int32_t rho_skip,
            const GridGeom* __restrict__ geom, const CutGeom* __restrict__ cut,
            const unsigned long long* __restrict__ hkeys, const uint2* __restrict__ hvals,
            int32_t* __restrict__ lambda, double* __restrict__ delta, FarQueue q, Counters* ctr) {
+  using S = typename std::conditional<F64, double, float>::type;
+  __shared__ __align__(16) float s_pts[kNearWarps * kNearCap * DP];
+  __shared__ unsigned long long s_key[kNearWarps * kNearCap];
+  __shared__ uint32_t s_pos[kNearWarps * kNearCap];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  float* wpts = s_pts + wib * kNearCap * DP;
+  unsigned long long* wkey = s_key + wib * kNearCap;
+  uint32_t* wpos = s_pos + wib * kNearCap;
+
   const int k = cut->k;
   const int R = cut->R;
-  const int W = 2 * R + 1;
   const int shift = G * k;
   const int cmax = (1 << (geom->B - k)) - 1;
-  const float cell_fine = (float)(1u << k);
   const uint32_t hmask = cut->hmask;
   const float bmul = cut->band_mul, badd = cut->band_add;
   const float far32 = cut->far32;
   const double far64 = cut->far64;
-  // fine-unit squared lower bound -> conservative float lower bound of s
-  const float f2lo = geom->f2 * (1.f - 1e-5f);
-  const double inv_f = geom->inv_f;
-  double org[G];
-#pragma unroll
-  for (int a = 0; a < G; ++a) org[a] = geom->org[a];
-  int ncell = 1;
-  for (int a = 0; a < G; ++a) ncell *= W;
+  const int sub = lane & 7;
+  const int grp = lane >> 3;
+  const uint32_t lanemask_lt = (1u << lane) - 1u;
 
-  unsigned long long rescans = 0;
-  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const unsigned long long K = skey[p];
-    const uint32_t id = key_id(K);
-    if ((int32_t)(K >> 32) < rho_skip) {
-      lambda[id] = -1;
-      delta[id] = __longlong_as_double(0x7ff8000000000000ll);  // NaN
-      continue;
+  const uint32_t nchunk = (n + 31) / 32;
+  for (uint32_t ch = blockIdx.x * kNearWarps + wib; ch < nchunk; ch += gridDim.x * kNearWarps) {
+    const uint32_t p0 = ch * 32;
+    const uint32_t p = p0 + lane;
+    const bool valid = p < n;
+    Pt<DP> me;
+#pragma unroll
+    for (int a = 0; a < DP; ++a) me.x[a] = 0.f;
+    unsigned long long K = ~0ull;
+    if (valid) {
+      me = load_pt<DP>(spts, p);
+      K = skey[p];
     }
-    const Pt<DP> xq = load_pt<DP>(spts, p);
-    float u[G];
-#pragma unroll
-    for (int a = 0; a < G; ++a) u[a] = (float)(((double)xq.x[a] - org[a]) * inv_f);
-    uint32_t c0[G];
-    unmorton<G>(scode[p] >> shift, c0);
-
-    using S = typename std::conditional<F64, double, float>::type;
-    Best<S> best;
-    best.init((S)INFINITY);
-    for (int o = 0; o < ncell; ++o) {
-      int rem = o;
-      uint32_t c[G];
-      float lb2 = 0.f;
-      bool inside = true;
-#pragma unroll
-      for (int a = 0; a < G; ++a) {
-        const int off = rem % W - R;
-        rem /= W;
-        const int ca = (int)c0[a] + off;
-        inside &= (ca >= 0) & (ca <= cmax);
-        c[a] = (uint32_t)ca;
-        const float lo = (float)ca * cell_fine;
-        const float l = lb_axis(lo, lo + cell_fine - 1.f, u[a]);
-        lb2 = fmaf(l, l, lb2);
-      }
-      if (!inside) continue;
-      const float lbs = lb2 * f2lo;
-      if constexpr (F64) {
-        if ((double)lbs > best.s1) continue;
-      } else {
-        if (beyond(lbs, band_of(best.s1, bmul, badd))) continue;
-      }
-      const uint2 run = clip_run(hash_find(hkeys, hvals, hmask, morton<G>(c)), n);
-      for (uint32_t t = run.x; t < run.y; ++t) {
-        const unsigned long long kt = skey[t];
-        if (kt <= K) continue;
-        const Pt<DP> x = load_pt<DP>(spts, t);
-        if constexpr (F64) best.add(dist64<DP>(xq, x), key_id(kt), t);
-        else best.add(dist32<DP>(xq, x), key_id(kt), t);
-      }
-    }
-
-    bool settled;
-    if constexpr (F64) {
-      settled = best.t1 != 0xffffffffu && best.s1 < far64;
-      if (settled) {
-        lambda[id] = (int32_t)best.o1;
-        delta[id] = sqrt(best.s1);
-      }
-    } else {
-      const float b = band_of(best.s1, bmul, badd);
-      settled = best.t1 != 0xffffffffu && b < far32;
-      if (settled) {
-        Exact ex;
-        ex.init();
-        if (best.s2 <= b) {
-          // ambiguous: re-rank every candidate inside the band in binary64
-          ++rescans;
-          for (int o = 0; o < ncell; ++o) {
-            int rem = o;
-            uint32_t c[G];
-            bool inside = true;
-#pragma unroll
-            for (int a = 0; a < G; ++a) {
-              const int ca = (int)c0[a] + rem % W - R;
-              rem /= W;
-              inside &= (ca >= 0) & (ca <= cmax);
-              c[a] = (uint32_t)ca;
-            }
-            if (!inside) continue;
-            const uint2 run = clip_run(hash_find(hkeys, hvals, hmask, morton<G>(c)), n);
-            for (uint32_t t = run.x; t < run.y; ++t) {
-              const unsigned long long kt = skey[t];
-              if (kt <= K) continue;
-              const Pt<DP> x = load_pt<DP>(spts, t);
-              if (dist32<DP>(xq, x) <= b) ex.add(dist64<DP>(xq, x), key_id(kt));
-            }
+    const unsigned long long mycell = valid ? (scode[p] >> shift) : ~0ull;
+    const bool skip = valid && (int32_t)(K >> 32) < rho_skip;
+    const int nvalid = (int)min(32u, n - p0);
+    Best<S> acc;
+    acc.init();
+    int s = 0;
+    while (s < nvalid) {
+      const unsigned long long cell = __shfl_sync(kFull, mycell, s);
+      const int e = s + __popc(__ballot_sync(kFull, mycell == cell));
+      uint32_t c0[G];
+      unmorton<G>(cell, c0);
+      BlockRuns br;
+      lookup_block<G>(c0, R, cmax, hkeys, hvals, hmask, n, lane, br);
+      for (uint32_t w0 = 0; w0 < br.total; w0 += kNearCap) {
+        const uint32_t T = min((uint32_t)kNearCap, br.total - w0);
+        __syncwarp();
+        stage_window<DP, true>(br, w0, kNearCap, spts, skey, wpts, wkey, wpos, lane);
+        __syncwarp();
+        for (int qb = s; qb < e; qb += 4) {
+          const int qi = qb + grp;
+          const int src = qi < e ? qi : s;
+          const Pt<DP> qp = shfl_pt<DP>(me, src);
+          const unsigned long long Kq = __shfl_sync(kFull, K, src);
+          Best<S> b;
+          b.init();
+          for (uint32_t t = sub; t < T; t += 8) {
+            const unsigned long long kt = wkey[t];
+            if (kt <= Kq) continue;
+            const Pt<DP> x = window_pt<DP>(wpts, t);
+            if constexpr (F64) b.add(dist64<DP>(qp, x), key_id(kt), wpos[t]);
+            else b.add(dist32<DP>(qp, x), key_id(kt), wpos[t]);
           }
-        } else {
-          ex.add(dist64<DP>(xq, load_pt<DP>(spts, best.t1)), best.o1);
+          b.merge_xor(4);
+          b.merge_xor(2);
+          b.merge_xor(1);
+#pragma unroll
+          for (int g = 0; g < 4; ++g) {
+            const S v1 = __shfl_sync(kFull, b.s1, g * 8);
+            const uint32_t vo = __shfl_sync(kFull, b.o1, g * 8);
+            const S v2 = __shfl_sync(kFull, b.s2, g * 8);
+            const uint32_t vt = __shfl_sync(kFull, b.t1, g * 8);
+            if (lane == qb + g && qb + g < e) acc.merge(v1, vo, v2, vt);
+          }
         }
-        lambda[id] = (int32_t)ex.o;
-        delta[id] = sqrt(ex.s);
       }
+      s = e;
     }
-    if (!settled) {
-      const uint32_t e = atomicAdd(&ctr->queue_n, 1u);
-      q.pos[e] = p;
-      if constexpr (F64) q.s1d[e] = best.s1;
-      else q.s1[e] = best.s1;
+
+    bool settled = false;
+    if (valid && !skip) {
+      const uint32_t id = key_id(K);
+      if constexpr (F64) {
+        settled = acc.t1 != 0xffffffffu && acc.s1 < far64;
+        if (settled) {
+          lambda[id] = (int32_t)acc.o1;
+          delta[id] = sqrt(acc.s1);
+        }
+      } else {
+        const float bnd = band_of(acc.s1, bmul, badd);
+        settled = acc.t1 != 0xffffffffu && bnd < far32 && acc.s2 > bnd;
+        if (settled) {
+          lambda[id] = (int32_t)acc.o1;
+          delta[id] = sqrt(dist64<DP>(me, load_pt<DP>(spts, acc.t1)));
+        }
+      }
+    } else if (valid) {
+      const uint32_t id = key_id(K);
+      lambda[id] = -1;
+      delta[id] = __longlong_as_double(0x7ff8000000000000ll);  // NaN: skipped
     }
-  }
-  if constexpr (!F64) {
-    for (int o = 16; o > 0; o >>= 1) rescans += __shfl_xor_sync(0xffffffffu, rescans, o);
-    if ((threadIdx.x & 31) == 0 && rescans) atomicAdd(&ctr->exact_rescans, rescans);
+    // unsettled queries (nothing near, or a near tie) go to the far phase
+    const bool push = valid && !skip && !settled;
+    const unsigned pm = __ballot_sync(kFull, push);
+    uint32_t base = 0;
+    if (lane == 0 && pm) base = atomicAdd(&ctr->queue_n, (unsigned)__popc(pm));
+    base = __shfl_sync(kFull, base, 0);
+    if (push) {
+      const uint32_t slot = base + __popc(pm & lanemask_lt);
+      q.pos[slot] = p;
+      if constexpr (F64) q.s1d[slot] = acc.s1;
+      else q.s1[slot] = acc.s1;
+    }
   }
 }
 
@@ -250,7 +269,9 @@ __device__ __forceinline__ float node_lb2(const Node& nd, int nbits, const float
 
 // Visit every candidate (leaf with key > K) not excluded by `prune`; calls
 // visit(t, kt) for each.  prune(lbs) says whether a region whose squared
-// distance is at least lbs can be skipped.
+// distance is at least lbs can be skipped.  Returns false if the tree is
+// malformed or the stack would overflow (neither happens for a tree built by
+// tree.cu: its depth is at most 64 + 32).
 template <int DP, int G, typename Prune, typename Visit>
 __device__ __forceinline__ bool tree_walk(const Node* __restrict__ nodes, uint32_t n, int nbits,
                                           const unsigned long long* __restrict__ skey,
@@ -271,7 +292,7 @@ __device__ __forceinline__ bool tree_walk(const Node* __restrict__ nodes, uint32
     --sp;
     const uint32_t ni = stk[sp];
     if (prune(stl[sp])) continue;
-    if (ni + 1 >= n) return false;  // not an internal node: corrupted tree
+    if (ni + 1 >= n) return false;
     const uint32_t ch[2] = {nodes[ni].left, nodes[ni].right};
     uint32_t keep[2];
     float keepl[2];
@@ -306,7 +327,7 @@ __device__ __forceinline__ bool tree_walk(const Node* __restrict__ nodes, uint32
 }
 
 template <int DP, int G, bool F64>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kFarThreads)
 k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__ skey, uint32_t n,
           const GridGeom* __restrict__ geom, const CutGeom* __restrict__ cut,
           const Node* __restrict__ nodes, FarQueue q, int32_t* __restrict__ lambda,
@@ -332,7 +353,7 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
 
     if constexpr (F64) {
       Best<double> best;
-      best.init(INFINITY);
+      best.init();
       const double s_init = q.s1d[e];
       overflow |= !tree_walk<DP, G>(
           nodes, n, nbits, skey, K, u, f2lo,
@@ -349,7 +370,7 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
       }
     } else {
       Best<float> best;
-      best.init(INFINITY);
+      best.init();
       const float s_init = q.s1[e];
       overflow |= !tree_walk<DP, G>(
           nodes, n, nbits, skey, K, u, f2lo,
@@ -381,14 +402,14 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
     }
   }
   if (overflow) set_status(geom->status, kStatusStack);
-  for (int o = 16; o > 0; o >>= 1) rescans += __shfl_xor_sync(0xffffffffu, rescans, o);
+  for (int o = 16; o > 0; o >>= 1) rescans += __shfl_xor_sync(kFull, rescans, o);
   if ((threadIdx.x & 31) == 0 && rescans) atomicAdd(&ctr->exact_rescans, rescans);
 }
 
 __global__ void k_far_count(Counters* ctr) { ctr->far_queries += ctr->queue_n; }
 
-inline unsigned grid_for(uint64_t n, unsigned cap) {
-  uint64_t b = (n + kThreads - 1) / kThreads;
+inline unsigned grid_for(uint64_t items, int per_block, unsigned cap) {
+  uint64_t b = (items + per_block - 1) / per_block;
   if (b < 1) b = 1;
   if (b > cap) b = cap;
   return (unsigned)b;
@@ -399,13 +420,13 @@ void near_dg(bool fp64, const float* spts, const unsigned long long* scode,
              const unsigned long long* skey, uint32_t n, int32_t rho_skip, const GridGeom* geom,
              const CutGeom* cut, const unsigned long long* hkeys, const uint2* hvals,
              int32_t* lambda, double* delta, FarQueue q, Counters* ctr, cudaStream_t st) {
-  const unsigned grid = grid_for(n, 152u * 128u);
+  const unsigned grid = grid_for((n + 31) / 32, kNearWarps, 152u * 64u);
   if (fp64)
-    k_dep_near<DP, G, true><<<grid, kThreads, 0, st>>>(spts, scode, skey, n, rho_skip, geom, cut,
-                                                       hkeys, hvals, lambda, delta, q, ctr);
+    k_dep_near<DP, G, true><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, n, rho_skip, geom,
+                                                           cut, hkeys, hvals, lambda, delta, q, ctr);
   else
-    k_dep_near<DP, G, false><<<grid, kThreads, 0, st>>>(spts, scode, skey, n, rho_skip, geom, cut,
-                                                        hkeys, hvals, lambda, delta, q, ctr);
+    k_dep_near<DP, G, false><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, n, rho_skip, geom,
+                                                            cut, hkeys, hvals, lambda, delta, q, ctr);
 }
 
 template <int DP, int G>
@@ -414,13 +435,13 @@ void far_dg(bool fp64, const float* spts, const unsigned long long* skey, uint32
             int32_t* lambda, double* delta, Counters* ctr, uint32_t qcap, cudaStream_t st) {
   // the queue length is known only on the device: launch enough threads for
   // a full SM load and let them stride over it
-  const unsigned grid = grid_for(qcap, 152u * 8u);
+  const unsigned grid = grid_for(qcap, kFarThreads, 152u * 8u);
   if (fp64)
-    k_dep_far<DP, G, true><<<grid, kThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, q, lambda,
-                                                      delta, ctr);
+    k_dep_far<DP, G, true><<<grid, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, q, lambda,
+                                                         delta, ctr);
   else
-    k_dep_far<DP, G, false><<<grid, kThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, q, lambda,
-                                                       delta, ctr);
+    k_dep_far<DP, G, false><<<grid, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, q, lambda,
+                                                          delta, ctr);
 }
 
 }  // namespace

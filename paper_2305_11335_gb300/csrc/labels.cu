@@ -4,12 +4,12 @@
 // The paper links every non-center point to its dependent point with a
 // concurrent union-find (Algorithm 3).  The dependent pointers already form a
 // forest with one parent edge per point, so the components are found here by
-// pointer jumping instead: each round replaces every pointer by its
-// pointer's pointer, so ceil(log2(depth)) rounds reach the roots.  Rounds are
-// launched a fixed ceil(log2 n) + 2 times; a round that sees no change in the
-// previous one returns at once, so the launch sequence does not depend on the
-// data.  A pointer still moving after the last round means the input was not
-// a forest, recorded as kStatusCycle.
+// pointer jumping instead: each round makes every pointer jump several times
+// towards its root (see k_label_jump for the rate).  Rounds are launched a
+// fixed number of times (label_rounds: enough for any forest of n points);
+// a round that sees no change in the previous one returns at once, so the
+// launch sequence does not depend on the data.  A pointer still moving after
+// the last round means the input was not a forest, recorded as kStatusCycle.
 #include "internal.h"
 
 namespace dpc {
@@ -35,16 +35,30 @@ __global__ void k_label_init(const int32_t* __restrict__ rho, const int32_t* __r
   if (blockIdx.x == 0 && threadIdx.x == 0) flags[0] = 1;  // round 0 always runs
 }
 
-// Round r (1-based): par[i] <- par[par[i]] while that changes something.
+// Round r (1-based): up to kJumps times, par[i] <- par[par[i]].  Pointers only
+// ever move towards the root, so concurrent updates by other threads are
+// harmless.  If every pointer covered at least L steps before a round, the
+// first jump covers 2L and each further one at least L more, so a round
+// multiplies the covered distance by at least kJumps + 1.
+constexpr int kJumps = 8;
 __global__ void k_label_jump(int32_t* par, uint32_t n, int32_t* flags, int r) {
   if (flags[r - 1] == 0) return;  // the previous round changed nothing
   int changed = 0;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int32_t p = par[i];
+    int32_t p = par[i];
     if (p < 0 || p == (int32_t)i) continue;
-    const int32_t pp = par[p];
-    if (pp != p) {
-      par[i] = pp;
+    int32_t p0 = p;
+#pragma unroll 1
+    for (int j = 0; j < kJumps; ++j) {
+      const int32_t pp = par[p];
+      if (pp == p || pp < 0) {
+        if (pp < 0) p = pp;
+        break;
+      }
+      p = pp;
+    }
+    if (p != p0) {
+      par[i] = p;
       changed = 1;
     }
   }
@@ -64,9 +78,15 @@ inline unsigned grid_for(uint64_t n) {
 
 }  // namespace
 
+// Rounds until every chain (at most n - 1 long) has reached its root, plus
+// one that sees no change: the smallest r with (kJumps + 1)^r >= n, plus 2.
 int label_rounds(uint32_t n) {
   int r = 0;
-  while ((1ull << r) < (unsigned long long)n) ++r;
+  unsigned long long reach = 1;
+  while (reach < (unsigned long long)n) {
+    reach *= (unsigned long long)(kJumps + 1);
+    ++r;
+  }
   return r + 2;
 }
 
