@@ -358,8 +358,9 @@ FarQueue queue_of(Workspace* w) {
   return q;
 }
 
-void dependent_step(Workspace* w, const Inst& in, CutGeom* cut, int32_t rho_skip, bool fp64,
-                    int32_t* lambda, double* delta) {
+void dependent_step(Workspace* w, const void* pts_all, int dtype, const Inst& in, CutGeom* cut,
+                    int32_t rho_skip, bool fp64, int32_t* lambda, double* delta) {
+  const void* pts = (const char*)pts_all + in.coord_off * 4;
   cudaStream_t st = w->stream;
   const uint32_t n = (uint32_t)in.n;
   const int d = in.d, g = g_of(d), dp = dp_of(d);
@@ -369,8 +370,8 @@ void dependent_step(Workspace* w, const Inst& in, CutGeom* cut, int32_t rho_skip
   }
   {
     Phase ph(w, DPC_PHASE_NEAR);
-    launch_dep_near(dp, g, fp64, w->spts, w->scode, w->skey, n, rho_skip, w->geom, cut, w->hkeys,
-                    w->hvals, lambda, delta, queue_of(w), w->ctr, st);
+    launch_dep_near(dp, g, fp64, w->spts, w->scode, w->skey, n, rho_skip, pts, dtype, d, w->geom, cut,
+                    w->hkeys, w->hvals, lambda, delta, queue_of(w), w->ctr, st);
   }
   {
     Phase ph(w, DPC_PHASE_FAR);
@@ -493,7 +494,7 @@ int dpc_dependent(const void* pts, int dtype, const dpc_batch* b, int32_t dcut_i
     tree_step(w, (uint32_t)in.n);
     cells_step(w, (uint32_t)in.n, w->cuts);
     launch_keys_from_rho(rho + in.pt_off, w->sid, (uint32_t)in.n, w->skey, w->stream);
-    dependent_step(w, in, w->cuts, rho_skip, fp64, lambda + in.pt_off, delta + in.pt_off);
+    dependent_step(w, pts, dtype, in, w->cuts, rho_skip, fp64, lambda + in.pt_off, delta + in.pt_off);
     w->last_ncut_used = 1;
   }
   return finish(w, flags);
@@ -546,7 +547,7 @@ static int run_device(Workspace* w, const void* pts, int dtype, const dpc_batch*
       CutGeom* cut = w->cuts + c;
       cells_step(w, n, cut);
       density_step(w, in, cut, fp64, rho + o);
-      dependent_step(w, in, cut, 0, fp64, lambda + o, delta + o);
+      dependent_step(w, pts, dtype, in, cut, 0, fp64, lambda + o, delta + o);
       labels_step(w, n, params[(size_t)i * b->n_dcut + c], rho + o, lambda + o, delta + o, label + o);
     }
     w->last_ncut_used = b->n_dcut;

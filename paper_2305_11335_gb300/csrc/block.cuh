@@ -78,15 +78,13 @@ __device__ __forceinline__ void lookup_block(const uint32_t* c0, int R, int cmax
 }
 
 // Copy candidates [w0, w0 + cap) of the concatenated block list into the
-// warp's window: coordinates (DP floats), and for KEYS also order keys and
-// sorted positions.
+// warp's window: coordinates (DP floats), and for KEYS also order keys.
 template <int DP, bool KEYS>
 __device__ __forceinline__ void stage_window(const BlockRuns& br, uint32_t w0, uint32_t cap,
                                              const float* __restrict__ spts,
                                              const unsigned long long* __restrict__ skey,
                                              float* __restrict__ wpts,
-                                             unsigned long long* __restrict__ wkey,
-                                             uint32_t* __restrict__ wpos, int lane) {
+                                             unsigned long long* __restrict__ wkey, int lane) {
   const uint32_t w1 = w0 + cap;
 #pragma unroll
   for (int r = 0; r < kRunRounds; ++r) {
@@ -113,10 +111,7 @@ __device__ __forceinline__ void stage_window(const BlockRuns& br, uint32_t w0, u
           d4[0] = __ldg(s4);
           d4[1] = __ldg(s4 + 1);
         }
-        if constexpr (KEYS) {
-          wkey[dst] = __ldg(skey + src);
-          wpos[dst] = src;
-        }
+        if constexpr (KEYS) wkey[dst] = __ldg(skey + src);
       }
     }
   }

@@ -1,12 +1,15 @@
 // density.cu -- rho_i = |{j : D(x_i, x_j) <= d_cut}| (Definition 1).
 //
 // A warp owns 32 consecutive Morton-sorted points.  For each level-k cell
-// they fall into, the warp looks up the (2R+1)^g cells of the cell's block in
-// parallel, stages their points in shared memory (in windows of kCap), and
-// counts, 4 queries at a time with 8 lanes per query:
-//   FP32_CERT: s32 <= t_in counts, s32 > t_out does not, anything between is
-//              re-evaluated with the canonical binary64 distance (rare: the
-//              band is about 1e-6 of d_cut^2 wide);
+// they fall into (a "segment"), the warp looks up the (2R+1)^g cells of the
+// cell's block in parallel and stages their points in shared memory (in
+// windows of kCap).  A segment of 32 queries (one dense cell) runs one query
+// per lane over the window with broadcast reads; smaller segments run 4
+// queries at a time with 8 lanes each.
+//   FP32_CERT: s32 <= t_in counts, s32 > t_out does not.  Pairs in between
+//              (about 1e-6 of d_cut^2 wide) are counted with the canonical
+//              binary64 distance in a separate pass that runs only when a
+//              warp meets one, so the hot loop stays float32.
 //   FP64:      every pair is evaluated in binary64.
 // Both give exactly the binary64 count.  The kernel also writes the order key
 // of every sorted point, (rho << 32) | ~id.
@@ -22,6 +25,23 @@ constexpr int kThreads = kWarps * 32;
 
 template <int DP>
 constexpr int density_cap() { return DP == 8 ? 256 : 512; }
+
+// Exact count of the band pairs among window candidates t0, t0+step, ... < T.
+template <int DP>
+__device__ __noinline__ int2 band_count(const float* __restrict__ wpts, uint32_t t0, uint32_t T,
+                                        uint32_t step, Pt<DP> q, float t_in, float t_out,
+                                        double dc2) {
+  int in = 0, seen = 0;
+  for (uint32_t t = t0; t < T; t += step) {
+    const Pt<DP> x = window_pt<DP>(wpts, t);
+    const float s32 = dist32<DP>(q, x);
+    if (s32 > t_in && s32 <= t_out) {
+      ++seen;
+      in += dist64<DP>(q, x) <= dc2;
+    }
+  }
+  return make_int2(in, seen);
+}
 
 template <int DP, int G, bool F64>
 __global__ void __launch_bounds__(kThreads)
@@ -70,24 +90,54 @@ k_density(const float* __restrict__ spts, const unsigned long long* __restrict__
       for (uint32_t w0 = 0; w0 < br.total; w0 += kCap) {
         const uint32_t T = min((uint32_t)kCap, br.total - w0);
         __syncwarp();
-        stage_window<DP, false>(br, w0, kCap, spts, nullptr, wpts, nullptr, nullptr, lane);
+        stage_window<DP, false>(br, w0, kCap, spts, nullptr, wpts, nullptr, lane);
         __syncwarp();
+        if (e - s == 32) {
+          // one query per lane, every lane reads the same candidate
+          int32_t c = 0;
+          bool amb = false;
+#pragma unroll 4
+          for (uint32_t t = 0; t < T; ++t) {
+            const Pt<DP> x = window_pt<DP>(wpts, t);
+            if constexpr (F64) {
+              c += dist64<DP>(me, x) <= dc2;
+            } else {
+              const float s32 = dist32<DP>(me, x);
+              c += s32 <= t_in;
+              amb |= (s32 > t_in) & (s32 <= t_out);
+            }
+          }
+          if constexpr (!F64) {
+            if (__any_sync(kFull, amb)) {
+              const int2 r = band_count<DP>(wpts, 0, T, 1, me, t_in, t_out, dc2);
+              c += r.x;
+              band += r.y;
+            }
+          }
+          count += c;
+          continue;
+        }
         for (int qb = s; qb < e; qb += 4) {
           const int qi = qb + grp;
           const Pt<DP> q = shfl_pt<DP>(me, qi < e ? qi : s);
           int32_t c = 0;
+          bool amb = false;
+#pragma unroll 2
           for (uint32_t t = sub; t < T; t += 8) {
             const Pt<DP> x = window_pt<DP>(wpts, t);
             if constexpr (F64) {
               c += dist64<DP>(q, x) <= dc2;
             } else {
               const float s32 = dist32<DP>(q, x);
-              if (s32 <= t_in) {
-                ++c;
-              } else if (s32 <= t_out) {
-                ++band;
-                c += dist64<DP>(q, x) <= dc2;
-              }
+              c += s32 <= t_in;
+              amb |= (s32 > t_in) & (s32 <= t_out);
+            }
+          }
+          if constexpr (!F64) {
+            if (__any_sync(kFull, amb)) {
+              const int2 r = band_count<DP>(wpts, sub, T, 8, q, t_in, t_out, dc2);
+              c += r.x;
+              if (qi < e) band += r.y;
             }
           }
           c += __shfl_xor_sync(kFull, c, 4);

@@ -121,22 +121,82 @@ __device__ __forceinline__ float lb_axis(float lo, float hi, float u) {
 // ---------------------------------------------------------------------------
 // near phase
 
+// (s32, id) packed so that one unsigned compare orders by distance, then id
+// (non-negative floats order like their bit patterns).
+__device__ __forceinline__ unsigned long long pack_sd(float s, uint32_t id) {
+  return ((unsigned long long)__float_as_uint(s) << 32) | id;
+}
+__device__ __forceinline__ float pack_s(unsigned long long v) { return __uint_as_float((uint32_t)(v >> 32)); }
+__device__ __forceinline__ uint32_t pack_id(unsigned long long v) { return (uint32_t)v; }
+
+// Smallest and second smallest packed value of a candidate set.
+struct Min2 {
+  unsigned long long b1, b2;
+  __device__ __forceinline__ void init() { b1 = b2 = ~0ull; }
+  __device__ __forceinline__ void add(unsigned long long v) {
+    b2 = min(b2, max(b1, v));
+    b1 = min(b1, v);
+  }
+  __device__ __forceinline__ void merge(unsigned long long o1, unsigned long long o2) {
+    b2 = min(max(b1, o1), min(b2, o2));
+    b1 = min(b1, o1);
+  }
+  __device__ __forceinline__ void merge_xor(int mask) {
+    const unsigned long long o1 = __shfl_xor_sync(kFull, b1, mask);
+    const unsigned long long o2 = __shfl_xor_sync(kFull, b2, mask);
+    merge(o1, o2);
+  }
+};
+
+// binary64 argmin over (s64, id) (FP64 mode).
+struct Min64 {
+  double s;
+  uint32_t o;
+  __device__ __forceinline__ void init() {
+    s = INFINITY;
+    o = 0xffffffffu;
+  }
+  __device__ __forceinline__ void add(double v, uint32_t id) {
+    const bool lt = v < s || (v == s && id < o);
+    s = lt ? v : s;
+    o = lt ? id : o;
+  }
+  __device__ __forceinline__ void merge_xor(int mask) {
+    add(__shfl_xor_sync(kFull, s, mask), __shfl_xor_sync(kFull, o, mask));
+  }
+};
+
+// Coordinates of point `id` from the caller's input (the same float values the
+// sorted copy holds: int32 inputs are exact in float32 by the range check).
+template <int DP>
+__device__ __forceinline__ Pt<DP> input_pt(const void* __restrict__ pts, int dtype, int d, uint32_t id) {
+  Pt<DP> p;
+#pragma unroll
+  for (int a = 0; a < DP; ++a) {
+    float v = 0.f;
+    if (a < d) {
+      const size_t e = (size_t)id * d + a;
+      v = dtype == 0 ? (float)__ldg((const int32_t*)pts + e) : __ldg((const float*)pts + e);
+    }
+    p.x[a] = v;
+  }
+  return p;
+}
+
 template <int DP, int G, bool F64>
 __global__ void __launch_bounds__(kNearThreads)
 k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict__ scode,
            const unsigned long long* __restrict__ skey, uint32_t n, int32_t rho_skip,
+           const void* __restrict__ pts, int dtype, int d,
            const GridGeom* __restrict__ geom, const CutGeom* __restrict__ cut,
            const unsigned long long* __restrict__ hkeys, const uint2* __restrict__ hvals,
            int32_t* __restrict__ lambda, double* __restrict__ delta, FarQueue q, Counters* ctr) {
-  using S = typename std::conditional<F64, double, float>::type;
   __shared__ __align__(16) float s_pts[kNearWarps * kNearCap * DP];
   __shared__ unsigned long long s_key[kNearWarps * kNearCap];
-  __shared__ uint32_t s_pos[kNearWarps * kNearCap];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   float* wpts = s_pts + wib * kNearCap * DP;
   unsigned long long* wkey = s_key + wib * kNearCap;
-  uint32_t* wpos = s_pos + wib * kNearCap;
 
   const int k = cut->k;
   const int R = cut->R;
@@ -166,8 +226,10 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
     const unsigned long long mycell = valid ? (scode[p] >> shift) : ~0ull;
     const bool skip = valid && (int32_t)(K >> 32) < rho_skip;
     const int nvalid = (int)min(32u, n - p0);
-    Best<S> acc;
+    Min2 acc;
     acc.init();
+    Min64 acc64;
+    acc64.init();
     int s = 0;
     while (s < nvalid) {
       const unsigned long long cell = __shfl_sync(kFull, mycell, s);
@@ -179,32 +241,62 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
       for (uint32_t w0 = 0; w0 < br.total; w0 += kNearCap) {
         const uint32_t T = min((uint32_t)kNearCap, br.total - w0);
         __syncwarp();
-        stage_window<DP, true>(br, w0, kNearCap, spts, skey, wpts, wkey, wpos, lane);
+        stage_window<DP, true>(br, w0, kNearCap, spts, skey, wpts, wkey, lane);
         __syncwarp();
+        if (e - s == 32) {
+          // one query per lane, every lane reads the same candidate
+#pragma unroll 4
+          for (uint32_t t = 0; t < T; ++t) {
+            const unsigned long long kt = wkey[t];
+            const Pt<DP> x = window_pt<DP>(wpts, t);
+            if constexpr (F64) {
+              if (kt > K) acc64.add(dist64<DP>(me, x), key_id(kt));
+            } else {
+              const unsigned long long v = kt > K ? pack_sd(dist32<DP>(me, x), key_id(kt)) : ~0ull;
+              acc.add(v);
+            }
+          }
+          continue;
+        }
         for (int qb = s; qb < e; qb += 4) {
           const int qi = qb + grp;
           const int src = qi < e ? qi : s;
           const Pt<DP> qp = shfl_pt<DP>(me, src);
           const unsigned long long Kq = __shfl_sync(kFull, K, src);
-          Best<S> b;
-          b.init();
-          for (uint32_t t = sub; t < T; t += 8) {
-            const unsigned long long kt = wkey[t];
-            if (kt <= Kq) continue;
-            const Pt<DP> x = window_pt<DP>(wpts, t);
-            if constexpr (F64) b.add(dist64<DP>(qp, x), key_id(kt), wpos[t]);
-            else b.add(dist32<DP>(qp, x), key_id(kt), wpos[t]);
-          }
-          b.merge_xor(4);
-          b.merge_xor(2);
-          b.merge_xor(1);
+          if constexpr (F64) {
+            Min64 b;
+            b.init();
+            for (uint32_t t = sub; t < T; t += 8) {
+              const unsigned long long kt = wkey[t];
+              if (kt > Kq) b.add(dist64<DP>(qp, window_pt<DP>(wpts, t)), key_id(kt));
+            }
+            b.merge_xor(4);
+            b.merge_xor(2);
+            b.merge_xor(1);
 #pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            const S v1 = __shfl_sync(kFull, b.s1, g * 8);
-            const uint32_t vo = __shfl_sync(kFull, b.o1, g * 8);
-            const S v2 = __shfl_sync(kFull, b.s2, g * 8);
-            const uint32_t vt = __shfl_sync(kFull, b.t1, g * 8);
-            if (lane == qb + g && qb + g < e) acc.merge(v1, vo, v2, vt);
+            for (int g = 0; g < 4; ++g) {
+              const double vs = __shfl_sync(kFull, b.s, g * 8);
+              const uint32_t vo = __shfl_sync(kFull, b.o, g * 8);
+              if (lane == qb + g && qb + g < e) acc64.add(vs, vo);
+            }
+          } else {
+            Min2 b;
+            b.init();
+#pragma unroll 2
+            for (uint32_t t = sub; t < T; t += 8) {
+              const unsigned long long kt = wkey[t];
+              const Pt<DP> x = window_pt<DP>(wpts, t);
+              b.add(kt > Kq ? pack_sd(dist32<DP>(qp, x), key_id(kt)) : ~0ull);
+            }
+            b.merge_xor(4);
+            b.merge_xor(2);
+            b.merge_xor(1);
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+              const unsigned long long v1 = __shfl_sync(kFull, b.b1, g * 8);
+              const unsigned long long v2 = __shfl_sync(kFull, b.b2, g * 8);
+              if (lane == qb + g && qb + g < e) acc.merge(v1, v2);
+            }
           }
         }
       }
@@ -212,20 +304,23 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
     }
 
     bool settled = false;
+    float s1 = INFINITY;
     if (valid && !skip) {
       const uint32_t id = key_id(K);
       if constexpr (F64) {
-        settled = acc.t1 != 0xffffffffu && acc.s1 < far64;
+        settled = acc64.o != 0xffffffffu && acc64.s < far64;
         if (settled) {
-          lambda[id] = (int32_t)acc.o1;
-          delta[id] = sqrt(acc.s1);
+          lambda[id] = (int32_t)acc64.o;
+          delta[id] = sqrt(acc64.s);
         }
-      } else {
-        const float bnd = band_of(acc.s1, bmul, badd);
-        settled = acc.t1 != 0xffffffffu && bnd < far32 && acc.s2 > bnd;
+      } else if (acc.b1 != ~0ull) {
+        s1 = pack_s(acc.b1);
+        const float bnd = band_of(s1, bmul, badd);
+        settled = bnd < far32 && pack_s(acc.b2) > bnd;
         if (settled) {
-          lambda[id] = (int32_t)acc.o1;
-          delta[id] = sqrt(dist64<DP>(me, load_pt<DP>(spts, acc.t1)));
+          const uint32_t w = pack_id(acc.b1);
+          lambda[id] = (int32_t)w;
+          delta[id] = sqrt(dist64<DP>(me, input_pt<DP>(pts, dtype, d, w)));
         }
       }
     } else if (valid) {
@@ -242,8 +337,8 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
     if (push) {
       const uint32_t slot = base + __popc(pm & lanemask_lt);
       q.pos[slot] = p;
-      if constexpr (F64) q.s1d[slot] = acc.s1;
-      else q.s1[slot] = acc.s1;
+      if constexpr (F64) q.s1d[slot] = acc64.s;
+      else q.s1[slot] = s1;
     }
   }
 }
@@ -417,16 +512,19 @@ inline unsigned grid_for(uint64_t items, int per_block, unsigned cap) {
 
 template <int DP, int G>
 void near_dg(bool fp64, const float* spts, const unsigned long long* scode,
-             const unsigned long long* skey, uint32_t n, int32_t rho_skip, const GridGeom* geom,
+             const unsigned long long* skey, uint32_t n, int32_t rho_skip, const void* pts,
+             int dtype, int d, const GridGeom* geom,
              const CutGeom* cut, const unsigned long long* hkeys, const uint2* hvals,
              int32_t* lambda, double* delta, FarQueue q, Counters* ctr, cudaStream_t st) {
   const unsigned grid = grid_for((n + 31) / 32, kNearWarps, 152u * 64u);
   if (fp64)
-    k_dep_near<DP, G, true><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, n, rho_skip, geom,
-                                                           cut, hkeys, hvals, lambda, delta, q, ctr);
+    k_dep_near<DP, G, true><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, n, rho_skip, pts, dtype,
+                                                           d, geom, cut, hkeys, hvals, lambda, delta,
+                                                           q, ctr);
   else
-    k_dep_near<DP, G, false><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, n, rho_skip, geom,
-                                                            cut, hkeys, hvals, lambda, delta, q, ctr);
+    k_dep_near<DP, G, false><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, n, rho_skip, pts,
+                                                            dtype, d, geom, cut, hkeys, hvals, lambda,
+                                                            delta, q, ctr);
 }
 
 template <int DP, int G>
@@ -447,16 +545,16 @@ void far_dg(bool fp64, const float* spts, const unsigned long long* skey, uint32
 }  // namespace
 
 void launch_dep_near(int dp, int g, bool fp64, const float* spts, const unsigned long long* scode,
-                     const unsigned long long* skey, uint32_t n, int32_t rho_skip,
-                     const GridGeom* geom, const CutGeom* cut, const unsigned long long* hkeys,
+                     const unsigned long long* skey, uint32_t n, int32_t rho_skip, const void* pts,
+                     int dtype, int d, const GridGeom* geom, const CutGeom* cut, const unsigned long long* hkeys,
                      const uint2* hvals, int32_t* lambda, double* delta, FarQueue q,
                      Counters* ctr, cudaStream_t st) {
   if (n == 0) return;
   cudaMemsetAsync(&ctr->queue_n, 0, sizeof(unsigned int), st);
-  if (g == 1) near_dg<2, 1>(fp64, spts, scode, skey, n, rho_skip, geom, cut, hkeys, hvals, lambda, delta, q, ctr, st);
-  else if (g == 2) near_dg<2, 2>(fp64, spts, scode, skey, n, rho_skip, geom, cut, hkeys, hvals, lambda, delta, q, ctr, st);
-  else if (dp == 4) near_dg<4, 3>(fp64, spts, scode, skey, n, rho_skip, geom, cut, hkeys, hvals, lambda, delta, q, ctr, st);
-  else near_dg<8, 3>(fp64, spts, scode, skey, n, rho_skip, geom, cut, hkeys, hvals, lambda, delta, q, ctr, st);
+  if (g == 1) near_dg<2, 1>(fp64, spts, scode, skey, n, rho_skip, pts, dtype, d, geom, cut, hkeys, hvals, lambda, delta, q, ctr, st);
+  else if (g == 2) near_dg<2, 2>(fp64, spts, scode, skey, n, rho_skip, pts, dtype, d, geom, cut, hkeys, hvals, lambda, delta, q, ctr, st);
+  else if (dp == 4) near_dg<4, 3>(fp64, spts, scode, skey, n, rho_skip, pts, dtype, d, geom, cut, hkeys, hvals, lambda, delta, q, ctr, st);
+  else near_dg<8, 3>(fp64, spts, scode, skey, n, rho_skip, pts, dtype, d, geom, cut, hkeys, hvals, lambda, delta, q, ctr, st);
   count_launches(1);
 }
 

@@ -65,8 +65,8 @@ struct FarQueue {
   double* s1d;     // best binary64 distance found by the near phase (FP64 mode)
 };
 void launch_dep_near(int dp, int g, bool fp64, const float* spts, const unsigned long long* scode,
-                     const unsigned long long* skey, uint32_t n, int32_t rho_skip,
-                     const GridGeom* geom, const CutGeom* cut, const unsigned long long* hkeys,
+                     const unsigned long long* skey, uint32_t n, int32_t rho_skip, const void* pts,
+                     int dtype, int d, const GridGeom* geom, const CutGeom* cut, const unsigned long long* hkeys,
                      const uint2* hvals, int32_t* lambda, double* delta, FarQueue q,
                      Counters* ctr, cudaStream_t st);
 void launch_dep_far(int dp, int g, bool fp64, const float* spts, const unsigned long long* skey,
