@@ -24,7 +24,11 @@ struct BlockRuns {
   uint32_t len[kRunRounds];
   uint32_t pre[kRunRounds];
   uint32_t total;
+  int rounds;  // rounds of 32 cells actually used
 };
+
+// floor(x / w) for 0 <= x < 2^10 and w in {1, 3, 5, 7}: x * ceil(2^16 / w) >> 16.
+__device__ __forceinline__ int div_small(int x, int inv) { return (x * inv) >> 16; }
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
 #pragma unroll
@@ -43,12 +47,18 @@ __device__ __forceinline__ void lookup_block(const uint32_t* c0, int R, int cmax
                                              const uint2* __restrict__ hvals, uint32_t hmask,
                                              uint32_t n, int lane, BlockRuns& br) {
   const int W = 2 * R + 1;
+  const int invW = (65536 + W - 1) / W;
   int ncell = W;
   if (G >= 2) ncell *= W;
   if (G >= 3) ncell *= W;
   uint32_t total = 0;
+  br.rounds = (ncell + 31) >> 5;
 #pragma unroll
   for (int r = 0; r < kRunRounds; ++r) {
+    br.start[r] = 0;
+    br.len[r] = 0;
+    br.pre[r] = total;
+    if (r >= br.rounds) continue;
     const int o = r * 32 + lane;
     uint32_t st = 0, len = 0;
     if (o < ncell) {
@@ -57,8 +67,9 @@ __device__ __forceinline__ void lookup_block(const uint32_t* c0, int R, int cmax
       bool inside = true;
 #pragma unroll
       for (int a = 0; a < G; ++a) {
-        const int ca = (int)c0[a] + rem % W - R;
-        rem /= W;
+        const int q = div_small(rem, invW);
+        const int ca = (int)c0[a] + (rem - q * W) - R;
+        rem = q;
         inside &= (ca >= 0) & (ca <= cmax);
         c[a] = (uint32_t)ca;
       }
@@ -88,6 +99,7 @@ __device__ __forceinline__ void stage_window(const BlockRuns& br, uint32_t w0, u
   const uint32_t w1 = w0 + cap;
 #pragma unroll
   for (int r = 0; r < kRunRounds; ++r) {
+    if (r >= br.rounds) break;
     const uint32_t lo = br.pre[r], hi = br.pre[r] + br.len[r];
     unsigned mask = __ballot_sync(kFull, br.len[r] > 0 && lo < w1 && hi > w0);
     while (mask) {

@@ -93,9 +93,9 @@ k_density(const float* __restrict__ spts, const unsigned long long* __restrict__
         stage_window<DP, false>(br, w0, kCap, spts, nullptr, wpts, nullptr, lane);
         __syncwarp();
         if (e - s == 32) {
-          // one query per lane, every lane reads the same candidate
-          int32_t c = 0;
-          bool amb = false;
+          // one query per lane, every lane reads the same candidate; c counts
+          // s32 <= t_in (certainly within d_cut), c2 counts s32 <= t_out
+          int32_t c = 0, c2 = 0;
 #pragma unroll 4
           for (uint32_t t = 0; t < T; ++t) {
             const Pt<DP> x = window_pt<DP>(wpts, t);
@@ -104,11 +104,11 @@ k_density(const float* __restrict__ spts, const unsigned long long* __restrict__
             } else {
               const float s32 = dist32<DP>(me, x);
               c += s32 <= t_in;
-              amb |= (s32 > t_in) & (s32 <= t_out);
+              c2 += s32 <= t_out;
             }
           }
           if constexpr (!F64) {
-            if (__any_sync(kFull, amb)) {
+            if (__any_sync(kFull, c2 != c)) {
               const int2 r = band_count<DP>(wpts, 0, T, 1, me, t_in, t_out, dc2);
               c += r.x;
               band += r.y;
@@ -120,8 +120,7 @@ k_density(const float* __restrict__ spts, const unsigned long long* __restrict__
         for (int qb = s; qb < e; qb += 4) {
           const int qi = qb + grp;
           const Pt<DP> q = shfl_pt<DP>(me, qi < e ? qi : s);
-          int32_t c = 0;
-          bool amb = false;
+          int32_t c = 0, c2 = 0;
 #pragma unroll 2
           for (uint32_t t = sub; t < T; t += 8) {
             const Pt<DP> x = window_pt<DP>(wpts, t);
@@ -130,11 +129,11 @@ k_density(const float* __restrict__ spts, const unsigned long long* __restrict__
             } else {
               const float s32 = dist32<DP>(q, x);
               c += s32 <= t_in;
-              amb |= (s32 > t_in) & (s32 <= t_out);
+              c2 += s32 <= t_out;
             }
           }
           if constexpr (!F64) {
-            if (__any_sync(kFull, amb)) {
+            if (__any_sync(kFull, c2 != c)) {
               const int2 r = band_count<DP>(wpts, sub, T, 8, q, t_in, t_out, dc2);
               c += r.x;
               if (qi < e) band += r.y;

@@ -121,30 +121,32 @@ __device__ __forceinline__ float lb_axis(float lo, float hi, float u) {
 // ---------------------------------------------------------------------------
 // near phase
 
-// (s32, id) packed so that one unsigned compare orders by distance, then id
-// (non-negative floats order like their bit patterns).
-__device__ __forceinline__ unsigned long long pack_sd(float s, uint32_t id) {
-  return ((unsigned long long)__float_as_uint(s) << 32) | id;
-}
-__device__ __forceinline__ float pack_s(unsigned long long v) { return __uint_as_float((uint32_t)(v >> 32)); }
-__device__ __forceinline__ uint32_t pack_id(unsigned long long v) { return (uint32_t)v; }
-
-// Smallest and second smallest packed value of a candidate set.
+// Smallest and second smallest float32 distance of a candidate set, and the id
+// of a candidate at the smallest.  Two candidates at the same smallest
+// distance leave s2 == s1, which the caller treats as ambiguous and resolves
+// in binary64 later, so ties need no id order here.
 struct Min2 {
-  unsigned long long b1, b2;
-  __device__ __forceinline__ void init() { b1 = b2 = ~0ull; }
-  __device__ __forceinline__ void add(unsigned long long v) {
-    b2 = min(b2, max(b1, v));
-    b1 = min(b1, v);
+  float s1, s2;
+  uint32_t o1;
+  __device__ __forceinline__ void init() {
+    s1 = s2 = INFINITY;
+    o1 = 0xffffffffu;
   }
-  __device__ __forceinline__ void merge(unsigned long long o1, unsigned long long o2) {
-    b2 = min(max(b1, o1), min(b2, o2));
-    b1 = min(b1, o1);
+  __device__ __forceinline__ void add(float v, uint32_t id) {
+    s2 = fminf(s2, fmaxf(s1, v));
+    o1 = v < s1 ? id : o1;
+    s1 = fminf(s1, v);
+  }
+  __device__ __forceinline__ void merge(float b1, uint32_t bo, float b2) {
+    s2 = fminf(fmaxf(s1, b1), fminf(s2, b2));
+    o1 = b1 < s1 ? bo : o1;
+    s1 = fminf(s1, b1);
   }
   __device__ __forceinline__ void merge_xor(int mask) {
-    const unsigned long long o1 = __shfl_xor_sync(kFull, b1, mask);
-    const unsigned long long o2 = __shfl_xor_sync(kFull, b2, mask);
-    merge(o1, o2);
+    const float b1 = __shfl_xor_sync(kFull, s1, mask);
+    const uint32_t bo = __shfl_xor_sync(kFull, o1, mask);
+    const float b2 = __shfl_xor_sync(kFull, s2, mask);
+    merge(b1, bo, b2);
   }
 };
 
@@ -252,8 +254,8 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
             if constexpr (F64) {
               if (kt > K) acc64.add(dist64<DP>(me, x), key_id(kt));
             } else {
-              const unsigned long long v = kt > K ? pack_sd(dist32<DP>(me, x), key_id(kt)) : ~0ull;
-              acc.add(v);
+              const float d32 = dist32<DP>(me, x);
+              acc.add(kt > K ? d32 : INFINITY, key_id(kt));
             }
           }
           continue;
@@ -285,17 +287,18 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
 #pragma unroll 2
             for (uint32_t t = sub; t < T; t += 8) {
               const unsigned long long kt = wkey[t];
-              const Pt<DP> x = window_pt<DP>(wpts, t);
-              b.add(kt > Kq ? pack_sd(dist32<DP>(qp, x), key_id(kt)) : ~0ull);
+              const float d32 = dist32<DP>(qp, window_pt<DP>(wpts, t));
+              b.add(kt > Kq ? d32 : INFINITY, key_id(kt));
             }
             b.merge_xor(4);
             b.merge_xor(2);
             b.merge_xor(1);
 #pragma unroll
             for (int g = 0; g < 4; ++g) {
-              const unsigned long long v1 = __shfl_sync(kFull, b.b1, g * 8);
-              const unsigned long long v2 = __shfl_sync(kFull, b.b2, g * 8);
-              if (lane == qb + g && qb + g < e) acc.merge(v1, v2);
+              const float v1 = __shfl_sync(kFull, b.s1, g * 8);
+              const uint32_t vo = __shfl_sync(kFull, b.o1, g * 8);
+              const float v2 = __shfl_sync(kFull, b.s2, g * 8);
+              if (lane == qb + g && qb + g < e) acc.merge(v1, vo, v2);
             }
           }
         }
@@ -313,12 +316,12 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
           lambda[id] = (int32_t)acc64.o;
           delta[id] = sqrt(acc64.s);
         }
-      } else if (acc.b1 != ~0ull) {
-        s1 = pack_s(acc.b1);
+      } else if (acc.o1 != 0xffffffffu) {
+        s1 = acc.s1;
         const float bnd = band_of(s1, bmul, badd);
-        settled = bnd < far32 && pack_s(acc.b2) > bnd;
+        settled = bnd < far32 && acc.s2 > bnd;
         if (settled) {
-          const uint32_t w = pack_id(acc.b1);
+          const uint32_t w = acc.o1;
           lambda[id] = (int32_t)w;
           delta[id] = sqrt(dist64<DP>(me, input_pt<DP>(pts, dtype, d, w)));
         }
