@@ -1,158 +1,139 @@
-// block.cuh -- warp-cooperative access to the (2R+1)^g grid block around a
-// cell: parallel hash lookups of the neighbour cells and staging of their
-// points (and keys) into the warp's shared-memory window.
+// block.cuh -- warp-cooperative visits of the grid blocks of 32 queries.
 //
 // Work layout shared by the density and near-dependent kernels: a warp owns
-// 32 consecutive Morton-sorted points.  They fall into one or more level-k
-// cells ("segments", contiguous because the order is by cell); for each
-// segment the warp stages the candidates of the cell's block once and runs
-// the segment's queries against them, 4 queries at a time with 8 lanes each.
+// 32 consecutive Morton-sorted points, one query per lane.  Query q needs the
+// points of the (2R+1)^g level-k cells around its own cell ("its block").
+// The warp takes the bounding box of its queries' cells, grows it by R cells
+// (the "union"), looks the union's cells up in the occupied-cell hash in
+// parallel (one cell per lane), and then streams every non-empty cell's run of
+// sorted points with all lanes reading the same point (one broadcast load).
+// A lane whose block does not contain the cell masks it out, so every query
+// sees exactly the points of its own block.  When the union would exceed
+// kMaxUnion cells (the 32 points straddle a jump of the Morton curve), the
+// warp splits its points into runs of equal cell and visits each separately.
 #pragma once
 
 #include "dpc_device.cuh"
 
 namespace dpc {
 
-constexpr int kMaxBlockCells = 128;  // (2R+1)^g <= 125
-constexpr int kRunRounds = kMaxBlockCells / 32;
+constexpr int kMaxUnion = 128;
 constexpr unsigned kFull = 0xffffffffu;
 
-// Runs of the block's cells: lane l holds the cells with offset index
-// l + 32 r.  pre[r] is the run's offset in the concatenated candidate list.
-struct BlockRuns {
-  uint32_t start[kRunRounds];
-  uint32_t len[kRunRounds];
-  uint32_t pre[kRunRounds];
-  uint32_t total;
-  int rounds;  // rounds of 32 cells actually used
-};
-
-// floor(x / w) for 0 <= x < 2^10 and w in {1, 3, 5, 7}: x * ceil(2^16 / w) >> 16.
+// floor(x / w) for 0 <= x < 128, 1 <= w <= 128: x * ceil(2^16 / w) >> 16 is exact
+// there (the rounding term x * (w * ceil(2^16 / w) - 2^16) stays below 2^16 / 4).
 __device__ __forceinline__ int div_small(int x, int inv) { return (x * inv) >> 16; }
 
-__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t t = __shfl_up_sync(kFull, v, o);
-    if (lane >= o) v += t;
+template <int G>
+struct Union {
+  int lo[G];   // first cell of the union per axis
+  int w[G];    // extent per axis
+  int inv[G];  // ceil(2^16 / w)
+  int ncell;
+};
+
+// Bounding box of the cells of the active lanes, grown by R and clipped to
+// the grid.  Returns false (union unusable) if it holds more than kMaxUnion
+// cells.
+template <int G>
+__device__ __forceinline__ bool make_union(const uint32_t* c0, bool active, int R, int cmax,
+                                           Union<G>& u) {
+  int n = 1;
+  if (!__any_sync(kFull, active)) {  // no query: an empty union
+    u.ncell = 0;
+    return true;
   }
-  return v;
+#pragma unroll
+  for (int a = 0; a < G; ++a) {
+    int mn = active ? (int)c0[a] : 0x7fffffff;
+    int mx = active ? (int)c0[a] : -1;
+    mn = __reduce_min_sync(kFull, mn);
+    mx = __reduce_max_sync(kFull, mx);
+    const int lo = max(mn - R, 0);
+    const int hi = min(mx + R, cmax);
+    u.lo[a] = lo;
+    u.w[a] = hi - lo + 1;
+    u.inv[a] = (65536 + u.w[a] - 1) / u.w[a];
+    n *= u.w[a];
+    if (n > kMaxUnion) {
+      n = kMaxUnion + 1;
+    }
+  }
+  u.ncell = n;
+  return n <= kMaxUnion;
 }
 
-// Look up every cell of the (2R+1)^G block around cell c0 (level-k indices,
-// valid range [0, cmax] per axis).
-template <int G>
-__device__ __forceinline__ void lookup_block(const uint32_t* c0, int R, int cmax,
-                                             const unsigned long long* __restrict__ hkeys,
-                                             const uint2* __restrict__ hvals, uint32_t hmask,
-                                             uint32_t n, int lane, BlockRuns& br) {
-  const int W = 2 * R + 1;
-  const int invW = (65536 + W - 1) / W;
-  int ncell = W;
-  if (G >= 2) ncell *= W;
-  if (G >= 3) ncell *= W;
-  uint32_t total = 0;
-  br.rounds = (ncell + 31) >> 5;
-#pragma unroll
-  for (int r = 0; r < kRunRounds; ++r) {
-    br.start[r] = 0;
-    br.len[r] = 0;
-    br.pre[r] = total;
-    if (r >= br.rounds) continue;
-    const int o = r * 32 + lane;
+// Visit every non-empty cell of the union: visit(start, len, cell[G]) is
+// called by all lanes with the same arguments (warp-uniform).
+template <int G, typename Visit>
+__device__ __forceinline__ void for_union_cells(const Union<G>& u,
+                                                const unsigned long long* __restrict__ hkeys,
+                                                const uint2* __restrict__ hvals, uint32_t hmask,
+                                                uint32_t n, int lane, Visit visit) {
+  for (int base = 0; base < u.ncell; base += 32) {
+    const int o = base + lane;
     uint32_t st = 0, len = 0;
-    if (o < ncell) {
+    uint32_t c[G];
+#pragma unroll
+    for (int a = 0; a < G; ++a) c[a] = 0;
+    if (o < u.ncell) {
       int rem = o;
-      uint32_t c[G];
-      bool inside = true;
 #pragma unroll
       for (int a = 0; a < G; ++a) {
-        const int q = div_small(rem, invW);
-        const int ca = (int)c0[a] + (rem - q * W) - R;
+        const int q = div_small(rem, u.inv[a]);
+        c[a] = (uint32_t)(u.lo[a] + rem - q * u.w[a]);
         rem = q;
-        inside &= (ca >= 0) & (ca <= cmax);
-        c[a] = (uint32_t)ca;
       }
-      if (inside) {
-        const uint2 run = clip_run(hash_find(hkeys, hvals, hmask, morton<G>(c)), n);
-        st = run.x;
-        len = run.y - run.x;
-      }
+      const uint2 run = clip_run(hash_find(hkeys, hvals, hmask, morton<G>(c)), n);
+      st = run.x;
+      len = run.y - run.x;
     }
-    const uint32_t incl = warp_incl_scan(len, lane);
-    br.start[r] = st;
-    br.len[r] = len;
-    br.pre[r] = total + incl - len;
-    total += __shfl_sync(kFull, incl, 31);
-  }
-  br.total = total;
-}
-
-// Copy candidates [w0, w0 + cap) of the concatenated block list into the
-// warp's window: coordinates (DP floats), and for KEYS also order keys.
-template <int DP, bool KEYS>
-__device__ __forceinline__ void stage_window(const BlockRuns& br, uint32_t w0, uint32_t cap,
-                                             const float* __restrict__ spts,
-                                             const unsigned long long* __restrict__ skey,
-                                             float* __restrict__ wpts,
-                                             unsigned long long* __restrict__ wkey, int lane) {
-  const uint32_t w1 = w0 + cap;
-#pragma unroll
-  for (int r = 0; r < kRunRounds; ++r) {
-    if (r >= br.rounds) break;
-    const uint32_t lo = br.pre[r], hi = br.pre[r] + br.len[r];
-    unsigned mask = __ballot_sync(kFull, br.len[r] > 0 && lo < w1 && hi > w0);
+    unsigned mask = __ballot_sync(kFull, len > 0);
     while (mask) {
       const int j = __ffs(mask) - 1;
       mask &= mask - 1;
-      const uint32_t rs = __shfl_sync(kFull, br.start[r], j);
-      const uint32_t rlo = __shfl_sync(kFull, lo, j);
-      const uint32_t rhi = __shfl_sync(kFull, hi, j);
-      const uint32_t a = rlo > w0 ? rlo : w0;
-      const uint32_t b = rhi < w1 ? rhi : w1;
-      for (uint32_t e = a + lane; e < b; e += 32) {
-        const uint32_t src = rs + (e - rlo);
-        const uint32_t dst = e - w0;
-        if constexpr (DP == 2) {
-          reinterpret_cast<float2*>(wpts)[dst] = __ldg(reinterpret_cast<const float2*>(spts) + src);
-        } else if constexpr (DP == 4) {
-          reinterpret_cast<float4*>(wpts)[dst] = __ldg(reinterpret_cast<const float4*>(spts) + src);
-        } else {
-          const float4* s4 = reinterpret_cast<const float4*>(spts) + 2 * (size_t)src;
-          float4* d4 = reinterpret_cast<float4*>(wpts) + 2 * (size_t)dst;
-          d4[0] = __ldg(s4);
-          d4[1] = __ldg(s4 + 1);
-        }
-        if constexpr (KEYS) wkey[dst] = __ldg(skey + src);
-      }
+      uint32_t cj[G];
+#pragma unroll
+      for (int a = 0; a < G; ++a) cj[a] = __shfl_sync(kFull, c[a], j);
+      visit(__shfl_sync(kFull, st, j), __shfl_sync(kFull, len, j), cj);
     }
   }
 }
 
-template <int DP>
-__device__ __forceinline__ Pt<DP> window_pt(const float* __restrict__ wpts, uint32_t i) {
-  Pt<DP> p;
-  if constexpr (DP == 2) {
-    float2 v = reinterpret_cast<const float2*>(wpts)[i];
-    p.x[0] = v.x; p.x[1] = v.y;
-  } else if constexpr (DP == 4) {
-    float4 v = reinterpret_cast<const float4*>(wpts)[i];
-    p.x[0] = v.x; p.x[1] = v.y; p.x[2] = v.z; p.x[3] = v.w;
-  } else {
-    const float4* q = reinterpret_cast<const float4*>(wpts) + 2 * (size_t)i;
-    float4 a = q[0], b = q[1];
-    p.x[0] = a.x; p.x[1] = a.y; p.x[2] = a.z; p.x[3] = a.w;
-    p.x[4] = b.x; p.x[5] = b.y; p.x[6] = b.z; p.x[7] = b.w;
-  }
-  return p;
+// Does the block of radius R around cell c0 contain cell c?
+template <int G>
+__device__ __forceinline__ bool in_block(const uint32_t* c0, const uint32_t* c, int R) {
+  bool in = true;
+#pragma unroll
+  for (int a = 0; a < G; ++a) in &= abs((int)c[a] - (int)c0[a]) <= R;
+  return in;
 }
 
-template <int DP>
-__device__ __forceinline__ Pt<DP> shfl_pt(const Pt<DP>& p, int src) {
-  Pt<DP> q;
-#pragma unroll
-  for (int k = 0; k < DP; ++k) q.x[k] = __shfl_sync(kFull, p.x[k], src);
-  return q;
+// The warp's groups of lanes: the whole chunk if its union is small enough,
+// else one group per cell.  group(active, union) is called for each group.
+// `valid` marks lanes holding a point (a prefix of the warp), `active` the
+// queries to answer (a subset of them).
+template <int G, typename Group>
+__device__ __forceinline__ void for_groups(const unsigned long long mycell, const uint32_t* c0,
+                                           bool valid, bool active, int nvalid, int R, int cmax,
+                                           int lane, Group group) {
+  Union<G> u;
+  if (make_union<G>(c0, active, R, cmax, u)) {
+    group(active, u);
+    return;
+  }
+  int s = 0;
+  while (s < nvalid) {
+    const unsigned long long cell = __shfl_sync(kFull, mycell, s);
+    const bool same = valid && mycell == cell;  // lanes s .. e-1 (sorted order)
+    const int e = s + __popc(__ballot_sync(kFull, same));
+    const bool act = same && active;
+    if (__any_sync(kFull, act)) {
+      make_union<G>(c0, act, R, cmax, u);  // one cell: (2R+1)^g <= kMaxUnion
+      group(act, u);
+    }
+    s = e;
+  }
 }
 
 }  // namespace dpc

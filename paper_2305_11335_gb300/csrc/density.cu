@@ -1,15 +1,12 @@
 // density.cu -- rho_i = |{j : D(x_i, x_j) <= d_cut}| (Definition 1).
 //
-// A warp owns 32 consecutive Morton-sorted points.  For each level-k cell
-// they fall into (a "segment"), the warp looks up the (2R+1)^g cells of the
-// cell's block in parallel and stages their points in shared memory (in
-// windows of kCap).  A segment of 32 queries (one dense cell) runs one query
-// per lane over the window with broadcast reads; smaller segments run 4
-// queries at a time with 8 lanes each.
+// One query per lane, 32 consecutive Morton-sorted queries per warp; the warp
+// streams the union of its queries' grid blocks with broadcast loads and each
+// lane counts the points of its own (2R+1)^g block (block.cuh).
 //   FP32_CERT: s32 <= t_in counts, s32 > t_out does not.  Pairs in between
 //              (about 1e-6 of d_cut^2 wide) are counted with the canonical
-//              binary64 distance in a separate pass that runs only when a
-//              warp meets one, so the hot loop stays float32.
+//              binary64 distance in a separate pass, taken only by a warp that
+//              met one, so the hot loop stays float32.
 //   FP64:      every pair is evaluated in binary64.
 // Both give exactly the binary64 count.  The kernel also writes the order key
 // of every sorted point, (rho << 32) | ~id.
@@ -23,23 +20,28 @@ namespace {
 constexpr int kWarps = 4;
 constexpr int kThreads = kWarps * 32;
 
-template <int DP>
-constexpr int density_cap() { return DP == 8 ? 256 : 512; }
-
-// Exact count of the band pairs among window candidates t0, t0+step, ... < T.
-template <int DP>
-__device__ __noinline__ int2 band_count(const float* __restrict__ wpts, uint32_t t0, uint32_t T,
-                                        uint32_t step, Pt<DP> q, float t_in, float t_out,
-                                        double dc2) {
+// Exact count of this lane's band pairs in the union (rare path).
+template <int DP, int G>
+__device__ __noinline__ int2 band_recount(const Union<G> u, const uint32_t* c0, bool act, int R,
+                                          Pt<DP> me, const float* __restrict__ spts,
+                                          const unsigned long long* __restrict__ hkeys,
+                                          const uint2* __restrict__ hvals, uint32_t hmask,
+                                          uint32_t n, int lane, float t_in, float t_out,
+                                          double dc2) {
   int in = 0, seen = 0;
-  for (uint32_t t = t0; t < T; t += step) {
-    const Pt<DP> x = window_pt<DP>(wpts, t);
-    const float s32 = dist32<DP>(q, x);
-    if (s32 > t_in && s32 <= t_out) {
-      ++seen;
-      in += dist64<DP>(q, x) <= dc2;
-    }
-  }
+  for_union_cells<G>(u, hkeys, hvals, hmask, n, lane,
+                     [&](uint32_t st, uint32_t len, const uint32_t* cc) {
+                       const bool need = act && in_block<G>(c0, cc, R);
+                       if (!need) return;
+                       for (uint32_t t = st; t < st + len; ++t) {
+                         const Pt<DP> x = load_pt<DP>(spts, t);
+                         const float s32 = dist32<DP>(me, x);
+                         if (s32 > t_in && s32 <= t_out) {
+                           ++seen;
+                           in += dist64<DP>(me, x) <= dc2;
+                         }
+                       }
+                     });
   return make_int2(in, seen);
 }
 
@@ -50,12 +52,8 @@ k_density(const float* __restrict__ spts, const unsigned long long* __restrict__
           const CutGeom* __restrict__ cut, const unsigned long long* __restrict__ hkeys,
           const uint2* __restrict__ hvals, int32_t* __restrict__ rho_out,
           unsigned long long* __restrict__ skey, Counters* ctr) {
-  constexpr int kCap = density_cap<DP>();
-  __shared__ __align__(16) float smem[kWarps * kCap * DP];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  float* wpts = smem + wib * kCap * DP;
-
   const int k = cut->k;
   const int R = cut->R;
   const int shift = G * k;
@@ -63,94 +61,49 @@ k_density(const float* __restrict__ spts, const unsigned long long* __restrict__
   const double dc2 = cut->dc2;
   const float t_in = cut->t_in, t_out = cut->t_out;
   const uint32_t hmask = cut->hmask;
-  const int sub = lane & 7;     // lane within its query group
-  const int grp = lane >> 3;    // query group 0..3
 
   unsigned long long band = 0;
   const uint32_t nchunk = (n + 31) / 32;
   for (uint32_t ch = blockIdx.x * kWarps + wib; ch < nchunk; ch += gridDim.x * kWarps) {
-    const uint32_t p0 = ch * 32;
-    const uint32_t p = p0 + lane;
+    const uint32_t p = ch * 32 + lane;
     const bool valid = p < n;
     Pt<DP> me;
 #pragma unroll
     for (int a = 0; a < DP; ++a) me.x[a] = 0.f;
     if (valid) me = load_pt<DP>(spts, p);
     const unsigned long long mycell = valid ? (scode[p] >> shift) : ~0ull;
-    const int nvalid = (int)min(32u, n - p0);
+    uint32_t c0[G];
+    unmorton<G>(valid ? mycell : 0ull, c0);
+    const int nvalid = (int)min(32u, n - ch * 32);
     int32_t count = 0;
-    int s = 0;
-    while (s < nvalid) {
-      const unsigned long long cell = __shfl_sync(kFull, mycell, s);
-      const int e = s + __popc(__ballot_sync(kFull, mycell == cell));
-      uint32_t c0[G];
-      unmorton<G>(cell, c0);
-      BlockRuns br;
-      lookup_block<G>(c0, R, cmax, hkeys, hvals, hmask, n, lane, br);
-      for (uint32_t w0 = 0; w0 < br.total; w0 += kCap) {
-        const uint32_t T = min((uint32_t)kCap, br.total - w0);
-        __syncwarp();
-        stage_window<DP, false>(br, w0, kCap, spts, nullptr, wpts, nullptr, lane);
-        __syncwarp();
-        if (e - s == 32) {
-          // one query per lane, every lane reads the same candidate; c counts
-          // s32 <= t_in (certainly within d_cut), c2 counts s32 <= t_out
-          int32_t c = 0, c2 = 0;
+    for_groups<G>(mycell, c0, valid, valid, nvalid, R, cmax, lane, [&](bool act, const Union<G>& u) {
+      int32_t c = 0, c2 = 0;
+      for_union_cells<G>(u, hkeys, hvals, hmask, n, lane,
+                         [&](uint32_t st, uint32_t len, const uint32_t* cc) {
+                           const bool need = act && in_block<G>(c0, cc, R);
+                           if (!__any_sync(kFull, need)) return;
 #pragma unroll 4
-          for (uint32_t t = 0; t < T; ++t) {
-            const Pt<DP> x = window_pt<DP>(wpts, t);
-            if constexpr (F64) {
-              c += dist64<DP>(me, x) <= dc2;
-            } else {
-              const float s32 = dist32<DP>(me, x);
-              c += s32 <= t_in;
-              c2 += s32 <= t_out;
-            }
-          }
-          if constexpr (!F64) {
-            if (__any_sync(kFull, c2 != c)) {
-              const int2 r = band_count<DP>(wpts, 0, T, 1, me, t_in, t_out, dc2);
-              c += r.x;
-              band += r.y;
-            }
-          }
-          count += c;
-          continue;
-        }
-        for (int qb = s; qb < e; qb += 4) {
-          const int qi = qb + grp;
-          const Pt<DP> q = shfl_pt<DP>(me, qi < e ? qi : s);
-          int32_t c = 0, c2 = 0;
-#pragma unroll 2
-          for (uint32_t t = sub; t < T; t += 8) {
-            const Pt<DP> x = window_pt<DP>(wpts, t);
-            if constexpr (F64) {
-              c += dist64<DP>(q, x) <= dc2;
-            } else {
-              const float s32 = dist32<DP>(q, x);
-              c += s32 <= t_in;
-              c2 += s32 <= t_out;
-            }
-          }
-          if constexpr (!F64) {
-            if (__any_sync(kFull, c2 != c)) {
-              const int2 r = band_count<DP>(wpts, sub, T, 8, q, t_in, t_out, dc2);
-              c += r.x;
-              if (qi < e) band += r.y;
-            }
-          }
-          c += __shfl_xor_sync(kFull, c, 4);
-          c += __shfl_xor_sync(kFull, c, 2);
-          c += __shfl_xor_sync(kFull, c, 1);
-#pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            const int v = __shfl_sync(kFull, c, g * 8);
-            if (lane == qb + g && qb + g < e) count += v;
-          }
+                           for (uint32_t t = st; t < st + len; ++t) {
+                             const Pt<DP> x = load_pt<DP>(spts, t);
+                             if constexpr (F64) {
+                               c += need & (dist64<DP>(me, x) <= dc2);
+                             } else {
+                               const float s32 = dist32<DP>(me, x);
+                               c += need & (s32 <= t_in);
+                               c2 += need & (s32 <= t_out);
+                             }
+                           }
+                         });
+      if constexpr (!F64) {
+        if (__any_sync(kFull, c2 != c)) {
+          const int2 r = band_recount<DP, G>(u, c0, act && c2 != c, R, me, spts, hkeys, hvals,
+                                             hmask, n, lane, t_in, t_out, dc2);
+          c += r.x;
+          band += r.y;
         }
       }
-      s = e;
-    }
+      count += c;
+    });
     if (valid) {
       const uint32_t id = sid[p];
       rho_out[id] = count;

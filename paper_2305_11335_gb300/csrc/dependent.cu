@@ -5,11 +5,11 @@
 // (Algorithm 1) on a priority search kd-tree.  Here each query runs in two
 // phases:
 //   near  the grid block around the point's cell (the cells the density
-//         used), scanned warp-cooperatively from shared memory.  If the best
-//         candidate is closer than anything outside the block can be, and no
-//         other candidate is within the float32 error band of it, the query
-//         is settled; this holds for most points, since a point's dependent
-//         point is usually within d_cut.
+//         used), streamed by the warp with one query per lane (block.cuh).
+//         If the best candidate is closer than anything outside the block
+//         can be, and no other candidate is within the float32 error band
+//         of it, the query is settled; this holds for most points, since a
+//         point's dependent point is usually within d_cut.
 //   far   the remaining queries (local density maxima, isolated points, near
 //         ties) walk the radix tree (tree.cu) depth first, nearer child
 //         first, skipping subtrees whose largest key is not above the query's
@@ -38,7 +38,6 @@ constexpr int kFarThreads = 128;
 constexpr int kStack = 128;
 constexpr int kNearWarps = 4;
 constexpr int kNearThreads = kNearWarps * 32;
-constexpr int kNearCap = 256;
 
 __device__ __forceinline__ float band_of(float s, float mul, float add) {
   return __fadd_ru(__fmul_ru(s, mul), add);
@@ -53,7 +52,7 @@ __device__ __forceinline__ bool beyond(float lbs, float bound) {
 }
 
 // Running minimum of (s, id), the second smallest s, and the sorted position
-// of the minimum.
+// of the minimum (tree phase).
 template <typename S>
 struct Best {
   S s1, s2;
@@ -74,24 +73,6 @@ struct Best {
     } else if (s < s2) {
       s2 = s;
     }
-  }
-  // union with another candidate set's summary
-  __device__ __forceinline__ void merge(S bs1, uint32_t bo1, S bs2, uint32_t bt1) {
-    if (bs1 < s1 || (bs1 == s1 && bo1 < o1)) {
-      s2 = s1 < bs2 ? s1 : bs2;
-      s1 = bs1;
-      o1 = bo1;
-      t1 = bt1;
-    } else {
-      s2 = s2 < bs1 ? s2 : bs1;
-    }
-  }
-  __device__ __forceinline__ void merge_xor(int mask) {
-    const S bs1 = __shfl_xor_sync(kFull, s1, mask);
-    const uint32_t bo1 = __shfl_xor_sync(kFull, o1, mask);
-    const S bs2 = __shfl_xor_sync(kFull, s2, mask);
-    const uint32_t bt1 = __shfl_xor_sync(kFull, t1, mask);
-    merge(bs1, bo1, bs2, bt1);
   }
 };
 
@@ -137,35 +118,6 @@ struct Min2 {
     o1 = v < s1 ? id : o1;
     s1 = fminf(s1, v);
   }
-  __device__ __forceinline__ void merge(float b1, uint32_t bo, float b2) {
-    s2 = fminf(fmaxf(s1, b1), fminf(s2, b2));
-    o1 = b1 < s1 ? bo : o1;
-    s1 = fminf(s1, b1);
-  }
-  __device__ __forceinline__ void merge_xor(int mask) {
-    const float b1 = __shfl_xor_sync(kFull, s1, mask);
-    const uint32_t bo = __shfl_xor_sync(kFull, o1, mask);
-    const float b2 = __shfl_xor_sync(kFull, s2, mask);
-    merge(b1, bo, b2);
-  }
-};
-
-// binary64 argmin over (s64, id) (FP64 mode).
-struct Min64 {
-  double s;
-  uint32_t o;
-  __device__ __forceinline__ void init() {
-    s = INFINITY;
-    o = 0xffffffffu;
-  }
-  __device__ __forceinline__ void add(double v, uint32_t id) {
-    const bool lt = v < s || (v == s && id < o);
-    s = lt ? v : s;
-    o = lt ? id : o;
-  }
-  __device__ __forceinline__ void merge_xor(int mask) {
-    add(__shfl_xor_sync(kFull, s, mask), __shfl_xor_sync(kFull, o, mask));
-  }
 };
 
 // Coordinates of point `id` from the caller's input (the same float values the
@@ -193,13 +145,8 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
            const GridGeom* __restrict__ geom, const CutGeom* __restrict__ cut,
            const unsigned long long* __restrict__ hkeys, const uint2* __restrict__ hvals,
            int32_t* __restrict__ lambda, double* __restrict__ delta, FarQueue q, Counters* ctr) {
-  __shared__ __align__(16) float s_pts[kNearWarps * kNearCap * DP];
-  __shared__ unsigned long long s_key[kNearWarps * kNearCap];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  float* wpts = s_pts + wib * kNearCap * DP;
-  unsigned long long* wkey = s_key + wib * kNearCap;
-
   const int k = cut->k;
   const int R = cut->R;
   const int shift = G * k;
@@ -208,14 +155,11 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
   const float bmul = cut->band_mul, badd = cut->band_add;
   const float far32 = cut->far32;
   const double far64 = cut->far64;
-  const int sub = lane & 7;
-  const int grp = lane >> 3;
   const uint32_t lanemask_lt = (1u << lane) - 1u;
 
   const uint32_t nchunk = (n + 31) / 32;
   for (uint32_t ch = blockIdx.x * kNearWarps + wib; ch < nchunk; ch += gridDim.x * kNearWarps) {
-    const uint32_t p0 = ch * 32;
-    const uint32_t p = p0 + lane;
+    const uint32_t p = ch * 32 + lane;
     const bool valid = p < n;
     Pt<DP> me;
 #pragma unroll
@@ -226,85 +170,33 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
       K = skey[p];
     }
     const unsigned long long mycell = valid ? (scode[p] >> shift) : ~0ull;
+    uint32_t c0[G];
+    unmorton<G>(valid ? mycell : 0ull, c0);
     const bool skip = valid && (int32_t)(K >> 32) < rho_skip;
-    const int nvalid = (int)min(32u, n - p0);
+    const int nvalid = (int)min(32u, n - ch * 32);
     Min2 acc;
     acc.init();
-    Min64 acc64;
+    Exact acc64;
     acc64.init();
-    int s = 0;
-    while (s < nvalid) {
-      const unsigned long long cell = __shfl_sync(kFull, mycell, s);
-      const int e = s + __popc(__ballot_sync(kFull, mycell == cell));
-      uint32_t c0[G];
-      unmorton<G>(cell, c0);
-      BlockRuns br;
-      lookup_block<G>(c0, R, cmax, hkeys, hvals, hmask, n, lane, br);
-      for (uint32_t w0 = 0; w0 < br.total; w0 += kNearCap) {
-        const uint32_t T = min((uint32_t)kNearCap, br.total - w0);
-        __syncwarp();
-        stage_window<DP, true>(br, w0, kNearCap, spts, skey, wpts, wkey, lane);
-        __syncwarp();
-        if (e - s == 32) {
-          // one query per lane, every lane reads the same candidate
+    for_groups<G>(mycell, c0, valid, valid && !skip, nvalid, R, cmax, lane,
+                  [&](bool act, const Union<G>& u) {
+      for_union_cells<G>(u, hkeys, hvals, hmask, n, lane,
+                         [&](uint32_t st, uint32_t len, const uint32_t* cc) {
+                           const bool need = act && in_block<G>(c0, cc, R);
+                           if (!__any_sync(kFull, need)) return;
 #pragma unroll 4
-          for (uint32_t t = 0; t < T; ++t) {
-            const unsigned long long kt = wkey[t];
-            const Pt<DP> x = window_pt<DP>(wpts, t);
-            if constexpr (F64) {
-              if (kt > K) acc64.add(dist64<DP>(me, x), key_id(kt));
-            } else {
-              const float d32 = dist32<DP>(me, x);
-              acc.add(kt > K ? d32 : INFINITY, key_id(kt));
-            }
-          }
-          continue;
-        }
-        for (int qb = s; qb < e; qb += 4) {
-          const int qi = qb + grp;
-          const int src = qi < e ? qi : s;
-          const Pt<DP> qp = shfl_pt<DP>(me, src);
-          const unsigned long long Kq = __shfl_sync(kFull, K, src);
-          if constexpr (F64) {
-            Min64 b;
-            b.init();
-            for (uint32_t t = sub; t < T; t += 8) {
-              const unsigned long long kt = wkey[t];
-              if (kt > Kq) b.add(dist64<DP>(qp, window_pt<DP>(wpts, t)), key_id(kt));
-            }
-            b.merge_xor(4);
-            b.merge_xor(2);
-            b.merge_xor(1);
-#pragma unroll
-            for (int g = 0; g < 4; ++g) {
-              const double vs = __shfl_sync(kFull, b.s, g * 8);
-              const uint32_t vo = __shfl_sync(kFull, b.o, g * 8);
-              if (lane == qb + g && qb + g < e) acc64.add(vs, vo);
-            }
-          } else {
-            Min2 b;
-            b.init();
-#pragma unroll 2
-            for (uint32_t t = sub; t < T; t += 8) {
-              const unsigned long long kt = wkey[t];
-              const float d32 = dist32<DP>(qp, window_pt<DP>(wpts, t));
-              b.add(kt > Kq ? d32 : INFINITY, key_id(kt));
-            }
-            b.merge_xor(4);
-            b.merge_xor(2);
-            b.merge_xor(1);
-#pragma unroll
-            for (int g = 0; g < 4; ++g) {
-              const float v1 = __shfl_sync(kFull, b.s1, g * 8);
-              const uint32_t vo = __shfl_sync(kFull, b.o1, g * 8);
-              const float v2 = __shfl_sync(kFull, b.s2, g * 8);
-              if (lane == qb + g && qb + g < e) acc.merge(v1, vo, v2);
-            }
-          }
-        }
-      }
-      s = e;
-    }
+                           for (uint32_t t = st; t < st + len; ++t) {
+                             const unsigned long long kt = __ldg(skey + t);
+                             const Pt<DP> x = load_pt<DP>(spts, t);
+                             if constexpr (F64) {
+                               if (need && kt > K) acc64.add(dist64<DP>(me, x), key_id(kt));
+                             } else {
+                               const float d32 = dist32<DP>(me, x);
+                               acc.add(need && kt > K ? d32 : INFINITY, key_id(kt));
+                             }
+                           }
+                         });
+    });
 
     bool settled = false;
     float s1 = INFINITY;
@@ -321,9 +213,8 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
         const float bnd = band_of(s1, bmul, badd);
         settled = bnd < far32 && acc.s2 > bnd;
         if (settled) {
-          const uint32_t w = acc.o1;
-          lambda[id] = (int32_t)w;
-          delta[id] = sqrt(dist64<DP>(me, input_pt<DP>(pts, dtype, d, w)));
+          lambda[id] = (int32_t)acc.o1;
+          delta[id] = sqrt(dist64<DP>(me, input_pt<DP>(pts, dtype, d, acc.o1)));
         }
       }
     } else if (valid) {
