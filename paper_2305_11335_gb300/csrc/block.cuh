@@ -100,6 +100,136 @@ __device__ __forceinline__ void for_union_cells(const Union<G>& u,
   }
 }
 
+// Per-warp shared-memory run table of a union: the non-empty cells in
+// order, each with its offset in the concatenated candidate list (pre), its
+// first sorted position (start) and its coordinates relative to the union
+// (7 bits per axis).  pre[nr] is the total.
+struct RunTable {
+  uint32_t pre[kMaxUnion + 1];
+  uint32_t start[kMaxUnion];
+  uint32_t cell[kMaxUnion];
+};
+
+// Look the union's cells up (one per lane) and fill the run table; returns
+// the number of non-empty runs (warp-uniform).
+template <int G>
+__device__ __forceinline__ int union_runs(const Union<G>& u,
+                                          const unsigned long long* __restrict__ hkeys,
+                                          const uint2* __restrict__ hvals, uint32_t hmask,
+                                          uint32_t n, int lane, RunTable& rt) {
+  const uint32_t lanemask_lt = (1u << lane) - 1u;
+  int nr = 0;
+  uint32_t total = 0;
+  for (int base = 0; base < u.ncell; base += 32) {
+    const int o = base + lane;
+    uint32_t st = 0, len = 0, rel = 0;
+    if (o < u.ncell) {
+      int rem = o;
+      uint32_t c[G];
+#pragma unroll
+      for (int a = 0; a < G; ++a) {
+        const int q = div_small(rem, u.inv[a]);
+        const uint32_t r = (uint32_t)(rem - q * u.w[a]);
+        c[a] = (uint32_t)u.lo[a] + r;
+        rel |= r << (7 * a);
+        rem = q;
+      }
+      const uint2 run = clip_run(hash_find(hkeys, hvals, hmask, morton<G>(c)), n);
+      st = run.x;
+      len = run.y - run.x;
+    }
+    const unsigned m = __ballot_sync(kFull, len > 0);
+    uint32_t incl = len;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t t = __shfl_up_sync(kFull, incl, d);
+      if (lane >= d) incl += t;
+    }
+    if (len > 0) {
+      const int slot = nr + __popc(m & lanemask_lt);
+      rt.pre[slot] = total + incl - len;
+      rt.start[slot] = st;
+      rt.cell[slot] = rel;
+    }
+    nr += __popc(m);
+    total += __shfl_sync(kFull, incl, 31);
+  }
+  if (lane == 0) rt.pre[nr] = total;
+  __syncwarp();
+  return nr;
+}
+
+// Copy candidates [w0, w1) of the concatenated list into the window: lane l
+// copies candidates w0 + l, w0 + l + 32, ...; all loads of a window are
+// independent, so the warp keeps many of them in flight.
+template <int DP, bool KEYS>
+__device__ __forceinline__ void stage_runs(const RunTable& rt, int nr, uint32_t w0, uint32_t w1,
+                                           const float* __restrict__ spts,
+                                           const unsigned long long* __restrict__ skey,
+                                           float* __restrict__ wpts,
+                                           unsigned long long* __restrict__ wkey, int lane) {
+  // first run holding candidate w0 + lane
+  int lo = 0, hi = nr - 1;
+  const uint32_t e0 = w0 + lane;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (rt.pre[mid] <= e0) lo = mid;
+    else hi = mid - 1;
+  }
+  int r = lo;
+  for (uint32_t e = e0; e < w1; e += 32) {
+    while (r + 1 < nr && rt.pre[r + 1] <= e) ++r;
+    const uint32_t src = rt.start[r] + (e - rt.pre[r]);
+    const uint32_t dst = e - w0;
+    if constexpr (DP == 2) {
+      reinterpret_cast<float2*>(wpts)[dst] = __ldg(reinterpret_cast<const float2*>(spts) + src);
+    } else if constexpr (DP == 4) {
+      reinterpret_cast<float4*>(wpts)[dst] = __ldg(reinterpret_cast<const float4*>(spts) + src);
+    } else {
+      const float4* s4 = reinterpret_cast<const float4*>(spts) + 2 * (size_t)src;
+      float4* d4 = reinterpret_cast<float4*>(wpts) + 2 * (size_t)dst;
+      d4[0] = __ldg(s4);
+      d4[1] = __ldg(s4 + 1);
+    }
+    if constexpr (KEYS) wkey[dst] = __ldg(skey + src);
+  }
+}
+
+// Visit the runs of window [w0, w1): visit(i0, i1, cell[G]) with window
+// indices [i0, i1), warp-uniform.
+template <int G, typename Visit>
+__device__ __forceinline__ void for_window_runs(const RunTable& rt, int nr, const Union<G>& u,
+                                                uint32_t w0, uint32_t w1, Visit visit) {
+  for (int r = 0; r < nr; ++r) {
+    const uint32_t a = rt.pre[r], b = rt.pre[r + 1];
+    if (b <= w0) continue;
+    if (a >= w1) break;
+    uint32_t c[G];
+    const uint32_t rel = rt.cell[r];
+#pragma unroll
+    for (int x = 0; x < G; ++x) c[x] = (uint32_t)u.lo[x] + ((rel >> (7 * x)) & 127u);
+    visit((a > w0 ? a : w0) - w0, (b < w1 ? b : w1) - w0, c);
+  }
+}
+
+template <int DP>
+__device__ __forceinline__ Pt<DP> window_pt(const float* __restrict__ wpts, uint32_t i) {
+  Pt<DP> p;
+  if constexpr (DP == 2) {
+    float2 v = reinterpret_cast<const float2*>(wpts)[i];
+    p.x[0] = v.x; p.x[1] = v.y;
+  } else if constexpr (DP == 4) {
+    float4 v = reinterpret_cast<const float4*>(wpts)[i];
+    p.x[0] = v.x; p.x[1] = v.y; p.x[2] = v.z; p.x[3] = v.w;
+  } else {
+    const float4* q = reinterpret_cast<const float4*>(wpts) + 2 * (size_t)i;
+    float4 a = q[0], b = q[1];
+    p.x[0] = a.x; p.x[1] = a.y; p.x[2] = a.z; p.x[3] = a.w;
+    p.x[4] = b.x; p.x[5] = b.y; p.x[6] = b.z; p.x[7] = b.w;
+  }
+  return p;
+}
+
 // Does the block of radius R around cell c0 contain cell c?
 template <int G>
 __device__ __forceinline__ bool in_block(const uint32_t* c0, const uint32_t* c, int R) {

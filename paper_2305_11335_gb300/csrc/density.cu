@@ -1,8 +1,9 @@
 // density.cu -- rho_i = |{j : D(x_i, x_j) <= d_cut}| (Definition 1).
 //
 // One query per lane, 32 consecutive Morton-sorted queries per warp; the warp
-// streams the union of its queries' grid blocks with broadcast loads and each
-// lane counts the points of its own (2R+1)^g block (block.cuh).
+// stages the union of its queries' grid blocks in shared memory (block.cuh)
+// and each lane counts the points of its own (2R+1)^g block, reading every
+// candidate as a broadcast.
 //   FP32_CERT: s32 <= t_in counts, s32 > t_out does not.  Pairs in between
 //              (about 1e-6 of d_cut^2 wide) are counted with the canonical
 //              binary64 distance in a separate pass, taken only by a warp that
@@ -20,28 +21,28 @@ namespace {
 constexpr int kWarps = 4;
 constexpr int kThreads = kWarps * 32;
 
-// Exact count of this lane's band pairs in the union (rare path).
+template <int DP>
+constexpr int density_cap() { return DP == 8 ? 256 : 512; }
+
+// Exact count of this lane's band pairs among the window's candidates (rare
+// path, taken only by a warp that met a band pair in this window).
 template <int DP, int G>
-__device__ __noinline__ int2 band_recount(const Union<G> u, const uint32_t* c0, bool act, int R,
-                                          Pt<DP> me, const float* __restrict__ spts,
-                                          const unsigned long long* __restrict__ hkeys,
-                                          const uint2* __restrict__ hvals, uint32_t hmask,
-                                          uint32_t n, int lane, float t_in, float t_out,
-                                          double dc2) {
+__device__ __noinline__ int2 band_recount(const RunTable& rt, int nr, const Union<G> u,
+                                          uint32_t w0, uint32_t w1, const float* wpts,
+                                          const uint32_t* c0, bool act, int R, Pt<DP> me,
+                                          float t_in, float t_out, double dc2) {
   int in = 0, seen = 0;
-  for_union_cells<G>(u, hkeys, hvals, hmask, n, lane,
-                     [&](uint32_t st, uint32_t len, const uint32_t* cc) {
-                       const bool need = act && in_block<G>(c0, cc, R);
-                       if (!need) return;
-                       for (uint32_t t = st; t < st + len; ++t) {
-                         const Pt<DP> x = load_pt<DP>(spts, t);
-                         const float s32 = dist32<DP>(me, x);
-                         if (s32 > t_in && s32 <= t_out) {
-                           ++seen;
-                           in += dist64<DP>(me, x) <= dc2;
-                         }
-                       }
-                     });
+  for_window_runs<G>(rt, nr, u, w0, w1, [&](uint32_t i0, uint32_t i1, const uint32_t* cc) {
+    if (!(act && in_block<G>(c0, cc, R))) return;
+    for (uint32_t i = i0; i < i1; ++i) {
+      const Pt<DP> x = window_pt<DP>(wpts, i);
+      const float s32 = dist32<DP>(me, x);
+      if (s32 > t_in && s32 <= t_out) {
+        ++seen;
+        in += dist64<DP>(me, x) <= dc2;
+      }
+    }
+  });
   return make_int2(in, seen);
 }
 
@@ -52,8 +53,13 @@ k_density(const float* __restrict__ spts, const unsigned long long* __restrict__
           const CutGeom* __restrict__ cut, const unsigned long long* __restrict__ hkeys,
           const uint2* __restrict__ hvals, int32_t* __restrict__ rho_out,
           unsigned long long* __restrict__ skey, Counters* ctr) {
+  constexpr int kCap = density_cap<DP>();
+  __shared__ __align__(16) float s_pts[kWarps * kCap * DP];
+  __shared__ RunTable s_rt[kWarps];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
+  float* wpts = s_pts + wib * kCap * DP;
+  RunTable& rt = s_rt[wib];
   const int k = cut->k;
   const int R = cut->R;
   const int shift = G * k;
@@ -77,32 +83,40 @@ k_density(const float* __restrict__ spts, const unsigned long long* __restrict__
     const int nvalid = (int)min(32u, n - ch * 32);
     int32_t count = 0;
     for_groups<G>(mycell, c0, valid, valid, nvalid, R, cmax, lane, [&](bool act, const Union<G>& u) {
-      int32_t c = 0, c2 = 0;
-      for_union_cells<G>(u, hkeys, hvals, hmask, n, lane,
-                         [&](uint32_t st, uint32_t len, const uint32_t* cc) {
-                           const bool need = act && in_block<G>(c0, cc, R);
-                           if (!__any_sync(kFull, need)) return;
+      const int nr = union_runs<G>(u, hkeys, hvals, hmask, n, lane, rt);
+      const uint32_t total = rt.pre[nr];
+      for (uint32_t w0 = 0; w0 < total; w0 += kCap) {
+        const uint32_t w1 = min(total, w0 + (uint32_t)kCap);
+        __syncwarp();
+        stage_runs<DP, false>(rt, nr, w0, w1, spts, nullptr, wpts, nullptr, lane);
+        __syncwarp();
+        int32_t c = 0, c2 = 0;
+        for_window_runs<G>(rt, nr, u, w0, w1, [&](uint32_t i0, uint32_t i1, const uint32_t* cc) {
+          const bool need = act && in_block<G>(c0, cc, R);
+          if (!__any_sync(kFull, need)) return;
 #pragma unroll 4
-                           for (uint32_t t = st; t < st + len; ++t) {
-                             const Pt<DP> x = load_pt<DP>(spts, t);
-                             if constexpr (F64) {
-                               c += need & (dist64<DP>(me, x) <= dc2);
-                             } else {
-                               const float s32 = dist32<DP>(me, x);
-                               c += need & (s32 <= t_in);
-                               c2 += need & (s32 <= t_out);
-                             }
-                           }
-                         });
-      if constexpr (!F64) {
-        if (__any_sync(kFull, c2 != c)) {
-          const int2 r = band_recount<DP, G>(u, c0, act && c2 != c, R, me, spts, hkeys, hvals,
-                                             hmask, n, lane, t_in, t_out, dc2);
-          c += r.x;
-          band += r.y;
+          for (uint32_t i = i0; i < i1; ++i) {
+            const Pt<DP> x = window_pt<DP>(wpts, i);
+            if constexpr (F64) {
+              c += need & (dist64<DP>(me, x) <= dc2);
+            } else {
+              const float s32 = dist32<DP>(me, x);
+              c += need & (s32 <= t_in);
+              c2 += need & (s32 <= t_out);
+            }
+          }
+        });
+        if constexpr (!F64) {
+          if (__any_sync(kFull, c2 != c)) {
+            const int2 r = band_recount<DP, G>(rt, nr, u, w0, w1, wpts, c0, act && c2 != c, R, me,
+                                               t_in, t_out, dc2);
+            c += r.x;
+            band += r.y;
+          }
         }
+        count += c;
       }
-      count += c;
+      __syncwarp();
     });
     if (valid) {
       const uint32_t id = sid[p];

@@ -38,6 +38,7 @@ constexpr int kFarThreads = 128;
 constexpr int kStack = 128;
 constexpr int kNearWarps = 4;
 constexpr int kNearThreads = kNearWarps * 32;
+constexpr int kNearCap = 256;
 
 __device__ __forceinline__ float band_of(float s, float mul, float add) {
   return __fadd_ru(__fmul_ru(s, mul), add);
@@ -145,8 +146,14 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
            const GridGeom* __restrict__ geom, const CutGeom* __restrict__ cut,
            const unsigned long long* __restrict__ hkeys, const uint2* __restrict__ hvals,
            int32_t* __restrict__ lambda, double* __restrict__ delta, FarQueue q, Counters* ctr) {
+  __shared__ __align__(16) float s_pts[kNearWarps * kNearCap * DP];
+  __shared__ unsigned long long s_key[kNearWarps * kNearCap];
+  __shared__ RunTable s_rt[kNearWarps];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
+  float* wpts = s_pts + wib * kNearCap * DP;
+  unsigned long long* wkey = s_key + wib * kNearCap;
+  RunTable& rt = s_rt[wib];
   const int k = cut->k;
   const int R = cut->R;
   const int shift = G * k;
@@ -180,22 +187,30 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
     acc64.init();
     for_groups<G>(mycell, c0, valid, valid && !skip, nvalid, R, cmax, lane,
                   [&](bool act, const Union<G>& u) {
-      for_union_cells<G>(u, hkeys, hvals, hmask, n, lane,
-                         [&](uint32_t st, uint32_t len, const uint32_t* cc) {
-                           const bool need = act && in_block<G>(c0, cc, R);
-                           if (!__any_sync(kFull, need)) return;
+      const int nr = union_runs<G>(u, hkeys, hvals, hmask, n, lane, rt);
+      const uint32_t total = rt.pre[nr];
+      for (uint32_t w0 = 0; w0 < total; w0 += kNearCap) {
+        const uint32_t w1 = min(total, w0 + (uint32_t)kNearCap);
+        __syncwarp();
+        stage_runs<DP, true>(rt, nr, w0, w1, spts, skey, wpts, wkey, lane);
+        __syncwarp();
+        for_window_runs<G>(rt, nr, u, w0, w1, [&](uint32_t i0, uint32_t i1, const uint32_t* cc) {
+          const bool need = act && in_block<G>(c0, cc, R);
+          if (!__any_sync(kFull, need)) return;
 #pragma unroll 4
-                           for (uint32_t t = st; t < st + len; ++t) {
-                             const unsigned long long kt = __ldg(skey + t);
-                             const Pt<DP> x = load_pt<DP>(spts, t);
-                             if constexpr (F64) {
-                               if (need && kt > K) acc64.add(dist64<DP>(me, x), key_id(kt));
-                             } else {
-                               const float d32 = dist32<DP>(me, x);
-                               acc.add(need && kt > K ? d32 : INFINITY, key_id(kt));
-                             }
-                           }
-                         });
+          for (uint32_t i = i0; i < i1; ++i) {
+            const unsigned long long kt = wkey[i];
+            const Pt<DP> x = window_pt<DP>(wpts, i);
+            if constexpr (F64) {
+              if (need && kt > K) acc64.add(dist64<DP>(me, x), key_id(kt));
+            } else {
+              const float d32 = dist32<DP>(me, x);
+              acc.add(need && kt > K ? d32 : INFINITY, key_id(kt));
+            }
+          }
+        });
+      }
+      __syncwarp();
     });
 
     bool settled = false;
