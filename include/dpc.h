@@ -153,6 +153,33 @@ int dpc_run_host(const void* pts_host, int dtype, const dpc_batch* b, const dpc_
                  int32_t* rho_host, int32_t* lambda_host, double* delta_host,
                  int32_t* label_host, uint32_t flags, void* stream);
 
+/* dpc_density for ONE point set without allocating device memory.  The paper
+ * has no counterpart: this entry point exists for callers that cannot let a
+ * library call cudaMalloc -- work enqueued while a stream is being captured
+ * into a CUDA graph (allocation is not allowed during capture), hosts that
+ * budget device memory through their own allocator, and paths that cannot
+ * afford the device synchronization an allocation may cause.
+ *   pts     device, [n][d] row-major, int32 or float32 (dtype), same range
+ *           rules as every other entry point
+ *   n       0 .. DPC_STATIC_MAX_POINTS; larger n fails with DPC_ERR_OVERFLOW
+ *           before any work is queued
+ *   d       1..8; d_cut finite and >= 0
+ *   rho     device, int32 [n]: rho[i] = density of point i (Definition 1),
+ *           identical to dpc_density's result
+ *   flags   precision (DPC_PREC_*) and DPC_FLAG_SYNC_CHECK as for dpc_density
+ * All scratch memory is one fixed array of about 7 MB compiled into the
+ * library, so every GPU that loads the library holds it until the process
+ * exits.  The first call on a device looks up that array's device address;
+ * make that first call before any stream capture.  The call never allocates
+ * (no cudaMalloc, cudaFree or allocating library routine) and issues only
+ * kernels and memsets on `stream`.  All calls share the one array: calls
+ * that overlap on the GPU (on different streams, or from several threads
+ * without ordering) race and corrupt each other's results; order them on
+ * one stream. */
+#define DPC_STATIC_MAX_POINTS 65536
+int dpc_density_static(const void* pts, int dtype, int64_t n, int32_t d, double d_cut,
+                       int32_t* rho, uint32_t flags, void* stream);
+
 /* Counters from the last call on `stream` (synchronizes the stream). */
 typedef struct {
   int64_t band_pairs;     /* density pairs re-evaluated in binary64          */

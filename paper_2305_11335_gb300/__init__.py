@@ -41,8 +41,10 @@ DPC_F32 = 1
 PREC = {"fp64": 0, "fp32": 1}
 DPC_FLAG_SYNC_CHECK = 1 << 8
 
-EXPORTS = ["dpc_density", "dpc_dependent", "dpc_cluster", "dpc_run", "dpc_run_host", "dpc_get_stats",
-           "dpc_get_phase_times", "dpc_last_status", "dpc_strerror", "dpc_version", "dpc_release"]
+EXPORTS = ["dpc_density", "dpc_dependent", "dpc_cluster", "dpc_run", "dpc_run_host", "dpc_density_static",
+           "dpc_get_stats", "dpc_get_phase_times", "dpc_last_status", "dpc_strerror", "dpc_version",
+           "dpc_release"]
+DPC_STATIC_MAX_POINTS = 65536
 
 
 class DpcError(RuntimeError):
@@ -96,6 +98,8 @@ def load(path: str = LIB_PATH):
     lib.dpc_cluster.argtypes = [bp, i32, pp, vp, vp, vp, vp, u32, vp]
     lib.dpc_run.argtypes = [vp, ctypes.c_int, bp, pp, vp, vp, vp, vp, u32, vp]
     lib.dpc_run_host.argtypes = [vp, ctypes.c_int, bp, pp, vp, vp, vp, vp, u32, vp]
+    lib.dpc_density_static.argtypes = [vp, ctypes.c_int, ctypes.c_int64, i32, ctypes.c_double, vp, u32, vp]
+    lib.dpc_density_static.restype = ctypes.c_int
     lib.dpc_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
     lib.dpc_get_phase_times.argtypes = [vp, ctypes.POINTER(_PhaseTimes)]
     lib.dpc_get_phase_times.restype = ctypes.c_int
@@ -291,6 +295,20 @@ def dpc_get_stats(stream=None) -> dict:
     s = _Stats()
     _check(lib.dpc_get_stats(_stream(stream), ctypes.byref(s)), "dpc_get_stats")
     return {f: getattr(s, f) for f, _ in _Stats._fields_}
+
+
+def dpc_density_static(pts: torch.Tensor, d_cut: float, precision: str = "fp32", sync: bool = False,
+                       stream=None, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Densities of one point set ``pts`` [n, d] with the library's fixed
+    scratch area (no device allocation inside the call; see dpc.h)."""
+    lib = load()
+    if pts.dim() == 1:
+        pts = pts.reshape(-1, 1)
+    n, d = pts.shape
+    rho = out if out is not None else torch.empty(n, dtype=torch.int32, device=pts.device)
+    _check(lib.dpc_density_static(_dev(pts, "pts"), _dtype_code(pts), n, d, float(d_cut), _dev(rho, "rho"),
+                                  _flags(precision, sync), _stream(stream)), "dpc_density_static")
+    return rho
 
 
 def dpc_get_phase_times(stream=None) -> dict:
