@@ -94,15 +94,18 @@ k_density(const float* __restrict__ spts, const unsigned long long* __restrict__
         for_window_runs<G>(rt, nr, u, w0, w1, [&](uint32_t i0, uint32_t i1, const uint32_t* cc) {
           const bool need = act && in_block<G>(c0, cc, R);
           if (!__any_sync(kFull, need)) return;
+          // a lane outside this cell's block compares against -1: never counts
+          const float ti = need ? t_in : -1.f, to = need ? t_out : -1.f;
+          const double dl = need ? dc2 : -1.0;
 #pragma unroll 4
           for (uint32_t i = i0; i < i1; ++i) {
             const Pt<DP> x = window_pt<DP>(wpts, i);
             if constexpr (F64) {
-              c += need & (dist64<DP>(me, x) <= dc2);
+              c += dist64<DP>(me, x) <= dl;
             } else {
               const float s32 = dist32<DP>(me, x);
-              c += need & (s32 <= t_in);
-              c2 += need & (s32 <= t_out);
+              c += s32 <= ti;
+              c2 += s32 <= to;
             }
           }
         });
