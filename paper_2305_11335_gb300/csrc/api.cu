@@ -375,7 +375,7 @@ void dependent_step(Workspace* w, const void* pts_all, int dtype, const Inst& in
   }
   {
     Phase ph(w, DPC_PHASE_FAR);
-    launch_dep_far(dp, g, fp64, w->spts, w->skey, n, w->geom, cut, w->nodes, w->leaf_parent, queue_of(w), lambda,
+    launch_dep_far(dp, g, fp64, w->spts, w->skey, n, w->geom, cut, w->nodes, queue_of(w), lambda,
                    delta, w->ctr, n, st);
   }
 }

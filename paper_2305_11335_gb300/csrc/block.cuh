@@ -212,6 +212,33 @@ __device__ __forceinline__ void for_window_runs(const RunTable& rt, int nr, cons
   }
 }
 
+// Copy the runs of `src` for which keep(cell) (warp-uniform) holds into
+// `dst`, recomputing the offsets; returns the number kept.
+template <int G, typename Keep>
+__device__ __forceinline__ int filter_runs(const RunTable& src, int nr, const Union<G>& u,
+                                           RunTable& dst, int lane, Keep keep) {
+  int m = 0;
+  uint32_t total = 0;
+  for (int r = 0; r < nr; ++r) {
+    uint32_t c[G];
+    const uint32_t rel = src.cell[r];
+#pragma unroll
+    for (int x = 0; x < G; ++x) c[x] = (uint32_t)u.lo[x] + ((rel >> (7 * x)) & 127u);
+    if (keep(c)) {
+      if (lane == 0) {
+        dst.pre[m] = total;
+        dst.start[m] = src.start[r];
+        dst.cell[m] = rel;
+      }
+      total += src.pre[r + 1] - src.pre[r];
+      ++m;
+    }
+  }
+  if (lane == 0) dst.pre[m] = total;
+  __syncwarp();
+  return m;
+}
+
 template <int DP>
 __device__ __forceinline__ Pt<DP> window_pt(const float* __restrict__ wpts, uint32_t i) {
   Pt<DP> p;

@@ -38,7 +38,6 @@ constexpr int kFarThreads = 128;
 constexpr int kStack = 128;
 constexpr int kNearWarps = 4;
 constexpr int kNearThreads = kNearWarps * 32;
-constexpr int kNearCap = 256;
 
 __device__ __forceinline__ float band_of(float s, float mul, float add) {
   return __fadd_ru(__fmul_ru(s, mul), add);
@@ -146,15 +145,24 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
            const GridGeom* __restrict__ geom, const CutGeom* __restrict__ cut,
            const unsigned long long* __restrict__ hkeys, const uint2* __restrict__ hvals,
            int32_t* __restrict__ lambda, double* __restrict__ delta, FarQueue q, Counters* ctr) {
+  constexpr int kNearCap = DP == 8 ? 128 : 256;
   __shared__ __align__(16) float s_pts[kNearWarps * kNearCap * DP];
   __shared__ unsigned long long s_key[kNearWarps * kNearCap];
   __shared__ RunTable s_rt[kNearWarps];
+  __shared__ RunTable s_rt2[kNearWarps];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   float* wpts = s_pts + wib * kNearCap * DP;
   unsigned long long* wkey = s_key + wib * kNearCap;
   RunTable& rt = s_rt[wib];
+  RunTable& rt2 = s_rt2[wib];
+  const float f2lo = geom->f2 * (1.f - 1e-5f);
+  const double inv_f = geom->inv_f;
+  double org[G];
+#pragma unroll
+  for (int a = 0; a < G; ++a) org[a] = geom->org[a];
   const int k = cut->k;
+  const float cell_fine = (float)(1u << cut->k);
   const int R = cut->R;
   const int shift = G * k;
   const int cmax = (1 << (geom->B - k)) - 1;
@@ -185,34 +193,68 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
     acc.init();
     Exact acc64;
     acc64.init();
+    // the query's position in fine units, for cell lower bounds
+    float uq[G];
+#pragma unroll
+    for (int a = 0; a < G; ++a) uq[a] = valid ? (float)(((double)me.x[a] - org[a]) * inv_f) : 0.f;
     for_groups<G>(mycell, c0, valid, valid && !skip, nvalid, R, cmax, lane,
                   [&](bool act, const Union<G>& u) {
       const int nr = union_runs<G>(u, hkeys, hvals, hmask, n, lane, rt);
-      const uint32_t total = rt.pre[nr];
-      for (uint32_t w0 = 0; w0 < total; w0 += kNearCap) {
-        const uint32_t w1 = min(total, w0 + (uint32_t)kNearCap);
-        __syncwarp();
-        stage_runs<DP, true>(rt, nr, w0, w1, spts, skey, wpts, wkey, lane);
-        __syncwarp();
-        for_window_runs<G>(rt, nr, u, w0, w1, [&](uint32_t i0, uint32_t i1, const uint32_t* cc) {
-          const bool need = act && in_block<G>(c0, cc, R);
-          if (!__any_sync(kFull, need)) return;
-          // a lane outside this cell's block takes no candidate: no key exceeds ~0
-          const unsigned long long Kl = need ? K : ~0ull;
+      // scan every run of a table, staged window by window
+      auto scan = [&](const RunTable& tab, int nt) {
+        const uint32_t total = tab.pre[nt];
+        for (uint32_t w0 = 0; w0 < total; w0 += kNearCap) {
+          const uint32_t w1 = min(total, w0 + (uint32_t)kNearCap);
+          __syncwarp();
+          stage_runs<DP, true>(tab, nt, w0, w1, spts, skey, wpts, wkey, lane);
+          __syncwarp();
+          for_window_runs<G>(tab, nt, u, w0, w1, [&](uint32_t i0, uint32_t i1, const uint32_t* cc) {
+            const bool need = act && in_block<G>(c0, cc, R);
+            if (!__any_sync(kFull, need)) return;
+            // a lane outside this cell's block takes no candidate: no key exceeds ~0
+            const unsigned long long Kl = need ? K : ~0ull;
 #pragma unroll 4
-          for (uint32_t i = i0; i < i1; ++i) {
-            const unsigned long long kt = wkey[i];
-            const Pt<DP> x = window_pt<DP>(wpts, i);
-            if constexpr (F64) {
-              if (kt > Kl) acc64.add(dist64<DP>(me, x), key_id(kt));
-            } else {
-              const float d32 = dist32<DP>(me, x);
-              acc.add(kt > Kl ? d32 : INFINITY, key_id(kt));
+            for (uint32_t i = i0; i < i1; ++i) {
+              const unsigned long long kt = wkey[i];
+              const Pt<DP> x = window_pt<DP>(wpts, i);
+              if constexpr (F64) {
+                if (kt > Kl) acc64.add(dist64<DP>(me, x), key_id(kt));
+              } else {
+                const float d32 = dist32<DP>(me, x);
+                acc.add(kt > Kl ? d32 : INFINITY, key_id(kt));
+              }
             }
+          });
+        }
+        __syncwarp();
+      };
+      auto own = [&](const uint32_t* cc) {
+        bool same = act;
+#pragma unroll
+        for (int a = 0; a < G; ++a) same &= cc[a] == c0[a];
+        return __any_sync(kFull, same) != 0;
+      };
+      // pass 1: the cells holding the group's own queries
+      scan(rt2, filter_runs<G>(rt, nr, u, rt2, lane, own));
+      // pass 2: the other cells of the blocks that can still hold a point
+      // closer than some lane's best (a conservative lower bound decides)
+      scan(rt2, filter_runs<G>(rt, nr, u, rt2, lane, [&](const uint32_t* cc) {
+        if (own(cc)) return false;
+        bool need = act && in_block<G>(c0, cc, R);
+        if (need) {
+          float lb2 = 0.f;
+#pragma unroll
+          for (int a = 0; a < G; ++a) {
+            const float lo = (float)cc[a] * cell_fine;
+            const float l = lb_axis(lo, lo + cell_fine - 1.f, uq[a]);
+            lb2 = fmaf(l, l, lb2);
           }
-        });
-      }
-      __syncwarp();
+          const float lbs = lb2 * f2lo;
+          if constexpr (F64) need = (double)lbs <= acc64.s;
+          else need = !beyond(lbs, band_of(acc.s1, bmul, badd));
+        }
+        return __any_sync(kFull, need) != 0;
+      }));
     });
 
     bool settled = false;
@@ -332,125 +374,11 @@ __device__ __forceinline__ bool tree_walk(const Node* __restrict__ nodes, uint32
   return true;
 }
 
-// Depth-first search of the subtree rooted at `start` (an internal node or an
-// encoded leaf); same contract as tree_walk.
-template <int DP, int G, typename Prune, typename Visit>
-__device__ __forceinline__ bool subtree_walk(const Node* __restrict__ nodes, uint32_t n, int nbits,
-                                             const unsigned long long* __restrict__ skey,
-                                             unsigned long long K, const float* u, float f2lo,
-                                             uint32_t start, Prune prune, Visit visit) {
-  if (start & kLeafBit) {
-    const uint32_t t = start & ~kLeafBit;
-    if (t >= n) return false;
-    const unsigned long long kt = skey[t];
-    if (kt > K) visit(t, kt);
-    return true;
-  }
-  if (start + 1 >= n) return false;
-  const Node nd = nodes[start];
-  if (nd.maxkey <= K) return true;
-  const float lbs = node_lb2<G>(nd, nbits, u) * f2lo;
-  if (prune(lbs)) return true;
-  uint32_t stk[kStack];
-  float stl[kStack];
-  int sp = 0;
-  stk[sp] = start;
-  stl[sp] = lbs;
-  ++sp;
-  while (sp > 0) {
-    --sp;
-    const uint32_t ni = stk[sp];
-    if (prune(stl[sp])) continue;
-    if (ni + 1 >= n) return false;
-    const uint32_t ch[2] = {nodes[ni].left, nodes[ni].right};
-    uint32_t keep[2];
-    float keepl[2];
-    int nk = 0;
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const uint32_t c = ch[s];
-      if (c & kLeafBit) {
-        const uint32_t t = c & ~kLeafBit;
-        if (t >= n) return false;
-        const unsigned long long kt = skey[t];
-        if (kt > K) visit(t, kt);
-      } else {
-        const Node cn = nodes[c];
-        if (cn.maxkey <= K) continue;
-        const float l = node_lb2<G>(cn, nbits, u) * f2lo;
-        if (prune(l)) continue;
-        keep[nk] = c;
-        keepl[nk] = l;
-        ++nk;
-      }
-    }
-    if (sp + nk > kStack) return false;
-    if (nk == 2 && keepl[0] < keepl[1]) {  // push the farther child first
-      stk[sp] = keep[1]; stl[sp] = keepl[1]; ++sp;
-      stk[sp] = keep[0]; stl[sp] = keepl[0]; ++sp;
-    } else {
-      for (int s = 0; s < nk; ++s) { stk[sp] = keep[s]; stl[sp] = keepl[s]; ++sp; }
-    }
-  }
-  return true;
-}
-
-// Squared lower bound (fine units) from the query, which lies inside the box
-// of node nd, to any point outside that box.  Valid only when the node holds
-// every point of its box, i.e. its prefix lies within the code (plen < nbits).
-template <int G>
-__device__ __forceinline__ float outside_lb2(const Node& nd, int nbits, const float* u) {
-  const int nb = nbits - (int)nd.plen;
-  uint32_t c[G];
-  unmorton<G>(nd.code, c);
-  float gap = INFINITY;
-#pragma unroll
-  for (int a = 0; a < G; ++a) {
-    const int fa = nb > a ? (nb - a + G - 1) / G : 0;
-    const float lo = (float)((c[a] >> fa) << fa);
-    const float hi1 = lo + (float)(1u << fa);  // one past the last fine index
-    // outside points sit below lo + 1e-9 or above hi1 - 1e-9 fine units; the
-    // query's float position is within 1/8 of its true one
-    gap = fminf(gap, fminf(u[a] - lo, hi1 - u[a]) - 0.25f);
-  }
-  gap = fmaxf(gap, 0.f);
-  return gap * gap;
-}
-
-// Search for candidates starting at leaf p and moving up: at each ancestor,
-// search the sibling subtree, then stop once every point outside the
-// ancestor's box is provably beyond the bound.  Each subtree search prunes by
-// maximum key and box distance like a top-down search, so every candidate
-// the bound admits is visited.
-template <int DP, int G, typename Prune, typename Visit>
-__device__ __forceinline__ bool leaf_up_walk(const Node* __restrict__ nodes,
-                                             const uint32_t* __restrict__ leaf_parent, uint32_t p,
-                                             uint32_t n, int nbits,
-                                             const unsigned long long* __restrict__ skey,
-                                             unsigned long long K, const float* u, float f2lo,
-                                             Prune prune, Visit visit) {
-  if (n < 2) return true;  // the query is the only point
-  uint32_t child = p | kLeafBit;
-  uint32_t node = leaf_parent[p];
-  for (int depth = 0; depth < 200; ++depth) {
-    if (node + 1 >= n) return false;
-    const Node nd = nodes[node];
-    const uint32_t sib = (nd.left == child) ? nd.right : nd.left;
-    if (!subtree_walk<DP, G>(nodes, n, nbits, skey, K, u, f2lo, sib, prune, visit)) return false;
-    if (node == 0) return true;  // the root: everything searched
-    if ((int)nd.plen < nbits && prune(outside_lb2<G>(nd, nbits, u) * f2lo)) return true;
-    child = node;
-    node = nd.parent;
-  }
-  return false;
-}
-
 template <int DP, int G, bool F64>
 __global__ void __launch_bounds__(kFarThreads)
 k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__ skey, uint32_t n,
           const GridGeom* __restrict__ geom, const CutGeom* __restrict__ cut,
-          const Node* __restrict__ nodes, const uint32_t* __restrict__ leaf_parent, FarQueue q,
-          int32_t* __restrict__ lambda,
+          const Node* __restrict__ nodes, FarQueue q, int32_t* __restrict__ lambda,
           double* __restrict__ delta, Counters* ctr) {
   const uint32_t qn = ctr->queue_n;
   const int nbits = geom->nbits;
@@ -475,8 +403,8 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
       Best<double> best;
       best.init();
       const double s_init = q.s1d[e];
-      overflow |= !leaf_up_walk<DP, G>(
-          nodes, leaf_parent, p, n, nbits, skey, K, u, f2lo,
+      overflow |= !tree_walk<DP, G>(
+          nodes, n, nbits, skey, K, u, f2lo,
           [&](float lbs) { return (double)lbs > fmin(best.s1, s_init); },
           [&](uint32_t t, unsigned long long kt) {
             best.add(dist64<DP>(xq, load_pt<DP>(spts, t)), key_id(kt), t);
@@ -492,8 +420,8 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
       Best<float> best;
       best.init();
       const float s_init = q.s1[e];
-      overflow |= !leaf_up_walk<DP, G>(
-          nodes, leaf_parent, p, n, nbits, skey, K, u, f2lo,
+      overflow |= !tree_walk<DP, G>(
+          nodes, n, nbits, skey, K, u, f2lo,
           [&](float lbs) { return beyond(lbs, band_of(fminf(best.s1, s_init), bmul, badd)); },
           [&](uint32_t t, unsigned long long kt) {
             best.add(dist32<DP>(xq, load_pt<DP>(spts, t)), key_id(kt), t);
@@ -508,9 +436,8 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
       ex.init();
       if (best.s2 <= b) {
         ++rescans;
-        overflow |= !leaf_up_walk<DP, G>(
-            nodes, leaf_parent, p, n, nbits, skey, K, u, f2lo,
-            [&](float lbs) { return beyond(lbs, b); },
+        overflow |= !tree_walk<DP, G>(
+            nodes, n, nbits, skey, K, u, f2lo, [&](float lbs) { return beyond(lbs, b); },
             [&](uint32_t t, unsigned long long kt) {
               const Pt<DP> x = load_pt<DP>(spts, t);
               if (dist32<DP>(xq, x) <= b) ex.add(dist64<DP>(xq, x), key_id(kt));
@@ -555,18 +482,17 @@ void near_dg(bool fp64, const float* spts, const unsigned long long* scode,
 
 template <int DP, int G>
 void far_dg(bool fp64, const float* spts, const unsigned long long* skey, uint32_t n,
-            const GridGeom* geom, const CutGeom* cut, const Node* nodes,
-            const uint32_t* leaf_parent, FarQueue q, int32_t* lambda, double* delta, Counters* ctr,
-            uint32_t qcap, cudaStream_t st) {
+            const GridGeom* geom, const CutGeom* cut, const Node* nodes, FarQueue q,
+            int32_t* lambda, double* delta, Counters* ctr, uint32_t qcap, cudaStream_t st) {
   // the queue length is known only on the device: launch enough threads for
   // a full SM load and let them stride over it
   const unsigned grid = grid_for(qcap, kFarThreads, 152u * 8u);
   if (fp64)
-    k_dep_far<DP, G, true><<<grid, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes,
-                                                         leaf_parent, q, lambda, delta, ctr);
+    k_dep_far<DP, G, true><<<grid, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, q, lambda,
+                                                         delta, ctr);
   else
-    k_dep_far<DP, G, false><<<grid, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes,
-                                                          leaf_parent, q, lambda, delta, ctr);
+    k_dep_far<DP, G, false><<<grid, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, q, lambda,
+                                                          delta, ctr);
 }
 
 }  // namespace
@@ -587,13 +513,13 @@ void launch_dep_near(int dp, int g, bool fp64, const float* spts, const unsigned
 
 void launch_dep_far(int dp, int g, bool fp64, const float* spts, const unsigned long long* skey,
                     uint32_t n, const GridGeom* geom, const CutGeom* cut, const Node* nodes,
-                    const uint32_t* leaf_parent, FarQueue q, int32_t* lambda, double* delta,
-                    Counters* ctr, uint32_t qcap, cudaStream_t st) {
+                    FarQueue q, int32_t* lambda, double* delta, Counters* ctr, uint32_t qcap,
+                    cudaStream_t st) {
   if (n == 0) return;
-  if (g == 1) far_dg<2, 1>(fp64, spts, skey, n, geom, cut, nodes, leaf_parent, q, lambda, delta, ctr, qcap, st);
-  else if (g == 2) far_dg<2, 2>(fp64, spts, skey, n, geom, cut, nodes, leaf_parent, q, lambda, delta, ctr, qcap, st);
-  else if (dp == 4) far_dg<4, 3>(fp64, spts, skey, n, geom, cut, nodes, leaf_parent, q, lambda, delta, ctr, qcap, st);
-  else far_dg<8, 3>(fp64, spts, skey, n, geom, cut, nodes, leaf_parent, q, lambda, delta, ctr, qcap, st);
+  if (g == 1) far_dg<2, 1>(fp64, spts, skey, n, geom, cut, nodes, q, lambda, delta, ctr, qcap, st);
+  else if (g == 2) far_dg<2, 2>(fp64, spts, skey, n, geom, cut, nodes, q, lambda, delta, ctr, qcap, st);
+  else if (dp == 4) far_dg<4, 3>(fp64, spts, skey, n, geom, cut, nodes, q, lambda, delta, ctr, qcap, st);
+  else far_dg<8, 3>(fp64, spts, skey, n, geom, cut, nodes, q, lambda, delta, ctr, qcap, st);
   k_far_count<<<1, 1, 0, st>>>(ctr);
   count_launches(2);
 }

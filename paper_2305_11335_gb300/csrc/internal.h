@@ -70,9 +70,9 @@ void launch_dep_near(int dp, int g, bool fp64, const float* spts, const unsigned
                      const uint2* hvals, int32_t* lambda, double* delta, FarQueue q,
                      Counters* ctr, cudaStream_t st);
 void launch_dep_far(int dp, int g, bool fp64, const float* spts, const unsigned long long* skey,
-                    uint32_t n, const GridGeom* geom, const CutGeom* cut, const Node* nodes,
-                    const uint32_t* leaf_parent, FarQueue q, int32_t* lambda, double* delta,
-                    Counters* ctr, uint32_t qcap, cudaStream_t st);
+                    uint32_t n, const GridGeom* geom, const CutGeom* cut, const Node* nodes, FarQueue q,
+                    int32_t* lambda, double* delta, Counters* ctr, uint32_t qcap,
+                    cudaStream_t st);
 
 // ---- labels (labels.cu) -------------------------------------------------------------
 int label_rounds(uint32_t n);
