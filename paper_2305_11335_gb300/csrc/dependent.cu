@@ -234,8 +234,19 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
         for (int a = 0; a < G; ++a) same &= cc[a] == c0[a];
         return __any_sync(kFull, same) != 0;
       };
-      // pass 1: the cells holding the group's own queries
-      scan(rt2, filter_runs<G>(rt, nr, u, rt2, lane, own));
+      // a small union: one pass over everything
+      if (rt.pre[nr] <= 4u * kNearCap) {
+        scan(rt, nr);
+        return;
+      }
+      // pass 1: the cells holding the group's own queries -- unless they hold
+      // too few points to bound the search, then one pass over everything
+      const int n1 = filter_runs<G>(rt, nr, u, rt2, lane, own);
+      if (rt2.pre[n1] < 96u) {
+        scan(rt, nr);
+        return;
+      }
+      scan(rt2, n1);
       // pass 2: the other cells of the blocks that can still hold a point
       // closer than some lane's best (a conservative lower bound decides)
       scan(rt2, filter_runs<G>(rt, nr, u, rt2, lane, [&](const uint32_t* cc) {
