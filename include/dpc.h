@@ -190,6 +190,8 @@ typedef struct {
   int32_t grid_level;     /* level of the density grid of the last cutoff    */
   int32_t bits_per_axis;  /* Morton bits per gridded axis of the last binning */
   int64_t kernel_launches;/* kernels the last call enqueued                  */
+  int64_t far_nodes;      /* radix-tree nodes expanded by the far queries    */
+  int64_t far_nodes_max;  /* most nodes expanded by a single far query       */
 } dpc_stats;
 int dpc_get_stats(void* stream, dpc_stats* out);
 

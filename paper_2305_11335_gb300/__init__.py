@@ -67,7 +67,8 @@ class _Stats(ctypes.Structure):
     _fields_ = [("band_pairs", ctypes.c_int64), ("far_queries", ctypes.c_int64),
                 ("exact_rescans", ctypes.c_int64), ("occupied_cells", ctypes.c_int64),
                 ("grid_level", ctypes.c_int32), ("bits_per_axis", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("far_nodes", ctypes.c_int64),
+                ("far_nodes_max", ctypes.c_int64)]
 
 
 PHASES = ["bin", "tree", "cells", "density", "maxkey", "near", "far", "labels"]

@@ -66,6 +66,9 @@ struct Workspace {
   uint32_t* qpos = nullptr;
   float* qs1 = nullptr;
   double* qs1d = nullptr;
+  uint32_t* qpos2 = nullptr;
+  float* qs1_2 = nullptr;
+  double* qs1d2 = nullptr;
 
   // host-buffer entry point staging
   void* io = nullptr;
@@ -147,6 +150,7 @@ struct Workspace {
     const size_t o_nodes = take(sizeof(Node) * N);
     const size_t o_lp = take(4 * N), o_visit = take(4 * N);
     const size_t o_qpos = take(4 * N), o_qs1 = take(4 * N), o_qs1d = take(8 * N);
+    const size_t o_qpos2 = take(4 * N), o_qs1_2 = take(4 * N), o_qs1d2 = take(8 * N);
     void* p = nullptr;
     if (cudaMalloc(&p, off) != cudaSuccess) {
       cudaGetLastError();
@@ -179,6 +183,9 @@ struct Workspace {
     qpos = (uint32_t*)(b + o_qpos);
     qs1 = (float*)(b + o_qs1);
     qs1d = (double*)(b + o_qs1d);
+    qpos2 = (uint32_t*)(b + o_qpos2);
+    qs1_2 = (float*)(b + o_qs1_2);
+    qs1d2 = (double*)(b + o_qs1d2);
     cap_n = N;
     cap_ncut = want_c;
     cudaMemsetAsync(status, 0, sizeof(int), stream);
@@ -355,6 +362,9 @@ FarQueue queue_of(Workspace* w) {
   q.pos = w->qpos;
   q.s1 = w->qs1;
   q.s1d = w->qs1d;
+  q.pos2 = w->qpos2;
+  q.s1_2 = w->qs1_2;
+  q.s1d2 = w->qs1d2;
   return q;
 }
 
@@ -648,6 +658,8 @@ int dpc_get_stats(void* stream, dpc_stats* out) {
   out->exact_rescans = (int64_t)c.exact_rescans;
   out->bits_per_axis = g.B;
   out->kernel_launches = w->launches_last;
+  out->far_nodes = (int64_t)c.far_nodes;
+  out->far_nodes_max = (int64_t)c.far_nodes_max;
   if (w->last_ncut_used > 0) {
     CutGeom cg;
     cudaMemcpy(&cg, w->cuts + (w->last_ncut_used - 1), sizeof(cg), cudaMemcpyDeviceToHost);

@@ -36,6 +36,8 @@ namespace {
 
 constexpr int kFarThreads = 128;
 constexpr int kStack = 128;
+constexpr int kWarpStack = 1024;  // shared stack entries per warp (far phase, round 2)
+constexpr uint32_t kFarBudget = 128;  // node expansions per query in round 1
 constexpr int kNearWarps = 4;
 constexpr int kNearThreads = kNearWarps * 32;
 
@@ -74,6 +76,24 @@ struct Best {
       s2 = s;
     }
   }
+  // union over the warp's lanes (every lane ends with the same summary)
+  __device__ __forceinline__ void merge_warp() {
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+      const S b1 = __shfl_xor_sync(kFull, s1, m);
+      const uint32_t bo = __shfl_xor_sync(kFull, o1, m);
+      const S b2 = __shfl_xor_sync(kFull, s2, m);
+      const uint32_t bt = __shfl_xor_sync(kFull, t1, m);
+      if (b1 < s1 || (b1 == s1 && bo < o1)) {
+        s2 = s1 < b2 ? s1 : b2;
+        s1 = b1;
+        o1 = bo;
+        t1 = bt;
+      } else {
+        s2 = s2 < b1 ? s2 : b1;
+      }
+    }
+  }
 };
 
 // Exact binary64 argmin over (s64, id).
@@ -89,6 +109,10 @@ struct Exact {
       s = v;
       o = id;
     }
+  }
+  __device__ __forceinline__ void merge_warp() {
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) add(__shfl_xor_sync(kFull, s, m), __shfl_xor_sync(kFull, o, m));
   }
 };
 
@@ -326,32 +350,32 @@ __device__ __forceinline__ float node_lb2(const Node& nd, int nbits, const float
   return lb2;
 }
 
-// Visit every candidate (leaf with key > K) not excluded by `prune`; calls
-// visit(t, kt) for each.  prune(lbs) says whether a region whose squared
-// distance is at least lbs can be skipped.  Returns false if the tree is
-// malformed or the stack would overflow (neither happens for a tree built by
-// tree.cu: its depth is at most 64 + 32).
+enum { kWalkDone = 0, kWalkBudget = 1, kWalkBad = -1 };
+
+// One thread's depth-first search below internal node `start`, nearer child
+// first: every leaf with key > K not excluded by `prune` is passed to
+// visit(t, kt).  Stops with kWalkBudget after `budget` node expansions, and
+// with kWalkBad on a malformed tree or stack overflow (neither happens for a
+// tree built by tree.cu: its depth is at most 64 + 32).
 template <int DP, int G, typename Prune, typename Visit>
-__device__ __forceinline__ bool tree_walk(const Node* __restrict__ nodes, uint32_t n, int nbits,
-                                          const unsigned long long* __restrict__ skey,
-                                          unsigned long long K, const float* u, float f2lo,
-                                          Prune prune, Visit visit) {
+__device__ __noinline__ int tree_walk_from(const Node* __restrict__ nodes, uint32_t n, int nbits,
+                                           const unsigned long long* __restrict__ skey,
+                                           unsigned long long K, const float* u, float f2lo,
+                                           uint32_t start, uint32_t budget, uint32_t& expanded,
+                                           Prune prune, Visit visit) {
   uint32_t stk[kStack];
   float stl[kStack];
   int sp = 0;
-  if (n == 1) {
-    const unsigned long long kt = skey[0];
-    if (kt > K) visit(0u, kt);
-    return true;
-  }
-  stk[sp] = 0u;
+  stk[sp] = start;
   stl[sp] = 0.f;
   ++sp;
   while (sp > 0) {
     --sp;
     const uint32_t ni = stk[sp];
     if (prune(stl[sp])) continue;
-    if (ni + 1 >= n) return false;
+    if (ni + 1 >= n) return kWalkBad;
+    if (expanded >= budget) return kWalkBudget;
+    ++expanded;
     const uint32_t ch[2] = {nodes[ni].left, nodes[ni].right};
     uint32_t keep[2];
     float keepl[2];
@@ -361,7 +385,7 @@ __device__ __forceinline__ bool tree_walk(const Node* __restrict__ nodes, uint32
       const uint32_t c = ch[s];
       if (c & kLeafBit) {
         const uint32_t t = c & ~kLeafBit;
-        if (t >= n) return false;
+        if (t >= n) return kWalkBad;
         const unsigned long long kt = skey[t];
         if (kt > K) visit(t, kt);
       } else {
@@ -374,7 +398,7 @@ __device__ __forceinline__ bool tree_walk(const Node* __restrict__ nodes, uint32
         ++nk;
       }
     }
-    if (sp + nk > kStack) return false;
+    if (sp + nk > kStack) return kWalkBad;
     if (nk == 2 && keepl[0] < keepl[1]) {  // push the farther child first
       stk[sp] = keep[1]; stl[sp] = keepl[1]; ++sp;
       stk[sp] = keep[0]; stl[sp] = keepl[0]; ++sp;
@@ -382,9 +406,32 @@ __device__ __forceinline__ bool tree_walk(const Node* __restrict__ nodes, uint32
       for (int s = 0; s < nk; ++s) { stk[sp] = keep[s]; stl[sp] = keepl[s]; ++sp; }
     }
   }
-  return true;
+  return kWalkDone;
 }
 
+// Per-query context shared by the two far kernels.
+template <int DP, int G>
+struct FarQuery {
+  uint32_t p, id;
+  unsigned long long K;
+  Pt<DP> xq;
+  float u[G];
+  __device__ __forceinline__ void load(uint32_t pos, const float* __restrict__ spts,
+                                       const unsigned long long* __restrict__ skey,
+                                       const double* org, double inv_f) {
+    p = pos;
+    K = skey[p];
+    id = key_id(K);
+    xq = load_pt<DP>(spts, p);
+#pragma unroll
+    for (int a = 0; a < G; ++a) u[a] = (float)(((double)xq.x[a] - org[a]) * inv_f);
+  }
+};
+
+// Far queries, first round: one thread per query, a depth-first search with
+// an expansion budget.  Most queries finish within it (they expand a few dozen
+// nodes); the others are passed to the second round with the best distance
+// found so far, which bounds their search there.
 template <int DP, int G, bool F64>
 __global__ void __launch_bounds__(kFarThreads)
 k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__ skey, uint32_t n,
@@ -399,73 +446,308 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
   double org[G];
 #pragma unroll
   for (int a = 0; a < G; ++a) org[a] = geom->org[a];
-  unsigned long long rescans = 0;
-  bool overflow = false;
-  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < qn; e += gridDim.x * blockDim.x) {
-    const uint32_t p = q.pos[e];
-    const unsigned long long K = skey[p];
-    const uint32_t id = key_id(K);
-    const Pt<DP> xq = load_pt<DP>(spts, p);
-    float u[G];
+  const uint32_t lanemask_lt = (1u << (threadIdx.x & 31)) - 1u;
+  unsigned long long rescans = 0, expanded_sum = 0;
+  uint32_t expanded_max = 0;
+  bool bad = false;
+  const uint32_t qn_pad = (qn + 31) & ~31u;  // whole warps, for the ballot below
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < qn_pad; e += gridDim.x * blockDim.x) {
+    bool pass_on = false;
+    double s_next = INFINITY;
+    uint32_t expanded = 0;
+    FarQuery<DP, G> fq;
+    if (e < qn) {
+      fq.load(q.pos[e], spts, skey, org, inv_f);
+      if (n < 2) {
+        lambda[fq.id] = -1;
+        delta[fq.id] = INFINITY;
+      } else if constexpr (F64) {
+        Best<double> best;
+        best.init();
+        const double s_init = q.s1d[e];
+        const int r = tree_walk_from<DP, G>(
+            nodes, n, nbits, skey, fq.K, fq.u, f2lo, 0u, kFarBudget, expanded,
+            [&](float lbs) { return (double)lbs > fmin(best.s1, s_init); },
+            [&](uint32_t t, unsigned long long kt) {
+              best.add(dist64<DP>(fq.xq, load_pt<DP>(spts, t)), key_id(kt), t);
+            });
+        bad |= r == kWalkBad;
+        if (r == kWalkBudget) {
+          pass_on = true;
+          s_next = fmin(best.s1, s_init);
+        } else if (best.t1 == 0xffffffffu) {
+          lambda[fq.id] = -1;
+          delta[fq.id] = INFINITY;
+        } else {
+          lambda[fq.id] = (int32_t)best.o1;
+          delta[fq.id] = sqrt(best.s1);
+        }
+      } else {
+        Best<float> best;
+        best.init();
+        const float s_init = q.s1[e];
+        const int r = tree_walk_from<DP, G>(
+            nodes, n, nbits, skey, fq.K, fq.u, f2lo, 0u, kFarBudget, expanded,
+            [&](float lbs) { return beyond(lbs, band_of(fminf(best.s1, s_init), bmul, badd)); },
+            [&](uint32_t t, unsigned long long kt) {
+              best.add(dist32<DP>(fq.xq, load_pt<DP>(spts, t)), key_id(kt), t);
+            });
+        bad |= r == kWalkBad;
+        if (r == kWalkBudget) {
+          pass_on = true;
+          s_next = fminf(best.s1, s_init);
+        } else if (best.t1 == 0xffffffffu) {
+          lambda[fq.id] = -1;
+          delta[fq.id] = INFINITY;
+        } else {
+          const float b = band_of(best.s1, bmul, badd);
+          Exact ex;
+          ex.init();
+          if (best.s2 <= b) {  // near tie: re-rank the band in binary64
+            ++rescans;
+            uint32_t more = 0;
+            bad |= tree_walk_from<DP, G>(
+                       nodes, n, nbits, skey, fq.K, fq.u, f2lo, 0u, 0xffffffffu, more,
+                       [&](float lbs) { return beyond(lbs, b); },
+                       [&](uint32_t t, unsigned long long kt) {
+                         const Pt<DP> x = load_pt<DP>(spts, t);
+                         if (dist32<DP>(fq.xq, x) <= b) ex.add(dist64<DP>(fq.xq, x), key_id(kt));
+                       }) != kWalkDone;
+            expanded += more;
+          } else {
+            ex.add(dist64<DP>(fq.xq, load_pt<DP>(spts, best.t1)), best.o1);
+          }
+          lambda[fq.id] = (int32_t)ex.o;
+          delta[fq.id] = sqrt(ex.s);
+        }
+      }
+    }
+    expanded_sum += expanded;
+    expanded_max = max(expanded_max, expanded);
+    const unsigned pm = __ballot_sync(kFull, pass_on);
+    uint32_t base = 0;
+    if ((threadIdx.x & 31) == 0 && pm) base = atomicAdd(&ctr->queue2_n, (unsigned)__popc(pm));
+    base = __shfl_sync(kFull, base, 0);
+    if (pass_on) {
+      const uint32_t slot = base + __popc(pm & lanemask_lt);
+      q.pos2[slot] = fq.p;
+      if constexpr (F64) q.s1d2[slot] = s_next;
+      else q.s1_2[slot] = (float)s_next;
+    }
+  }
+  if (bad) set_status(geom->status, kStatusStack);
+  for (int o = 16; o > 0; o >>= 1) {
+    rescans += __shfl_xor_sync(kFull, rescans, o);
+    expanded_sum += __shfl_xor_sync(kFull, expanded_sum, o);
+    expanded_max = max(expanded_max, __shfl_xor_sync(kFull, expanded_max, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (rescans) atomicAdd(&ctr->exact_rescans, rescans);
+    if (expanded_sum) atomicAdd(&ctr->far_nodes, expanded_sum);
+    if (expanded_max) atomicMax(&ctr->far_nodes_max, expanded_max);
+  }
+}
+
+// Far queries, second round: the queries that exceeded the first round's
+// budget, one warp per query.  The search restarts at the root with the
+// first round's best as its bound, so the warp can expand 32 nodes per step
+// (one per lane) without wandering: every round pops up to 32 entries from
+// the warp's shared stack, each lane expands its node, and the survivors are
+// pushed with a warp prefix sum.  Children that do not fit on the stack are
+// searched by their lane alone.
+template <int DP, int G, bool F64>
+__global__ void __launch_bounds__(kFarThreads)
+k_dep_far_wide(const float* __restrict__ spts, const unsigned long long* __restrict__ skey,
+               uint32_t n, const GridGeom* __restrict__ geom, const CutGeom* __restrict__ cut,
+               const Node* __restrict__ nodes, FarQueue q, int32_t* __restrict__ lambda,
+               double* __restrict__ delta, Counters* ctr) {
+  constexpr int kWarpsPerBlock = kFarThreads / 32;
+  __shared__ uint32_t s_stk[kWarpsPerBlock][kWarpStack];
+  __shared__ float s_lb[kWarpsPerBlock][kWarpStack];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  uint32_t* stk = s_stk[wib];
+  float* stl = s_lb[wib];
+  const uint32_t qn = ctr->queue2_n;
+  const int nbits = geom->nbits;
+  const float bmul = cut->band_mul, badd = cut->band_add;
+  const float f2lo = geom->f2 * (1.f - 1e-5f);
+  const double inv_f = geom->inv_f;
+  double org[G];
 #pragma unroll
-    for (int a = 0; a < G; ++a) u[a] = (float)(((double)xq.x[a] - org[a]) * inv_f);
+  for (int a = 0; a < G; ++a) org[a] = geom->org[a];
+  unsigned long long rescans = 0, expanded_sum = 0;
+  uint32_t expanded_max = 0;
+  bool bad = false;
+  const uint32_t nwarps = gridDim.x * kWarpsPerBlock;
+  for (uint32_t e = blockIdx.x * kWarpsPerBlock + wib; e < qn; e += nwarps) {
+    FarQuery<DP, G> fq;
+    fq.load(q.pos2[e], spts, skey, org, inv_f);
+    uint32_t expanded = 0;
+
+    auto search = [&](auto refresh, auto prune, auto visit) {
+      if (lane == 0) {
+        stk[0] = 0u;
+        stl[0] = 0.f;
+      }
+      int sp = 1;
+      __syncwarp();
+      while (sp > 0) {
+        refresh();
+        const int take = sp < 32 ? sp : 32;
+        const int base = sp - take;
+        uint32_t keep[2];
+        float keepl[2];
+        int nk = 0;
+        if (lane < take) {
+          const uint32_t ni = stk[base + lane];
+          const float lbn = stl[base + lane];
+          if (!prune(lbn)) {
+            if (ni + 1 >= n) {
+              bad = true;
+            } else {
+              ++expanded;
+              const uint32_t ch[2] = {nodes[ni].left, nodes[ni].right};
+#pragma unroll
+              for (int s = 0; s < 2; ++s) {
+                const uint32_t c = ch[s];
+                if (c & kLeafBit) {
+                  const uint32_t t = c & ~kLeafBit;
+                  if (t >= n) {
+                    bad = true;
+                    continue;
+                  }
+                  const unsigned long long kt = skey[t];
+                  if (kt > fq.K) visit(t, kt);
+                } else {
+                  const Node cn = nodes[c];
+                  if (cn.maxkey <= fq.K) continue;
+                  const float l = node_lb2<G>(cn, nbits, fq.u) * f2lo;
+                  if (prune(l)) continue;
+                  keep[nk] = c;
+                  keepl[nk] = l;
+                  ++nk;
+                }
+              }
+              if (nk == 2 && keepl[0] < keepl[1]) {  // farther first: nearer is popped sooner
+                const uint32_t tc = keep[0]; keep[0] = keep[1]; keep[1] = tc;
+                const float tl = keepl[0]; keepl[0] = keepl[1]; keepl[1] = tl;
+              }
+            }
+          }
+        }
+        uint32_t incl = (uint32_t)nk;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t t = __shfl_up_sync(kFull, incl, d);
+          if (lane >= d) incl += t;
+        }
+        const int total = (int)__shfl_sync(kFull, incl, 31);
+        const int pos = base + (int)incl - nk;
+        __syncwarp();
+        for (int s = 0; s < nk; ++s) {
+          if (pos + s < kWarpStack) {
+            stk[pos + s] = keep[s];
+            stl[pos + s] = keepl[s];
+          } else {  // no room: this lane searches the subtree alone
+            bad |= tree_walk_from<DP, G>(nodes, n, nbits, skey, fq.K, fq.u, f2lo, keep[s],
+                                         0xffffffffu, expanded, prune, visit) != kWalkDone;
+          }
+        }
+        sp = min(base + total, kWarpStack);
+        __syncwarp();
+      }
+    };
 
     if constexpr (F64) {
       Best<double> best;
       best.init();
-      const double s_init = q.s1d[e];
-      overflow |= !tree_walk<DP, G>(
-          nodes, n, nbits, skey, K, u, f2lo,
-          [&](float lbs) { return (double)lbs > fmin(best.s1, s_init); },
+      const double s_init = q.s1d2[e];
+      double wbest = s_init;  // the warp's best, refreshed every round
+      search(
+          [&] {
+            double m = best.s1;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(kFull, m, o));
+            wbest = fmin(m, s_init);
+          },
+          [&](float lbs) { return (double)lbs > fmin(best.s1, wbest); },
           [&](uint32_t t, unsigned long long kt) {
-            best.add(dist64<DP>(xq, load_pt<DP>(spts, t)), key_id(kt), t);
+            best.add(dist64<DP>(fq.xq, load_pt<DP>(spts, t)), key_id(kt), t);
           });
-      if (best.t1 == 0xffffffffu) {
-        lambda[id] = -1;
-        delta[id] = INFINITY;
-      } else {
-        lambda[id] = (int32_t)best.o1;
-        delta[id] = sqrt(best.s1);
+      best.merge_warp();
+      if (lane == 0) {
+        if (best.t1 == 0xffffffffu) {
+          lambda[fq.id] = -1;
+          delta[fq.id] = INFINITY;
+        } else {
+          lambda[fq.id] = (int32_t)best.o1;
+          delta[fq.id] = sqrt(best.s1);
+        }
       }
     } else {
       Best<float> best;
       best.init();
-      const float s_init = q.s1[e];
-      overflow |= !tree_walk<DP, G>(
-          nodes, n, nbits, skey, K, u, f2lo,
-          [&](float lbs) { return beyond(lbs, band_of(fminf(best.s1, s_init), bmul, badd)); },
+      const float s_init = q.s1_2[e];
+      float wbest = s_init;  // the warp's best, refreshed every round
+      search(
+          [&] {
+            float m = best.s1;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(kFull, m, o));
+            wbest = fminf(m, s_init);
+          },
+          [&](float lbs) { return beyond(lbs, band_of(fminf(best.s1, wbest), bmul, badd)); },
           [&](uint32_t t, unsigned long long kt) {
-            best.add(dist32<DP>(xq, load_pt<DP>(spts, t)), key_id(kt), t);
+            best.add(dist32<DP>(fq.xq, load_pt<DP>(spts, t)), key_id(kt), t);
           });
+      best.merge_warp();
       if (best.t1 == 0xffffffffu) {
-        lambda[id] = -1;
-        delta[id] = INFINITY;
-        continue;
-      }
-      const float b = band_of(best.s1, bmul, badd);
-      Exact ex;
-      ex.init();
-      if (best.s2 <= b) {
-        ++rescans;
-        overflow |= !tree_walk<DP, G>(
-            nodes, n, nbits, skey, K, u, f2lo, [&](float lbs) { return beyond(lbs, b); },
-            [&](uint32_t t, unsigned long long kt) {
-              const Pt<DP> x = load_pt<DP>(spts, t);
-              if (dist32<DP>(xq, x) <= b) ex.add(dist64<DP>(xq, x), key_id(kt));
-            });
+        if (lane == 0) {
+          lambda[fq.id] = -1;
+          delta[fq.id] = INFINITY;
+        }
       } else {
-        ex.add(dist64<DP>(xq, load_pt<DP>(spts, best.t1)), best.o1);
+        const float b = band_of(best.s1, bmul, badd);
+        Exact ex;
+        ex.init();
+        if (best.s2 <= b) {  // near tie: re-rank the band in binary64
+          ++rescans;
+          search([] {}, [&](float lbs) { return beyond(lbs, b); },
+                 [&](uint32_t t, unsigned long long kt) {
+                   const Pt<DP> x = load_pt<DP>(spts, t);
+                   if (dist32<DP>(fq.xq, x) <= b) ex.add(dist64<DP>(fq.xq, x), key_id(kt));
+                 });
+          ex.merge_warp();
+        } else if (lane == 0) {
+          ex.add(dist64<DP>(fq.xq, load_pt<DP>(spts, best.t1)), best.o1);
+        }
+        if (lane == 0) {
+          lambda[fq.id] = (int32_t)ex.o;
+          delta[fq.id] = sqrt(ex.s);
+        }
       }
-      lambda[id] = (int32_t)ex.o;
-      delta[id] = sqrt(ex.s);
     }
+    expanded_sum += expanded;
+    uint32_t qexp = expanded;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) qexp += __shfl_xor_sync(kFull, qexp, o);
+    expanded_max = max(expanded_max, qexp);
   }
-  if (overflow) set_status(geom->status, kStatusStack);
-  for (int o = 16; o > 0; o >>= 1) rescans += __shfl_xor_sync(kFull, rescans, o);
-  if ((threadIdx.x & 31) == 0 && rescans) atomicAdd(&ctr->exact_rescans, rescans);
+  if (__any_sync(kFull, bad) && lane == 0) set_status(geom->status, kStatusStack);
+  for (int o = 16; o > 0; o >>= 1) expanded_sum += __shfl_xor_sync(kFull, expanded_sum, o);
+  if (lane == 0) {
+    if (rescans) atomicAdd(&ctr->exact_rescans, rescans);
+    if (expanded_sum) atomicAdd(&ctr->far_nodes, expanded_sum);
+    if (expanded_max) atomicMax(&ctr->far_nodes_max, expanded_max);
+  }
 }
 
-__global__ void k_far_count(Counters* ctr) { ctr->far_queries += ctr->queue_n; }
+__global__ void k_far_count(Counters* ctr) {
+  ctr->far_queries += ctr->queue_n;
+  ctr->far_wide_queries += ctr->queue2_n;
+}
+
 
 inline unsigned grid_for(uint64_t items, int per_block, unsigned cap) {
   uint64_t b = (items + per_block - 1) / per_block;
@@ -498,12 +780,18 @@ void far_dg(bool fp64, const float* spts, const unsigned long long* skey, uint32
   // the queue length is known only on the device: launch enough threads for
   // a full SM load and let them stride over it
   const unsigned grid = grid_for(qcap, kFarThreads, 152u * 8u);
-  if (fp64)
+  const unsigned grid2 = grid_for(qcap, kFarThreads / 32, 152u * 16u);
+  if (fp64) {
     k_dep_far<DP, G, true><<<grid, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, q, lambda,
                                                          delta, ctr);
-  else
+    k_dep_far_wide<DP, G, true><<<grid2, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, q,
+                                                                lambda, delta, ctr);
+  } else {
     k_dep_far<DP, G, false><<<grid, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, q, lambda,
                                                           delta, ctr);
+    k_dep_far_wide<DP, G, false><<<grid2, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, q,
+                                                                 lambda, delta, ctr);
+  }
 }
 
 }  // namespace
@@ -515,6 +803,7 @@ void launch_dep_near(int dp, int g, bool fp64, const float* spts, const unsigned
                      Counters* ctr, cudaStream_t st) {
   if (n == 0) return;
   cudaMemsetAsync(&ctr->queue_n, 0, sizeof(unsigned int), st);
+  cudaMemsetAsync(&ctr->queue2_n, 0, sizeof(unsigned int), st);
   if (g == 1) near_dg<2, 1>(fp64, spts, scode, skey, n, rho_skip, pts, dtype, d, geom, cut, hkeys, hvals, lambda, delta, q, ctr, st);
   else if (g == 2) near_dg<2, 2>(fp64, spts, scode, skey, n, rho_skip, pts, dtype, d, geom, cut, hkeys, hvals, lambda, delta, q, ctr, st);
   else if (dp == 4) near_dg<4, 3>(fp64, spts, scode, skey, n, rho_skip, pts, dtype, d, geom, cut, hkeys, hvals, lambda, delta, q, ctr, st);
@@ -532,7 +821,7 @@ void launch_dep_far(int dp, int g, bool fp64, const float* spts, const unsigned 
   else if (dp == 4) far_dg<4, 3>(fp64, spts, skey, n, geom, cut, nodes, q, lambda, delta, ctr, qcap, st);
   else far_dg<8, 3>(fp64, spts, skey, n, geom, cut, nodes, q, lambda, delta, ctr, qcap, st);
   k_far_count<<<1, 1, 0, st>>>(ctr);
-  count_launches(2);
+  count_launches(3);
 }
 
 }  // namespace dpc

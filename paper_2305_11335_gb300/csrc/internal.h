@@ -63,6 +63,9 @@ struct FarQueue {
   uint32_t* pos;   // sorted position of each queued query
   float* s1;       // best float32 distance found by the near phase (FP32 mode)
   double* s1d;     // best binary64 distance found by the near phase (FP64 mode)
+  uint32_t* pos2;  // the same for the queries passed to the far phase's second round
+  float* s1_2;
+  double* s1d2;
 };
 void launch_dep_near(int dp, int g, bool fp64, const float* spts, const unsigned long long* scode,
                      const unsigned long long* skey, uint32_t n, int32_t rho_skip, const void* pts,
