@@ -61,6 +61,8 @@ struct Workspace {
   uint2* hvals = nullptr;
   uint32_t hcap = 0;
   Node* nodes = nullptr;
+  float* nbox = nullptr;    // per-node bounding boxes, [lo(dp) | hi(dp)]
+  bool boxes_ready = false; // nbox matches the current binning
   uint32_t* leaf_parent = nullptr;
   uint32_t* visit = nullptr;
   uint32_t* qpos = nullptr;
@@ -148,6 +150,7 @@ struct Workspace {
     const size_t o_skey = take(8 * N);
     const size_t o_hk = take(8 * (size_t)hc), o_hv = take(8 * (size_t)hc);
     const size_t o_nodes = take(sizeof(Node) * N);
+    const size_t o_nbox = take(4 * 16 * N);
     const size_t o_lp = take(4 * N), o_visit = take(4 * N);
     const size_t o_qpos = take(4 * N), o_qs1 = take(4 * N), o_qs1d = take(8 * N);
     const size_t o_qpos2 = take(4 * N), o_qs1_2 = take(4 * N), o_qs1d2 = take(8 * N);
@@ -178,6 +181,7 @@ struct Workspace {
     hvals = (uint2*)(b + o_hv);
     hcap = hc;
     nodes = (Node*)(b + o_nodes);
+    nbox = (float*)(b + o_nbox);
     leaf_parent = (uint32_t*)(b + o_lp);
     visit = (uint32_t*)(b + o_visit);
     qpos = (uint32_t*)(b + o_qpos);
@@ -339,6 +343,7 @@ void bin_instance(Workspace* w, const void* pts, int dtype, const Inst& in,
   const size_t esz = 4;
   const void* p = (const char*)pts + in.coord_off * esz;
   Phase ph(w, DPC_PHASE_BIN);
+  w->boxes_ready = false;
   launch_geom_init(w->geom, w->status, g, st);
   launch_bbox(p, dtype, n, d, g, w->geom, st);
   launch_setup(w->geom, w->cuts, cuts.data(), (int)cuts.size(), st);
@@ -376,7 +381,9 @@ void dependent_step(Workspace* w, const void* pts_all, int dtype, const Inst& in
   const int d = in.d, g = g_of(d), dp = dp_of(d);
   {
     Phase ph(w, DPC_PHASE_MAXKEY);
-    launch_tree_maxkey(w->skey, n, w->nodes, w->leaf_parent, w->visit, st);
+    launch_tree_maxkey(w->skey, w->spts, dp, n, w->nodes, w->leaf_parent, w->visit, w->nbox,
+                       !w->boxes_ready, st);
+    w->boxes_ready = true;
   }
   {
     Phase ph(w, DPC_PHASE_NEAR);
@@ -385,8 +392,8 @@ void dependent_step(Workspace* w, const void* pts_all, int dtype, const Inst& in
   }
   {
     Phase ph(w, DPC_PHASE_FAR);
-    launch_dep_far(dp, g, fp64, w->spts, w->skey, n, w->geom, cut, w->nodes, queue_of(w), lambda,
-                   delta, w->ctr, n, st);
+    launch_dep_far(dp, fp64, w->spts, w->skey, n, w->geom, cut, w->nodes, w->nbox, queue_of(w),
+                   lambda, delta, w->ctr, n, st);
   }
 }
 

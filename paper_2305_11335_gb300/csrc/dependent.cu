@@ -334,20 +334,27 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
 // ---------------------------------------------------------------------------
 // far phase: depth-first priority search of the radix tree
 
-template <int G>
-__device__ __forceinline__ float node_lb2(const Node& nd, int nbits, const float* u) {
-  const int nb = nbits - (int)nd.plen;  // free low bits of the code
-  uint32_t c[G];
-  unmorton<G>(nd.code, c);
+// Squared lower bound between the query and the bounding box of a subtree
+// (all coordinates; box layout [lo(DP) | hi(DP)] per node, tree.cu), scaled
+// 1e-5 down so that it stays below the float32 distance of every point inside
+// despite the rounding of this evaluation and of dist32.
+template <int DP>
+__device__ __forceinline__ float box_lb2(const float* __restrict__ nbox, uint32_t node,
+                                         const Pt<DP>& x) {
+  const float4* b = reinterpret_cast<const float4*>(nbox) + (size_t)node * (DP / 2);
+  float v[2 * DP];
+#pragma unroll
+  for (int k = 0; k < DP / 2; ++k) {
+    const float4 q = __ldg(b + k);
+    v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
+  }
   float lb2 = 0.f;
 #pragma unroll
-  for (int a = 0; a < G; ++a) {
-    const int fa = nb > a ? (nb - a + G - 1) / G : 0;
-    const uint32_t lo = (c[a] >> fa) << fa;
-    const float l = lb_axis((float)lo, (float)lo + (float)((1u << fa) - 1u), u[a]);
+  for (int a = 0; a < DP; ++a) {
+    const float l = fmaxf(fmaxf(v[a] - x.x[a], x.x[a] - v[DP + a]), 0.f);
     lb2 = fmaf(l, l, lb2);
   }
-  return lb2;
+  return lb2 * (1.f - 1e-5f);
 }
 
 enum { kWalkDone = 0, kWalkBudget = 1, kWalkBad = -1 };
@@ -357,10 +364,11 @@ enum { kWalkDone = 0, kWalkBudget = 1, kWalkBad = -1 };
 // visit(t, kt).  Stops with kWalkBudget after `budget` node expansions, and
 // with kWalkBad on a malformed tree or stack overflow (neither happens for a
 // tree built by tree.cu: its depth is at most 64 + 32).
-template <int DP, int G, typename Prune, typename Visit>
-__device__ __noinline__ int tree_walk_from(const Node* __restrict__ nodes, uint32_t n, int nbits,
+template <int DP, typename Prune, typename Visit>
+__device__ __noinline__ int tree_walk_from(const Node* __restrict__ nodes,
+                                           const float* __restrict__ nbox, uint32_t n,
                                            const unsigned long long* __restrict__ skey,
-                                           unsigned long long K, const float* u, float f2lo,
+                                           unsigned long long K, const Pt<DP>& xq,
                                            uint32_t start, uint32_t budget, uint32_t& expanded,
                                            Prune prune, Visit visit) {
   uint32_t stk[kStack];
@@ -389,9 +397,8 @@ __device__ __noinline__ int tree_walk_from(const Node* __restrict__ nodes, uint3
         const unsigned long long kt = skey[t];
         if (kt > K) visit(t, kt);
       } else {
-        const Node nd = nodes[c];
-        if (nd.maxkey <= K) continue;
-        const float lbs = node_lb2<G>(nd, nbits, u) * f2lo;
+        if (nodes[c].maxkey <= K) continue;
+        const float lbs = box_lb2<DP>(nbox, c, xq);
         if (prune(lbs)) continue;
         keep[nk] = c;
         keepl[nk] = lbs;
@@ -410,21 +417,17 @@ __device__ __noinline__ int tree_walk_from(const Node* __restrict__ nodes, uint3
 }
 
 // Per-query context shared by the two far kernels.
-template <int DP, int G>
+template <int DP>
 struct FarQuery {
   uint32_t p, id;
   unsigned long long K;
   Pt<DP> xq;
-  float u[G];
   __device__ __forceinline__ void load(uint32_t pos, const float* __restrict__ spts,
-                                       const unsigned long long* __restrict__ skey,
-                                       const double* org, double inv_f) {
+                                       const unsigned long long* __restrict__ skey) {
     p = pos;
     K = skey[p];
     id = key_id(K);
     xq = load_pt<DP>(spts, p);
-#pragma unroll
-    for (int a = 0; a < G; ++a) u[a] = (float)(((double)xq.x[a] - org[a]) * inv_f);
   }
 };
 
@@ -432,20 +435,14 @@ struct FarQuery {
 // an expansion budget.  Most queries finish within it (they expand a few dozen
 // nodes); the others are passed to the second round with the best distance
 // found so far, which bounds their search there.
-template <int DP, int G, bool F64>
+template <int DP, bool F64>
 __global__ void __launch_bounds__(kFarThreads)
 k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__ skey, uint32_t n,
           const GridGeom* __restrict__ geom, const CutGeom* __restrict__ cut,
-          const Node* __restrict__ nodes, FarQueue q, int32_t* __restrict__ lambda,
-          double* __restrict__ delta, Counters* ctr) {
+          const Node* __restrict__ nodes, const float* __restrict__ nbox, FarQueue q,
+          int32_t* __restrict__ lambda, double* __restrict__ delta, Counters* ctr) {
   const uint32_t qn = ctr->queue_n;
-  const int nbits = geom->nbits;
   const float bmul = cut->band_mul, badd = cut->band_add;
-  const float f2lo = geom->f2 * (1.f - 1e-5f);
-  const double inv_f = geom->inv_f;
-  double org[G];
-#pragma unroll
-  for (int a = 0; a < G; ++a) org[a] = geom->org[a];
   const uint32_t lanemask_lt = (1u << (threadIdx.x & 31)) - 1u;
   unsigned long long rescans = 0, expanded_sum = 0;
   uint32_t expanded_max = 0;
@@ -455,9 +452,9 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
     bool pass_on = false;
     double s_next = INFINITY;
     uint32_t expanded = 0;
-    FarQuery<DP, G> fq;
+    FarQuery<DP> fq;
     if (e < qn) {
-      fq.load(q.pos[e], spts, skey, org, inv_f);
+      fq.load(q.pos[e], spts, skey);
       if (n < 2) {
         lambda[fq.id] = -1;
         delta[fq.id] = INFINITY;
@@ -465,8 +462,8 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
         Best<double> best;
         best.init();
         const double s_init = q.s1d[e];
-        const int r = tree_walk_from<DP, G>(
-            nodes, n, nbits, skey, fq.K, fq.u, f2lo, 0u, kFarBudget, expanded,
+        const int r = tree_walk_from<DP>(
+            nodes, nbox, n, skey, fq.K, fq.xq, 0u, kFarBudget, expanded,
             [&](float lbs) { return (double)lbs > fmin(best.s1, s_init); },
             [&](uint32_t t, unsigned long long kt) {
               best.add(dist64<DP>(fq.xq, load_pt<DP>(spts, t)), key_id(kt), t);
@@ -486,8 +483,8 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
         Best<float> best;
         best.init();
         const float s_init = q.s1[e];
-        const int r = tree_walk_from<DP, G>(
-            nodes, n, nbits, skey, fq.K, fq.u, f2lo, 0u, kFarBudget, expanded,
+        const int r = tree_walk_from<DP>(
+            nodes, nbox, n, skey, fq.K, fq.xq, 0u, kFarBudget, expanded,
             [&](float lbs) { return beyond(lbs, band_of(fminf(best.s1, s_init), bmul, badd)); },
             [&](uint32_t t, unsigned long long kt) {
               best.add(dist32<DP>(fq.xq, load_pt<DP>(spts, t)), key_id(kt), t);
@@ -506,8 +503,8 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
           if (best.s2 <= b) {  // near tie: re-rank the band in binary64
             ++rescans;
             uint32_t more = 0;
-            bad |= tree_walk_from<DP, G>(
-                       nodes, n, nbits, skey, fq.K, fq.u, f2lo, 0u, 0xffffffffu, more,
+            bad |= tree_walk_from<DP>(
+                       nodes, nbox, n, skey, fq.K, fq.xq, 0u, 0xffffffffu, more,
                        [&](float lbs) { return beyond(lbs, b); },
                        [&](uint32_t t, unsigned long long kt) {
                          const Pt<DP> x = load_pt<DP>(spts, t);
@@ -555,12 +552,12 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
 // the warp's shared stack, each lane expands its node, and the survivors are
 // pushed with a warp prefix sum.  Children that do not fit on the stack are
 // searched by their lane alone.
-template <int DP, int G, bool F64>
+template <int DP, bool F64>
 __global__ void __launch_bounds__(kFarThreads)
 k_dep_far_wide(const float* __restrict__ spts, const unsigned long long* __restrict__ skey,
                uint32_t n, const GridGeom* __restrict__ geom, const CutGeom* __restrict__ cut,
-               const Node* __restrict__ nodes, FarQueue q, int32_t* __restrict__ lambda,
-               double* __restrict__ delta, Counters* ctr) {
+               const Node* __restrict__ nodes, const float* __restrict__ nbox, FarQueue q,
+               int32_t* __restrict__ lambda, double* __restrict__ delta, Counters* ctr) {
   constexpr int kWarpsPerBlock = kFarThreads / 32;
   __shared__ uint32_t s_stk[kWarpsPerBlock][kWarpStack];
   __shared__ float s_lb[kWarpsPerBlock][kWarpStack];
@@ -569,20 +566,14 @@ k_dep_far_wide(const float* __restrict__ spts, const unsigned long long* __restr
   uint32_t* stk = s_stk[wib];
   float* stl = s_lb[wib];
   const uint32_t qn = ctr->queue2_n;
-  const int nbits = geom->nbits;
   const float bmul = cut->band_mul, badd = cut->band_add;
-  const float f2lo = geom->f2 * (1.f - 1e-5f);
-  const double inv_f = geom->inv_f;
-  double org[G];
-#pragma unroll
-  for (int a = 0; a < G; ++a) org[a] = geom->org[a];
   unsigned long long rescans = 0, expanded_sum = 0;
   uint32_t expanded_max = 0;
   bool bad = false;
   const uint32_t nwarps = gridDim.x * kWarpsPerBlock;
   for (uint32_t e = blockIdx.x * kWarpsPerBlock + wib; e < qn; e += nwarps) {
-    FarQuery<DP, G> fq;
-    fq.load(q.pos2[e], spts, skey, org, inv_f);
+    FarQuery<DP> fq;
+    fq.load(q.pos2[e], spts, skey);
     uint32_t expanded = 0;
 
     auto search = [&](auto refresh, auto prune, auto visit) {
@@ -620,9 +611,8 @@ k_dep_far_wide(const float* __restrict__ spts, const unsigned long long* __restr
                   const unsigned long long kt = skey[t];
                   if (kt > fq.K) visit(t, kt);
                 } else {
-                  const Node cn = nodes[c];
-                  if (cn.maxkey <= fq.K) continue;
-                  const float l = node_lb2<G>(cn, nbits, fq.u) * f2lo;
+                  if (nodes[c].maxkey <= fq.K) continue;
+                  const float l = box_lb2<DP>(nbox, c, fq.xq);
                   if (prune(l)) continue;
                   keep[nk] = c;
                   keepl[nk] = l;
@@ -650,8 +640,8 @@ k_dep_far_wide(const float* __restrict__ spts, const unsigned long long* __restr
             stk[pos + s] = keep[s];
             stl[pos + s] = keepl[s];
           } else {  // no room: this lane searches the subtree alone
-            bad |= tree_walk_from<DP, G>(nodes, n, nbits, skey, fq.K, fq.u, f2lo, keep[s],
-                                         0xffffffffu, expanded, prune, visit) != kWalkDone;
+            bad |= tree_walk_from<DP>(nodes, nbox, n, skey, fq.K, fq.xq, keep[s], 0xffffffffu,
+                                      expanded, prune, visit) != kWalkDone;
           }
         }
         sp = min(base + total, kWarpStack);
@@ -773,24 +763,25 @@ void near_dg(bool fp64, const float* spts, const unsigned long long* scode,
                                                             delta, q, ctr);
 }
 
-template <int DP, int G>
-void far_dg(bool fp64, const float* spts, const unsigned long long* skey, uint32_t n,
-            const GridGeom* geom, const CutGeom* cut, const Node* nodes, FarQueue q,
-            int32_t* lambda, double* delta, Counters* ctr, uint32_t qcap, cudaStream_t st) {
+template <int DP>
+void far_dp(bool fp64, const float* spts, const unsigned long long* skey, uint32_t n,
+            const GridGeom* geom, const CutGeom* cut, const Node* nodes, const float* nbox,
+            FarQueue q, int32_t* lambda, double* delta, Counters* ctr, uint32_t qcap,
+            cudaStream_t st) {
   // the queue length is known only on the device: launch enough threads for
   // a full SM load and let them stride over it
   const unsigned grid = grid_for(qcap, kFarThreads, 152u * 8u);
   const unsigned grid2 = grid_for(qcap, kFarThreads / 32, 152u * 16u);
   if (fp64) {
-    k_dep_far<DP, G, true><<<grid, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, q, lambda,
-                                                         delta, ctr);
-    k_dep_far_wide<DP, G, true><<<grid2, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, q,
-                                                                lambda, delta, ctr);
+    k_dep_far<DP, true><<<grid, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, nbox, q,
+                                                      lambda, delta, ctr);
+    k_dep_far_wide<DP, true><<<grid2, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, nbox,
+                                                            q, lambda, delta, ctr);
   } else {
-    k_dep_far<DP, G, false><<<grid, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, q, lambda,
-                                                          delta, ctr);
-    k_dep_far_wide<DP, G, false><<<grid2, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, q,
-                                                                 lambda, delta, ctr);
+    k_dep_far<DP, false><<<grid, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, nbox, q,
+                                                       lambda, delta, ctr);
+    k_dep_far_wide<DP, false><<<grid2, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, nbox,
+                                                             q, lambda, delta, ctr);
   }
 }
 
@@ -811,15 +802,14 @@ void launch_dep_near(int dp, int g, bool fp64, const float* spts, const unsigned
   count_launches(1);
 }
 
-void launch_dep_far(int dp, int g, bool fp64, const float* spts, const unsigned long long* skey,
+void launch_dep_far(int dp, bool fp64, const float* spts, const unsigned long long* skey,
                     uint32_t n, const GridGeom* geom, const CutGeom* cut, const Node* nodes,
-                    FarQueue q, int32_t* lambda, double* delta, Counters* ctr, uint32_t qcap,
-                    cudaStream_t st) {
+                    const float* nbox, FarQueue q, int32_t* lambda, double* delta, Counters* ctr,
+                    uint32_t qcap, cudaStream_t st) {
   if (n == 0) return;
-  if (g == 1) far_dg<2, 1>(fp64, spts, skey, n, geom, cut, nodes, q, lambda, delta, ctr, qcap, st);
-  else if (g == 2) far_dg<2, 2>(fp64, spts, skey, n, geom, cut, nodes, q, lambda, delta, ctr, qcap, st);
-  else if (dp == 4) far_dg<4, 3>(fp64, spts, skey, n, geom, cut, nodes, q, lambda, delta, ctr, qcap, st);
-  else far_dg<8, 3>(fp64, spts, skey, n, geom, cut, nodes, q, lambda, delta, ctr, qcap, st);
+  if (dp == 2) far_dp<2>(fp64, spts, skey, n, geom, cut, nodes, nbox, q, lambda, delta, ctr, qcap, st);
+  else if (dp == 4) far_dp<4>(fp64, spts, skey, n, geom, cut, nodes, nbox, q, lambda, delta, ctr, qcap, st);
+  else far_dp<8>(fp64, spts, skey, n, geom, cut, nodes, nbox, q, lambda, delta, ctr, qcap, st);
   k_far_count<<<1, 1, 0, st>>>(ctr);
   count_launches(3);
 }

@@ -46,8 +46,12 @@ void launch_sort(unsigned long long* codes_a, unsigned long long* codes_b, uint3
 // ---- radix tree (tree.cu) ------------------------------------------------------
 void launch_tree_build(const unsigned long long* scode, uint32_t n, const GridGeom* geom,
                        Node* nodes, uint32_t* leaf_parent, cudaStream_t st);
-void launch_tree_maxkey(const unsigned long long* skey, uint32_t n, Node* nodes,
-                        const uint32_t* leaf_parent, uint32_t* visit, cudaStream_t st);
+// Largest order key of every subtree; with `boxes`, also every node's
+// bounding box over all dp coordinates into nbox ([lo(dp) | hi(dp)] floats per
+// node; the box depends only on the points, so once per binning suffices).
+void launch_tree_maxkey(const unsigned long long* skey, const float* spts, int dp, uint32_t n,
+                        Node* nodes, const uint32_t* leaf_parent, uint32_t* visit, float* nbox,
+                        bool boxes, cudaStream_t st);
 
 // ---- density (density.cu) -------------------------------------------------------
 void launch_density(int dp, int g, bool fp64, const float* spts, const unsigned long long* scode,
@@ -72,10 +76,10 @@ void launch_dep_near(int dp, int g, bool fp64, const float* spts, const unsigned
                      int dtype, int d, const GridGeom* geom, const CutGeom* cut, const unsigned long long* hkeys,
                      const uint2* hvals, int32_t* lambda, double* delta, FarQueue q,
                      Counters* ctr, cudaStream_t st);
-void launch_dep_far(int dp, int g, bool fp64, const float* spts, const unsigned long long* skey,
-                    uint32_t n, const GridGeom* geom, const CutGeom* cut, const Node* nodes, FarQueue q,
-                    int32_t* lambda, double* delta, Counters* ctr, uint32_t qcap,
-                    cudaStream_t st);
+void launch_dep_far(int dp, bool fp64, const float* spts, const unsigned long long* skey,
+                    uint32_t n, const GridGeom* geom, const CutGeom* cut, const Node* nodes,
+                    const float* nbox, FarQueue q, int32_t* lambda, double* delta, Counters* ctr,
+                    uint32_t qcap, cudaStream_t st);
 
 // ---- labels (labels.cu) -------------------------------------------------------------
 int label_rounds(uint32_t n);

@@ -75,10 +75,36 @@ __global__ void k_tree_build(const unsigned long long* __restrict__ code, uint32
 
 __global__ void k_root_parent(Node* nodes) { nodes[0].parent = 0u; }
 
-// Bottom-up maximum key: the second child to arrive at a node computes it.
-__global__ void k_tree_maxkey(const unsigned long long* __restrict__ skey, uint32_t n,
-                              Node* nodes, const uint32_t* __restrict__ leaf_parent,
-                              uint32_t* visit) {
+// Bottom-up pass: the second child to arrive at a node computes its largest
+// key and, on the first pass after a binning, its bounding box over all DP
+// coordinates (layout [lo(DP) | hi(DP)] per node; a leaf's box is its point).
+template <int DP>
+__device__ __forceinline__ void child_box(uint32_t c, const float* __restrict__ spts,
+                                          const float* nbox, float* lo, float* hi) {
+  if (c & kLeafBit) {
+    const Pt<DP> p = load_pt<DP>(spts, c & ~kLeafBit);
+#pragma unroll
+    for (int a = 0; a < DP; ++a) lo[a] = hi[a] = p.x[a];
+  } else {
+    const float4* b = reinterpret_cast<const float4*>(nbox) + (size_t)c * (DP / 2);
+    float v[2 * DP];
+#pragma unroll
+    for (int k = 0; k < DP / 2; ++k) {
+      const float4 q = __ldcg(b + k);
+      v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
+    }
+#pragma unroll
+    for (int a = 0; a < DP; ++a) {
+      lo[a] = v[a];
+      hi[a] = v[DP + a];
+    }
+  }
+}
+
+template <int DP, bool BOX>
+__global__ void k_tree_up(const unsigned long long* __restrict__ skey,
+                          const float* __restrict__ spts, uint32_t n, Node* nodes,
+                          const uint32_t* __restrict__ leaf_parent, uint32_t* visit, float* nbox) {
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     uint32_t node = leaf_parent[t];
     for (uint32_t depth = 0; depth < 2u * n + 64u; ++depth) {
@@ -91,6 +117,21 @@ __global__ void k_tree_maxkey(const unsigned long long* __restrict__ skey, uint3
       const unsigned long long kr =
           (r & kLeafBit) ? skey[r & ~kLeafBit] : __ldcg(&nodes[r].maxkey);
       __stcg(&nodes[node].maxkey, kl > kr ? kl : kr);
+      if constexpr (BOX) {
+        float lo[DP], hi[DP], lo2[DP], hi2[DP];
+        child_box<DP>(l, spts, nbox, lo, hi);
+        child_box<DP>(r, spts, nbox, lo2, hi2);
+        float v[2 * DP];
+#pragma unroll
+        for (int a = 0; a < DP; ++a) {
+          v[a] = fminf(lo[a], lo2[a]);
+          v[DP + a] = fmaxf(hi[a], hi2[a]);
+        }
+        float4* b = reinterpret_cast<float4*>(nbox) + (size_t)node * (DP / 2);
+#pragma unroll
+        for (int k = 0; k < DP / 2; ++k)
+          __stcg(b + k, make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
+      }
       if (node == 0u) break;
       node = nodes[node].parent;
     }
@@ -114,11 +155,24 @@ void launch_tree_build(const unsigned long long* scode, uint32_t n, const GridGe
   count_launches(2);
 }
 
-void launch_tree_maxkey(const unsigned long long* skey, uint32_t n, Node* nodes,
-                        const uint32_t* leaf_parent, uint32_t* visit, cudaStream_t st) {
+template <int DP>
+void tree_up_dp(const unsigned long long* skey, const float* spts, uint32_t n, Node* nodes,
+                const uint32_t* leaf_parent, uint32_t* visit, float* nbox, bool boxes,
+                cudaStream_t st) {
+  if (boxes)
+    k_tree_up<DP, true><<<grid_for(n), kThreads, 0, st>>>(skey, spts, n, nodes, leaf_parent, visit, nbox);
+  else
+    k_tree_up<DP, false><<<grid_for(n), kThreads, 0, st>>>(skey, spts, n, nodes, leaf_parent, visit, nbox);
+}
+
+void launch_tree_maxkey(const unsigned long long* skey, const float* spts, int dp, uint32_t n,
+                        Node* nodes, const uint32_t* leaf_parent, uint32_t* visit, float* nbox,
+                        bool boxes, cudaStream_t st) {
   if (n < 2) return;
   cudaMemsetAsync(visit, 0, sizeof(uint32_t) * (n - 1), st);
-  k_tree_maxkey<<<grid_for(n), kThreads, 0, st>>>(skey, n, nodes, leaf_parent, visit);
+  if (dp == 2) tree_up_dp<2>(skey, spts, n, nodes, leaf_parent, visit, nbox, boxes, st);
+  else if (dp == 4) tree_up_dp<4>(skey, spts, n, nodes, leaf_parent, visit, nbox, boxes, st);
+  else tree_up_dp<8>(skey, spts, n, nodes, leaf_parent, visit, nbox, boxes, st);
   count_launches(1);
 }
 
