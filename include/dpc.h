@@ -64,7 +64,8 @@ typedef enum {
   DPC_ERR_CUDA = -2,        /* a CUDA call failed or no device is available    */
   DPC_ERR_OOM = -3,         /* workspace allocation failed                     */
   DPC_ERR_TIMEOUT = -4,     /* a bounded device-side wait gave up              */
-  DPC_ERR_OVERFLOW = -5,    /* an instance has 2^31 or more points             */
+  DPC_ERR_OVERFLOW = -5,    /* an instance, or the whole batch, has 2^31 or
+                               more points                                     */
   DPC_ERR_UNSUPPORTED = -6, /* valid request this build does not implement     */
   DPC_ERR_DATA = -7         /* coordinates out of the supported range / NaN, or
                                dependent pointers that do not form a forest    */
@@ -139,7 +140,10 @@ int dpc_cluster(const dpc_batch* b, int32_t dcut_index, const dpc_params* params
                 uint32_t flags, void* stream);
 
 /* The whole pipeline for every cutoff: one binning per instance, then for each
- * cutoff density, dependent points and labels.
+ * cutoff density, dependent points and labels.  The instances of a batch are
+ * processed together in at most four groups of equal padded dimension
+ * (d = 1; d = 2; d = 3..4; d = 5..8), each kernel launched once per group, so
+ * the launch count does not grow with the number of instances.
  *   params                   host, [n_inst * n_dcut] thresholds
  *   rho, lambda, delta, label  device, [n_dcut][N] each (cutoff-major) */
 int dpc_run(const void* pts, int dtype, const dpc_batch* b, const dpc_params* params,

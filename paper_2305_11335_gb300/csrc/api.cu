@@ -1,14 +1,21 @@
 // api.cu -- the C ABI (include/dpc.h): argument checks, the per-(device,
 // stream) workspace, and the order in which the kernels run.
 //
-// Pipeline of one instance (all on the caller's stream, no host sync):
-//   binning   bbox -> grid setup -> Morton codes -> radix sort -> gather
-//   tree      radix tree over the sorted codes (dependent points only)
+// The instances of a call are grouped into classes of equal padded dimension
+// dp and gridded dimension g (at most four: (2,1), (2,2), (4,3), (8,3)).  Each
+// class runs as one unit, every kernel launched once for all its instances
+// (dpc_device.cuh describes the layout):
+//   binning   bbox -> grid setup -> sort keys -> radix sort -> gather
+//   tree      radix tree over the sorted keys (dependent points only)
 //   per cutoff
 //     cells     occupied level-k cells -> hash
 //     density   rho (Definition 1) + order keys
 //     dependent maxkeys of the tree -> near phase -> far phase (Definitions 2-3)
 //     labels    pointer jumping (Definitions 4-5)
+// All on the caller's stream, with no host synchronization; a multi-instance
+// class first copies its instance table and cutoffs to the device (one
+// asynchronous copy per call from a page-locked staging buffer).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -37,19 +44,124 @@ inline uint32_t next_pow2(uint64_t x) {
   return (uint32_t)t;
 }
 
+inline int dp_of(int d) { return d <= 2 ? 2 : (d <= 4 ? 4 : 8); }
+inline int g_of(int d) { return d < 3 ? d : 3; }
+
+// ---- argument checks -----------------------------------------------------------
+
+struct Inst {
+  uint64_t n;
+  int d;
+  uint64_t pt_off;     // into result arrays
+  uint64_t coord_off;  // into pts, in elements
+};
+
+int check_batch(const dpc_batch* b, std::vector<Inst>* insts, uint64_t* total) {
+  if (!b || b->n_inst < 1 || !b->pt_offset || !b->dim || b->n_dcut < 1 || !b->d_cut) return DPC_ERR_ARG;
+  if (b->pt_offset[0] != 0) return DPC_ERR_ARG;
+  insts->clear();
+  insts->reserve(b->n_inst);
+  for (int i = 0; i < b->n_inst; ++i) {
+    const int64_t lo = b->pt_offset[i], hi = b->pt_offset[i + 1];
+    if (hi < lo) return DPC_ERR_ARG;
+    const int d = b->dim[i];
+    if (d < 1 || d > kMaxDim) return DPC_ERR_ARG;
+    if (hi - lo >= (int64_t)0x7fffffff) return DPC_ERR_OVERFLOW;
+    Inst in;
+    in.n = (uint64_t)(hi - lo);
+    in.d = d;
+    in.pt_off = (uint64_t)lo;
+    in.coord_off = b->coord_offset ? (uint64_t)b->coord_offset[i] : (uint64_t)lo * (uint64_t)d;
+    if (b->coord_offset && b->coord_offset[i] < 0) return DPC_ERR_ARG;
+    for (int c = 0; c < b->n_dcut; ++c) {
+      const double dc = b->d_cut[(size_t)i * b->n_dcut + c];
+      if (!std::isfinite(dc) || dc < 0.0) return DPC_ERR_ARG;
+    }
+    insts->push_back(in);
+  }
+  // output indices are 32-bit inside the library
+  if (b->pt_offset[b->n_inst] >= (int64_t)0x7fffffff) return DPC_ERR_OVERFLOW;
+  *total = (uint64_t)b->pt_offset[b->n_inst];
+  return DPC_OK;
+}
+
+int check_flags(uint32_t flags) {
+  const uint32_t prec = flags & DPC_PREC_MASK;
+  if (prec != DPC_PREC_FP64 && prec != DPC_PREC_FP32_CERT) return DPC_ERR_UNSUPPORTED;
+  if (flags & ~(DPC_PREC_MASK | DPC_FLAG_SYNC_CHECK | DPC_FLAG_PHASE_TIMES)) return DPC_ERR_ARG;
+  return DPC_OK;
+}
+
+int status_to_code(int s) {
+  if (s == 0) return DPC_OK;
+  if (s & (kStatusBadCoord | kStatusCycle)) return DPC_ERR_DATA;
+  if (s & kStatusStack) return DPC_ERR_UNSUPPORTED;
+  return DPC_ERR_CUDA;
+}
+
+// ---- classes -------------------------------------------------------------------
+
+// One class of a call: the non-empty instances sharing (dp, g), in batch order.
+struct ClassPlan {
+  int dp = 0, g = 0;
+  std::vector<int> members;  // batch indices
+  uint32_t N = 0, nchunk = 0, nmax = 0;
+  int ib = 0, bcap = kMaxBits;
+  // offsets of this class's tables in the upload block (multi-instance only)
+  size_t off_inst = 0, off_cut = 0, off_par = 0;
+  // tables on the device (several instances, or more cutoffs than fit in
+  // kernel arguments); a single instance otherwise runs without them
+  bool upload = false;
+  bool uploaded() const { return upload; }
+};
+
+// Groups the instances into classes; `all_one` puts every instance in one
+// class (labels only, where the dimension does not matter).
+std::vector<ClassPlan> plan_classes(const std::vector<Inst>& insts, bool all_one) {
+  std::vector<ClassPlan> out;
+  const int keys[4][2] = {{2, 1}, {2, 2}, {4, 3}, {8, 3}};
+  for (int k = 0; k < (all_one ? 1 : 4); ++k) {
+    ClassPlan c;
+    c.dp = keys[k][0];
+    c.g = keys[k][1];
+    for (size_t i = 0; i < insts.size(); ++i) {
+      const Inst& in = insts[i];
+      if (in.n == 0) continue;
+      if (!all_one && (dp_of(in.d) != c.dp || g_of(in.d) != c.g)) continue;
+      c.members.push_back((int)i);
+      c.N += (uint32_t)in.n;
+      c.nchunk += (uint32_t)((in.n + 31) / 32);
+      c.nmax = std::max(c.nmax, (uint32_t)in.n);
+    }
+    if (c.members.empty()) continue;
+    int ib = 0;
+    while ((size_t(1) << ib) < c.members.size()) ++ib;
+    c.ib = ib;
+    c.bcap = std::min(kMaxBits, (63 - ib) / c.g);
+    out.push_back(std::move(c));
+  }
+  return out;
+}
+
 struct Workspace {
   int device = -1;
   cudaStream_t stream = nullptr;
-  uint64_t cap_n = 0;     // points per instance the buffers hold
+  uint64_t cap_n = 0;     // points per class the buffers hold
+  uint32_t cap_inst = 0;  // instances per class
   int cap_ncut = 0;
   void* base = nullptr;   // one allocation, carved below
   size_t bytes = 0;
 
-  GridGeom* geom = nullptr;
-  CutGeom* cuts = nullptr;
+  GridGeom* geom = nullptr;   // [cap_inst]
+  CutGeom* cuts = nullptr;    // [cap_ncut][cap_inst]
+  ClassGeom* cls = nullptr;
+  HashInfo* hinfo = nullptr;
   Counters* ctr = nullptr;
   int* status = nullptr;
   int32_t* flags = nullptr;
+  uint32_t* roots = nullptr;  // [cap_inst]
+  uint32_t* chunk_inst = nullptr;
+  uint32_t* chunk_pos = nullptr;
   unsigned long long *codes_a = nullptr, *codes_b = nullptr;
   uint32_t *ids_a = nullptr, *ids_b = nullptr;
   uint32_t* hist = nullptr;
@@ -72,12 +184,21 @@ struct Workspace {
   float* qs1_2 = nullptr;
   double* qs1d2 = nullptr;
 
+  // instance tables and cutoffs of multi-instance classes: filled in the
+  // page-locked host buffer, copied to the device buffer once per call
+  void* up_dev = nullptr;
+  void* up_host = nullptr;
+  size_t up_bytes = 0;
+  cudaEvent_t up_done = nullptr;  // the last copy out of up_host has finished
+
   // host-buffer entry point staging
   void* io = nullptr;
   size_t io_bytes = 0;
 
-  int last_level = 0;     // for dpc_get_stats
-  int last_ncut_used = 0;
+  // for dpc_get_stats: the last class and cutoff that ran
+  const CutGeom* last_cut = nullptr;
+  const GridGeom* last_geom = nullptr;
+  bool have_last = false;
   long long launches_last = 0;
 
   // phase timing (DPC_FLAG_PHASE_TIMES)
@@ -99,8 +220,8 @@ struct Workspace {
     return ev_pool[ev_used++];
   }
 
-  void begin_call(uint32_t flags) {
-    timing = (flags & DPC_FLAG_PHASE_TIMES) != 0;
+  void begin_call(uint32_t fl) {
+    timing = (fl & DPC_FLAG_PHASE_TIMES) != 0;
     recs.clear();
     ev_used = 0;
     g_kernel_launches = 0;
@@ -114,19 +235,23 @@ struct Workspace {
     recs.clear();
     if (base) cudaFree(base);
     if (io) cudaFree(io);
-    base = nullptr;
-    io = nullptr;
-    bytes = io_bytes = 0;
+    if (up_dev) cudaFree(up_dev);
+    if (up_host) cudaFreeHost(up_host);
+    if (up_done) cudaEventDestroy(up_done);
+    base = io = up_dev = up_host = nullptr;
+    up_done = nullptr;
+    bytes = io_bytes = up_bytes = 0;
     cap_n = 0;
+    cap_inst = 0;
     cap_ncut = 0;
+    have_last = false;
   }
 
-  int reserve(uint64_t n, int ncut) {
-    if (n <= cap_n && ncut <= cap_ncut && base) return DPC_OK;
-    uint64_t want_n = n > cap_n ? n : cap_n;
-    int want_c = ncut > cap_ncut ? ncut : cap_ncut;
-    if (want_n < 1024) want_n = 1024;
-    if (want_c < 8) want_c = 8;
+  int reserve(uint64_t n, uint32_t ninst, int ncut) {
+    if (n <= cap_n && ninst <= cap_inst && ncut <= cap_ncut && base) return DPC_OK;
+    uint64_t want_n = std::max<uint64_t>(std::max<uint64_t>(n, cap_n), 1024);
+    uint32_t want_i = std::max<uint32_t>(std::max<uint32_t>(ninst, cap_inst), 1);
+    int want_c = std::max(std::max(ncut, cap_ncut), 8);
     if (base) {
       cudaStreamSynchronize(stream);
       cudaFree(base);
@@ -134,13 +259,18 @@ struct Workspace {
     }
     const uint64_t N = want_n;
     const uint32_t hc = next_pow2(2 * N);
+    const uint64_t nchunk = N / 32 + want_i + 1;
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off += align_up(b); return o; };
-    const size_t o_geom = take(sizeof(GridGeom));
-    const size_t o_cuts = take(sizeof(CutGeom) * want_c);
+    const size_t o_geom = take(sizeof(GridGeom) * want_i);
+    const size_t o_cuts = take(sizeof(CutGeom) * want_i * (size_t)want_c);
+    const size_t o_cls = take(sizeof(ClassGeom));
+    const size_t o_hi = take(sizeof(HashInfo));
     const size_t o_ctr = take(sizeof(Counters));
     const size_t o_status = take(sizeof(int));
     const size_t o_flags = take(sizeof(int32_t) * 80);
+    const size_t o_roots = take(sizeof(uint32_t) * want_i);
+    const size_t o_ci = take(4 * nchunk), o_cp = take(4 * nchunk);
     const size_t o_ca = take(8 * N), o_cb = take(8 * N);
     const size_t o_ia = take(4 * N), o_ib = take(4 * N);
     const size_t o_hist = take(4 * sort_hist_words((uint32_t)N));
@@ -158,6 +288,7 @@ struct Workspace {
     if (cudaMalloc(&p, off) != cudaSuccess) {
       cudaGetLastError();
       cap_n = 0;
+      cap_inst = 0;
       return DPC_ERR_OOM;
     }
     base = p;
@@ -165,9 +296,14 @@ struct Workspace {
     char* b = (char*)p;
     geom = (GridGeom*)(b + o_geom);
     cuts = (CutGeom*)(b + o_cuts);
+    cls = (ClassGeom*)(b + o_cls);
+    hinfo = (HashInfo*)(b + o_hi);
     ctr = (Counters*)(b + o_ctr);
     status = (int*)(b + o_status);
     flags = (int32_t*)(b + o_flags);
+    roots = (uint32_t*)(b + o_roots);
+    chunk_inst = (uint32_t*)(b + o_ci);
+    chunk_pos = (uint32_t*)(b + o_cp);
     codes_a = (unsigned long long*)(b + o_ca);
     codes_b = (unsigned long long*)(b + o_cb);
     ids_a = (uint32_t*)(b + o_ia);
@@ -191,9 +327,46 @@ struct Workspace {
     qs1_2 = (float*)(b + o_qs1_2);
     qs1d2 = (double*)(b + o_qs1d2);
     cap_n = N;
+    cap_inst = want_i;
     cap_ncut = want_c;
+    have_last = false;
     cudaMemsetAsync(status, 0, sizeof(int), stream);
     cudaMemsetAsync(ctr, 0, sizeof(Counters), stream);
+    return DPC_OK;
+  }
+
+  // Makes the upload buffers at least `b` bytes and waits until the previous
+  // copy out of the host buffer has finished, so it can be rewritten.
+  int reserve_upload(size_t b) {
+    if (!up_done) {
+      if (cudaEventCreateWithFlags(&up_done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return DPC_ERR_CUDA;
+      }
+    } else if (cudaEventSynchronize(up_done) != cudaSuccess) {
+      cudaGetLastError();
+      return DPC_ERR_CUDA;
+    }
+    if (b <= up_bytes && up_dev) return DPC_OK;
+    if (up_dev) {
+      cudaStreamSynchronize(stream);
+      cudaFree(up_dev);
+      cudaFreeHost(up_host);
+      up_dev = up_host = nullptr;
+      up_bytes = 0;
+    }
+    if (cudaMalloc(&up_dev, b) != cudaSuccess) {
+      cudaGetLastError();
+      up_dev = nullptr;
+      return DPC_ERR_OOM;
+    }
+    if (cudaMallocHost(&up_host, b) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(up_dev);
+      up_dev = up_host = nullptr;
+      return DPC_ERR_OOM;
+    }
+    up_bytes = b;
     return DPC_OK;
   }
 
@@ -261,59 +434,6 @@ int get_workspace(cudaStream_t st, Workspace** out) {
   return DPC_OK;
 }
 
-// ---- argument checks -----------------------------------------------------------
-
-struct Inst {
-  uint64_t n;
-  int d;
-  uint64_t pt_off;     // into result arrays
-  uint64_t coord_off;  // into pts, in elements
-};
-
-int check_batch(const dpc_batch* b, std::vector<Inst>* insts, uint64_t* total) {
-  if (!b || b->n_inst < 1 || !b->pt_offset || !b->dim || b->n_dcut < 1 || !b->d_cut) return DPC_ERR_ARG;
-  if (b->pt_offset[0] != 0) return DPC_ERR_ARG;
-  insts->clear();
-  insts->reserve(b->n_inst);
-  for (int i = 0; i < b->n_inst; ++i) {
-    const int64_t lo = b->pt_offset[i], hi = b->pt_offset[i + 1];
-    if (hi < lo) return DPC_ERR_ARG;
-    const int d = b->dim[i];
-    if (d < 1 || d > kMaxDim) return DPC_ERR_ARG;
-    if (hi - lo >= (int64_t)0x7fffffff) return DPC_ERR_OVERFLOW;
-    Inst in;
-    in.n = (uint64_t)(hi - lo);
-    in.d = d;
-    in.pt_off = (uint64_t)lo;
-    in.coord_off = b->coord_offset ? (uint64_t)b->coord_offset[i] : (uint64_t)lo * (uint64_t)d;
-    if (b->coord_offset && b->coord_offset[i] < 0) return DPC_ERR_ARG;
-    for (int c = 0; c < b->n_dcut; ++c) {
-      const double dc = b->d_cut[(size_t)i * b->n_dcut + c];
-      if (!std::isfinite(dc) || dc < 0.0) return DPC_ERR_ARG;
-    }
-    insts->push_back(in);
-  }
-  *total = (uint64_t)b->pt_offset[b->n_inst];
-  return DPC_OK;
-}
-
-int check_flags(uint32_t flags) {
-  const uint32_t prec = flags & DPC_PREC_MASK;
-  if (prec != DPC_PREC_FP64 && prec != DPC_PREC_FP32_CERT) return DPC_ERR_UNSUPPORTED;
-  if (flags & ~(DPC_PREC_MASK | DPC_FLAG_SYNC_CHECK | DPC_FLAG_PHASE_TIMES)) return DPC_ERR_ARG;
-  return DPC_OK;
-}
-
-inline int dp_of(int d) { return d <= 2 ? 2 : (d <= 4 ? 4 : 8); }
-inline int g_of(int d) { return d < 3 ? d : 3; }
-
-int status_to_code(int s) {
-  if (s == 0) return DPC_OK;
-  if (s & (kStatusBadCoord | kStatusCycle)) return DPC_ERR_DATA;
-  if (s & kStatusStack) return DPC_ERR_UNSUPPORTED;
-  return DPC_ERR_CUDA;
-}
-
 int finish(Workspace* w, uint32_t flags) {
   w->end_call();
   if (cudaGetLastError() != cudaSuccess) return DPC_ERR_CUDA;
@@ -332,34 +452,140 @@ int finish(Workspace* w, uint32_t flags) {
   return DPC_OK;
 }
 
-// ---- pipeline pieces --------------------------------------------------------------
+// ---- one call: plan, upload, classes ----------------------------------------------
 
-// Binning of one instance: geometry for the given cutoffs, sorted points.
-void bin_instance(Workspace* w, const void* pts, int dtype, const Inst& in,
-                  const std::vector<CutHost>& cuts) {
-  cudaStream_t st = w->stream;
-  const uint32_t n = (uint32_t)in.n;
-  const int d = in.d, g = g_of(d), dp = dp_of(d);
-  const size_t esz = 4;
-  const void* p = (const char*)pts + in.coord_off * esz;
-  Phase ph(w, DPC_PHASE_BIN);
-  w->boxes_ready = false;
-  launch_geom_init(w->geom, w->status, g, st);
-  launch_bbox(p, dtype, n, d, g, w->geom, st);
-  launch_setup(w->geom, w->cuts, cuts.data(), (int)cuts.size(), st);
-  launch_codes(p, dtype, n, d, w->geom, w->codes_a, w->ids_a, st);
-  launch_sort(w->codes_a, w->codes_b, w->ids_a, w->ids_b, n, w->geom, w->hist, st);
-  launch_gather(p, dtype, n, d, dp, w->geom, w->codes_a, w->codes_b, w->ids_a, w->ids_b, w->spts,
-                w->scode, w->sid, st);
+// What a call runs.  cut_first/ncut select the cutoffs (all, or one);
+// params (may be null) are the labelling thresholds.
+struct CallPlan {
+  std::vector<ClassPlan> classes;
+  int ncut_all = 1;   // n_dcut of the batch
+  int cut_first = 0;  // first cutoff this call uses
+  int ncut = 1;       // cutoffs this call uses
+  uint32_t max_inst = 0;
+  uint64_t max_n = 0;
+};
+
+CallPlan make_plan(const dpc_batch* b, const std::vector<Inst>& insts, int cut_first, int ncut,
+                   bool all_one) {
+  CallPlan P;
+  P.classes = plan_classes(insts, all_one);
+  P.ncut_all = b->n_dcut;
+  P.cut_first = cut_first;
+  P.ncut = ncut;
+  for (auto& c : P.classes) {
+    c.upload = c.members.size() > 1 || ncut > kCutChunk;
+    P.max_inst = std::max<uint32_t>(P.max_inst, (uint32_t)c.members.size());
+    P.max_n = std::max<uint64_t>(P.max_n, c.N);
+  }
+  return P;
 }
 
-std::vector<CutHost> host_cuts(const dpc_batch* b, int inst, int dp, int only = -1) {
-  std::vector<CutHost> v;
-  for (int c = 0; c < b->n_dcut; ++c) {
-    if (only >= 0 && c != only) continue;
-    v.push_back(make_cut_host(b->d_cut[(size_t)inst * b->n_dcut + c], dp));
+// Fills and copies the tables of every multi-instance class (instance
+// descriptors, cutoff constants [inst][cut], label thresholds [cut][inst]).
+int upload_tables(Workspace* w, CallPlan& P, const dpc_batch* b, const std::vector<Inst>& insts,
+                  const dpc_params* params) {
+  size_t total = 0;
+  for (auto& c : P.classes) {
+    if (!c.uploaded()) continue;
+    const size_t m = c.members.size();
+    c.off_inst = total;
+    total += align_up(sizeof(InstDev) * m);
+    c.off_cut = total;
+    total += align_up(sizeof(CutHost) * m * P.ncut);
+    c.off_par = total;
+    total += align_up(sizeof(LabelParams) * m * P.ncut);
+  }
+  if (total == 0) return DPC_OK;
+  int rc = w->reserve_upload(total);
+  if (rc) return rc;
+  char* h = (char*)w->up_host;
+  for (auto& c : P.classes) {
+    if (!c.uploaded()) continue;
+    const size_t m = c.members.size();
+    InstDev* id = (InstDev*)(h + c.off_inst);
+    CutHost* ch = (CutHost*)(h + c.off_cut);
+    LabelParams* lp = (LabelParams*)(h + c.off_par);
+    uint32_t start = 0, chunk = 0;
+    for (size_t j = 0; j < m; ++j) {
+      const int bi = c.members[j];
+      const Inst& in = insts[bi];
+      id[j].start = start;
+      id[j].n = (uint32_t)in.n;
+      id[j].out = in.pt_off;
+      id[j].coord = in.coord_off;
+      id[j].d = in.d;
+      id[j].chunk0 = chunk;
+      start += (uint32_t)in.n;
+      chunk += (uint32_t)((in.n + 31) / 32);
+      for (int k = 0; k < P.ncut; ++k) {
+        const int cut = P.cut_first + k;
+        ch[j * P.ncut + k] = make_cut_host(b->d_cut[(size_t)bi * P.ncut_all + cut], c.dp);
+        LabelParams L{0, 0, 0.0};
+        if (params) {
+          const dpc_params& q = params[(size_t)bi * P.ncut_all + cut];
+          L.rho_noise = q.rho_noise;
+          L.rho_min = q.rho_min;
+          L.delta_min = q.delta_min;
+        }
+        lp[(size_t)k * m + j] = L;
+      }
+    }
+  }
+  cudaMemcpyAsync(w->up_dev, w->up_host, total, cudaMemcpyHostToDevice, w->stream);
+  cudaEventRecord(w->up_done, w->stream);
+  return DPC_OK;
+}
+
+// The device view of one class.
+ClassView view_of(Workspace* w, const ClassPlan& c, const std::vector<Inst>& insts) {
+  ClassView v;
+  std::memset(&v, 0, sizeof(v));
+  v.N = c.N;
+  v.ninst = (uint32_t)c.members.size();
+  v.nchunk = c.nchunk;
+  v.geom = w->geom;
+  v.cls = w->cls;
+  if (c.uploaded()) {
+    v.inst = (const InstDev*)((char*)w->up_dev + c.off_inst);
+    v.chunk_inst = w->chunk_inst;
+    v.chunk_pos = w->chunk_pos;
+  } else {
+    const Inst& in = insts[c.members[0]];
+    v.one.start = 0;
+    v.one.n = (uint32_t)in.n;
+    v.one.out = in.pt_off;
+    v.one.coord = in.coord_off;
+    v.one.d = in.d;
+    v.one.chunk0 = 0;
   }
   return v;
+}
+
+const CutHost* cut_table(Workspace* w, const ClassPlan& c) {
+  return c.uploaded() ? (const CutHost*)((char*)w->up_dev + c.off_cut) : nullptr;
+}
+
+// Binning of one class: geometry for the call's cutoffs, sorted points.
+void bin_class(Workspace* w, const void* pts, int dtype, const CallPlan& P, const ClassPlan& c,
+               const ClassView& cv, const dpc_batch* b, const std::vector<Inst>& insts) {
+  cudaStream_t st = w->stream;
+  Phase ph(w, DPC_PHASE_BIN);
+  w->boxes_ready = false;
+  launch_class_init(cv, c.g, c.ib, c.bcap, w->status, st);
+  launch_chunks(cv, w->chunk_inst, w->chunk_pos, st);
+  launch_bbox(pts, dtype, cv, c.g, st);
+  std::vector<CutHost> hc;
+  if (!c.uploaded()) {
+    const int bi = c.members[0];
+    for (int k = 0; k < P.ncut && k < kCutChunk; ++k)
+      hc.push_back(make_cut_host(b->d_cut[(size_t)bi * P.ncut_all + P.cut_first + k], c.dp));
+  }
+  launch_setup(cv, w->cuts, P.ncut, cut_table(w, c), hc.data(), st);
+  launch_codes(pts, dtype, cv, c.g, w->codes_a, w->ids_a, st);
+  launch_sort(w->codes_a, w->codes_b, w->ids_a, w->ids_b, cv.N, w->cls, w->hist, st);
+  launch_gather(pts, dtype, cv, c.dp, w->codes_a, w->codes_b, w->ids_a, w->ids_b, w->spts,
+                w->scode, w->sid, st);
+  (void)insts;
 }
 
 FarQueue queue_of(Workspace* w) {
@@ -373,63 +599,83 @@ FarQueue queue_of(Workspace* w) {
   return q;
 }
 
-void dependent_step(Workspace* w, const void* pts_all, int dtype, const Inst& in, CutGeom* cut,
-                    int32_t rho_skip, bool fp64, int32_t* lambda, double* delta) {
-  const void* pts = (const char*)pts_all + in.coord_off * 4;
+void tree_step(Workspace* w, const ClassView& cv) {
+  Phase ph(w, DPC_PHASE_TREE);
+  launch_tree_build(w->scode, cv, w->nodes, w->leaf_parent, w->roots, w->stream);
+}
+
+void cells_step(Workspace* w, const ClassPlan& c, const ClassView& cv, const CutGeom* cuts) {
+  Phase ph(w, DPC_PHASE_CELLS);
+  launch_cells(w->scode, cv, c.g, cuts, w->hinfo, w->hkeys, w->hvals, w->hcap, w->stream);
+  w->last_cut = cuts;
+  w->last_geom = w->geom;
+  w->have_last = true;
+}
+
+void density_step(Workspace* w, const ClassPlan& c, const ClassView& cv, const CutGeom* cuts,
+                  bool fp64, int32_t* rho) {
+  Phase ph(w, DPC_PHASE_DENSITY);
+  launch_density(c.dp, c.g, fp64, w->spts, w->scode, w->sid, cv, cuts, w->hinfo, w->hkeys,
+                 w->hvals, rho, w->skey, w->ctr, w->stream);
+}
+
+void dependent_step(Workspace* w, const ClassPlan& c, const ClassView& cv, const CutGeom* cuts,
+                    const void* pts, int dtype, int32_t rho_skip, bool fp64, int32_t* lambda,
+                    double* delta) {
   cudaStream_t st = w->stream;
-  const uint32_t n = (uint32_t)in.n;
-  const int d = in.d, g = g_of(d), dp = dp_of(d);
   {
     Phase ph(w, DPC_PHASE_MAXKEY);
-    launch_tree_maxkey(w->skey, w->spts, dp, n, w->nodes, w->leaf_parent, w->visit, w->nbox,
+    launch_tree_maxkey(w->skey, w->spts, c.dp, cv.N, w->nodes, w->leaf_parent, w->visit, w->nbox,
                        !w->boxes_ready, st);
     w->boxes_ready = true;
   }
   {
     Phase ph(w, DPC_PHASE_NEAR);
-    launch_dep_near(dp, g, fp64, w->spts, w->scode, w->skey, n, rho_skip, pts, dtype, d, w->geom, cut,
-                    w->hkeys, w->hvals, lambda, delta, queue_of(w), w->ctr, st);
+    launch_dep_near(c.dp, c.g, fp64, w->spts, w->scode, w->skey, cv, rho_skip, pts, dtype, cuts,
+                    w->hinfo, w->hkeys, w->hvals, lambda, delta, queue_of(w), w->ctr, st);
   }
   {
     Phase ph(w, DPC_PHASE_FAR);
-    launch_dep_far(dp, fp64, w->spts, w->skey, n, w->geom, cut, w->nodes, w->nbox, queue_of(w),
-                   lambda, delta, w->ctr, n, st);
+    launch_dep_far(c.dp, fp64, w->spts, w->scode, w->skey, cv, cuts, w->nodes, w->nbox, w->roots,
+                   queue_of(w), lambda, delta, w->ctr, st);
   }
 }
 
-void cells_step(Workspace* w, uint32_t n, CutGeom* cut) {
-  Phase ph(w, DPC_PHASE_CELLS);
-  launch_cells(w->scode, n, w->geom, cut, w->hkeys, w->hvals, w->hcap, w->stream);
-}
-
-void density_step(Workspace* w, const Inst& in, CutGeom* cut, bool fp64, int32_t* rho) {
-  Phase ph(w, DPC_PHASE_DENSITY);
-  launch_density(dp_of(in.d), g_of(in.d), fp64, w->spts, w->scode, w->sid, (uint32_t)in.n, w->geom,
-                 cut, w->hkeys, w->hvals, rho, w->skey, w->ctr, w->stream);
-}
-
-void tree_step(Workspace* w, uint32_t n) {
-  Phase ph(w, DPC_PHASE_TREE);
-  launch_tree_build(w->scode, n, w->geom, w->nodes, w->leaf_parent, w->stream);
-}
-
-void labels_step(Workspace* w, uint32_t n, const dpc_params& P, const int32_t* rho,
-                 const int32_t* lambda, const double* delta, int32_t* label) {
+void labels_step(Workspace* w, const ClassPlan& c, const ClassView& cv, int k_in_call,
+                 const LabelParams& one, const int32_t* rho, const int32_t* lambda,
+                 const double* delta, int32_t* label) {
   Phase ph(w, DPC_PHASE_LABELS);
-  launch_labels(rho, lambda, delta, n, P.rho_noise, P.rho_min, P.delta_min, label, w->flags,
-                w->geom, w->stream);
+  const LabelParams* par =
+      c.uploaded()
+          ? (const LabelParams*)((char*)w->up_dev + c.off_par) + (size_t)k_in_call * c.members.size()
+          : nullptr;
+  launch_labels(rho, lambda, delta, cv, c.nmax, par, one, label, w->flags, w->stream);
 }
 
-uint64_t max_n(const std::vector<Inst>& v) {
-  uint64_t m = 0;
-  for (auto& i : v) m = i.n > m ? i.n : m;
-  return m;
+LabelParams one_params(const dpc_params* params, const ClassPlan& c, int ncut_all, int cut) {
+  LabelParams L{0, 0, 0.0};
+  if (params && !c.uploaded()) {
+    const dpc_params& q = params[(size_t)c.members[0] * ncut_all + cut];
+    L.rho_noise = q.rho_noise;
+    L.rho_min = q.rho_min;
+    L.delta_min = q.delta_min;
+  }
+  return L;
 }
 
 void reset_call(Workspace* w, uint32_t flags) {
   w->begin_call(flags);
   cudaMemsetAsync(w->status, 0, sizeof(int), w->stream);
   cudaMemsetAsync(w->ctr, 0, sizeof(Counters), w->stream);
+}
+
+// Reserves the workspace for a plan and uploads its tables.
+int prepare(Workspace* w, CallPlan& P, const dpc_batch* b, const std::vector<Inst>& insts,
+            const dpc_params* params, uint32_t flags) {
+  int rc = w->reserve(P.max_n, P.max_inst, P.ncut);
+  if (rc) return rc;
+  reset_call(w, flags);
+  return upload_tables(w, P, b, insts, params);
 }
 
 }  // namespace
@@ -439,7 +685,7 @@ using namespace dpc;
 
 extern "C" {
 
-const char* dpc_version(void) { return "0.1.0"; }
+const char* dpc_version(void) { return "0.2.0"; }
 
 const char* dpc_strerror(int status) {
   switch (status) {
@@ -448,7 +694,7 @@ const char* dpc_strerror(int status) {
     case DPC_ERR_CUDA: return "CUDA error or no CUDA device";
     case DPC_ERR_OOM: return "device memory allocation failed";
     case DPC_ERR_TIMEOUT: return "a bounded device-side wait gave up";
-    case DPC_ERR_OVERFLOW: return "an instance has 2^31 or more points";
+    case DPC_ERR_OVERFLOW: return "an instance, or the whole batch, has 2^31 or more points";
     case DPC_ERR_UNSUPPORTED: return "not supported by this build";
     case DPC_ERR_DATA: return "coordinates out of range or NaN, or dependent pointers not a forest";
     default: return "unknown status";
@@ -467,20 +713,17 @@ int dpc_density(const void* pts, int dtype, const dpc_batch* b, int32_t* rho, ui
   Workspace* w = nullptr;
   if ((rc = get_workspace((cudaStream_t)stream, &w))) return rc;
   std::lock_guard<std::mutex> lk(g_mu);
-  if ((rc = w->reserve(max_n(insts), b->n_dcut))) return rc;
-  reset_call(w, flags);
+  CallPlan P = make_plan(b, insts, 0, b->n_dcut, false);
+  if ((rc = prepare(w, P, b, insts, nullptr, flags))) return rc;
   const bool fp64 = (flags & DPC_PREC_MASK) == DPC_PREC_FP64;
-  for (int i = 0; i < b->n_inst; ++i) {
-    const Inst& in = insts[i];
-    if (in.n == 0) continue;
-    const int dp = dp_of(in.d);
-    std::vector<CutHost> cuts = host_cuts(b, i, dp);
-    bin_instance(w, pts, dtype, in, cuts);
-    for (int c = 0; c < b->n_dcut; ++c) {
-      cells_step(w, (uint32_t)in.n, w->cuts + c);
-      density_step(w, in, w->cuts + c, fp64, rho + (size_t)c * N + in.pt_off);
+  for (const ClassPlan& c : P.classes) {
+    const ClassView cv = view_of(w, c, insts);
+    bin_class(w, pts, dtype, P, c, cv, b, insts);
+    for (int k = 0; k < P.ncut; ++k) {
+      const CutGeom* cuts = w->cuts + (size_t)k * cv.ninst;
+      cells_step(w, c, cv, cuts);
+      density_step(w, c, cv, cuts, fp64, rho + (size_t)k * N);
     }
-    w->last_ncut_used = b->n_dcut;
   }
   return finish(w, flags);
 }
@@ -499,20 +742,16 @@ int dpc_dependent(const void* pts, int dtype, const dpc_batch* b, int32_t dcut_i
   Workspace* w = nullptr;
   if ((rc = get_workspace((cudaStream_t)stream, &w))) return rc;
   std::lock_guard<std::mutex> lk(g_mu);
-  if ((rc = w->reserve(max_n(insts), 1))) return rc;
-  reset_call(w, flags);
+  CallPlan P = make_plan(b, insts, dcut_index, 1, false);
+  if ((rc = prepare(w, P, b, insts, nullptr, flags))) return rc;
   const bool fp64 = (flags & DPC_PREC_MASK) == DPC_PREC_FP64;
-  for (int i = 0; i < b->n_inst; ++i) {
-    const Inst& in = insts[i];
-    if (in.n == 0) continue;
-    const int dp = dp_of(in.d);
-    std::vector<CutHost> cuts = host_cuts(b, i, dp, dcut_index);
-    bin_instance(w, pts, dtype, in, cuts);
-    tree_step(w, (uint32_t)in.n);
-    cells_step(w, (uint32_t)in.n, w->cuts);
-    launch_keys_from_rho(rho + in.pt_off, w->sid, (uint32_t)in.n, w->skey, w->stream);
-    dependent_step(w, pts, dtype, in, w->cuts, rho_skip, fp64, lambda + in.pt_off, delta + in.pt_off);
-    w->last_ncut_used = 1;
+  for (const ClassPlan& c : P.classes) {
+    const ClassView cv = view_of(w, c, insts);
+    bin_class(w, pts, dtype, P, c, cv, b, insts);
+    tree_step(w, cv);
+    cells_step(w, c, cv, w->cuts);
+    launch_keys_from_rho(rho, w->sid, cv.N, w->skey, w->stream);
+    dependent_step(w, c, cv, w->cuts, pts, dtype, rho_skip, fp64, lambda, delta);
   }
   return finish(w, flags);
 }
@@ -532,15 +771,14 @@ int dpc_cluster(const dpc_batch* b, int32_t dcut_index, const dpc_params* params
   Workspace* w = nullptr;
   if ((rc = get_workspace((cudaStream_t)stream, &w))) return rc;
   std::lock_guard<std::mutex> lk(g_mu);
-  if ((rc = w->reserve(max_n(insts), 1))) return rc;
-  reset_call(w, flags);
-  for (int i = 0; i < b->n_inst; ++i) {
-    const Inst& in = insts[i];
-    if (in.n == 0) continue;
-    const dpc_params& P = params[(size_t)i * b->n_dcut + dcut_index];
-    launch_geom_init(w->geom, w->status, g_of(in.d), w->stream);
-    labels_step(w, (uint32_t)in.n, P, rho + in.pt_off, lambda + in.pt_off, delta + in.pt_off,
-                label + in.pt_off);
+  CallPlan P = make_plan(b, insts, dcut_index, 1, true);
+  if ((rc = prepare(w, P, b, insts, params, flags))) return rc;
+  for (const ClassPlan& c : P.classes) {
+    const ClassView cv = view_of(w, c, insts);
+    launch_class_init(cv, c.g, c.ib, c.bcap, w->status, w->stream);
+    launch_chunks(cv, w->chunk_inst, w->chunk_pos, w->stream);
+    labels_step(w, c, cv, 0, one_params(params, c, P.ncut_all, dcut_index), rho, lambda, delta,
+                label);
   }
   return finish(w, flags);
 }
@@ -550,24 +788,22 @@ static int run_device(Workspace* w, const void* pts, int dtype, const dpc_batch*
                       int32_t* rho, int32_t* lambda, double* delta, int32_t* label,
                       uint32_t flags) {
   const bool fp64 = (flags & DPC_PREC_MASK) == DPC_PREC_FP64;
-  reset_call(w, flags);
-  for (int i = 0; i < b->n_inst; ++i) {
-    const Inst& in = insts[i];
-    if (in.n == 0) continue;
-    const uint32_t n = (uint32_t)in.n;
-    const int dp = dp_of(in.d);
-    std::vector<CutHost> cuts = host_cuts(b, i, dp);
-    bin_instance(w, pts, dtype, in, cuts);
-    tree_step(w, n);
-    for (int c = 0; c < b->n_dcut; ++c) {
-      const size_t o = (size_t)c * N + in.pt_off;
-      CutGeom* cut = w->cuts + c;
-      cells_step(w, n, cut);
-      density_step(w, in, cut, fp64, rho + o);
-      dependent_step(w, pts, dtype, in, cut, 0, fp64, lambda + o, delta + o);
-      labels_step(w, n, params[(size_t)i * b->n_dcut + c], rho + o, lambda + o, delta + o, label + o);
+  CallPlan P = make_plan(b, insts, 0, b->n_dcut, false);
+  int rc = prepare(w, P, b, insts, params, flags);
+  if (rc) return rc;
+  for (const ClassPlan& c : P.classes) {
+    const ClassView cv = view_of(w, c, insts);
+    bin_class(w, pts, dtype, P, c, cv, b, insts);
+    tree_step(w, cv);
+    for (int k = 0; k < P.ncut; ++k) {
+      const size_t o = (size_t)k * N;
+      const CutGeom* cuts = w->cuts + (size_t)k * cv.ninst;
+      cells_step(w, c, cv, cuts);
+      density_step(w, c, cv, cuts, fp64, rho + o);
+      dependent_step(w, c, cv, cuts, pts, dtype, 0, fp64, lambda + o, delta + o);
+      labels_step(w, c, cv, k, one_params(params, c, P.ncut_all, k), rho + o, lambda + o,
+                  delta + o, label + o);
     }
-    w->last_ncut_used = b->n_dcut;
   }
   return cudaGetLastError() == cudaSuccess ? DPC_OK : DPC_ERR_CUDA;
 }
@@ -595,7 +831,6 @@ int dpc_run(const void* pts, int dtype, const dpc_batch* b, const dpc_params* pa
   Workspace* w = nullptr;
   if ((rc = get_workspace((cudaStream_t)stream, &w))) return rc;
   std::lock_guard<std::mutex> lk(g_mu);
-  if ((rc = w->reserve(max_n(insts), b->n_dcut))) return rc;
   if ((rc = run_device(w, pts, dtype, b, insts, N, params, rho, lambda, delta, label, flags))) return rc;
   return finish(w, flags);
 }
@@ -611,7 +846,6 @@ int dpc_run_host(const void* pts_host, int dtype, const dpc_batch* b, const dpc_
   Workspace* w = nullptr;
   if ((rc = get_workspace((cudaStream_t)stream, &w))) return rc;
   std::lock_guard<std::mutex> lk(g_mu);
-  if ((rc = w->reserve(max_n(insts), b->n_dcut))) return rc;
   uint64_t elems = 0;
   for (auto& in : insts) {
     uint64_t e = in.coord_off + in.n * (uint64_t)in.d;
@@ -657,21 +891,23 @@ int dpc_get_stats(void* stream, dpc_stats* out) {
     return DPC_ERR_CUDA;
   }
   Counters c;
-  GridGeom g;
   cudaMemcpy(&c, w->ctr, sizeof(c), cudaMemcpyDeviceToHost);
-  cudaMemcpy(&g, w->geom, sizeof(g), cudaMemcpyDeviceToHost);
   out->band_pairs = (int64_t)c.band_pairs;
   out->far_queries = (int64_t)c.far_queries;
   out->exact_rescans = (int64_t)c.exact_rescans;
-  out->bits_per_axis = g.B;
   out->kernel_launches = w->launches_last;
   out->far_nodes = (int64_t)c.far_nodes;
   out->far_nodes_max = (int64_t)c.far_nodes_max;
-  if (w->last_ncut_used > 0) {
+  if (w->have_last) {
     CutGeom cg;
-    cudaMemcpy(&cg, w->cuts + (w->last_ncut_used - 1), sizeof(cg), cudaMemcpyDeviceToHost);
-    out->occupied_cells = cg.m;
+    GridGeom g;
+    HashInfo hi;
+    cudaMemcpy(&cg, w->last_cut, sizeof(cg), cudaMemcpyDeviceToHost);
+    cudaMemcpy(&g, w->last_geom, sizeof(g), cudaMemcpyDeviceToHost);
+    cudaMemcpy(&hi, w->hinfo, sizeof(hi), cudaMemcpyDeviceToHost);
+    out->occupied_cells = hi.m;
     out->grid_level = cg.k;
+    out->bits_per_axis = g.B;
   }
   return cudaGetLastError() == cudaSuccess ? DPC_OK : DPC_ERR_CUDA;
 }

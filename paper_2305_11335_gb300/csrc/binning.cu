@@ -25,85 +25,107 @@ inline unsigned grid_for(uint64_t n, int threads = kThreads, unsigned cap = 152u
   return (unsigned)b;
 }
 
-__global__ void k_geom_init(GridGeom* geom, int* status, int g) {
-  geom->g = g;
-  geom->status = status;
+// Class and per-instance geometry reset (one thread per instance).
+__global__ void k_class_init(ClassView cv, int g, int ib, int bcap, int* status) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) {
+    cv.cls->S = 0;
+    cv.cls->ib = ib;
+    cv.cls->bcap = bcap;
+    cv.cls->status = status;
+  }
+  if (t >= cv.ninst) return;
+  GridGeom& G = cv.geom[t];
+  G.g = g;
+  G.status = status;
   for (int a = 0; a < 3; ++a) {
-    geom->bbox_ord[a] = 0xffffffffu;  // min accumulators
-    geom->bbox_ord[3 + a] = 0u;       // max accumulators
+    G.bbox_ord[a] = 0xffffffffu;  // min accumulators
+    G.bbox_ord[3 + a] = 0u;       // max accumulators
   }
 }
 
-// Bounding box of the gridded axes and the coordinate range check.
+// Bounding box of the gridded axes of every instance, and the coordinate
+// range check.  Each warp takes a contiguous range of chunks and keeps a
+// running box while the instance stays the same, so most instances see one
+// atomic per warp and axis.
 template <typename T>
-__global__ void k_bbox(const T* __restrict__ pts, uint32_t n, int d, int g, GridGeom* geom) {
-  float mn[3] = {FLT_MAX, FLT_MAX, FLT_MAX};
-  float mx[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+__global__ void k_bbox(const T* __restrict__ pts, ClassView cv, int g) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nw = gridDim.x * (blockDim.x >> 5);
+  const uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const uint32_t per = (cv.nchunk + nw - 1) / nw;
+  const uint32_t c0 = w * per, c1 = min(cv.nchunk, c0 + per);
+  float mn[3], mx[3];
+  uint32_t cur = 0xffffffffu;
   int bad = 0;
-  const uint64_t total = (uint64_t)n * d;
-  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < total;
-       e += (uint64_t)gridDim.x * blockDim.x) {
-    T v = pts[e];
-    float x;
-    if constexpr (std::is_integral<T>::value) {
-      bad |= (v > (1 << 24)) | (v < -(1 << 24));
-      x = (float)v;
-    } else {
-      x = (float)v;
-      bad |= !(fabsf(x) <= 1.152921504606846976e18f);  // 2^60; false for NaN
-    }
-    int a = (int)(e % (uint64_t)d);
-    if (a < g) {
+  auto flush = [&]() {
 #pragma unroll
-      for (int k = 0; k < 3; ++k)
-        if (k == a) { mn[k] = fminf(mn[k], x); mx[k] = fmaxf(mx[k], x); }
-    }
-  }
-  // warp reduce, block reduce through shared memory, one atomic per block
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    for (int o = 16; o > 0; o >>= 1) {
-      mn[k] = fminf(mn[k], __shfl_xor_sync(0xffffffffu, mn[k], o));
-      mx[k] = fmaxf(mx[k], __shfl_xor_sync(0xffffffffu, mx[k], o));
-    }
-  }
-  __shared__ float s_mn[32][3], s_mx[32][3];
-  __shared__ int s_bad;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  if (threadIdx.x == 0) s_bad = 0;
-  __syncthreads();
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) { s_mn[w][k] = mn[k]; s_mx[w][k] = mx[k]; }
-  }
-  if (bad) s_bad = 1;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < g; ++k) {
-      float a = s_mn[0][k], b = s_mx[0][k];
-      for (int j = 1; j < nw; ++j) { a = fminf(a, s_mn[j][k]); b = fmaxf(b, s_mx[j][k]); }
-      if (a <= b) {
-        atomicMin(&geom->bbox_ord[k], float_ord(a));
-        atomicMax(&geom->bbox_ord[3 + k], float_ord(b));
+    for (int k = 0; k < 3; ++k) {
+      const uint32_t lo = __reduce_min_sync(0xffffffffu, float_ord(mn[k]));
+      const uint32_t hi = __reduce_max_sync(0xffffffffu, float_ord(mx[k]));
+      if (lane == 0 && k < g && ord_float(lo) <= ord_float(hi)) {
+        atomicMin(&cv.geom[cur].bbox_ord[k], lo);
+        atomicMax(&cv.geom[cur].bbox_ord[3 + k], hi);
       }
     }
-    if (s_bad) set_status(geom->status, kStatusBadCoord);
+  };
+  for (uint32_t c = c0; c < c1; ++c) {
+    uint32_t i, p0, end;
+    cv.chunk(c, i, p0, end);
+    if (i != cur) {
+      if (cur != 0xffffffffu) flush();
+      cur = i;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        mn[k] = FLT_MAX;
+        mx[k] = -FLT_MAX;
+      }
+    }
+    const InstDev I = cv.instance(i);
+    const uint32_t p = p0 + lane;
+    if (p < end) {
+      const T* row = pts + I.coord + (size_t)(p - I.start) * I.d;
+      for (int a = 0; a < I.d; ++a) {
+        const T v = row[a];
+        float x;
+        if constexpr (std::is_integral<T>::value) {
+          bad |= (v > (1 << 24)) | (v < -(1 << 24));
+          x = (float)v;
+        } else {
+          x = (float)v;
+          bad |= !(fabsf(x) <= 1.152921504606846976e18f);  // 2^60; false for NaN
+        }
+        if (a < 3) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+            if (k == a) { mn[k] = fminf(mn[k], x); mx[k] = fmaxf(mx[k], x); }
+        }
+      }
+    }
   }
+  if (cur != 0xffffffffu) flush();
+  if (__any_sync(0xffffffffu, bad) && lane == 0) set_status(cv.cls->status, kStatusBadCoord);
 }
 
-// Grid geometry from the bounding box.
+// Grid geometry of every instance from its bounding box (one thread each).
 //
-// Fine grid: the fine cell is 1/8 of the smallest cutoff (times 1 + 2^-20),
-// so the level-3 cell is just wider than d_cut and the 3^g block around it
-// holds every point within d_cut with the least volume a cell grid allows.
-// At most kMaxBits bits per axis keep fine-unit coordinates exact to 1/8 cell
-// in float32; a wider bounding box gets a coarser fine cell instead.
-// A point's fine index c = floor((x - org) * inv_f) is within 1e-9 cells of the
-// exact real value, so its real position lies in [c - 0.5, c + 1.5) fine units;
-// every bound below is derived from that interval.
-__global__ void k_setup_geom(GridGeom* geom, double dcmin) {
-  if (threadIdx.x != 0) return;
+// Fine grid: the fine cell is 1/8 of the instance's smallest cutoff (times
+// 1 + 2^-20), so the level-3 cell is just wider than d_cut and the 3^g block
+// around it holds every point within d_cut with the least volume a cell grid
+// allows.  At most bcap <= kMaxBits bits per axis keep fine-unit coordinates
+// exact to 1/8 cell in float32 (and the sort key below 2^63); a wider bounding
+// box gets a coarser fine cell instead.  A point's fine index
+// c = floor((x - org) * inv_f) is within 1e-9 cells of the exact real value,
+// so its real position lies in [c - 0.5, c + 1.5) fine units; every bound
+// below is derived from that interval.
+__global__ void k_setup_geom(ClassView cv, int ncut, const CutHost* __restrict__ hc, CutArgs args) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cv.ninst) return;
+  GridGeom* geom = cv.geom + t;
+  double dcmin = INFINITY;
+  for (int c = 0; c < ncut; ++c) dcmin = fmin(dcmin, hc ? hc[(size_t)t * ncut + c].dc : args.h[c].dc);
   const int g = geom->g;
+  const int bcap = cv.cls->bcap;
   double E = 0.0;
   for (int a = 0; a < g; ++a) {
     uint32_t lo = geom->bbox_ord[a], hi = geom->bbox_ord[3 + a];
@@ -122,12 +144,12 @@ __global__ void k_setup_geom(GridGeom* geom, double dcmin) {
     f = 1.0;
   } else {
     const double f_fit = dcmin * (1.0 + 0x1p-20) * 0.125;
-    if (f_fit > 0.0 && E / f_fit < ldexp(1.0, kMaxBits) * (1.0 - 0x1p-20)) {
+    if (f_fit > 0.0 && E / f_fit < ldexp(1.0, bcap) * (1.0 - 0x1p-20)) {
       f = f_fit;
       B = 1;
       while (ldexp(f, B) <= E * (1.0 + 0x1p-30)) ++B;  // E / f < 2^B with margin
     } else {
-      B = kMaxBits;
+      B = bcap;
       f = ldexp(E, -B) * (1.0 + 0x1p-20);
     }
   }
@@ -136,28 +158,30 @@ __global__ void k_setup_geom(GridGeom* geom, double dcmin) {
   geom->inv_f = 1.0 / f;
   geom->f2 = __double2float_rd(f * f);
   geom->nbits = g * B;
-  geom->npass = (g * B + 7) / 8;
+  atomicMax(&cv.cls->S, g * B);
 }
 
-// Per-cutoff search parameters: the grid level k whose cells are at least
-// d_cut wide (so the (2R+1)^g block with R = 1 holds every point within
-// d_cut), the density prune bound and the far bound of the dependent search.
-constexpr int kCutChunk = 16;
-struct CutArgs {
-  CutHost h[kCutChunk];
-};
-__global__ void k_setup_cuts(const GridGeom* __restrict__ geom, CutGeom* cuts, int ncut, CutArgs a) {
-  const int c = threadIdx.x;
-  if (c >= ncut) return;
+// Per (instance, cutoff) search parameters, one thread each: the grid level k
+// whose cells are at least d_cut wide (so the (2R+1)^g block with R = 1 holds
+// every point within d_cut), the density prune bound and the far bound of the
+// dependent search.  cuts is [ncut][ninst].
+__global__ void k_setup_cuts(ClassView cv, CutGeom* cuts, int ncut, const CutHost* __restrict__ hc,
+                             CutArgs args) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cv.ninst * (uint32_t)ncut) return;
+  const uint32_t i = t / ncut;
+  const int c = (int)(t - i * ncut);
+  const GridGeom* geom = cv.geom + i;
+  const CutHost H = hc ? hc[(size_t)i * ncut + c] : args.h[c];
   const double f = geom->f;
   const int B = geom->B;
-  CutGeom& C = cuts[c];
-  C.dc = a.h[c].dc;
-  C.dc2 = a.h[c].dc2;
-  C.t_in = a.h[c].t_in;
-  C.t_out = a.h[c].t_out;
-  C.band_mul = a.h[c].band_mul;
-  C.band_add = a.h[c].band_add;
+  CutGeom& C = cuts[(size_t)c * cv.ninst + i];
+  C.dc = H.dc;
+  C.dc2 = H.dc2;
+  C.t_in = H.t_in;
+  C.t_out = H.t_out;
+  C.band_mul = H.band_mul;
+  C.band_add = H.band_add;
   // Two points within d_cut differ by at most D fine indices on each axis.
   // Choose the level k and block radius R (R * 2^k >= D).  R = 1 (the 3^g
   // block of cells at least d_cut wide) unless a larger R on finer cells
@@ -196,52 +220,70 @@ __global__ void k_setup_cuts(const GridGeom* __restrict__ geom, CutGeom* cuts, i
   C.far64 = lb2 * (1.0 - 1e-9);
   double l32 = lb2 * (1.0 - 1e-5) - 0x1p-100;
   C.far32 = l32 <= 0.0 ? 0.0f : (l32 >= 3.0e38 ? 3.0e38f : __double2float_rd(l32));
-  C.m = 0;
-  C.hmask = 0;
 }
 
-// Fine-grid Morton code of every point.
+// Sort key of every point: (instance << S) | fine-grid Morton code; the
+// payload is the point's class position.
 template <typename T, int G>
-__global__ void k_codes(const T* __restrict__ pts, uint32_t n, int d, const GridGeom* __restrict__ geom,
+__global__ void k_codes(const T* __restrict__ pts, ClassView cv,
                         unsigned long long* __restrict__ codes, uint32_t* __restrict__ ids) {
-  const double inv_f = geom->inv_f;
-  const uint32_t cmax = (1u << geom->B) - 1u;
-  double org[G];
-#pragma unroll
-  for (int a = 0; a < G; ++a) org[a] = geom->org[a];
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  const int S = cv.cls->S, ib = cv.cls->ib;
+  const uint64_t total = (uint64_t)cv.nchunk * 32u;
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < total;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t i, p0, end;
+    cv.chunk((uint32_t)(e >> 5), i, p0, end);
+    const uint32_t p = p0 + (uint32_t)(e & 31u);
+    if (p >= end) continue;
+    const InstDev I = cv.instance(i);
+    const GridGeom* geom = cv.geom + i;
+    const double inv_f = geom->inv_f;
+    const uint32_t cmax = (1u << geom->B) - 1u;
+    const T* row = pts + I.coord + (size_t)(p - I.start) * I.d;
     uint32_t c[G];
 #pragma unroll
     for (int a = 0; a < G; ++a) {
-      double x = (double)(float)pts[(size_t)i * d + a];
-      double v = (x - org[a]) * inv_f;
+      double x = (double)(float)row[a];
+      double v = (x - geom->org[a]) * inv_f;
       v = fmin(fmax(v, 0.0), (double)cmax);
       c[a] = (uint32_t)v;
     }
-    codes[i] = morton<G>(c);
-    ids[i] = i;
+    codes[p] = (ib ? ((unsigned long long)i << S) : 0ull) | morton<G>(c);
+    ids[p] = p;
   }
 }
 
-// Points into Morton order, converted to float and zero padded to DP.
+// Points into key order, converted to float and zero padded to DP; sid gets
+// each sorted point's output index.
 template <typename T, int DP>
-__global__ void k_gather(const T* __restrict__ pts, uint32_t n, int d, const GridGeom* __restrict__ geom,
+__global__ void k_gather(const T* __restrict__ pts, ClassView cv,
                          const unsigned long long* codes_a, const unsigned long long* codes_b,
                          const uint32_t* ids_a, const uint32_t* ids_b,
                          float* __restrict__ spts, unsigned long long* __restrict__ scode,
                          uint32_t* __restrict__ sid) {
-  const bool odd = geom->npass & 1;
+  const int S = cv.cls->S, ib = cv.cls->ib;
+  const bool odd = sort_passes(S, ib) & 1;
   const unsigned long long* __restrict__ ck = odd ? codes_b : codes_a;
   const uint32_t* __restrict__ ci = odd ? ids_b : ids_a;
+  const uint32_t n = cv.N;
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const unsigned long long key = ck[p];
+    uint32_t inst = key_inst(key, S, ib);
     uint32_t o = ci[p];
-    if (o >= n) {
-      set_status(geom->status, kStatusIndex);
-      o = 0;
+    if (inst >= cv.ninst) {
+      set_status(cv.cls->status, kStatusIndex);
+      inst = 0;
     }
+    const InstDev I = cv.instance(inst);
+    if (o < I.start || o >= I.start + I.n) {
+      set_status(cv.cls->status, kStatusIndex);
+      o = I.start;
+    }
+    const uint32_t local = o - I.start;
+    const T* row = pts + I.coord + (size_t)local * I.d;
     float x[DP];
 #pragma unroll
-    for (int k = 0; k < DP; ++k) x[k] = (k < d) ? (float)pts[(size_t)o * d + k] : 0.f;
+    for (int k = 0; k < DP; ++k) x[k] = (k < I.d) ? (float)row[k] : 0.f;
     if constexpr (DP == 2) {
       reinterpret_cast<float2*>(spts)[p] = make_float2(x[0], x[1]);
     } else if constexpr (DP == 4) {
@@ -251,49 +293,68 @@ __global__ void k_gather(const T* __restrict__ pts, uint32_t n, int d, const Gri
       q[0] = make_float4(x[0], x[1], x[2], x[3]);
       q[1] = make_float4(x[4], x[5], x[6], x[7]);
     }
-    scode[p] = ck[p];
-    sid[p] = o;
+    scode[p] = key;
+    sid[p] = (uint32_t)(I.out + local);
   }
 }
 
 // ---- occupied cells of level k ------------------------------------------------
 
-__global__ void k_cells_count(const unsigned long long* __restrict__ scode, uint32_t n,
-                              const GridGeom* __restrict__ geom, CutGeom* cut) {
-  const int sh = geom->g * cut->k;
+// Hash key of the level-k cell holding sorted key `key` of instance `inst`.
+__device__ __forceinline__ unsigned long long key_cell(unsigned long long key, int S, int ib,
+                                                      int shift) {
+  return ib ? (((key >> S) << S) | (key_code(key, S, ib) >> shift)) : (key >> shift);
+}
+
+__device__ __forceinline__ int cell_shift(const ClassView& cv, const CutGeom* __restrict__ cuts,
+                                          unsigned long long key, int S, int ib, int g) {
+  uint32_t i = key_inst(key, S, ib);
+  if (i >= cv.ninst) i = 0;
+  return g * cuts[i].k;
+}
+
+__global__ void k_cells_count(const unsigned long long* __restrict__ scode, ClassView cv, int g,
+                              const CutGeom* __restrict__ cuts, HashInfo* hi) {
+  const int S = cv.cls->S, ib = cv.cls->ib;
+  const uint32_t n = cv.N;
   uint32_t local = 0;
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    unsigned long long c = scode[p] >> sh;
-    local += (p == 0 || (scode[p - 1] >> sh) != c) ? 1u : 0u;
+    const unsigned long long key = scode[p];
+    const int sh = cell_shift(cv, cuts, key, S, ib, g);
+    const unsigned long long c = key_cell(key, S, ib, sh);
+    local += (p == 0 || key_cell(scode[p - 1], S, ib, sh) != c) ? 1u : 0u;
   }
   for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
-  if ((threadIdx.x & 31) == 0 && local) atomicAdd(&cut->m, local);
+  if ((threadIdx.x & 31) == 0 && local) atomicAdd(&hi->m, local);
 }
 
-__global__ void k_hash_size(CutGeom* cut, uint32_t hcap) {
-  uint32_t want = 2u * cut->m;
+__global__ void k_hash_size(HashInfo* hi, uint32_t hcap) {
+  uint32_t want = 2u * hi->m;
   uint32_t t = 16;
   while (t < want && t < hcap) t <<= 1;
-  cut->hmask = t - 1;
+  hi->hmask = t - 1;
 }
 
-__global__ void k_hash_clear(unsigned long long* __restrict__ hkeys, const CutGeom* __restrict__ cut) {
-  const uint32_t T = cut->hmask + 1;
+__global__ void k_hash_clear(unsigned long long* __restrict__ hkeys, const HashInfo* __restrict__ hi) {
+  const uint32_t T = hi->hmask + 1;
   for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h < T; h += gridDim.x * blockDim.x)
     hkeys[h] = kEmpty;
 }
 
 // The first point of a cell records its start, the last its end; both find
 // the same slot by probing with compare-and-swap on the key.
-__global__ void k_hash_insert(const unsigned long long* __restrict__ scode, uint32_t n,
-                              const GridGeom* __restrict__ geom, const CutGeom* __restrict__ cut,
+__global__ void k_hash_insert(const unsigned long long* __restrict__ scode, ClassView cv, int g,
+                              const CutGeom* __restrict__ cuts, const HashInfo* __restrict__ hi,
                               unsigned long long* hkeys, uint2* hvals) {
-  const int sh = geom->g * cut->k;
-  const uint32_t mask = cut->hmask;
+  const int S = cv.cls->S, ib = cv.cls->ib;
+  const uint32_t n = cv.N;
+  const uint32_t mask = hi->hmask;
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    unsigned long long c = scode[p] >> sh;
-    bool first = (p == 0) || ((scode[p - 1] >> sh) != c);
-    bool last = (p == n - 1) || ((scode[p + 1] >> sh) != c);
+    const unsigned long long key = scode[p];
+    const int sh = cell_shift(cv, cuts, key, S, ib, g);
+    const unsigned long long c = key_cell(key, S, ib, sh);
+    const bool first = (p == 0) || (key_cell(scode[p - 1], S, ib, sh) != c);
+    const bool last = (p == n - 1) || (key_cell(scode[p + 1], S, ib, sh) != c);
     if (!first && !last) continue;
     uint32_t h = hash_slot(c, mask);
     bool placed = false;
@@ -307,7 +368,21 @@ __global__ void k_hash_insert(const unsigned long long* __restrict__ scode, uint
       }
       h = (h + 1) & mask;
     }
-    if (!placed) set_status(geom->status, kStatusHashFull);
+    if (!placed) set_status(cv.cls->status, kStatusHashFull);
+  }
+}
+
+// Chunk tables of a multi-instance class: block b writes the chunks of
+// instance b (grid-stride over instances).
+__global__ void k_chunks(const InstDev* __restrict__ inst, uint32_t ninst, uint32_t* chunk_inst,
+                         uint32_t* chunk_pos) {
+  for (uint32_t i = blockIdx.x; i < ninst; i += gridDim.x) {
+    const InstDev I = inst[i];
+    const uint32_t nc = (I.n + 31) / 32;
+    for (uint32_t j = threadIdx.x; j < nc; j += blockDim.x) {
+      chunk_inst[I.chunk0 + j] = i;
+      chunk_pos[I.chunk0 + j] = I.start + 32 * j;
+    }
   }
 }
 
@@ -351,86 +426,86 @@ CutHost make_cut_host(double d_cut, int dp) {
   return h;
 }
 
-void launch_geom_init(GridGeom* geom, int* status, int g, cudaStream_t st) {
-  k_geom_init<<<1, 1, 0, st>>>(geom, status, g);
+void launch_class_init(const ClassView& cv, int g, int ib, int bcap, int* status, cudaStream_t st) {
+  k_class_init<<<grid_for(cv.ninst), kThreads, 0, st>>>(cv, g, ib, bcap, status);
   count_launches(1);
 }
 
-void launch_bbox(const void* pts, int dtype, uint32_t n, int d, int g, GridGeom* geom,
-                 cudaStream_t st) {
-  if (n == 0) return;
-  unsigned grid = grid_for((uint64_t)n * d);
+void launch_chunks(const ClassView& cv, uint32_t* chunk_inst, uint32_t* chunk_pos, cudaStream_t st) {
+  if (!cv.inst || cv.ninst == 0) return;
+  k_chunks<<<grid_for(cv.ninst, 1, 152u * 16u), 128, 0, st>>>(cv.inst, cv.ninst, chunk_inst, chunk_pos);
+  count_launches(1);
+}
+
+void launch_bbox(const void* pts, int dtype, const ClassView& cv, int g, cudaStream_t st) {
+  if (cv.N == 0) return;
+  const unsigned grid = grid_for((uint64_t)cv.nchunk * 32u, kThreads, 152u * 4u);
   if (dtype == 0)
-    k_bbox<int32_t><<<grid, kThreads, 0, st>>>((const int32_t*)pts, n, d, g, geom);
+    k_bbox<int32_t><<<grid, kThreads, 0, st>>>((const int32_t*)pts, cv, g);
   else
-    k_bbox<float><<<grid, kThreads, 0, st>>>((const float*)pts, n, d, g, geom);
+    k_bbox<float><<<grid, kThreads, 0, st>>>((const float*)pts, cv, g);
   count_launches(1);
 }
 
-void launch_setup(GridGeom* geom, CutGeom* cuts, const CutHost* host_cuts, int ncut,
-                  cudaStream_t st) {
-  double dcmin = INFINITY;
-  for (int c = 0; c < ncut; ++c) dcmin = fmin(dcmin, host_cuts[c].dc);
-  k_setup_geom<<<1, 32, 0, st>>>(geom, dcmin);
-  for (int c0 = 0; c0 < ncut; c0 += kCutChunk) {
-    CutArgs a;
-    int m = ncut - c0 < kCutChunk ? ncut - c0 : kCutChunk;
-    for (int c = 0; c < m; ++c) a.h[c] = host_cuts[c0 + c];
-    k_setup_cuts<<<1, 32, 0, st>>>(geom, cuts + c0, m, a);
-    count_launches(1);
-  }
-  count_launches(1);
+void launch_setup(const ClassView& cv, CutGeom* cuts, int ncut, const CutHost* hc_dev,
+                  const CutHost* hc_host, cudaStream_t st) {
+  CutArgs a;
+  if (!hc_dev)
+    for (int c = 0; c < ncut && c < kCutChunk; ++c) a.h[c] = hc_host[c];
+  k_setup_geom<<<grid_for(cv.ninst), kThreads, 0, st>>>(cv, ncut, hc_dev, a);
+  k_setup_cuts<<<grid_for((uint64_t)cv.ninst * ncut), kThreads, 0, st>>>(cv, cuts, ncut, hc_dev, a);
+  count_launches(2);
 }
 
 template <typename T>
-static void codes_t(const T* pts, uint32_t n, int d, const GridGeom* geom,
-                    unsigned long long* codes, uint32_t* ids, cudaStream_t st) {
-  unsigned grid = grid_for(n);
-  int g = d < 3 ? d : 3;
-  if (g == 1) k_codes<T, 1><<<grid, kThreads, 0, st>>>(pts, n, d, geom, codes, ids);
-  else if (g == 2) k_codes<T, 2><<<grid, kThreads, 0, st>>>(pts, n, d, geom, codes, ids);
-  else k_codes<T, 3><<<grid, kThreads, 0, st>>>(pts, n, d, geom, codes, ids);
+static void codes_t(const T* pts, const ClassView& cv, int g, unsigned long long* codes,
+                    uint32_t* ids, cudaStream_t st) {
+  const unsigned grid = grid_for((uint64_t)cv.nchunk * 32u);
+  if (g == 1) k_codes<T, 1><<<grid, kThreads, 0, st>>>(pts, cv, codes, ids);
+  else if (g == 2) k_codes<T, 2><<<grid, kThreads, 0, st>>>(pts, cv, codes, ids);
+  else k_codes<T, 3><<<grid, kThreads, 0, st>>>(pts, cv, codes, ids);
   count_launches(1);
 }
 
-void launch_codes(const void* pts, int dtype, uint32_t n, int d, const GridGeom* geom,
-                  unsigned long long* codes, uint32_t* ids, cudaStream_t st) {
-  if (n == 0) return;
-  if (dtype == 0) codes_t((const int32_t*)pts, n, d, geom, codes, ids, st);
-  else codes_t((const float*)pts, n, d, geom, codes, ids, st);
+void launch_codes(const void* pts, int dtype, const ClassView& cv, int g, unsigned long long* codes,
+                  uint32_t* ids, cudaStream_t st) {
+  if (cv.N == 0) return;
+  if (dtype == 0) codes_t((const int32_t*)pts, cv, g, codes, ids, st);
+  else codes_t((const float*)pts, cv, g, codes, ids, st);
 }
 
 template <typename T>
-static void gather_t(const T* pts, uint32_t n, int d, int dp, const GridGeom* geom,
-                     const unsigned long long* ca, const unsigned long long* cb, const uint32_t* ia,
-                     const uint32_t* ib, float* spts, unsigned long long* scode, uint32_t* sid,
-                     cudaStream_t st) {
-  unsigned grid = grid_for(n);
-  if (dp == 2) k_gather<T, 2><<<grid, kThreads, 0, st>>>(pts, n, d, geom, ca, cb, ia, ib, spts, scode, sid);
-  else if (dp == 4) k_gather<T, 4><<<grid, kThreads, 0, st>>>(pts, n, d, geom, ca, cb, ia, ib, spts, scode, sid);
-  else k_gather<T, 8><<<grid, kThreads, 0, st>>>(pts, n, d, geom, ca, cb, ia, ib, spts, scode, sid);
+static void gather_t(const T* pts, const ClassView& cv, int dp, const unsigned long long* ca,
+                     const unsigned long long* cb, const uint32_t* ia, const uint32_t* ib,
+                     float* spts, unsigned long long* scode, uint32_t* sid, cudaStream_t st) {
+  const unsigned grid = grid_for(cv.N);
+  if (dp == 2) k_gather<T, 2><<<grid, kThreads, 0, st>>>(pts, cv, ca, cb, ia, ib, spts, scode, sid);
+  else if (dp == 4) k_gather<T, 4><<<grid, kThreads, 0, st>>>(pts, cv, ca, cb, ia, ib, spts, scode, sid);
+  else k_gather<T, 8><<<grid, kThreads, 0, st>>>(pts, cv, ca, cb, ia, ib, spts, scode, sid);
   count_launches(1);
 }
 
-void launch_gather(const void* pts, int dtype, uint32_t n, int d, int dp, const GridGeom* geom,
+void launch_gather(const void* pts, int dtype, const ClassView& cv, int dp,
                    const unsigned long long* codes_a, const unsigned long long* codes_b,
                    const uint32_t* ids_a, const uint32_t* ids_b, float* spts,
                    unsigned long long* scode, uint32_t* sid, cudaStream_t st) {
-  if (n == 0) return;
+  if (cv.N == 0) return;
   if (dtype == 0)
-    gather_t((const int32_t*)pts, n, d, dp, geom, codes_a, codes_b, ids_a, ids_b, spts, scode, sid, st);
+    gather_t((const int32_t*)pts, cv, dp, codes_a, codes_b, ids_a, ids_b, spts, scode, sid, st);
   else
-    gather_t((const float*)pts, n, d, dp, geom, codes_a, codes_b, ids_a, ids_b, spts, scode, sid, st);
+    gather_t((const float*)pts, cv, dp, codes_a, codes_b, ids_a, ids_b, spts, scode, sid, st);
 }
 
-void launch_cells(const unsigned long long* scode, uint32_t n, const GridGeom* geom, CutGeom* cut,
-                  unsigned long long* hkeys, uint2* hvals, uint32_t hcap, cudaStream_t st) {
-  if (n == 0) return;
-  unsigned grid = grid_for(n);
-  k_cells_count<<<grid, kThreads, 0, st>>>(scode, n, geom, cut);
-  k_hash_size<<<1, 1, 0, st>>>(cut, hcap);
-  k_hash_clear<<<grid_for(hcap), kThreads, 0, st>>>(hkeys, cut);
-  k_hash_insert<<<grid, kThreads, 0, st>>>(scode, n, geom, cut, hkeys, hvals);
+void launch_cells(const unsigned long long* scode, const ClassView& cv, int g, const CutGeom* cuts,
+                  HashInfo* hi, unsigned long long* hkeys, uint2* hvals, uint32_t hcap,
+                  cudaStream_t st) {
+  if (cv.N == 0) return;
+  const unsigned grid = grid_for(cv.N);
+  cudaMemsetAsync(hi, 0, sizeof(HashInfo), st);
+  k_cells_count<<<grid, kThreads, 0, st>>>(scode, cv, g, cuts, hi);
+  k_hash_size<<<1, 1, 0, st>>>(hi, hcap);
+  k_hash_clear<<<grid_for(hcap), kThreads, 0, st>>>(hkeys, hi);
+  k_hash_insert<<<grid, kThreads, 0, st>>>(scode, cv, g, cuts, hi, hkeys, hvals);
   count_launches(4);
 }
 

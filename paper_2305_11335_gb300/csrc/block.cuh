@@ -63,43 +63,6 @@ __device__ __forceinline__ bool make_union(const uint32_t* c0, bool active, int 
   return n <= kMaxUnion;
 }
 
-// Visit every non-empty cell of the union: visit(start, len, cell[G]) is
-// called by all lanes with the same arguments (warp-uniform).
-template <int G, typename Visit>
-__device__ __forceinline__ void for_union_cells(const Union<G>& u,
-                                                const unsigned long long* __restrict__ hkeys,
-                                                const uint2* __restrict__ hvals, uint32_t hmask,
-                                                uint32_t n, int lane, Visit visit) {
-  for (int base = 0; base < u.ncell; base += 32) {
-    const int o = base + lane;
-    uint32_t st = 0, len = 0;
-    uint32_t c[G];
-#pragma unroll
-    for (int a = 0; a < G; ++a) c[a] = 0;
-    if (o < u.ncell) {
-      int rem = o;
-#pragma unroll
-      for (int a = 0; a < G; ++a) {
-        const int q = div_small(rem, u.inv[a]);
-        c[a] = (uint32_t)(u.lo[a] + rem - q * u.w[a]);
-        rem = q;
-      }
-      const uint2 run = clip_run(hash_find(hkeys, hvals, hmask, morton<G>(c)), n);
-      st = run.x;
-      len = run.y - run.x;
-    }
-    unsigned mask = __ballot_sync(kFull, len > 0);
-    while (mask) {
-      const int j = __ffs(mask) - 1;
-      mask &= mask - 1;
-      uint32_t cj[G];
-#pragma unroll
-      for (int a = 0; a < G; ++a) cj[a] = __shfl_sync(kFull, c[a], j);
-      visit(__shfl_sync(kFull, st, j), __shfl_sync(kFull, len, j), cj);
-    }
-  }
-}
-
 // Per-warp shared-memory run table of a union: the non-empty cells in
 // order, each with its offset in the concatenated candidate list (pre), its
 // first sorted position (start) and its coordinates relative to the union
@@ -111,12 +74,14 @@ struct RunTable {
 };
 
 // Look the union's cells up (one per lane) and fill the run table; returns
-// the number of non-empty runs (warp-uniform).
+// the number of non-empty runs (warp-uniform).  hb is the instance field of
+// the hash keys (key_cell in binning.cu).
 template <int G>
 __device__ __forceinline__ int union_runs(const Union<G>& u,
                                           const unsigned long long* __restrict__ hkeys,
                                           const uint2* __restrict__ hvals, uint32_t hmask,
-                                          uint32_t n, int lane, RunTable& rt) {
+                                          unsigned long long hb, uint32_t n, int lane,
+                                          RunTable& rt) {
   const uint32_t lanemask_lt = (1u << lane) - 1u;
   int nr = 0;
   uint32_t total = 0;
@@ -134,7 +99,7 @@ __device__ __forceinline__ int union_runs(const Union<G>& u,
         rel |= r << (7 * a);
         rem = q;
       }
-      const uint2 run = clip_run(hash_find(hkeys, hvals, hmask, morton<G>(c)), n);
+      const uint2 run = clip_run(hash_find(hkeys, hvals, hmask, hb | morton<G>(c)), n);
       st = run.x;
       len = run.y - run.x;
     }

@@ -46,11 +46,16 @@ __device__ __noinline__ int2 band_recount(const RunTable& rt, int nr, const Unio
   return make_int2(in, seen);
 }
 
+// Resident blocks per SM the register budget must allow (shared memory
+// allows 10 of the 2-D and 5 of the wider blocks).
+template <int DP>
+constexpr int density_min_blocks() { return DP == 2 ? 7 : 5; }
+
 template <int DP, int G, bool F64>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, density_min_blocks<DP>())
 k_density(const float* __restrict__ spts, const unsigned long long* __restrict__ scode,
-          const uint32_t* __restrict__ sid, uint32_t n, const GridGeom* __restrict__ geom,
-          const CutGeom* __restrict__ cut, const unsigned long long* __restrict__ hkeys,
+          const uint32_t* __restrict__ sid, ClassView cv, const CutGeom* __restrict__ cuts,
+          const HashInfo* __restrict__ hi, const unsigned long long* __restrict__ hkeys,
           const uint2* __restrict__ hvals, int32_t* __restrict__ rho_out,
           unsigned long long* __restrict__ skey, Counters* ctr) {
   constexpr int kCap = density_cap<DP>();
@@ -60,30 +65,35 @@ k_density(const float* __restrict__ spts, const unsigned long long* __restrict__
   const int wib = threadIdx.x >> 5;
   float* wpts = s_pts + wib * kCap * DP;
   RunTable& rt = s_rt[wib];
-  const int k = cut->k;
-  const int R = cut->R;
-  const int shift = G * k;
-  const int cmax = (1 << (geom->B - k)) - 1;
-  const double dc2 = cut->dc2;
-  const float t_in = cut->t_in, t_out = cut->t_out;
-  const uint32_t hmask = cut->hmask;
+  const int S = cv.cls->S, ib = cv.cls->ib;
+  const uint32_t hmask = hi->hmask;
+  const uint32_t n = cv.N;
 
   unsigned long long band = 0;
-  const uint32_t nchunk = (n + 31) / 32;
-  for (uint32_t ch = blockIdx.x * kWarps + wib; ch < nchunk; ch += gridDim.x * kWarps) {
-    const uint32_t p = ch * 32 + lane;
-    const bool valid = p < n;
+  for (uint32_t ch = blockIdx.x * kWarps + wib; ch < cv.nchunk; ch += gridDim.x * kWarps) {
+    uint32_t inst, p0, end;
+    cv.chunk(ch, inst, p0, end);
+    const CutGeom& C = cuts[inst];
+    const int k = C.k;
+    const int R = C.R;
+    const int shift = G * k;
+    const int cmax = (1 << (cv.geom[inst].B - k)) - 1;
+    const double dc2 = C.dc2;
+    const float t_in = C.t_in, t_out = C.t_out;
+    const unsigned long long hb = ib ? ((unsigned long long)inst << S) : 0ull;
+    const uint32_t p = p0 + lane;
+    const bool valid = p < end;
     Pt<DP> me;
 #pragma unroll
     for (int a = 0; a < DP; ++a) me.x[a] = 0.f;
     if (valid) me = load_pt<DP>(spts, p);
-    const unsigned long long mycell = valid ? (scode[p] >> shift) : ~0ull;
+    const unsigned long long mycell = valid ? (key_code(scode[p], S, ib) >> shift) : ~0ull;
     uint32_t c0[G];
     unmorton<G>(valid ? mycell : 0ull, c0);
-    const int nvalid = (int)min(32u, n - ch * 32);
+    const int nvalid = (int)min(32u, end - p0);
     int32_t count = 0;
     for_groups<G>(mycell, c0, valid, valid, nvalid, R, cmax, lane, [&](bool act, const Union<G>& u) {
-      const int nr = union_runs<G>(u, hkeys, hvals, hmask, n, lane, rt);
+      const int nr = union_runs<G>(u, hkeys, hvals, hmask, hb, n, lane, rt);
       const uint32_t total = rt.pre[nr];
       for (uint32_t w0 = 0; w0 < total; w0 += kCap) {
         const uint32_t w1 = min(total, w0 + (uint32_t)kCap);
@@ -150,15 +160,15 @@ inline unsigned grid_for(uint64_t items, int per_block, unsigned cap) {
 
 template <int DP, int G>
 void density_dg(bool fp64, const float* spts, const unsigned long long* scode, const uint32_t* sid,
-                uint32_t n, const GridGeom* geom, const CutGeom* cut,
+                const ClassView& cv, const CutGeom* cuts, const HashInfo* hi,
                 const unsigned long long* hkeys, const uint2* hvals, int32_t* rho_out,
                 unsigned long long* skey, Counters* ctr, cudaStream_t st) {
-  const unsigned grid = grid_for((n + 31) / 32, kWarps, 152u * 64u);
+  const unsigned grid = grid_for(cv.nchunk, kWarps, 152u * 64u);
   if (fp64)
-    k_density<DP, G, true><<<grid, kThreads, 0, st>>>(spts, scode, sid, n, geom, cut, hkeys, hvals,
+    k_density<DP, G, true><<<grid, kThreads, 0, st>>>(spts, scode, sid, cv, cuts, hi, hkeys, hvals,
                                                       rho_out, skey, ctr);
   else
-    k_density<DP, G, false><<<grid, kThreads, 0, st>>>(spts, scode, sid, n, geom, cut, hkeys, hvals,
+    k_density<DP, G, false><<<grid, kThreads, 0, st>>>(spts, scode, sid, cv, cuts, hi, hkeys, hvals,
                                                        rho_out, skey, ctr);
   count_launches(1);
 }
@@ -166,14 +176,14 @@ void density_dg(bool fp64, const float* spts, const unsigned long long* scode, c
 }  // namespace
 
 void launch_density(int dp, int g, bool fp64, const float* spts, const unsigned long long* scode,
-                    const uint32_t* sid, uint32_t n, const GridGeom* geom, const CutGeom* cut,
-                    const unsigned long long* hkeys, const uint2* hvals, int32_t* rho_out,
-                    unsigned long long* skey, Counters* ctr, cudaStream_t st) {
-  if (n == 0) return;
-  if (g == 1) density_dg<2, 1>(fp64, spts, scode, sid, n, geom, cut, hkeys, hvals, rho_out, skey, ctr, st);
-  else if (g == 2) density_dg<2, 2>(fp64, spts, scode, sid, n, geom, cut, hkeys, hvals, rho_out, skey, ctr, st);
-  else if (dp == 4) density_dg<4, 3>(fp64, spts, scode, sid, n, geom, cut, hkeys, hvals, rho_out, skey, ctr, st);
-  else density_dg<8, 3>(fp64, spts, scode, sid, n, geom, cut, hkeys, hvals, rho_out, skey, ctr, st);
+                    const uint32_t* sid, const ClassView& cv, const CutGeom* cuts,
+                    const HashInfo* hi, const unsigned long long* hkeys, const uint2* hvals,
+                    int32_t* rho_out, unsigned long long* skey, Counters* ctr, cudaStream_t st) {
+  if (cv.N == 0) return;
+  if (g == 1) density_dg<2, 1>(fp64, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
+  else if (g == 2) density_dg<2, 2>(fp64, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
+  else if (dp == 4) density_dg<4, 3>(fp64, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
+  else density_dg<8, 3>(fp64, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
 }
 
 void launch_keys_from_rho(const int32_t* rho, const uint32_t* sid, uint32_t n,

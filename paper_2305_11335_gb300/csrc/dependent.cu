@@ -144,16 +144,18 @@ struct Min2 {
   }
 };
 
-// Coordinates of point `id` from the caller's input (the same float values the
-// sorted copy holds: int32 inputs are exact in float32 by the range check).
+// Coordinates of point `id` of the instance whose coordinates start at
+// element `coord` of the caller's input (the same float values the sorted copy
+// holds: int32 inputs are exact in float32 by the range check).
 template <int DP>
-__device__ __forceinline__ Pt<DP> input_pt(const void* __restrict__ pts, int dtype, int d, uint32_t id) {
+__device__ __forceinline__ Pt<DP> input_pt(const void* __restrict__ pts, int dtype, uint64_t coord,
+                                           int d, uint32_t id) {
   Pt<DP> p;
 #pragma unroll
   for (int a = 0; a < DP; ++a) {
     float v = 0.f;
     if (a < d) {
-      const size_t e = (size_t)id * d + a;
+      const size_t e = coord + (size_t)id * d + a;
       v = dtype == 0 ? (float)__ldg((const int32_t*)pts + e) : __ldg((const float*)pts + e);
     }
     p.x[a] = v;
@@ -164,11 +166,11 @@ __device__ __forceinline__ Pt<DP> input_pt(const void* __restrict__ pts, int dty
 template <int DP, int G, bool F64>
 __global__ void __launch_bounds__(kNearThreads)
 k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict__ scode,
-           const unsigned long long* __restrict__ skey, uint32_t n, int32_t rho_skip,
-           const void* __restrict__ pts, int dtype, int d,
-           const GridGeom* __restrict__ geom, const CutGeom* __restrict__ cut,
-           const unsigned long long* __restrict__ hkeys, const uint2* __restrict__ hvals,
-           int32_t* __restrict__ lambda, double* __restrict__ delta, FarQueue q, Counters* ctr) {
+           const unsigned long long* __restrict__ skey, ClassView cv, int32_t rho_skip,
+           const void* __restrict__ pts, int dtype, const CutGeom* __restrict__ cuts,
+           const HashInfo* __restrict__ hi, const unsigned long long* __restrict__ hkeys,
+           const uint2* __restrict__ hvals, int32_t* __restrict__ lambda,
+           double* __restrict__ delta, FarQueue q, Counters* ctr) {
   constexpr int kNearCap = DP == 8 ? 128 : 256;
   __shared__ __align__(16) float s_pts[kNearWarps * kNearCap * DP];
   __shared__ unsigned long long s_key[kNearWarps * kNearCap];
@@ -180,26 +182,33 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
   unsigned long long* wkey = s_key + wib * kNearCap;
   RunTable& rt = s_rt[wib];
   RunTable& rt2 = s_rt2[wib];
-  const float f2lo = geom->f2 * (1.f - 1e-5f);
-  const double inv_f = geom->inv_f;
-  double org[G];
-#pragma unroll
-  for (int a = 0; a < G; ++a) org[a] = geom->org[a];
-  const int k = cut->k;
-  const float cell_fine = (float)(1u << cut->k);
-  const int R = cut->R;
-  const int shift = G * k;
-  const int cmax = (1 << (geom->B - k)) - 1;
-  const uint32_t hmask = cut->hmask;
-  const float bmul = cut->band_mul, badd = cut->band_add;
-  const float far32 = cut->far32;
-  const double far64 = cut->far64;
+  const int S = cv.cls->S, ib = cv.cls->ib;
+  const uint32_t hmask = hi->hmask;
+  const uint32_t n = cv.N;
   const uint32_t lanemask_lt = (1u << lane) - 1u;
 
-  const uint32_t nchunk = (n + 31) / 32;
-  for (uint32_t ch = blockIdx.x * kNearWarps + wib; ch < nchunk; ch += gridDim.x * kNearWarps) {
-    const uint32_t p = ch * 32 + lane;
-    const bool valid = p < n;
+  for (uint32_t ch = blockIdx.x * kNearWarps + wib; ch < cv.nchunk; ch += gridDim.x * kNearWarps) {
+    uint32_t inst, p0, end;
+    cv.chunk(ch, inst, p0, end);
+    const InstDev I = cv.instance(inst);
+    const GridGeom* geom = cv.geom + inst;
+    const CutGeom& C = cuts[inst];
+    const float f2lo = geom->f2 * (1.f - 1e-5f);
+    const double inv_f = geom->inv_f;
+    double org[G];
+#pragma unroll
+    for (int a = 0; a < G; ++a) org[a] = geom->org[a];
+    const int k = C.k;
+    const float cell_fine = (float)(1u << k);
+    const int R = C.R;
+    const int shift = G * k;
+    const int cmax = (1 << (geom->B - k)) - 1;
+    const float bmul = C.band_mul, badd = C.band_add;
+    const float far32 = C.far32;
+    const double far64 = C.far64;
+    const unsigned long long hb = ib ? ((unsigned long long)inst << S) : 0ull;
+    const uint32_t p = p0 + lane;
+    const bool valid = p < end;
     Pt<DP> me;
 #pragma unroll
     for (int a = 0; a < DP; ++a) me.x[a] = 0.f;
@@ -208,11 +217,11 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
       me = load_pt<DP>(spts, p);
       K = skey[p];
     }
-    const unsigned long long mycell = valid ? (scode[p] >> shift) : ~0ull;
+    const unsigned long long mycell = valid ? (key_code(scode[p], S, ib) >> shift) : ~0ull;
     uint32_t c0[G];
     unmorton<G>(valid ? mycell : 0ull, c0);
     const bool skip = valid && (int32_t)(K >> 32) < rho_skip;
-    const int nvalid = (int)min(32u, n - ch * 32);
+    const int nvalid = (int)min(32u, end - p0);
     Min2 acc;
     acc.init();
     Exact acc64;
@@ -223,7 +232,7 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
     for (int a = 0; a < G; ++a) uq[a] = valid ? (float)(((double)me.x[a] - org[a]) * inv_f) : 0.f;
     for_groups<G>(mycell, c0, valid, valid && !skip, nvalid, R, cmax, lane,
                   [&](bool act, const Union<G>& u) {
-      const int nr = union_runs<G>(u, hkeys, hvals, hmask, n, lane, rt);
+      const int nr = union_runs<G>(u, hkeys, hvals, hmask, hb, n, lane, rt);
       // scan every run of a table, staged window by window
       auto scan = [&](const RunTable& tab, int nt) {
         const uint32_t total = tab.pre[nt];
@@ -299,7 +308,7 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
       if constexpr (F64) {
         settled = acc64.o != 0xffffffffu && acc64.s < far64;
         if (settled) {
-          lambda[id] = (int32_t)acc64.o;
+          lambda[id] = (int32_t)(acc64.o - (uint32_t)I.out);
           delta[id] = sqrt(acc64.s);
         }
       } else if (acc.o1 != 0xffffffffu) {
@@ -307,8 +316,9 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
         const float bnd = band_of(s1, bmul, badd);
         settled = bnd < far32 && acc.s2 > bnd;
         if (settled) {
-          lambda[id] = (int32_t)acc.o1;
-          delta[id] = sqrt(dist64<DP>(me, input_pt<DP>(pts, dtype, d, acc.o1)));
+          const uint32_t o = acc.o1 - (uint32_t)I.out;
+          lambda[id] = (int32_t)o;
+          delta[id] = sqrt(dist64<DP>(me, input_pt<DP>(pts, dtype, I.coord, I.d, o)));
         }
       }
     } else if (valid) {
@@ -420,14 +430,23 @@ __device__ __noinline__ int tree_walk_from(const Node* __restrict__ nodes,
 template <int DP>
 struct FarQuery {
   uint32_t p, id;
+  uint32_t base;   // output index of the instance's point 0 (ids - base = local ids)
+  uint32_t root;   // the instance's subtree, kNoNode for a single point
   unsigned long long K;
   Pt<DP> xq;
   __device__ __forceinline__ void load(uint32_t pos, const float* __restrict__ spts,
-                                       const unsigned long long* __restrict__ skey) {
+                                       const unsigned long long* __restrict__ scode,
+                                       const unsigned long long* __restrict__ skey,
+                                       const ClassView& cv, const uint32_t* __restrict__ roots,
+                                       int S, int ib) {
     p = pos;
     K = skey[p];
     id = key_id(K);
     xq = load_pt<DP>(spts, p);
+    uint32_t inst = key_inst(scode[p], S, ib);
+    if (inst >= cv.ninst) inst = 0;
+    base = (uint32_t)cv.instance(inst).out;
+    root = roots[inst];
   }
 };
 
@@ -437,12 +456,16 @@ struct FarQuery {
 // found so far, which bounds their search there.
 template <int DP, bool F64>
 __global__ void __launch_bounds__(kFarThreads)
-k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__ skey, uint32_t n,
-          const GridGeom* __restrict__ geom, const CutGeom* __restrict__ cut,
-          const Node* __restrict__ nodes, const float* __restrict__ nbox, FarQueue q,
+k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__ scode,
+          const unsigned long long* __restrict__ skey, ClassView cv,
+          const CutGeom* __restrict__ cuts, const Node* __restrict__ nodes,
+          const float* __restrict__ nbox, const uint32_t* __restrict__ roots, FarQueue q,
           int32_t* __restrict__ lambda, double* __restrict__ delta, Counters* ctr) {
   const uint32_t qn = ctr->queue_n;
-  const float bmul = cut->band_mul, badd = cut->band_add;
+  const uint32_t n = cv.N;
+  const int S = cv.cls->S, ib = cv.cls->ib;
+  // the band depends only on DP, the same for every instance of the class
+  const float bmul = cuts[0].band_mul, badd = cuts[0].band_add;
   const uint32_t lanemask_lt = (1u << (threadIdx.x & 31)) - 1u;
   unsigned long long rescans = 0, expanded_sum = 0;
   uint32_t expanded_max = 0;
@@ -454,8 +477,8 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
     uint32_t expanded = 0;
     FarQuery<DP> fq;
     if (e < qn) {
-      fq.load(q.pos[e], spts, skey);
-      if (n < 2) {
+      fq.load(q.pos[e], spts, scode, skey, cv, roots, S, ib);
+      if (fq.root == kNoNode) {
         lambda[fq.id] = -1;
         delta[fq.id] = INFINITY;
       } else if constexpr (F64) {
@@ -463,7 +486,7 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
         best.init();
         const double s_init = q.s1d[e];
         const int r = tree_walk_from<DP>(
-            nodes, nbox, n, skey, fq.K, fq.xq, 0u, kFarBudget, expanded,
+            nodes, nbox, n, skey, fq.K, fq.xq, fq.root, kFarBudget, expanded,
             [&](float lbs) { return (double)lbs > fmin(best.s1, s_init); },
             [&](uint32_t t, unsigned long long kt) {
               best.add(dist64<DP>(fq.xq, load_pt<DP>(spts, t)), key_id(kt), t);
@@ -476,7 +499,7 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
           lambda[fq.id] = -1;
           delta[fq.id] = INFINITY;
         } else {
-          lambda[fq.id] = (int32_t)best.o1;
+          lambda[fq.id] = (int32_t)(best.o1 - fq.base);
           delta[fq.id] = sqrt(best.s1);
         }
       } else {
@@ -484,7 +507,7 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
         best.init();
         const float s_init = q.s1[e];
         const int r = tree_walk_from<DP>(
-            nodes, nbox, n, skey, fq.K, fq.xq, 0u, kFarBudget, expanded,
+            nodes, nbox, n, skey, fq.K, fq.xq, fq.root, kFarBudget, expanded,
             [&](float lbs) { return beyond(lbs, band_of(fminf(best.s1, s_init), bmul, badd)); },
             [&](uint32_t t, unsigned long long kt) {
               best.add(dist32<DP>(fq.xq, load_pt<DP>(spts, t)), key_id(kt), t);
@@ -504,7 +527,7 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
             ++rescans;
             uint32_t more = 0;
             bad |= tree_walk_from<DP>(
-                       nodes, nbox, n, skey, fq.K, fq.xq, 0u, 0xffffffffu, more,
+                       nodes, nbox, n, skey, fq.K, fq.xq, fq.root, 0xffffffffu, more,
                        [&](float lbs) { return beyond(lbs, b); },
                        [&](uint32_t t, unsigned long long kt) {
                          const Pt<DP> x = load_pt<DP>(spts, t);
@@ -514,7 +537,7 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
           } else {
             ex.add(dist64<DP>(fq.xq, load_pt<DP>(spts, best.t1)), best.o1);
           }
-          lambda[fq.id] = (int32_t)ex.o;
+          lambda[fq.id] = (int32_t)(ex.o - fq.base);
           delta[fq.id] = sqrt(ex.s);
         }
       }
@@ -532,7 +555,7 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
       else q.s1_2[slot] = (float)s_next;
     }
   }
-  if (bad) set_status(geom->status, kStatusStack);
+  if (bad) set_status(cv.cls->status, kStatusStack);
   for (int o = 16; o > 0; o >>= 1) {
     rescans += __shfl_xor_sync(kFull, rescans, o);
     expanded_sum += __shfl_xor_sync(kFull, expanded_sum, o);
@@ -554,9 +577,10 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
 // searched by their lane alone.
 template <int DP, bool F64>
 __global__ void __launch_bounds__(kFarThreads)
-k_dep_far_wide(const float* __restrict__ spts, const unsigned long long* __restrict__ skey,
-               uint32_t n, const GridGeom* __restrict__ geom, const CutGeom* __restrict__ cut,
-               const Node* __restrict__ nodes, const float* __restrict__ nbox, FarQueue q,
+k_dep_far_wide(const float* __restrict__ spts, const unsigned long long* __restrict__ scode,
+               const unsigned long long* __restrict__ skey, ClassView cv,
+               const CutGeom* __restrict__ cuts, const Node* __restrict__ nodes,
+               const float* __restrict__ nbox, const uint32_t* __restrict__ roots, FarQueue q,
                int32_t* __restrict__ lambda, double* __restrict__ delta, Counters* ctr) {
   constexpr int kWarpsPerBlock = kFarThreads / 32;
   __shared__ uint32_t s_stk[kWarpsPerBlock][kWarpStack];
@@ -566,19 +590,21 @@ k_dep_far_wide(const float* __restrict__ spts, const unsigned long long* __restr
   uint32_t* stk = s_stk[wib];
   float* stl = s_lb[wib];
   const uint32_t qn = ctr->queue2_n;
-  const float bmul = cut->band_mul, badd = cut->band_add;
+  const uint32_t n = cv.N;
+  const int S = cv.cls->S, ib = cv.cls->ib;
+  const float bmul = cuts[0].band_mul, badd = cuts[0].band_add;
   unsigned long long rescans = 0, expanded_sum = 0;
   uint32_t expanded_max = 0;
   bool bad = false;
   const uint32_t nwarps = gridDim.x * kWarpsPerBlock;
   for (uint32_t e = blockIdx.x * kWarpsPerBlock + wib; e < qn; e += nwarps) {
     FarQuery<DP> fq;
-    fq.load(q.pos2[e], spts, skey);
+    fq.load(q.pos2[e], spts, scode, skey, cv, roots, S, ib);
     uint32_t expanded = 0;
 
     auto search = [&](auto refresh, auto prune, auto visit) {
       if (lane == 0) {
-        stk[0] = 0u;
+        stk[0] = fq.root;
         stl[0] = 0.f;
       }
       int sp = 1;
@@ -671,7 +697,7 @@ k_dep_far_wide(const float* __restrict__ spts, const unsigned long long* __restr
           lambda[fq.id] = -1;
           delta[fq.id] = INFINITY;
         } else {
-          lambda[fq.id] = (int32_t)best.o1;
+          lambda[fq.id] = (int32_t)(best.o1 - fq.base);
           delta[fq.id] = sqrt(best.s1);
         }
       }
@@ -713,7 +739,7 @@ k_dep_far_wide(const float* __restrict__ spts, const unsigned long long* __restr
           ex.add(dist64<DP>(fq.xq, load_pt<DP>(spts, best.t1)), best.o1);
         }
         if (lane == 0) {
-          lambda[fq.id] = (int32_t)ex.o;
+          lambda[fq.id] = (int32_t)(ex.o - fq.base);
           delta[fq.id] = sqrt(ex.s);
         }
       }
@@ -724,7 +750,7 @@ k_dep_far_wide(const float* __restrict__ spts, const unsigned long long* __restr
     for (int o = 16; o > 0; o >>= 1) qexp += __shfl_xor_sync(kFull, qexp, o);
     expanded_max = max(expanded_max, qexp);
   }
-  if (__any_sync(kFull, bad) && lane == 0) set_status(geom->status, kStatusStack);
+  if (__any_sync(kFull, bad) && lane == 0) set_status(cv.cls->status, kStatusStack);
   for (int o = 16; o > 0; o >>= 1) expanded_sum += __shfl_xor_sync(kFull, expanded_sum, o);
   if (lane == 0) {
     if (rescans) atomicAdd(&ctr->exact_rescans, rescans);
@@ -748,68 +774,68 @@ inline unsigned grid_for(uint64_t items, int per_block, unsigned cap) {
 
 template <int DP, int G>
 void near_dg(bool fp64, const float* spts, const unsigned long long* scode,
-             const unsigned long long* skey, uint32_t n, int32_t rho_skip, const void* pts,
-             int dtype, int d, const GridGeom* geom,
-             const CutGeom* cut, const unsigned long long* hkeys, const uint2* hvals,
-             int32_t* lambda, double* delta, FarQueue q, Counters* ctr, cudaStream_t st) {
-  const unsigned grid = grid_for((n + 31) / 32, kNearWarps, 152u * 64u);
+             const unsigned long long* skey, const ClassView& cv, int32_t rho_skip,
+             const void* pts, int dtype, const CutGeom* cuts, const HashInfo* hi,
+             const unsigned long long* hkeys, const uint2* hvals, int32_t* lambda, double* delta,
+             FarQueue q, Counters* ctr, cudaStream_t st) {
+  const unsigned grid = grid_for(cv.nchunk, kNearWarps, 152u * 64u);
   if (fp64)
-    k_dep_near<DP, G, true><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, n, rho_skip, pts, dtype,
-                                                           d, geom, cut, hkeys, hvals, lambda, delta,
-                                                           q, ctr);
+    k_dep_near<DP, G, true><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, cv, rho_skip, pts,
+                                                           dtype, cuts, hi, hkeys, hvals, lambda,
+                                                           delta, q, ctr);
   else
-    k_dep_near<DP, G, false><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, n, rho_skip, pts,
-                                                            dtype, d, geom, cut, hkeys, hvals, lambda,
+    k_dep_near<DP, G, false><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, cv, rho_skip, pts,
+                                                            dtype, cuts, hi, hkeys, hvals, lambda,
                                                             delta, q, ctr);
 }
 
 template <int DP>
-void far_dp(bool fp64, const float* spts, const unsigned long long* skey, uint32_t n,
-            const GridGeom* geom, const CutGeom* cut, const Node* nodes, const float* nbox,
-            FarQueue q, int32_t* lambda, double* delta, Counters* ctr, uint32_t qcap,
-            cudaStream_t st) {
+void far_dp(bool fp64, const float* spts, const unsigned long long* scode,
+            const unsigned long long* skey, const ClassView& cv, const CutGeom* cuts,
+            const Node* nodes, const float* nbox, const uint32_t* root, FarQueue q,
+            int32_t* lambda, double* delta, Counters* ctr, cudaStream_t st) {
   // the queue length is known only on the device: launch enough threads for
   // a full SM load and let them stride over it
-  const unsigned grid = grid_for(qcap, kFarThreads, 152u * 8u);
-  const unsigned grid2 = grid_for(qcap, kFarThreads / 32, 152u * 16u);
+  const unsigned grid = grid_for(cv.N, kFarThreads, 152u * 8u);
+  const unsigned grid2 = grid_for(cv.N, kFarThreads / 32, 152u * 16u);
   if (fp64) {
-    k_dep_far<DP, true><<<grid, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, nbox, q,
-                                                      lambda, delta, ctr);
-    k_dep_far_wide<DP, true><<<grid2, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, nbox,
-                                                            q, lambda, delta, ctr);
+    k_dep_far<DP, true><<<grid, kFarThreads, 0, st>>>(spts, scode, skey, cv, cuts, nodes, nbox,
+                                                      root, q, lambda, delta, ctr);
+    k_dep_far_wide<DP, true><<<grid2, kFarThreads, 0, st>>>(spts, scode, skey, cv, cuts, nodes,
+                                                            nbox, root, q, lambda, delta, ctr);
   } else {
-    k_dep_far<DP, false><<<grid, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, nbox, q,
-                                                       lambda, delta, ctr);
-    k_dep_far_wide<DP, false><<<grid2, kFarThreads, 0, st>>>(spts, skey, n, geom, cut, nodes, nbox,
-                                                             q, lambda, delta, ctr);
+    k_dep_far<DP, false><<<grid, kFarThreads, 0, st>>>(spts, scode, skey, cv, cuts, nodes, nbox,
+                                                       root, q, lambda, delta, ctr);
+    k_dep_far_wide<DP, false><<<grid2, kFarThreads, 0, st>>>(spts, scode, skey, cv, cuts, nodes,
+                                                             nbox, root, q, lambda, delta, ctr);
   }
 }
 
 }  // namespace
 
 void launch_dep_near(int dp, int g, bool fp64, const float* spts, const unsigned long long* scode,
-                     const unsigned long long* skey, uint32_t n, int32_t rho_skip, const void* pts,
-                     int dtype, int d, const GridGeom* geom, const CutGeom* cut, const unsigned long long* hkeys,
-                     const uint2* hvals, int32_t* lambda, double* delta, FarQueue q,
-                     Counters* ctr, cudaStream_t st) {
-  if (n == 0) return;
+                     const unsigned long long* skey, const ClassView& cv, int32_t rho_skip,
+                     const void* pts, int dtype, const CutGeom* cuts, const HashInfo* hi,
+                     const unsigned long long* hkeys, const uint2* hvals, int32_t* lambda,
+                     double* delta, FarQueue q, Counters* ctr, cudaStream_t st) {
+  if (cv.N == 0) return;
   cudaMemsetAsync(&ctr->queue_n, 0, sizeof(unsigned int), st);
   cudaMemsetAsync(&ctr->queue2_n, 0, sizeof(unsigned int), st);
-  if (g == 1) near_dg<2, 1>(fp64, spts, scode, skey, n, rho_skip, pts, dtype, d, geom, cut, hkeys, hvals, lambda, delta, q, ctr, st);
-  else if (g == 2) near_dg<2, 2>(fp64, spts, scode, skey, n, rho_skip, pts, dtype, d, geom, cut, hkeys, hvals, lambda, delta, q, ctr, st);
-  else if (dp == 4) near_dg<4, 3>(fp64, spts, scode, skey, n, rho_skip, pts, dtype, d, geom, cut, hkeys, hvals, lambda, delta, q, ctr, st);
-  else near_dg<8, 3>(fp64, spts, scode, skey, n, rho_skip, pts, dtype, d, geom, cut, hkeys, hvals, lambda, delta, q, ctr, st);
+  if (g == 1) near_dg<2, 1>(fp64, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
+  else if (g == 2) near_dg<2, 2>(fp64, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
+  else if (dp == 4) near_dg<4, 3>(fp64, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
+  else near_dg<8, 3>(fp64, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
   count_launches(1);
 }
 
-void launch_dep_far(int dp, bool fp64, const float* spts, const unsigned long long* skey,
-                    uint32_t n, const GridGeom* geom, const CutGeom* cut, const Node* nodes,
-                    const float* nbox, FarQueue q, int32_t* lambda, double* delta, Counters* ctr,
-                    uint32_t qcap, cudaStream_t st) {
-  if (n == 0) return;
-  if (dp == 2) far_dp<2>(fp64, spts, skey, n, geom, cut, nodes, nbox, q, lambda, delta, ctr, qcap, st);
-  else if (dp == 4) far_dp<4>(fp64, spts, skey, n, geom, cut, nodes, nbox, q, lambda, delta, ctr, qcap, st);
-  else far_dp<8>(fp64, spts, skey, n, geom, cut, nodes, nbox, q, lambda, delta, ctr, qcap, st);
+void launch_dep_far(int dp, bool fp64, const float* spts, const unsigned long long* scode,
+                    const unsigned long long* skey, const ClassView& cv, const CutGeom* cuts,
+                    const Node* nodes, const float* nbox, const uint32_t* root, FarQueue q,
+                    int32_t* lambda, double* delta, Counters* ctr, cudaStream_t st) {
+  if (cv.N == 0) return;
+  if (dp == 2) far_dp<2>(fp64, spts, scode, skey, cv, cuts, nodes, nbox, root, q, lambda, delta, ctr, st);
+  else if (dp == 4) far_dp<4>(fp64, spts, scode, skey, cv, cuts, nodes, nbox, root, q, lambda, delta, ctr, st);
+  else far_dp<8>(fp64, spts, scode, skey, cv, cuts, nodes, nbox, root, q, lambda, delta, ctr, st);
   k_far_count<<<1, 1, 0, st>>>(ctr);
   count_launches(3);
 }

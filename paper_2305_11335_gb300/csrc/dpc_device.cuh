@@ -1,20 +1,31 @@
 // dpc_device.cuh -- device-side data structures and helpers shared by the
 // kernels of the exact DPC library (sm_103a).
 //
-// Layout in HBM for one instance of n points (see the kernels for who writes
-// what):
-//   codes      u64[n]   Morton code of the fine grid cell of each point
-//   spts       float[n][DP] points in Morton order, zero padded to DP = 2/4/8
-//   skey       u64[n]   order key of each sorted point, (rho << 32) | ~id
-//   hash       u64[T] keys + uint2[T] (start, end) of each occupied cell of
-//              the density grid level, open addressing, T a power of two
-//   tree       Node[n-1] binary radix tree over the sorted codes
+// Work is organised in classes: the instances of a batch that share the
+// padded dimension DP and the gridded dimension g are processed together, one
+// launch per kernel for the whole class.  Their points are concatenated
+// (instance i owns positions [start_i, start_i + n_i)) and sorted by the key
+// (i << S) | Morton code, so every instance stays a contiguous range of the
+// sorted order and each of its grid cells a contiguous run inside it.
 //
-// The grid: a fine uniform grid of 2^B cells per gridded axis (the first
-// g = min(d, 3) coordinates) covers the bounding box; a point's fine index is
-// floor((x - org) / f).  Level k of the grid merges 2^k fine cells per axis;
-// since the Morton code interleaves the axes, every level-k cell is the
-// contiguous run of sorted points sharing code >> (g*k).
+// Layout in HBM for one class of N points (see the kernels for who writes
+// what):
+//   codes      u64[N]   sort key of each point, (instance << S) | Morton code
+//   spts       float[N][DP] points in key order, zero padded to DP = 2/4/8
+//   sid        u32[N]   output index of each sorted point (the instance's
+//                       offset in the caller's arrays + its id there)
+//   skey       u64[N]   order key of each sorted point, (rho << 32) | ~sid
+//   hash       u64[T] keys + uint2[T] (start, end) of each occupied cell of
+//              the density grid level of every instance, open addressing
+//   tree       Node[N-1] binary radix tree over the sorted keys; instance i
+//              is the subtree below root[i]
+//
+// The grid of an instance: a fine uniform grid of 2^B cells per gridded axis
+// (the first g = min(d, 3) coordinates) covers its bounding box; a point's
+// fine index is floor((x - org) / f).  Level k of the grid merges 2^k fine
+// cells per axis; since the Morton code interleaves the axes, every level-k
+// cell is the contiguous run of sorted points sharing key >> (g*k) (the
+// instance field sits above every code bit).
 #pragma once
 
 #include <cstdint>
@@ -45,10 +56,83 @@ struct GridGeom {
   int g;             // gridded axes
   int B;             // fine-grid bits per axis
   int nbits;         // g * B
-  int npass;         // 8-bit radix passes needed to sort nbits-bit codes
   int* status;       // the workspace's device status word (kStatus* bits)
   uint32_t bbox_ord[6];  // ordered-uint min (0..2) and max (3..5) accumulators
 };
+
+// Per-class sort-key layout and status.
+struct ClassGeom {
+  int S;         // bit position of the instance field: max over instances of g*B
+  int ib;        // bits of the instance field (0 for a single instance)
+  int bcap;      // largest B allowed, so that the key stays below 2^63
+  int pad;
+  int* status;   // the workspace's device status word
+};
+
+// One instance of a class (device copy of the host's description).
+struct InstDev {
+  uint32_t start;      // first position of the instance in the class's arrays
+  uint32_t n;          // points
+  uint64_t out;        // offset of the instance in the caller's result arrays
+  uint64_t coord;      // element offset of its coordinates in the caller's pts
+  int32_t d;           // dimension
+  uint32_t chunk0;     // first 32-point chunk of the instance
+};
+
+// Labelling thresholds of one (instance, cutoff) (same layout as dpc_params).
+struct LabelParams {
+  int32_t rho_noise;
+  int32_t rho_min;
+  double delta_min;
+};
+
+constexpr uint32_t kNoNode = 0xffffffffu;  // no internal node (instance of one point)
+
+// Hash-table size of one class and cutoff.
+struct HashInfo {
+  uint32_t m;          // occupied cells (all instances)
+  uint32_t hmask;      // table size - 1
+};
+
+// What a kernel needs to know about the class it works on.  A chunk is up to
+// 32 consecutive positions of one instance; chunk c of a single-instance
+// class holds positions 32c .. 32c+31, so it needs no tables.
+struct ClassView {
+  uint32_t N;                     // points of the class
+  uint32_t ninst;                 // instances
+  uint32_t nchunk;                // chunks
+  const InstDev* inst;            // [ninst], or null for a single instance (`one`)
+  const uint32_t* chunk_inst;     // [nchunk] instance of each chunk (null: single)
+  const uint32_t* chunk_pos;      // [nchunk] first position of each chunk
+  InstDev one;                    // the single instance when inst is null
+  GridGeom* geom;                 // [ninst]
+  ClassGeom* cls;
+
+  __device__ __forceinline__ InstDev instance(uint32_t i) const { return inst ? inst[i] : one; }
+  // instance, first position and end of the instance's range for chunk c
+  __device__ __forceinline__ void chunk(uint32_t c, uint32_t& i, uint32_t& p0, uint32_t& end) const {
+    if (chunk_inst) {
+      i = chunk_inst[c];
+      p0 = chunk_pos[c];
+      const InstDev I = inst[i];
+      end = I.start + I.n;
+    } else {
+      i = 0;
+      p0 = c * 32u;
+      end = N;
+    }
+  }
+};
+
+// Instance field and Morton code of a sort key.
+__device__ __forceinline__ uint32_t key_inst(unsigned long long key, int S, int ib) {
+  return ib ? (uint32_t)(key >> S) : 0u;
+}
+__device__ __forceinline__ unsigned long long key_code(unsigned long long key, int S, int ib) {
+  return ib ? (key & ((1ull << S) - 1ull)) : key;
+}
+// 8-bit radix passes that sort keys of S + ib bits.
+__host__ __device__ __forceinline__ int sort_passes(int S, int ib) { return (S + ib + 7) / 8; }
 
 // Per (instance, cutoff) parameters.  Fields marked [host] are filled before
 // the launch; the others by the setup kernels.
@@ -82,13 +166,12 @@ struct Counters {
   unsigned int pad;
 };
 
-// One internal node of the binary radix tree over sorted Morton codes.
-struct __align__(16) Node {
+// One internal node of the binary radix tree over the sorted keys.
+struct __align__(8) Node {
   uint32_t left, right;   // child index; kLeafBit marks a leaf (sorted point)
   unsigned long long maxkey;  // largest order key in the subtree (per cutoff)
-  unsigned long long code;    // code of the first leaf of the node's range
-  uint32_t plen;          // length of the common code prefix, <= nbits
   uint32_t parent;        // parent internal node (root: itself)
+  uint32_t pad;
 };
 
 // ---------------------------------------------------------------------------

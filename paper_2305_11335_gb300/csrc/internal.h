@@ -1,4 +1,7 @@
 // internal.h -- host-side launchers of the library's kernels (not part of the ABI).
+//
+// Every launcher works on one class (dpc_device.cuh): the instances of a call
+// that share the padded dimension dp and the gridded dimension g.
 #pragma once
 
 #include <cstdint>
@@ -20,32 +23,46 @@ struct CutHost {
 };
 CutHost make_cut_host(double d_cut, int dp);
 
+// Cutoffs passed by value (single-instance calls that have no device copy).
+constexpr int kCutChunk = 16;
+struct CutArgs {
+  CutHost h[kCutChunk];
+};
+
 // ---- binning (binning.cu) ---------------------------------------------------
-void launch_geom_init(GridGeom* geom, int* status, int g, cudaStream_t st);
-void launch_bbox(const void* pts, int dtype, uint32_t n, int d, int g, GridGeom* geom,
-                 cudaStream_t st);
-void launch_setup(GridGeom* geom, CutGeom* cuts, const CutHost* host_cuts, int ncut,
-                  cudaStream_t st);
-void launch_codes(const void* pts, int dtype, uint32_t n, int d, const GridGeom* geom,
-                  unsigned long long* codes, uint32_t* ids, cudaStream_t st);
-void launch_gather(const void* pts, int dtype, uint32_t n, int d, int dp, const GridGeom* geom,
+void launch_class_init(const ClassView& cv, int g, int ib, int bcap, int* status, cudaStream_t st);
+// chunk tables of a multi-instance class (InstDev::chunk0 gives each instance's first chunk)
+void launch_chunks(const ClassView& cv, uint32_t* chunk_inst, uint32_t* chunk_pos, cudaStream_t st);
+void launch_bbox(const void* pts, int dtype, const ClassView& cv, int g, cudaStream_t st);
+// per-instance grid and per (instance, cutoff) parameters; cutoffs come from
+// hc_dev ([ninst][ncut], device) or, when it is null, from hc_host (ncut <= kCutChunk)
+void launch_setup(const ClassView& cv, CutGeom* cuts, int ncut, const CutHost* hc_dev,
+                  const CutHost* hc_host, cudaStream_t st);
+void launch_codes(const void* pts, int dtype, const ClassView& cv, int g, unsigned long long* codes,
+                  uint32_t* ids, cudaStream_t st);
+void launch_gather(const void* pts, int dtype, const ClassView& cv, int dp,
                    const unsigned long long* codes_a, const unsigned long long* codes_b,
                    const uint32_t* ids_a, const uint32_t* ids_b, float* spts,
                    unsigned long long* scode, uint32_t* sid, cudaStream_t st);
-void launch_cells(const unsigned long long* scode, uint32_t n, const GridGeom* geom, CutGeom* cut,
-                  unsigned long long* hkeys, uint2* hvals, uint32_t hcap, cudaStream_t st);
+// occupied level-k cells of every instance for one cutoff (cuts: [ninst]) -> hash
+void launch_cells(const unsigned long long* scode, const ClassView& cv, int g, const CutGeom* cuts,
+                  HashInfo* hi, unsigned long long* hkeys, uint2* hvals, uint32_t hcap,
+                  cudaStream_t st);
 
 // ---- radix sort (sort.cu) ------------------------------------------------------
 size_t sort_hist_words(uint32_t n);
 // Sorts (codes_a, ids_a) by code, LSD over the device-side pass count
-// geom->npass; the result lands in the _a buffers if npass is even, else _b.
+// sort_passes(cls->S, cls->ib); the result lands in the _a buffers if that
+// count is even, else in _b.
 void launch_sort(unsigned long long* codes_a, unsigned long long* codes_b, uint32_t* ids_a,
-                 uint32_t* ids_b, uint32_t n, const GridGeom* geom, uint32_t* hist,
+                 uint32_t* ids_b, uint32_t n, const ClassGeom* cls, uint32_t* hist,
                  cudaStream_t st);
 
 // ---- radix tree (tree.cu) ------------------------------------------------------
-void launch_tree_build(const unsigned long long* scode, uint32_t n, const GridGeom* geom,
-                       Node* nodes, uint32_t* leaf_parent, cudaStream_t st);
+// Tree over the class's sorted keys; root[i] = the internal node whose leaves
+// are exactly instance i (kNoNode for an instance of one point).
+void launch_tree_build(const unsigned long long* scode, const ClassView& cv, Node* nodes,
+                       uint32_t* leaf_parent, uint32_t* root, cudaStream_t st);
 // Largest order key of every subtree; with `boxes`, also every node's
 // bounding box over all dp coordinates into nbox ([lo(dp) | hi(dp)] floats per
 // node; the box depends only on the points, so once per binning suffices).
@@ -54,11 +71,13 @@ void launch_tree_maxkey(const unsigned long long* skey, const float* spts, int d
                         bool boxes, cudaStream_t st);
 
 // ---- density (density.cu) -------------------------------------------------------
+// rho of every point for one cutoff (cuts: [ninst]); rho_out is indexed by
+// output index (sid)
 void launch_density(int dp, int g, bool fp64, const float* spts, const unsigned long long* scode,
-                    const uint32_t* sid, uint32_t n, const GridGeom* geom, const CutGeom* cut,
-                    const unsigned long long* hkeys, const uint2* hvals, int32_t* rho_out,
-                    unsigned long long* skey, Counters* ctr, cudaStream_t st);
-// order keys of sorted points from densities given in original order
+                    const uint32_t* sid, const ClassView& cv, const CutGeom* cuts,
+                    const HashInfo* hi, const unsigned long long* hkeys, const uint2* hvals,
+                    int32_t* rho_out, unsigned long long* skey, Counters* ctr, cudaStream_t st);
+// order keys of sorted points from densities given by output index
 void launch_keys_from_rho(const int32_t* rho, const uint32_t* sid, uint32_t n,
                           unsigned long long* skey, cudaStream_t st);
 
@@ -71,20 +90,25 @@ struct FarQueue {
   float* s1_2;
   double* s1d2;
 };
+// lambda and delta are indexed by output index; lambda values are
+// instance-local ids
 void launch_dep_near(int dp, int g, bool fp64, const float* spts, const unsigned long long* scode,
-                     const unsigned long long* skey, uint32_t n, int32_t rho_skip, const void* pts,
-                     int dtype, int d, const GridGeom* geom, const CutGeom* cut, const unsigned long long* hkeys,
-                     const uint2* hvals, int32_t* lambda, double* delta, FarQueue q,
-                     Counters* ctr, cudaStream_t st);
-void launch_dep_far(int dp, bool fp64, const float* spts, const unsigned long long* skey,
-                    uint32_t n, const GridGeom* geom, const CutGeom* cut, const Node* nodes,
-                    const float* nbox, FarQueue q, int32_t* lambda, double* delta, Counters* ctr,
-                    uint32_t qcap, cudaStream_t st);
+                     const unsigned long long* skey, const ClassView& cv, int32_t rho_skip,
+                     const void* pts, int dtype, const CutGeom* cuts, const HashInfo* hi,
+                     const unsigned long long* hkeys, const uint2* hvals, int32_t* lambda,
+                     double* delta, FarQueue q, Counters* ctr, cudaStream_t st);
+void launch_dep_far(int dp, bool fp64, const float* spts, const unsigned long long* scode,
+                    const unsigned long long* skey, const ClassView& cv, const CutGeom* cuts,
+                    const Node* nodes, const float* nbox, const uint32_t* root, FarQueue q,
+                    int32_t* lambda, double* delta, Counters* ctr, cudaStream_t st);
 
 // ---- labels (labels.cu) -------------------------------------------------------------
 int label_rounds(uint32_t n);
-void launch_labels(const int32_t* rho, const int32_t* lambda, const double* delta, uint32_t n,
-                   int32_t rho_noise, int32_t rho_min, double delta_min, int32_t* label,
-                   int32_t* flags, GridGeom* geom, cudaStream_t st);
+// Labels of every point of the class for one cutoff (arrays indexed by output
+// index); params: [ninst] on the device, or null for a single instance (`one`);
+// nmax: the largest instance; flags needs label_rounds(nmax) + 1 ints.
+void launch_labels(const int32_t* rho, const int32_t* lambda, const double* delta,
+                   const ClassView& cv, uint32_t nmax, const LabelParams* params,
+                   LabelParams one, int32_t* label, int32_t* flags, cudaStream_t st);
 
 }  // namespace dpc

@@ -18,20 +18,42 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// par[i] = -1 (noise), i (center) or lambda_i (follows its dependent point).
+// Every point of the class once: f(inst, output index, instance).
+template <typename F>
+__device__ __forceinline__ void for_class_points(const ClassView& cv, F f) {
+  if (!cv.chunk_inst) {  // one instance: positions 0 .. N-1
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < cv.N; p += gridDim.x * blockDim.x)
+      f(0u, (int32_t)(cv.one.out + p), cv.one);
+    return;
+  }
+  const uint64_t total = (uint64_t)cv.nchunk * 32u;
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < total;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t inst, p0, end;
+    cv.chunk((uint32_t)(e >> 5), inst, p0, end);
+    const uint32_t p = p0 + (uint32_t)(e & 31u);
+    if (p >= end) continue;
+    const InstDev I = cv.instance(inst);
+    f(inst, (int32_t)(I.out + (p - I.start)), I);
+  }
+}
+
+// par[i] = -1 (noise), i (center) or lambda_i (follows its dependent point),
+// all as output indices.
 __global__ void k_label_init(const int32_t* __restrict__ rho, const int32_t* __restrict__ lambda,
-                             const double* __restrict__ delta, uint32_t n, int32_t rho_noise,
-                             int32_t rho_min, double delta_min, int32_t* __restrict__ par,
-                             int32_t* __restrict__ flags) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+                             const double* __restrict__ delta, ClassView cv,
+                             const LabelParams* __restrict__ params, LabelParams one,
+                             int32_t* __restrict__ par, int32_t* __restrict__ flags) {
+  for_class_points(cv, [&](uint32_t inst, int32_t i, const InstDev& I) {
+    const LabelParams P = params ? params[inst] : one;
     const int32_t r = rho[i];
     const int32_t l = lambda[i];
     int32_t v;
-    if (r < rho_noise) v = -1;                                        // Definition 4
-    else if (l < 0 || (r >= rho_min && delta[i] >= delta_min)) v = (int32_t)i;  // Definition 5
-    else v = (l < (int32_t)n) ? l : -1;
+    if (r < P.rho_noise) v = -1;                                             // Definition 4
+    else if (l < 0 || (r >= P.rho_min && delta[i] >= P.delta_min)) v = i;    // Definition 5
+    else v = (l < (int32_t)I.n) ? (int32_t)(I.out + (uint32_t)l) : -1;
     par[i] = v;
-  }
+  });
   if (blockIdx.x == 0 && threadIdx.x == 0) flags[0] = 1;  // round 0 always runs
 }
 
@@ -41,13 +63,13 @@ __global__ void k_label_init(const int32_t* __restrict__ rho, const int32_t* __r
 // first jump covers 2L and each further one at least L more, so a round
 // multiplies the covered distance by at least kJumps + 1.
 constexpr int kJumps = 8;
-__global__ void k_label_jump(int32_t* par, uint32_t n, int32_t* flags, int r) {
+__global__ void k_label_jump(int32_t* par, ClassView cv, int32_t* flags, int r) {
   if (flags[r - 1] == 0) return;  // the previous round changed nothing
   int changed = 0;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for_class_points(cv, [&](uint32_t, int32_t i, const InstDev&) {
     int32_t p = par[i];
-    if (p < 0 || p == (int32_t)i) continue;
-    int32_t p0 = p;
+    if (p < 0 || p == i) return;
+    const int32_t p0 = p;
 #pragma unroll 1
     for (int j = 0; j < kJumps; ++j) {
       const int32_t pp = par[p];
@@ -61,12 +83,20 @@ __global__ void k_label_jump(int32_t* par, uint32_t n, int32_t* flags, int r) {
       par[i] = p;
       changed = 1;
     }
-  }
+  });
   if (__syncthreads_or(changed) && threadIdx.x == 0) flags[r] = 1;
 }
 
-__global__ void k_label_check(const int32_t* __restrict__ flags, int last, GridGeom* geom) {
-  if (flags[last]) set_status(geom->status, kStatusCycle);
+// Output indices of the centers back to instance-local ids.
+__global__ void k_label_local(int32_t* par, ClassView cv) {
+  for_class_points(cv, [&](uint32_t, int32_t i, const InstDev& I) {
+    const int32_t v = par[i];
+    par[i] = v < 0 ? -1 : (int32_t)((uint32_t)v - (uint32_t)I.out);
+  });
+}
+
+__global__ void k_label_check(const int32_t* __restrict__ flags, int last, ClassGeom* cls) {
+  if (flags[last]) set_status(cls->status, kStatusCycle);
 }
 
 inline unsigned grid_for(uint64_t n) {
@@ -90,19 +120,19 @@ int label_rounds(uint32_t n) {
   return r + 2;
 }
 
-// `label` doubles as the pointer array; `flags` needs label_rounds(n) + 1 ints.
-void launch_labels(const int32_t* rho, const int32_t* lambda, const double* delta, uint32_t n,
-                   int32_t rho_noise, int32_t rho_min, double delta_min, int32_t* label,
-                   int32_t* flags, GridGeom* geom, cudaStream_t st) {
-  if (n == 0) return;
-  const int rounds = label_rounds(n);
+// `label` doubles as the pointer array; `flags` needs label_rounds(nmax) + 1 ints.
+void launch_labels(const int32_t* rho, const int32_t* lambda, const double* delta,
+                   const ClassView& cv, uint32_t nmax, const LabelParams* params,
+                   LabelParams one, int32_t* label, int32_t* flags, cudaStream_t st) {
+  if (cv.N == 0) return;
+  const int rounds = label_rounds(nmax);
   cudaMemsetAsync(flags, 0, sizeof(int32_t) * (rounds + 1), st);
-  const unsigned grid = grid_for(n);
-  k_label_init<<<grid, kThreads, 0, st>>>(rho, lambda, delta, n, rho_noise, rho_min, delta_min,
-                                          label, flags);
-  for (int r = 1; r <= rounds; ++r) k_label_jump<<<grid, kThreads, 0, st>>>(label, n, flags, r);
-  k_label_check<<<1, 1, 0, st>>>(flags, rounds, geom);
-  count_launches(rounds + 2);
+  const unsigned grid = grid_for((uint64_t)cv.nchunk * 32u);
+  k_label_init<<<grid, kThreads, 0, st>>>(rho, lambda, delta, cv, params, one, label, flags);
+  for (int r = 1; r <= rounds; ++r) k_label_jump<<<grid, kThreads, 0, st>>>(label, cv, flags, r);
+  k_label_local<<<grid, kThreads, 0, st>>>(label, cv);
+  k_label_check<<<1, 1, 0, st>>>(flags, rounds, cv.cls);
+  count_launches(rounds + 3);
 }
 
 }  // namespace dpc

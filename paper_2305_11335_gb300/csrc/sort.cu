@@ -7,9 +7,10 @@
 //   scatter stable rank of every item inside its tile (warp multi-split with
 //           __match_any_sync, warps in tile order), a shared-memory reorder,
 //           then coalesced runs to the global position
-// The number of passes (ceil(nbits / 8)) is known only on the device: passes
-// beyond it return at once, so the launch sequence is fixed and the result
-// lands in buffer (npass & 1).
+// The number of passes (ceil((S + ib) / 8) for keys of S + ib bits, see
+// ClassGeom) is known only on the device: passes beyond it return at once,
+// so the launch sequence is fixed and the result lands in buffer
+// (passes & 1).
 #include "internal.h"
 
 namespace dpc {
@@ -25,8 +26,8 @@ constexpr int kMaxPasses = 8;
 
 __global__ void __launch_bounds__(kRsThreads)
 k_rs_hist(const unsigned long long* __restrict__ keys, uint32_t n, int pass,
-          const GridGeom* __restrict__ geom, uint32_t* __restrict__ hist, uint32_t ntiles) {
-  if (pass >= geom->npass) return;
+          const ClassGeom* __restrict__ cls, uint32_t* __restrict__ hist, uint32_t ntiles) {
+  if (pass >= sort_passes(cls->S, cls->ib)) return;
   __shared__ uint32_t cnt[kRsWarps][256];
   for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&cnt[0][0])[i] = 0;
   __syncthreads();
@@ -50,8 +51,8 @@ k_rs_hist(const unsigned long long* __restrict__ keys, uint32_t n, int pass,
 // One block per digit: exclusive scan of that digit's per-tile counts; the
 // digit total goes to hist[256 * ntiles + digit].
 __global__ void __launch_bounds__(kRsThreads)
-k_rs_scan(uint32_t* __restrict__ hist, uint32_t ntiles, int pass, const GridGeom* __restrict__ geom) {
-  if (pass >= geom->npass) return;
+k_rs_scan(uint32_t* __restrict__ hist, uint32_t ntiles, int pass, const ClassGeom* __restrict__ cls) {
+  if (pass >= sort_passes(cls->S, cls->ib)) return;
   __shared__ uint32_t part[kRsThreads];
   const int d = blockIdx.x;
   uint32_t* row = hist + (size_t)d * ntiles;
@@ -89,9 +90,9 @@ struct ScatterSmem {
 __global__ void __launch_bounds__(kRsThreads)
 k_rs_scatter(const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin,
              unsigned long long* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t n,
-             int pass, const GridGeom* __restrict__ geom, const uint32_t* __restrict__ hist,
+             int pass, const ClassGeom* __restrict__ cls, const uint32_t* __restrict__ hist,
              uint32_t ntiles) {
-  if (pass >= geom->npass) return;
+  if (pass >= sort_passes(cls->S, cls->ib)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ScatterSmem& S = *reinterpret_cast<ScatterSmem*>(smem_raw);
   const int shift = 8 * pass;
@@ -175,7 +176,7 @@ k_rs_scatter(const unsigned long long* __restrict__ kin, const uint32_t* __restr
         S.keys[pos] = key[r];
         S.vals[pos] = val[r];
       } else {
-        set_status(geom->status, kStatusIndex);
+        set_status(cls->status, kStatusIndex);
       }
     }
   }
@@ -192,7 +193,7 @@ k_rs_scatter(const unsigned long long* __restrict__ kin, const uint32_t* __restr
       kout[dst] = k;
       vout[dst] = S.vals[pos];
     } else {
-      set_status(geom->status, kStatusIndex);
+      set_status(cls->status, kStatusIndex);
     }
   }
 }
@@ -204,7 +205,7 @@ inline uint32_t tiles_for(uint32_t n) { return (n + kRsTile - 1) / kRsTile; }
 size_t sort_hist_words(uint32_t n) { return (size_t)257 * (tiles_for(n) ? tiles_for(n) : 1); }
 
 void launch_sort(unsigned long long* codes_a, unsigned long long* codes_b, uint32_t* ids_a,
-                 uint32_t* ids_b, uint32_t n, const GridGeom* geom, uint32_t* hist,
+                 uint32_t* ids_b, uint32_t n, const ClassGeom* cls, uint32_t* hist,
                  cudaStream_t st) {
   if (n == 0) return;
   const uint32_t nt = tiles_for(n);
@@ -218,10 +219,10 @@ void launch_sort(unsigned long long* codes_a, unsigned long long* codes_b, uint3
   uint32_t* vb[2] = {ids_a, ids_b};
   for (int pass = 0; pass < kMaxPasses; ++pass) {
     const int i = pass & 1, o = (pass + 1) & 1;
-    k_rs_hist<<<nt, kRsThreads, 0, st>>>(kb[i], n, pass, geom, hist, nt);
-    k_rs_scan<<<256, kRsThreads, 0, st>>>(hist, nt, pass, geom);
+    k_rs_hist<<<nt, kRsThreads, 0, st>>>(kb[i], n, pass, cls, hist, nt);
+    k_rs_scan<<<256, kRsThreads, 0, st>>>(hist, nt, pass, cls);
     k_rs_scatter<<<nt, kRsThreads, sizeof(ScatterSmem), st>>>(kb[i], vb[i], kb[o], vb[o], n, pass,
-                                                              geom, hist, nt);
+                                                              cls, hist, nt);
   }
   count_launches(3 * kMaxPasses);
 }

@@ -6,6 +6,7 @@
 // there), hosts whose device memory is budgeted by their own allocator, and
 // latency-critical paths (cudaMalloc may synchronize the device).  The price
 // is a fixed maximum size and a single shared scratch area (see dpc.h).
+#include <cstring>
 #include <mutex>
 
 #include "../../include/dpc.h"
@@ -29,7 +30,9 @@ constexpr size_t kTiles = (kStaticN + 4095) / 4096;
 // Layout of the scratch array (byte offsets).
 constexpr size_t kOffGeom = 0;
 constexpr size_t kOffCut = kOffGeom + al(sizeof(GridGeom));
-constexpr size_t kOffCtr = kOffCut + al(sizeof(CutGeom));
+constexpr size_t kOffCls = kOffCut + al(sizeof(CutGeom));
+constexpr size_t kOffHash = kOffCls + al(sizeof(ClassGeom));
+constexpr size_t kOffCtr = kOffHash + al(sizeof(HashInfo));
 constexpr size_t kOffStatus = kOffCtr + al(sizeof(Counters));
 constexpr size_t kOffCodesA = kOffStatus + al(sizeof(int));
 constexpr size_t kOffCodesB = kOffCodesA + al(8 * kStaticN);
@@ -96,6 +99,8 @@ extern "C" int dpc_density_static(const void* pts, int dtype, int64_t n, int32_t
 
   GridGeom* geom = (GridGeom*)(base + kOffGeom);
   CutGeom* cut = (CutGeom*)(base + kOffCut);
+  ClassGeom* cls = (ClassGeom*)(base + kOffCls);
+  HashInfo* hinfo = (HashInfo*)(base + kOffHash);
   Counters* ctr = (Counters*)(base + kOffCtr);
   int* status = (int*)(base + kOffStatus);
   unsigned long long* codes_a = (unsigned long long*)(base + kOffCodesA);
@@ -118,14 +123,24 @@ extern "C" int dpc_density_static(const void* pts, int dtype, int64_t n, int32_t
   // accumulate (status, counters); every other buffer is fully rewritten
   cudaMemsetAsync(status, 0, sizeof(int), st);
   cudaMemsetAsync(ctr, 0, sizeof(Counters), st);
-  launch_geom_init(geom, status, g, st);
-  launch_bbox(pts, dtype, nn, d, g, geom, st);
-  launch_setup(geom, cut, &ch, 1, st);
-  launch_codes(pts, dtype, nn, d, geom, codes_a, ids_a, st);
-  launch_sort(codes_a, codes_b, ids_a, ids_b, nn, geom, hist, st);
-  launch_gather(pts, dtype, nn, d, dp, geom, codes_a, codes_b, ids_a, ids_b, spts, scode, sid, st);
-  launch_cells(scode, nn, geom, cut, hkeys, hvals, kStaticHash, st);
-  launch_density(dp, g, prec == DPC_PREC_FP64, spts, scode, sid, nn, geom, cut, hkeys, hvals, rho,
+  // one instance: a class without instance or chunk tables
+  ClassView cv;
+  memset(&cv, 0, sizeof(cv));
+  cv.N = nn;
+  cv.ninst = 1;
+  cv.nchunk = (nn + 31) / 32;
+  cv.one.n = nn;
+  cv.one.d = d;
+  cv.geom = geom;
+  cv.cls = cls;
+  launch_class_init(cv, g, 0, kMaxBits, status, st);
+  launch_bbox(pts, dtype, cv, g, st);
+  launch_setup(cv, cut, 1, nullptr, &ch, st);
+  launch_codes(pts, dtype, cv, g, codes_a, ids_a, st);
+  launch_sort(codes_a, codes_b, ids_a, ids_b, nn, cls, hist, st);
+  launch_gather(pts, dtype, cv, dp, codes_a, codes_b, ids_a, ids_b, spts, scode, sid, st);
+  launch_cells(scode, cv, g, cut, hinfo, hkeys, hvals, kStaticHash, st);
+  launch_density(dp, g, prec == DPC_PREC_FP64, spts, scode, sid, cv, cut, hinfo, hkeys, hvals, rho,
                  skey, ctr, st);
   if (cudaGetLastError() != cudaSuccess) return DPC_ERR_CUDA;
   if (flags & DPC_FLAG_SYNC_CHECK) {

@@ -8,7 +8,9 @@
 // parallel from the sorted codes, one internal node per thread (Karras, HPG
 // 2012); equal codes are split by their sorted position.  Its shape depends only
 // on the points, so it is built once per binning; the keys are recomputed for
-// every cutoff by one bottom-up pass.
+// every cutoff by one bottom-up pass.  One tree covers a whole class: the
+// instance field heads the sort key, so each instance's points are exactly
+// the leaves of one internal node (its root).
 #include "internal.h"
 
 namespace dpc {
@@ -27,10 +29,11 @@ __device__ __forceinline__ int prefix_len(const unsigned long long* __restrict__
   return 64 + __clz((int)((uint32_t)i ^ (uint32_t)j));
 }
 
-__global__ void k_tree_build(const unsigned long long* __restrict__ code, uint32_t n,
-                             const GridGeom* __restrict__ geom, Node* __restrict__ nodes,
-                             uint32_t* __restrict__ leaf_parent) {
-  const int nbits = geom->nbits;
+__global__ void k_tree_build(const unsigned long long* __restrict__ code, ClassView cv,
+                             Node* __restrict__ nodes, uint32_t* __restrict__ leaf_parent,
+                             uint32_t* __restrict__ root) {
+  const uint32_t n = cv.N;
+  const int S = cv.cls->S, ib = cv.cls->ib;
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t + 1 < n; t += gridDim.x * blockDim.x) {
     const int i = (int)t;
     const int dir = (prefix_len(code, n, i, i + 1) - prefix_len(code, n, i, i - 1)) >= 0 ? 1 : -1;
@@ -52,24 +55,21 @@ __global__ void k_tree_build(const unsigned long long* __restrict__ code, uint32
     const int gamma = i + split * dir + (dir < 0 ? -1 : 0);
     const int lo = i < j ? i : j;
     const int hi = i < j ? j : i;
-    Node nd;
-    nd.left = (lo == gamma) ? ((uint32_t)gamma | kLeafBit) : (uint32_t)gamma;
-    nd.right = (hi == gamma + 1) ? ((uint32_t)(gamma + 1) | kLeafBit) : (uint32_t)(gamma + 1);
-    nd.maxkey = 0ull;
-    nd.code = code[lo];
-    // prefix inside the nbits-bit code (the top 64 - nbits bits are always 0)
-    int pl = dnode - (64 - nbits);
-    nd.plen = (uint32_t)(pl < 0 ? 0 : (pl > nbits ? nbits : pl));
-    nd.parent = (uint32_t)i;  // root keeps itself; children overwrite below
-    nodes[i].left = nd.left;
-    nodes[i].right = nd.right;
-    nodes[i].maxkey = nd.maxkey;
-    nodes[i].code = nd.code;
-    nodes[i].plen = nd.plen;
-    if (nd.left & kLeafBit) leaf_parent[nd.left & ~kLeafBit] = (uint32_t)i;
-    else nodes[nd.left].parent = (uint32_t)i;
-    if (nd.right & kLeafBit) leaf_parent[nd.right & ~kLeafBit] = (uint32_t)i;
-    else nodes[nd.right].parent = (uint32_t)i;
+    const uint32_t left = (lo == gamma) ? ((uint32_t)gamma | kLeafBit) : (uint32_t)gamma;
+    const uint32_t right = (hi == gamma + 1) ? ((uint32_t)(gamma + 1) | kLeafBit) : (uint32_t)(gamma + 1);
+    nodes[i].left = left;
+    nodes[i].right = right;
+    nodes[i].maxkey = 0ull;
+    if (left & kLeafBit) leaf_parent[left & ~kLeafBit] = (uint32_t)i;
+    else nodes[left].parent = (uint32_t)i;
+    if (right & kLeafBit) leaf_parent[right & ~kLeafBit] = (uint32_t)i;
+    else nodes[right].parent = (uint32_t)i;
+    // the node whose leaves are exactly one instance is that instance's root
+    const uint32_t inst = key_inst(code[lo], S, ib);
+    if (inst < cv.ninst) {
+      const InstDev I = cv.instance(inst);
+      if ((uint32_t)lo == I.start && (uint32_t)hi + 1 == I.start + I.n) root[inst] = (uint32_t)i;
+    }
   }
 }
 
@@ -147,10 +147,11 @@ inline unsigned grid_for(uint64_t n) {
 
 }  // namespace
 
-void launch_tree_build(const unsigned long long* scode, uint32_t n, const GridGeom* geom,
-                       Node* nodes, uint32_t* leaf_parent, cudaStream_t st) {
-  if (n < 2) return;
-  k_tree_build<<<grid_for(n - 1), kThreads, 0, st>>>(scode, n, geom, nodes, leaf_parent);
+void launch_tree_build(const unsigned long long* scode, const ClassView& cv, Node* nodes,
+                       uint32_t* leaf_parent, uint32_t* root, cudaStream_t st) {
+  cudaMemsetAsync(root, 0xff, sizeof(uint32_t) * cv.ninst, st);
+  if (cv.N < 2) return;
+  k_tree_build<<<grid_for(cv.N - 1), kThreads, 0, st>>>(scode, cv, nodes, leaf_parent, root);
   k_root_parent<<<1, 1, 0, st>>>(nodes);
   count_launches(2);
 }

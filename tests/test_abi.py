@@ -73,6 +73,8 @@ def test_argument_errors_are_host_side(lib):
     assert _call_run(lib, b, params=dpc.make_params(b, 1, 1, math.nan)) == dpc.DPC_ERR_ARG
     big = dpc.Batch([0, 1 << 31], [2], [[1.0]])
     assert _call_run(lib, big) == dpc.DPC_ERR_OVERFLOW
+    big_total = dpc.Batch([0, 3 << 29, 6 << 29], [2, 3], [[1.0], [1.0]])  # each < 2^31, sum >= 2^31
+    assert _call_run(lib, big_total) == dpc.DPC_ERR_OVERFLOW
     bad_order = dpc.Batch([0, 5, 3], [2, 2], [[1.0], [1.0]])
     assert _call_run(lib, bad_order) == dpc.DPC_ERR_ARG
     p = ctypes.c_void_p(1)
