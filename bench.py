@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Exact-DPC throughput on GB300: points/s for rho + lambda/delta + labels.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1|c5]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1|c4|c5]
                     [--precision fp32|fp64] [--impl ours|reference]
 
 One step is one ``dpc_run`` call: binning, density, dependent points and
@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -53,7 +54,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fast", action="store_true", help="skip the fp64, e2e and CPU legs (profiling runs)")
@@ -62,7 +63,45 @@ def parse():
 
 
 def load_workload(name):
-    return {"c1": W.c1, "c2": W.c2, "c3": W.c3, "c5": W.c5}[name]()
+    return {"c1": W.c1, "c2": W.c2, "c3": W.c3, "c4": W.c4, "c5": W.c5}[name]()
+
+
+class Job:
+    """One workload as the library sees it: packed coordinates, the batch
+    descriptor arguments and the thresholds (single point sets are batches of
+    one instance)."""
+
+    def __init__(self, w):
+        self.w = w
+        self.name = w.name
+        if isinstance(w, W.BatchWorkload):
+            self.flat = w.flat
+            self.sizes, self.dims, self.coord_offset = list(w.sizes), list(w.dims), list(w.coord_offset)
+            self.d_cut = [list(r) for r in w.d_cut]
+        else:
+            self.flat = w.pts
+            self.sizes, self.dims, self.coord_offset = [w.n], [w.d], [0]
+            self.d_cut = [list(w.d_cut)]
+        self.rho_noise, self.rho_min, self.delta_min = w.rho_noise, w.rho_min, w.delta_min
+        self.n_dcut = len(self.d_cut[0])
+        self.N = int(sum(self.sizes))
+        self.pt_offset = [0]
+        for n in self.sizes:
+            self.pt_offset.append(self.pt_offset[-1] + n)
+
+    def instance(self, i):
+        o = self.coord_offset[i]
+        return np.asarray(self.flat[o:o + self.sizes[i] * self.dims[i]]).reshape(self.sizes[i], self.dims[i])
+
+    def config(self):
+        if len(self.sizes) == 1:
+            return {"workload": self.name, "n": self.N, "d": self.dims[0], "d_cut": self.d_cut[0],
+                    "rho_noise": self.rho_noise, "rho_min": self.rho_min, "delta_min": self.delta_min}
+        return {"workload": self.name, "instances": len(self.sizes), "points": self.N,
+                "d_counts": {str(d): self.dims.count(d) for d in sorted(set(self.dims))},
+                "n_range": [min(self.sizes), max(self.sizes)], "d_cuts_per_instance": self.n_dcut,
+                "thresholds": "per (instance, cutoff): rho_noise = rho_min = 2 x median rho, "
+                              "delta_min = 5 d_cut"}
 
 
 def peaks():
@@ -133,42 +172,54 @@ class ClockSampler:
 # the CPU oracle on a bounded sample
 
 
-def cpu_oracle_sample(pts, d_cuts, m, seed):
-    """rho, lambda and delta of m seeded sample points of the full workload,
-    evaluated from the definitions by the oracle.  Returns (points/s, seconds,
-    threads)."""
+def cpu_oracle_sample(job, m, seed):
+    """rho, lambda and delta of m seeded sample points of the full workload
+    (drawn over all points, so instances in proportion to their size), every
+    cutoff, evaluated from the definitions by the oracle.  Returns (points x
+    cutoffs / s, seconds, threads, sample size)."""
     import oracle
     rng = np.random.default_rng(seed)
-    idx = np.sort(rng.choice(pts.shape[0], size=min(m, pts.shape[0]), replace=False)).astype(np.int64)
+    m = min(m, job.N)
+    glob = np.sort(rng.choice(job.N, size=m, replace=False)).astype(np.int64)
+    inst = np.searchsorted(np.asarray(job.pt_offset), glob, side="right") - 1
     t0 = time.perf_counter()
-    for dc in d_cuts:
-        oracle.density(pts, dc, idx=idx)
-        oracle.dependent_at(pts, dc, idx, max_checks=256)
+    for i in np.unique(inst):
+        pts = job.instance(int(i))
+        idx = glob[inst == i] - job.pt_offset[int(i)]
+        for dc in job.d_cut[int(i)]:
+            oracle.density(pts, dc, idx=idx)
+            oracle.dependent_at(pts, dc, idx, max_checks=256)
     dt = time.perf_counter() - t0
-    return len(idx) * len(d_cuts) / dt, dt, oracle.threads()
+    return m * job.n_dcut / dt, dt, oracle.threads(), m
 
 
 # ---------------------------------------------------------------------------
-# roofline of one phase
+# roofline of the search kernels
 
-def phase_model(phase, w, out_rho):
-    """Algorithmic work of one launch of the density or near-dependent kernel:
-    per point the candidates of the 3^g block of cells of side d_cut, each
-    d subtractions and d multiply-adds (3d flops).  Defined for d <= 3, where
-    the grid covers every coordinate."""
-    n, d = w.n, w.d
-    g = min(d, 3)
-    if d > 3:
-        return None, None, None, ""
-    if phase == "density":
-        # candidates of the 3^g block at cell side d_cut per point:
-        # rho * 3^g / V_g (V_g = volume of the unit ball in g dims, times 2^g / 2^g),
-        # each d subtractions and d FMAs = 3d flops
-        vol = {1: 2.0, 2: np.pi, 3: 4.0 / 3.0 * np.pi}[g]
-        cand = float(out_rho.astype(np.float64).mean()) * (3.0 ** g) / vol
-        flops = n * cand * 3 * d
-        return "alu", flops, "TFLOP/s", "%d points x %.1f block candidates x %d flops" % (n, cand, 3 * d)
-    return None, None, None, ""
+
+def ball_volume(d):
+    return math.pi ** (d / 2.0) / math.gamma(d / 2.0 + 1.0)
+
+
+def block_work(job, rho_dev):
+    """Algorithmic flops of the density (or near-dependent) launches of one
+    step, summed over instances and cutoffs: per point, the candidates of the
+    3^d block of grid cells of side d_cut around it, rho * 3^d / V_d (V_d the
+    volume of the unit d-ball), each d subtractions and d multiply-adds
+    (3d flops).  For d > 3 this counts the candidates of an ideal grid over all
+    d coordinates, fewer than the library's 3-coordinate grid visits."""
+    import torch
+    po = torch.tensor(job.pt_offset, dtype=torch.int64, device=rho_dev.device)
+    factor = torch.tensor([3.0 ** d / ball_volume(d) * 3 * d for d in job.dims], dtype=torch.float64,
+                          device=rho_dev.device)
+    total = 0.0
+    for c in range(rho_dev.shape[0]):
+        cs = torch.cumsum(rho_dev[c].to(torch.float64), 0)
+        cs = torch.cat([torch.zeros(1, dtype=torch.float64, device=cs.device), cs])
+        per = cs[po[1:]] - cs[po[:-1]]
+        total += float((per * factor).sum().item())
+    mean_rho = float(rho_dev[0].to(torch.float64).mean().item()) if job.N else 0.0
+    return total, mean_rho
 
 
 def combine_ranks(total_ms, units_per_rank, steps, world, device=None):
@@ -213,19 +264,18 @@ def run_ours(args, rank, world, dev):
         _build.build()
     if world > 1:
         torch.distributed.barrier()
-    w = load_workload(args.workload)
-    n, d = w.n, w.d
-    batch = dpc.Batch.single(n, d, w.d_cut)
-    params = dpc.make_params(batch, w.rho_noise, w.rho_min, w.delta_min)
+    job = Job(load_workload(args.workload))
+    batch = dpc.Batch(job.pt_offset, job.dims, job.d_cut, coord_offset=job.coord_offset)
+    params = dpc.make_params(batch, job.rho_noise, job.rho_min, job.delta_min)
     stream = torch.cuda.current_stream()
-    pts = torch.from_numpy(w.pts).to(dev)
-    shape = (batch.n_dcut, n)
+    pts = torch.from_numpy(job.flat).to(dev)
+    shape = (batch.n_dcut, job.N)
     out = {"rho": torch.empty(shape, dtype=torch.int32, device=dev),
            "lam": torch.empty(shape, dtype=torch.int32, device=dev),
            "delta": torch.empty(shape, dtype=torch.float64, device=dev),
            "label": torch.empty(shape, dtype=torch.int32, device=dev)}
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    units = n * batch.n_dcut
+    units = job.N * batch.n_dcut
 
     def timed_steps(k, precision, phase_times):
         times, phases = [], {}
@@ -267,52 +317,53 @@ def run_ours(args, rank, world, dev):
     total_ms, value = combine_ranks(sum(times), units, args.steps, world, dev)
     ms_per_step = total_ms / args.steps
 
+    config = job.config()
+    config.update({"precision": args.precision, "l2": "flushed between steps (512 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"})
     res = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32 filter + f64 recheck" if args.precision == "fp32" else "f64",
            "data": "synthetic (seeded generator standing in for the paper's data sets)",
-           "config": {"workload": w.name, "n": n, "d": d, "d_cut": w.d_cut, "rho_noise": w.rho_noise,
-                      "rho_min": w.rho_min, "delta_min": w.delta_min, "precision": args.precision,
-                      "l2": "flushed between steps (512 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+           "config": config,
            "gpu_launches": int(stats["kernel_launches"]) * args.steps,
            "phases_ms": {p: round(v[0] / args.steps, 5) for p, v in phases.items()},
            "stats": {k: int(v) for k, v in stats.items()}}
     if rank != 0:
         return None
 
-    # roofline of the dominant kernel: the longest single-launch phase
-    rho_host = out["rho"].cpu().numpy()
+    # roofline of the dominant kernel (density or near-dependent, whichever
+    # takes longer): algorithmic flops per launch / CUDA-event time per launch
     pk, pk_kind = peaks()
     single = {p: v for p, v in phases.items() if p in ("density", "near", "far", "tree", "maxkey")}
     dom = max(single, key=lambda p: single[p][0]) if single else None
-    roof = None
     kernels = {"density": "k_density", "near": "k_dep_near"}
     model_phase = dom if dom in kernels else max(("density", "near"), key=lambda p: phases[p][0])
-    bound, work, unit, how = phase_model("density", w, rho_host)
-    if work is not None:
-        per_launch_ms = phases[model_phase][0] / phases[model_phase][1]
-        achieved = work / (per_launch_ms / 1e3) / 1e12
-        clk = pk.get("sm_max_mhz", 2070.0)
-        peak = SMS * FP32_LANES * 2 * clk * 1e6 / 1e12
-        roof = {"bound": bound, "kernel": kernels[model_phase], "achieved": achieved, "peak": peak,
-                "unit": unit, "frac": achieved / peak,
-                "traffic": load_traffic(kernels[model_phase], w.name),
-                "peak_source": "derived (no FP32 figure is measured): 152 SMs x 128 FP32 lanes x 2 flops x "
-                               "%.0f MHz max SM clock" % clk,
-                "work": how, "ms_per_launch": per_launch_ms}
-    res["roofline"] = roof
+    work, mean_rho = block_work(job, out["rho"])
+    launches = phases[model_phase][1]
+    per_launch_ms = phases[model_phase][0] / launches
+    achieved = work / (phases[model_phase][0] / 1e3) / 1e12
+    clk = pk.get("sm_max_mhz", 2070.0)
+    peak = SMS * FP32_LANES * 2 * clk * 1e6 / 1e12
+    res["roofline"] = {
+        "bound": "alu", "kernel": kernels[model_phase], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        "frac": achieved / peak, "traffic": load_traffic(kernels[model_phase], job.name),
+        "peak_source": "derived (no FP32 figure is measured): 152 SMs x 128 FP32 lanes x 2 flops x "
+                       "%.0f MHz max SM clock" % clk,
+        "work": "%.4g flops per step over %d launches: per point rho x 3^d / V_d block candidates x 3d flops "
+                "(mean rho %.1f at the first cutoff)" % (work, launches, mean_rho),
+        "ms_per_launch": per_launch_ms}
     res["dominant_phase"] = dom
 
     if not args.fast:
         # the plain FP64 path on the same workload
         other = "fp64" if args.precision == "fp32" else "fp32"
         dpc.dpc_run(pts, batch, params, precision=other, stream=stream, out=out, sync=True)
-        k2 = max(3, args.steps // 3)
+        k2 = max(1, min(max(3, args.steps // 3), int(20000.0 / max(1.0, ms_per_step * 10))))
         t2, _ = timed_steps(k2, other, False)
         res[other + "_path"] = {"value": units * k2 / (sum(t2) / 1e3), "ms_per_step": sum(t2) / k2,
                                 "steps": k2}
         # end to end through the host-buffer entry point
-        hp = torch.from_numpy(w.pts).pin_memory()
+        hp = torch.from_numpy(job.flat).pin_memory()
         hout = {"rho": torch.empty(shape, dtype=torch.int32).pin_memory(),
                 "lam": torch.empty(shape, dtype=torch.int32).pin_memory(),
                 "delta": torch.empty(shape, dtype=torch.float64).pin_memory(),
@@ -329,15 +380,15 @@ def run_ours(args, rank, world, dev):
             b.synchronize()
             te.append(a.elapsed_time(b))
         res["e2e"] = {"value": units / (statistics.mean(te) / 1e3), "unit": "points/s",
-                      "ms_per_step": statistics.mean(te), "h2d_bytes_per_step": int(w.pts.nbytes),
+                      "ms_per_step": statistics.mean(te), "h2d_bytes_per_step": int(job.flat.nbytes),
                       "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in hout.values())),
                       "api": "dpc_run_host"}
         # CPU oracle on a bounded sample
-        v, dt, th = cpu_oracle_sample(w.pts, w.d_cut, args.cpu_sample, 99)
+        v, dt, th, m = cpu_oracle_sample(job, args.cpu_sample, 99)
         res["cpu_baseline"] = {"value": v, "unit": "points/s", "cores": th, "kind": "oracle",
-                               "sample": "rho, lambda, delta of %d seeded sample points of the full %s "
-                                         "(O(n) each from the definitions, labels omitted), %.1f s wall"
-                                         % (min(args.cpu_sample, n), w.name, dt)}
+                               "sample": "rho, lambda, delta of %d seeded sample points of the full %s at "
+                                         "each of its %d cutoffs (O(n) each from the definitions, labels "
+                                         "omitted), %.1f s wall" % (m, job.name, job.n_dcut, dt)}
     res["clocks"] = clocks
     return res
 
@@ -345,25 +396,24 @@ def run_ours(args, rank, world, dev):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    w = load_workload(args.workload)
-    m = 512
+    job = Job(load_workload(args.workload))
+    m = max(16, 512 // job.n_dcut)
     for s in range(args.warmup):
-        cpu_oracle_sample(w.pts, w.d_cut, 64, 1000 + s)
-    vals, secs = [], []
+        cpu_oracle_sample(job, 16, 1000 + s)
+    secs = []
     th = 1
     for s in range(args.steps):
-        v, dt, th = cpu_oracle_sample(w.pts, w.d_cut, m, 2000 + s)
-        vals.append(v)
+        _, dt, th, m = cpu_oracle_sample(job, m, 2000 + s)
         secs.append(dt)
-    value = m * len(w.d_cut) * len(secs) / sum(secs)
+    value = m * job.n_dcut * len(secs) / sum(secs)
     ms = 1e3 * sum(secs) / len(secs)
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "n": w.n, "d": w.d, "d_cut": w.d_cut},
+            "config": job.config(),
             "cpu_baseline": {"kind": "oracle", "cores": th, "value": value,
-                             "sample": "%d seeded sample points of %s per step (rho, lambda, delta from the "
-                                       "definitions; labels omitted)" % (m, w.name)},
+                             "sample": "%d seeded sample points of %s per step, every cutoff (rho, lambda, "
+                                       "delta from the definitions; labels omitted)" % (m, job.name)},
             "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

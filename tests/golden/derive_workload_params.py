@@ -16,6 +16,10 @@ fixed d_cut = 30, Table 2):
 * c5: d_cut0 from the same 30th-nearest rule (2048 sample points); the sweep is
   d_cut0 * 1.25^k, k = 0..3, with rho_min = 2 x median density at each cutoff
   (1024 sample points).
+* c4 (``--c4``, written to ``tests/golden/c4_params.json``): per instance,
+  d_cut0 = the median distance to the 8th nearest point (self counted first)
+  over 1024 seeded sample points; rho_min = 2 x median density over 256
+  seeded sample points at each cutoff d_cut0 * 1.25^k, k = 0..7.
 
 Every number comes from ``oracle`` routines; nothing here runs the CUDA path.
 """
@@ -33,6 +37,7 @@ import oracle  # noqa: E402
 import workloads as W  # noqa: E402
 
 OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "workload_params.json")
+OUT_C4 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "c4_params.json")
 
 
 def sample(n, m, seed):
@@ -79,5 +84,27 @@ def main():
         f.write("\n")
 
 
+def main_c4():
+    t = time.time()
+    specs = W.c4_instance_specs()
+    d0, rmins = [], []
+    for i, s in enumerate(specs):
+        pts = W.c4_instance(s)
+        dc = kth_cut(pts, 8, 1024, 10_000 + i)
+        d0.append(dc)
+        rmins.append([int(round(2 * median_rho(pts, dc * 1.25 ** k, 20_000 + 8 * i + k, m=256)))
+                      for k in range(W.C4_NCUT)])
+        if i % 512 == 0:
+            print("c4", i, dc, rmins[-1], "%.1fs" % (time.time() - t), flush=True)
+    with open(OUT_C4, "w") as f:
+        json.dump({"_how": "tests/golden/derive_workload_params.py --c4 (CPU oracle only)",
+                   "d_cut0": d0, "rho_min": rmins}, f, separators=(",", ":"))
+        f.write("\n")
+    print("c4 done %.1fs" % (time.time() - t))
+
+
 if __name__ == "__main__":
-    main()
+    if "--c4" in sys.argv:
+        main_c4()
+    else:
+        main()

@@ -109,3 +109,42 @@ def test_c5_full_sweep():
         assert np.all(out["rho"][c] >= out["rho"][c - 1]) if c else True  # rho grows with d_cut
     check_samples(w, out, 0, 96, w.noise_ids[:16], 51, max_checks=24)
     check_samples(w, out, 3, 48, w.noise_ids[16:24], 52, max_checks=24)
+
+
+def test_c4_full_batch():
+    """The 4096-instance batch with 8 cutoffs each, in one dpc_run (the call
+    bench.py times).  The 8 smallest instances are compared with the oracle in
+    full for every cutoff; 40 random instances get the whole-instance
+    properties and sampled oracle checks at the first and last cutoff."""
+    from types import SimpleNamespace
+    from _gpu_util import assert_same
+
+    w = W.c4()
+    batch = dpc.Batch([0] + list(np.cumsum(w.sizes)), w.dims, w.d_cut, coord_offset=w.coord_offset)
+    params = dpc.make_params(batch, w.rho_noise, w.rho_min, w.delta_min)
+    out = dpc.dpc_run(torch.from_numpy(w.flat).cuda(), batch, params, sync=True)
+    po = batch.pt_offset
+    ncut = batch.n_dcut
+
+    def inst_out(i):
+        return {k: v[:, po[i]:po[i + 1]].cpu().numpy() for k, v in out.items()}
+
+    order = np.argsort(w.sizes, kind="stable")
+    for i in order[:8]:
+        got = inst_out(i)
+        pts = w.instance(i)
+        for c in range(ncut):
+            j = i * ncut + c
+            ref = oracle.run(pts, w.d_cut[i][c], w.rho_noise[j], w.rho_min[j], w.delta_min[j])
+            assert_same({k: v[c] for k, v in got.items()}, ref, "instance %d cut %d" % (i, c))
+    rng = np.random.default_rng(41)
+    for i in rng.choice(len(w.sizes), 40, replace=False):
+        got = inst_out(i)
+        view = SimpleNamespace(pts=w.instance(i), n=w.sizes[i], d_cut=w.d_cut[i],
+                               rho_noise=w.rho_noise[i * ncut:(i + 1) * ncut],
+                               rho_min=w.rho_min[i * ncut:(i + 1) * ncut],
+                               delta_min=w.delta_min[i * ncut:(i + 1) * ncut])
+        for c in (0, ncut - 1):
+            check_properties(view, got, c)
+            check_samples(view, got, c, 12, np.zeros(0, np.int64), 4100 + int(i), min_resolved=0.5,
+                          max_checks=32)

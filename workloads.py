@@ -34,6 +34,7 @@ import numpy as np
 
 _PARAMS_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
                             "workload_params.json")
+_C4_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "c4_params.json")
 
 
 @dataclass
@@ -199,6 +200,57 @@ def c4_instance(spec) -> np.ndarray:
     pts = gaussian_mixture(rng, n, nb, d, 1e-3, 2e-2)
     pts, _ = _shuffle(rng, pts, 0)
     return pts.astype(np.float32)
+
+
+C4_NCUT = 8
+
+
+@dataclass
+class BatchWorkload:
+    """Independent instances packed back to back (instance i owns rows
+    [offset[i], offset[i+1]) of ``flat`` viewed per instance as (n_i, d_i))."""
+    name: str
+    sizes: list
+    dims: list
+    flat: np.ndarray                # float32, every instance's coordinates concatenated
+    coord_offset: list              # element offset of each instance in ``flat``
+    d_cut: list                     # [n_inst][n_dcut]
+    rho_noise: list                 # [n_inst * n_dcut]
+    rho_min: list                   # [n_inst * n_dcut]
+    delta_min: list                 # [n_inst * n_dcut]
+
+    @property
+    def n_inst(self) -> int:
+        return len(self.sizes)
+
+    @property
+    def N(self) -> int:
+        return int(sum(self.sizes))
+
+    def instance(self, i: int) -> np.ndarray:
+        o = self.coord_offset[i]
+        return self.flat[o:o + self.sizes[i] * self.dims[i]].reshape(self.sizes[i], self.dims[i])
+
+
+def c4(seed: int = 4, n_inst: int = 4096) -> BatchWorkload:
+    """The batched workload: per instance the sweep d_cut0 * 1.25^k (k < 8),
+    rho_noise = rho_min = 2 x median density at each cutoff, delta_min =
+    5 d_cut (d_cut0 and the densities from tests/golden/c4_params.json)."""
+    specs = c4_instance_specs(seed, n_inst)
+    with open(_C4_PATH) as f:
+        par = json.load(f)
+    parts, co, o = [], [], 0
+    for s in specs:
+        p = c4_instance(s)
+        parts.append(p.reshape(-1))
+        co.append(o)
+        o += p.size
+    flat = np.concatenate(parts)
+    cuts = [[par["d_cut0"][i] * 1.25 ** k for k in range(C4_NCUT)] for i in range(n_inst)]
+    rmin = [int(r) for i in range(n_inst) for r in par["rho_min"][i]]
+    dmin = [5.0 * c for row in cuts for c in row]
+    return BatchWorkload("c4_batch4096_f32_d235_x8cuts", [s[0] for s in specs], [s[1] for s in specs],
+                         flat, co, cuts, list(rmin), rmin, dmin)
 
 
 # ---------------------------------------------------------------------------
