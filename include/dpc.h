@@ -83,6 +83,21 @@ enum {
 #define DPC_FLAG_SYNC_CHECK (1u << 8)  /* synchronize and return the device status */
 #define DPC_FLAG_PHASE_TIMES (1u << 9) /* record CUDA events around every phase
                                           (read with dpc_get_phase_times)      */
+/* Autotune the grid level: the first dpc_run / dpc_density call that sees a
+ * new (dimension class, instance count, point count, cutoff) shape runs the
+ * cell-hash and density steps once per candidate block radius (R = 1, 2, 3
+ * for d <= 2; R = 1, 2 for d = 3; d >= 4 has R = 1 only; the cells shrink as R
+ * grows), timing each
+ * with CUDA events and synchronizing the stream, and keeps the fastest for
+ * that shape in the workspace; later calls (with or without the flag) reuse
+ * the choice without synchronizing.  Results do not depend on the choice.
+ * Do not set it on a call that is being captured into a CUDA graph. */
+#define DPC_FLAG_AUTOTUNE (1u << 10)
+/* Fixed block radius r = 1..5 instead of the default rule or the autotuned
+ * choice (larger radii are clamped to the largest the dimension allows: 5 for
+ * d <= 2, 2 for d = 3, 1 for d >= 4).  Results do not depend on it. */
+#define DPC_FLAG_RADIUS(r) ((uint32_t)(r) << 12)
+#define DPC_FLAG_RADIUS_MASK (0x7u << 12)
 
 /* A batch of independent point sets packed back to back.  n_inst = 1 for a
  * single point set.  All arrays are HOST arrays read during the call only. */
@@ -196,6 +211,9 @@ typedef struct {
   int64_t kernel_launches;/* kernels the last call enqueued                  */
   int64_t far_nodes;      /* radix-tree nodes expanded by the far queries    */
   int64_t far_nodes_max;  /* most nodes expanded by a single far query       */
+  int32_t block_radius;   /* block radius R of the last cutoff (cells per side
+                             of the (2R+1)^g block around a query's cell)     */
+  int32_t reserved;
 } dpc_stats;
 int dpc_get_stats(void* stream, dpc_stats* out);
 

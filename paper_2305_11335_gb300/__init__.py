@@ -68,11 +68,17 @@ class _Stats(ctypes.Structure):
                 ("exact_rescans", ctypes.c_int64), ("occupied_cells", ctypes.c_int64),
                 ("grid_level", ctypes.c_int32), ("bits_per_axis", ctypes.c_int32),
                 ("kernel_launches", ctypes.c_int64), ("far_nodes", ctypes.c_int64),
-                ("far_nodes_max", ctypes.c_int64)]
+                ("far_nodes_max", ctypes.c_int64), ("block_radius", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 PHASES = ["bin", "tree", "cells", "density", "maxkey", "near", "far", "labels"]
 DPC_FLAG_PHASE_TIMES = 1 << 9
+DPC_FLAG_AUTOTUNE = 1 << 10
+
+
+def DPC_FLAG_RADIUS(r: int) -> int:
+    return (int(r) & 7) << 12
 
 
 class _PhaseTimes(ctypes.Structure):
@@ -214,8 +220,11 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _flags(precision: str, sync: bool) -> int:
-    return PREC[precision] | (DPC_FLAG_SYNC_CHECK if sync else 0)
+def _flags(precision: str, sync: bool, radius: int = 0, autotune: bool = False) -> int:
+    """Call flags: precision mode, synchronous status check, a fixed block
+    radius (0 = default rule or autotuned choice) and autotuning."""
+    return (PREC[precision] | (DPC_FLAG_SYNC_CHECK if sync else 0) | DPC_FLAG_RADIUS(radius)
+            | (DPC_FLAG_AUTOTUNE if autotune else 0))
 
 
 def _check(rc: int, what: str):
@@ -224,24 +233,25 @@ def _check(rc: int, what: str):
 
 
 def dpc_density(pts: torch.Tensor, batch: Batch, precision: str = "fp32", sync: bool = False,
-                stream=None, out: torch.Tensor | None = None) -> torch.Tensor:
+                stream=None, out: torch.Tensor | None = None, autotune: bool = False,
+                radius: int = 0) -> torch.Tensor:
     lib = load()
     rho = out if out is not None else torch.empty((batch.n_dcut, batch.N), dtype=torch.int32, device=pts.device)
-    _check(lib.dpc_density(_dev(pts, "pts"), _dtype_code(pts), batch.ptr, _dev(rho, "rho"), _flags(precision, sync),
-                           _stream(stream)), "dpc_density")
+    _check(lib.dpc_density(_dev(pts, "pts"), _dtype_code(pts), batch.ptr, _dev(rho, "rho"),
+                           _flags(precision, sync, radius, autotune), _stream(stream)), "dpc_density")
     return rho
 
 
 def dpc_dependent(pts: torch.Tensor, batch: Batch, dcut_index: int, rho: torch.Tensor, rho_skip: int = 0,
-                  precision: str = "fp32", sync: bool = False, stream=None):
+                  precision: str = "fp32", sync: bool = False, stream=None, radius: int = 0):
     lib = load()
     if rho.dtype != torch.int32 or rho.numel() != batch.N:
         raise ValueError("rho must be int32 [N]")
     lam = torch.empty(batch.N, dtype=torch.int32, device=pts.device)
     delta = torch.empty(batch.N, dtype=torch.float64, device=pts.device)
     _check(lib.dpc_dependent(_dev(pts, "pts"), _dtype_code(pts), batch.ptr, int(dcut_index), _dev(rho, "rho"),
-                             int(rho_skip), _dev(lam, "lambda"), _dev(delta, "delta"), _flags(precision, sync),
-                             _stream(stream)), "dpc_dependent")
+                             int(rho_skip), _dev(lam, "lambda"), _dev(delta, "delta"),
+                             _flags(precision, sync, radius), _stream(stream)), "dpc_dependent")
     return lam, delta
 
 
@@ -256,7 +266,8 @@ def dpc_cluster(batch: Batch, dcut_index: int, params, rho: torch.Tensor, lam: t
 
 
 def dpc_run(pts: torch.Tensor, batch: Batch, params, precision: str = "fp32", sync: bool = False, stream=None,
-            out: dict | None = None, phase_times: bool = False) -> dict:
+            out: dict | None = None, phase_times: bool = False, autotune: bool = False,
+            radius: int = 0) -> dict:
     lib = load()
     shape = (batch.n_dcut, batch.N)
     if out is None:
@@ -266,7 +277,8 @@ def dpc_run(pts: torch.Tensor, batch: Batch, params, precision: str = "fp32", sy
                "label": torch.empty(shape, dtype=torch.int32, device=pts.device)}
     _check(lib.dpc_run(_dev(pts, "pts"), _dtype_code(pts), batch.ptr, params, _dev(out["rho"], "rho"),
                        _dev(out["lam"], "lambda"), _dev(out["delta"], "delta"), _dev(out["label"], "label"),
-                       _flags(precision, sync) | (DPC_FLAG_PHASE_TIMES if phase_times else 0), _stream(stream)),
+                       _flags(precision, sync, radius, autotune) | (DPC_FLAG_PHASE_TIMES if phase_times else 0),
+                       _stream(stream)),
            "dpc_run")
     return out
 
@@ -329,7 +341,7 @@ def dpc_last_status(stream=None) -> int:
 
 
 def run(pts: torch.Tensor, d_cut, rho_noise, rho_min, delta_min, precision: str = "fp32", sync: bool = True,
-        stream=None) -> dict:
+        stream=None, autotune: bool = False, radius: int = 0) -> dict:
     """DPC of one point set ``pts`` [n, d] (CUDA, int32/float32) for one or more cutoffs."""
     if pts.dim() == 1:
         pts = pts.reshape(-1, 1)
@@ -337,5 +349,6 @@ def run(pts: torch.Tensor, d_cut, rho_noise, rho_min, delta_min, precision: str 
     cuts = list(d_cut) if isinstance(d_cut, (list, tuple)) else [d_cut]
     batch = Batch.single(n, d, cuts)
     params = make_params(batch, rho_noise, rho_min, delta_min)
-    return dpc_run(pts.contiguous(), batch, params, precision=precision, sync=sync, stream=stream)
+    return dpc_run(pts.contiguous(), batch, params, precision=precision, sync=sync, stream=stream,
+                   autotune=autotune, radius=radius)
 

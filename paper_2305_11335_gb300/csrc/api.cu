@@ -2,7 +2,7 @@
 // stream) workspace, and the order in which the kernels run.
 //
 // The instances of a call are grouped into classes of equal padded dimension
-// dp and gridded dimension g (at most four: (2,1), (2,2), (4,3), (8,3)).  Each
+// dp and gridded dimension g (at most five: (2,1), (2,2), (4,3), (4,4), (8,4)).  Each
 // class runs as one unit, every kernel launched once for all its instances
 // (dpc_device.cuh describes the layout):
 //   binning   bbox -> grid setup -> sort keys -> radix sort -> gather
@@ -21,6 +21,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <string>
 #include <mutex>
 #include <utility>
 #include <vector>
@@ -45,7 +46,7 @@ inline uint32_t next_pow2(uint64_t x) {
 }
 
 inline int dp_of(int d) { return d <= 2 ? 2 : (d <= 4 ? 4 : 8); }
-inline int g_of(int d) { return d < 3 ? d : 3; }
+inline int g_of(int d) { return grid_dims(d); }
 
 // ---- argument checks -----------------------------------------------------------
 
@@ -85,10 +86,14 @@ int check_batch(const dpc_batch* b, std::vector<Inst>* insts, uint64_t* total) {
   return DPC_OK;
 }
 
+constexpr uint32_t kKnownFlags = DPC_PREC_MASK | DPC_FLAG_SYNC_CHECK | DPC_FLAG_PHASE_TIMES |
+                                 DPC_FLAG_AUTOTUNE | DPC_FLAG_RADIUS_MASK;
+
 int check_flags(uint32_t flags) {
   const uint32_t prec = flags & DPC_PREC_MASK;
   if (prec != DPC_PREC_FP64 && prec != DPC_PREC_FP32_CERT) return DPC_ERR_UNSUPPORTED;
-  if (flags & ~(DPC_PREC_MASK | DPC_FLAG_SYNC_CHECK | DPC_FLAG_PHASE_TIMES)) return DPC_ERR_ARG;
+  if (flags & ~kKnownFlags) return DPC_ERR_ARG;
+  if (((flags & DPC_FLAG_RADIUS_MASK) >> 12) > 5) return DPC_ERR_ARG;
   return DPC_OK;
 }
 
@@ -119,8 +124,8 @@ struct ClassPlan {
 // class (labels only, where the dimension does not matter).
 std::vector<ClassPlan> plan_classes(const std::vector<Inst>& insts, bool all_one) {
   std::vector<ClassPlan> out;
-  const int keys[4][2] = {{2, 1}, {2, 2}, {4, 3}, {8, 3}};
-  for (int k = 0; k < (all_one ? 1 : 4); ++k) {
+  const int keys[5][2] = {{2, 1}, {2, 2}, {4, 3}, {4, 4}, {8, 4}};
+  for (int k = 0; k < (all_one ? 1 : 5); ++k) {
     ClassPlan c;
     c.dp = keys[k][0];
     c.g = keys[k][1];
@@ -195,6 +200,10 @@ struct Workspace {
   void* io = nullptr;
   size_t io_bytes = 0;
 
+  // autotuned block radius per (class shape, cutoff), see tune_radius
+  std::map<std::string, int> tuned;
+  cudaEvent_t tune_a = nullptr, tune_b = nullptr;
+
   // for dpc_get_stats: the last class and cutoff that ran
   const CutGeom* last_cut = nullptr;
   const GridGeom* last_geom = nullptr;
@@ -238,8 +247,11 @@ struct Workspace {
     if (up_dev) cudaFree(up_dev);
     if (up_host) cudaFreeHost(up_host);
     if (up_done) cudaEventDestroy(up_done);
+    if (tune_a) cudaEventDestroy(tune_a);
+    if (tune_b) cudaEventDestroy(tune_b);
     base = io = up_dev = up_host = nullptr;
-    up_done = nullptr;
+    up_done = tune_a = tune_b = nullptr;
+    tuned.clear();
     bytes = io_bytes = up_bytes = 0;
     cap_n = 0;
     cap_inst = 0;
@@ -663,6 +675,73 @@ LabelParams one_params(const dpc_params* params, const ClassPlan& c, int ncut_al
   return L;
 }
 
+// ---- autotuning of the cell level -------------------------------------------------
+//
+// The block radius R (and with it the grid level: finer cells for larger R)
+// decides how many candidates a query scans and how many cells a warp looks
+// up.  The default rule keeps R = 1 unless a larger R shrinks the block side
+// by 20%; with DPC_FLAG_AUTOTUNE the first call for a class shape times the
+// density step once per radius (R = 1, 2, 3 in 1-2 gridded dims, R = 1, 2 in
+// 3; 4 gridded dims allow only R = 1) and keeps the fastest for later calls of
+// the same shape.
+
+std::string tune_key(const ClassPlan& c, const dpc_batch* b, int cut) {
+  char buf[160];
+  const double dc = b->d_cut[(size_t)c.members[0] * b->n_dcut + cut];
+  unsigned long long bits;
+  std::memcpy(&bits, &dc, sizeof(bits));
+  std::snprintf(buf, sizeof(buf), "%d/%d/%zu/%u/%d/%llx", c.dp, c.g, c.members.size(), c.N, cut, bits);
+  return buf;
+}
+
+// Applies the radius preference of (class, cutoff) to cuts ([ninst]),
+// measuring it first when the call asked for autotuning and the shape is new.
+// rho_scratch receives the densities of the trial runs.
+void apply_radius(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cuts,
+                  const dpc_batch* b, int cut, bool fp64, int32_t* rho_scratch, uint32_t flags) {
+  const int fixed = (int)((flags & DPC_FLAG_RADIUS_MASK) >> 12);
+  if (fixed > 0) {
+    launch_set_radius(cv, cuts, fixed, w->stream);
+    return;
+  }
+  const std::string key = tune_key(c, b, cut);
+  auto it = w->tuned.find(key);
+  if (it == w->tuned.end() && (flags & DPC_FLAG_AUTOTUNE) && c.g >= 4) {
+    it = w->tuned.emplace(key, 1).first;  // (2R+1)^4 cells: only R = 1 fits a union
+  } else if (it == w->tuned.end() && (flags & DPC_FLAG_AUTOTUNE)) {
+    cudaStream_t st = w->stream;
+    if (!w->tune_a) {
+      cudaEventCreate(&w->tune_a);
+      cudaEventCreate(&w->tune_b);
+    }
+    const int rmax = c.g == 3 ? 2 : 3;
+    float best_ms = 0.f;
+    int best = 0;
+    for (int r = 1; r <= rmax; ++r) {
+      launch_set_radius(cv, cuts, r, st);
+      cudaEventRecord(w->tune_a, st);
+      launch_cells(w->scode, cv, c.g, cuts, w->hinfo, w->hkeys, w->hvals, w->hcap, st);
+      launch_density(c.dp, c.g, fp64, w->spts, w->scode, w->sid, cv, cuts, w->hinfo, w->hkeys,
+                     w->hvals, rho_scratch, w->skey, w->ctr, st);
+      cudaEventRecord(w->tune_b, st);
+      float ms = 0.f;
+      if (cudaEventSynchronize(w->tune_b) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, w->tune_a, w->tune_b) != cudaSuccess) {
+        cudaGetLastError();
+        best = 0;
+        break;
+      }
+      if (best == 0 || ms < best_ms) {
+        best_ms = ms;
+        best = r;
+      }
+    }
+    it = w->tuned.emplace(key, best).first;
+  }
+  const int r = it == w->tuned.end() ? 0 : it->second;
+  if (r > 0) launch_set_radius(cv, cuts, r, w->stream);
+}
+
 void reset_call(Workspace* w, uint32_t flags) {
   w->begin_call(flags);
   cudaMemsetAsync(w->status, 0, sizeof(int), w->stream);
@@ -720,7 +799,8 @@ int dpc_density(const void* pts, int dtype, const dpc_batch* b, int32_t* rho, ui
     const ClassView cv = view_of(w, c, insts);
     bin_class(w, pts, dtype, P, c, cv, b, insts);
     for (int k = 0; k < P.ncut; ++k) {
-      const CutGeom* cuts = w->cuts + (size_t)k * cv.ninst;
+      CutGeom* cuts = w->cuts + (size_t)k * cv.ninst;
+      apply_radius(w, c, cv, cuts, b, k, fp64, rho + (size_t)k * N, flags);
       cells_step(w, c, cv, cuts);
       density_step(w, c, cv, cuts, fp64, rho + (size_t)k * N);
     }
@@ -749,6 +829,7 @@ int dpc_dependent(const void* pts, int dtype, const dpc_batch* b, int32_t dcut_i
     const ClassView cv = view_of(w, c, insts);
     bin_class(w, pts, dtype, P, c, cv, b, insts);
     tree_step(w, cv);
+    apply_radius(w, c, cv, w->cuts, b, dcut_index, fp64, nullptr, flags & ~DPC_FLAG_AUTOTUNE);
     cells_step(w, c, cv, w->cuts);
     launch_keys_from_rho(rho, w->sid, cv.N, w->skey, w->stream);
     dependent_step(w, c, cv, w->cuts, pts, dtype, rho_skip, fp64, lambda, delta);
@@ -763,7 +844,7 @@ int dpc_cluster(const dpc_batch* b, int32_t dcut_index, const dpc_params* params
   uint64_t N = 0;
   int rc = check_batch(b, &insts, &N);
   if (rc) return rc;
-  if (flags & ~(DPC_PREC_MASK | DPC_FLAG_SYNC_CHECK | DPC_FLAG_PHASE_TIMES)) return DPC_ERR_ARG;
+  if (flags & ~kKnownFlags) return DPC_ERR_ARG;
   if (dcut_index < 0 || dcut_index >= b->n_dcut || !params) return DPC_ERR_ARG;
   if (N > 0 && (!rho || !lambda || !delta || !label)) return DPC_ERR_ARG;
   for (int i = 0; i < b->n_inst; ++i)
@@ -797,7 +878,8 @@ static int run_device(Workspace* w, const void* pts, int dtype, const dpc_batch*
     tree_step(w, cv);
     for (int k = 0; k < P.ncut; ++k) {
       const size_t o = (size_t)k * N;
-      const CutGeom* cuts = w->cuts + (size_t)k * cv.ninst;
+      CutGeom* cuts = w->cuts + (size_t)k * cv.ninst;
+      apply_radius(w, c, cv, cuts, b, k, fp64, rho + o, flags);
       cells_step(w, c, cv, cuts);
       density_step(w, c, cv, cuts, fp64, rho + o);
       dependent_step(w, c, cv, cuts, pts, dtype, 0, fp64, lambda + o, delta + o);
@@ -907,6 +989,7 @@ int dpc_get_stats(void* stream, dpc_stats* out) {
     cudaMemcpy(&hi, w->hinfo, sizeof(hi), cudaMemcpyDeviceToHost);
     out->occupied_cells = hi.m;
     out->grid_level = cg.k;
+    out->block_radius = cg.R;
     out->bits_per_axis = g.B;
   }
   return cudaGetLastError() == cudaSuccess ? DPC_OK : DPC_ERR_CUDA;

@@ -38,9 +38,9 @@ __global__ void k_class_init(ClassView cv, int g, int ib, int bcap, int* status)
   GridGeom& G = cv.geom[t];
   G.g = g;
   G.status = status;
-  for (int a = 0; a < 3; ++a) {
-    G.bbox_ord[a] = 0xffffffffu;  // min accumulators
-    G.bbox_ord[3 + a] = 0u;       // max accumulators
+  for (int a = 0; a < kMaxGrid; ++a) {
+    G.bbox_ord[a] = 0xffffffffu;        // min accumulators
+    G.bbox_ord[kMaxGrid + a] = 0u;      // max accumulators
   }
 }
 
@@ -55,17 +55,17 @@ __global__ void k_bbox(const T* __restrict__ pts, ClassView cv, int g) {
   const uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const uint32_t per = (cv.nchunk + nw - 1) / nw;
   const uint32_t c0 = w * per, c1 = min(cv.nchunk, c0 + per);
-  float mn[3], mx[3];
+  float mn[kMaxGrid], mx[kMaxGrid];
   uint32_t cur = 0xffffffffu;
   int bad = 0;
   auto flush = [&]() {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < kMaxGrid; ++k) {
       const uint32_t lo = __reduce_min_sync(0xffffffffu, float_ord(mn[k]));
       const uint32_t hi = __reduce_max_sync(0xffffffffu, float_ord(mx[k]));
       if (lane == 0 && k < g && ord_float(lo) <= ord_float(hi)) {
         atomicMin(&cv.geom[cur].bbox_ord[k], lo);
-        atomicMax(&cv.geom[cur].bbox_ord[3 + k], hi);
+        atomicMax(&cv.geom[cur].bbox_ord[kMaxGrid + k], hi);
       }
     }
   };
@@ -76,7 +76,7 @@ __global__ void k_bbox(const T* __restrict__ pts, ClassView cv, int g) {
       if (cur != 0xffffffffu) flush();
       cur = i;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
+      for (int k = 0; k < kMaxGrid; ++k) {
         mn[k] = FLT_MAX;
         mx[k] = -FLT_MAX;
       }
@@ -95,9 +95,9 @@ __global__ void k_bbox(const T* __restrict__ pts, ClassView cv, int g) {
           x = (float)v;
           bad |= !(fabsf(x) <= 1.152921504606846976e18f);  // 2^60; false for NaN
         }
-        if (a < 3) {
+        if (a < kMaxGrid) {
 #pragma unroll
-          for (int k = 0; k < 3; ++k)
+          for (int k = 0; k < kMaxGrid; ++k)
             if (k == a) { mn[k] = fminf(mn[k], x); mx[k] = fmaxf(mx[k], x); }
         }
       }
@@ -128,7 +128,7 @@ __global__ void k_setup_geom(ClassView cv, int ncut, const CutHost* __restrict__
   const int bcap = cv.cls->bcap;
   double E = 0.0;
   for (int a = 0; a < g; ++a) {
-    uint32_t lo = geom->bbox_ord[a], hi = geom->bbox_ord[3 + a];
+    uint32_t lo = geom->bbox_ord[a], hi = geom->bbox_ord[kMaxGrid + a];
     double mn = 0.0, mx = 0.0;
     if (lo != 0xffffffffu) {
       mn = (double)ord_float(lo);
@@ -161,45 +161,35 @@ __global__ void k_setup_geom(ClassView cv, int ncut, const CutHost* __restrict__
   atomicMax(&cv.cls->S, g * B);
 }
 
-// Per (instance, cutoff) search parameters, one thread each: the grid level k
-// whose cells are at least d_cut wide (so the (2R+1)^g block with R = 1 holds
-// every point within d_cut), the density prune bound and the far bound of the
-// dependent search.  cuts is [ncut][ninst].
-__global__ void k_setup_cuts(ClassView cv, CutGeom* cuts, int ncut, const CutHost* __restrict__ hc,
-                             CutArgs args) {
-  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cv.ninst * (uint32_t)ncut) return;
-  const uint32_t i = t / ncut;
-  const int c = (int)(t - i * ncut);
-  const GridGeom* geom = cv.geom + i;
-  const CutHost H = hc ? hc[(size_t)i * ncut + c] : args.h[c];
+// Grid level k and block radius R of one (instance, cutoff), and the bounds
+// that follow from them.  Two points within d_cut differ by at most D fine
+// indices on each axis, so any (k, R) with R * 2^k >= D puts every point
+// within d_cut of a query in the (2R+1)^g block of level-k cells around it.
+// rpref = 0: R = 1 (the 3^g block of cells at least d_cut wide) unless a
+// larger R on finer cells shrinks the block side by more than 20%, which pays
+// for its extra cell lookups (it happens when d_cut falls just above a
+// power-of-two multiple of the fine cell, e.g. the larger cutoffs of a sweep).
+// rpref > 0: the finest level whose block radius is at most rpref (the
+// autotuner's choice, see api.cu).
+__device__ void choose_level(CutGeom& C, const GridGeom* geom, int rpref) {
   const double f = geom->f;
   const int B = geom->B;
-  CutGeom& C = cuts[(size_t)c * cv.ninst + i];
-  C.dc = H.dc;
-  C.dc2 = H.dc2;
-  C.t_in = H.t_in;
-  C.t_out = H.t_out;
-  C.band_mul = H.band_mul;
-  C.band_add = H.band_add;
-  // Two points within d_cut differ by at most D fine indices on each axis.
-  // Choose the level k and block radius R (R * 2^k >= D).  R = 1 (the 3^g
-  // block of cells at least d_cut wide) unless a larger R on finer cells
-  // shrinks the block side by more than 20%, which pays for its extra cell
-  // lookups (it happens when d_cut falls just above a power-of-two multiple
-  // of the fine cell, e.g. the larger cutoffs of a sweep).
   const double Dd = floor(C.dc * geom->inv_f * (1.0 + 1e-9) + 1e-6) + 1.0;
   const int g = geom->g;
-  const int rmax = g == 3 ? 2 : 3;  // (2R+1)^g <= 125 cells
+  const int rmax = g >= 4 ? 1 : (g == 3 ? 2 : (g == 2 ? 5 : 16));  // (2R+1)^g <= kMaxUnion cells
   int k = B, R = 1;
   double best = INFINITY;
   for (int r = 1; r <= rmax; ++r) {
+    if (rpref > 0 && r > rpref) break;
+    if (rpref == 0 && r > (g >= 3 ? 2 : 3)) break;
     int kk = 0;
     while (kk < B && ldexp((double)r, kk) < Dd) ++kk;
     const int rr = (int)fmax(1.0, ceil(Dd / ldexp(1.0, kk)));
     if (rr > rmax) continue;
     const double side = (2.0 * rr + 1.0) * ldexp(1.0, kk);
-    if (side < (best < INFINITY ? 0.8 * best : INFINITY)) {
+    const bool take = rpref > 0 ? (kk < k || !(best < INFINITY))
+                                : side < (best < INFINITY ? 0.8 * best : INFINITY);
+    if (take) {
       best = side;
       k = kk;
       R = rr;
@@ -220,6 +210,33 @@ __global__ void k_setup_cuts(ClassView cv, CutGeom* cuts, int ncut, const CutHos
   C.far64 = lb2 * (1.0 - 1e-9);
   double l32 = lb2 * (1.0 - 1e-5) - 0x1p-100;
   C.far32 = l32 <= 0.0 ? 0.0f : (l32 >= 3.0e38 ? 3.0e38f : __double2float_rd(l32));
+}
+
+// Per (instance, cutoff) search parameters, one thread each.  cuts is
+// [ncut][ninst].
+__global__ void k_setup_cuts(ClassView cv, CutGeom* cuts, int ncut, const CutHost* __restrict__ hc,
+                             CutArgs args) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cv.ninst * (uint32_t)ncut) return;
+  const uint32_t i = t / ncut;
+  const int c = (int)(t - i * ncut);
+  const CutHost H = hc ? hc[(size_t)i * ncut + c] : args.h[c];
+  CutGeom& C = cuts[(size_t)c * cv.ninst + i];
+  C.dc = H.dc;
+  C.dc2 = H.dc2;
+  C.t_in = H.t_in;
+  C.t_out = H.t_out;
+  C.band_mul = H.band_mul;
+  C.band_add = H.band_add;
+  choose_level(C, cv.geom + i, 0);
+}
+
+// The level and radius of one cutoff of every instance again, with a
+// preferred block radius.
+__global__ void k_set_radius(ClassView cv, CutGeom* cuts, int rpref) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cv.ninst) return;
+  choose_level(cuts[i], cv.geom + i, rpref);
 }
 
 // Sort key of every point: (instance << S) | fine-grid Morton code; the
@@ -437,6 +454,11 @@ void launch_chunks(const ClassView& cv, uint32_t* chunk_inst, uint32_t* chunk_po
   count_launches(1);
 }
 
+void launch_set_radius(const ClassView& cv, CutGeom* cuts, int rpref, cudaStream_t st) {
+  k_set_radius<<<grid_for(cv.ninst), kThreads, 0, st>>>(cv, cuts, rpref);
+  count_launches(1);
+}
+
 void launch_bbox(const void* pts, int dtype, const ClassView& cv, int g, cudaStream_t st) {
   if (cv.N == 0) return;
   const unsigned grid = grid_for((uint64_t)cv.nchunk * 32u, kThreads, 152u * 4u);
@@ -463,7 +485,8 @@ static void codes_t(const T* pts, const ClassView& cv, int g, unsigned long long
   const unsigned grid = grid_for((uint64_t)cv.nchunk * 32u);
   if (g == 1) k_codes<T, 1><<<grid, kThreads, 0, st>>>(pts, cv, codes, ids);
   else if (g == 2) k_codes<T, 2><<<grid, kThreads, 0, st>>>(pts, cv, codes, ids);
-  else k_codes<T, 3><<<grid, kThreads, 0, st>>>(pts, cv, codes, ids);
+  else if (g == 3) k_codes<T, 3><<<grid, kThreads, 0, st>>>(pts, cv, codes, ids);
+  else k_codes<T, 4><<<grid, kThreads, 0, st>>>(pts, cv, codes, ids);
   count_launches(1);
 }
 

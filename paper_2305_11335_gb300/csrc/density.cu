@@ -182,8 +182,9 @@ void launch_density(int dp, int g, bool fp64, const float* spts, const unsigned 
   if (cv.N == 0) return;
   if (g == 1) density_dg<2, 1>(fp64, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
   else if (g == 2) density_dg<2, 2>(fp64, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
-  else if (dp == 4) density_dg<4, 3>(fp64, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
-  else density_dg<8, 3>(fp64, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
+  else if (g == 3) density_dg<4, 3>(fp64, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
+  else if (dp == 4) density_dg<4, 4>(fp64, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
+  else density_dg<8, 4>(fp64, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
 }
 
 void launch_keys_from_rho(const int32_t* rho, const uint32_t* sid, uint32_t n,

@@ -823,8 +823,9 @@ void launch_dep_near(int dp, int g, bool fp64, const float* spts, const unsigned
   cudaMemsetAsync(&ctr->queue2_n, 0, sizeof(unsigned int), st);
   if (g == 1) near_dg<2, 1>(fp64, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
   else if (g == 2) near_dg<2, 2>(fp64, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
-  else if (dp == 4) near_dg<4, 3>(fp64, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
-  else near_dg<8, 3>(fp64, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
+  else if (g == 3) near_dg<4, 3>(fp64, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
+  else if (dp == 4) near_dg<4, 4>(fp64, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
+  else near_dg<8, 4>(fp64, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
   count_launches(1);
 }
 

@@ -21,7 +21,7 @@
 //              is the subtree below root[i]
 //
 // The grid of an instance: a fine uniform grid of 2^B cells per gridded axis
-// (the first g = min(d, 3) coordinates) covers its bounding box; a point's
+// (the first g = min(d, 4) coordinates) covers its bounding box; a point's
 // fine index is floor((x - org) / f).  Level k of the grid merges 2^k fine
 // cells per axis; since the Morton code interleaves the axes, every level-k
 // cell is the contiguous run of sorted points sharing key >> (g*k) (the
@@ -34,7 +34,11 @@
 namespace dpc {
 
 constexpr int kMaxDim = 8;
-constexpr int kMaxBits = 21;              // fine-grid bits per axis (see choose_bits)
+constexpr int kMaxBits = 21;              // fine-grid bits per axis (k_setup_geom)
+constexpr int kMaxGrid = 4;               // gridded coordinates
+
+// Gridded coordinates of a d-dimensional instance.
+__host__ __device__ __forceinline__ int grid_dims(int d) { return d < kMaxGrid ? d : kMaxGrid; }
 constexpr uint64_t kEmpty = ~0ull;        // empty hash slot (codes are < 2^63)
 constexpr uint32_t kLeafBit = 0x80000000u;
 
@@ -49,7 +53,7 @@ enum : int {
 
 // Per-instance grid geometry, written by the setup kernel from the bounding box.
 struct GridGeom {
-  double org[3];     // bounding-box minimum of the gridded axes
+  double org[kMaxGrid];  // bounding-box minimum of the gridded axes
   double f;          // fine cell side
   double inv_f;      // 1 / f
   float f2;          // f*f rounded down (for lower bounds)
@@ -57,7 +61,7 @@ struct GridGeom {
   int B;             // fine-grid bits per axis
   int nbits;         // g * B
   int* status;       // the workspace's device status word (kStatus* bits)
-  uint32_t bbox_ord[6];  // ordered-uint min (0..2) and max (3..5) accumulators
+  uint32_t bbox_ord[2 * kMaxGrid];  // ordered-uint min (0..3) and max (4..7) accumulators
 };
 
 // Per-class sort-key layout and status.
@@ -214,17 +218,39 @@ __host__ __device__ __forceinline__ uint32_t compact3(uint64_t x) {
   return (uint32_t)x;
 }
 
+__host__ __device__ __forceinline__ uint64_t spread4(uint64_t x) {  // 16 -> 64 bits
+  x &= 0xffffull;
+  x = (x ^ (x << 24)) & 0x000000ff000000ffull;
+  x = (x ^ (x << 12)) & 0x000f000f000f000full;
+  x = (x ^ (x << 6)) & 0x0303030303030303ull;
+  x = (x ^ (x << 3)) & 0x1111111111111111ull;
+  return x;
+}
+__host__ __device__ __forceinline__ uint32_t compact4(uint64_t x) {
+  x &= 0x1111111111111111ull;
+  x = (x ^ (x >> 3)) & 0x0303030303030303ull;
+  x = (x ^ (x >> 6)) & 0x000f000f000f000full;
+  x = (x ^ (x >> 12)) & 0x000000ff000000ffull;
+  x = (x ^ (x >> 24)) & 0x000000000000ffffull;
+  return (uint32_t)x;
+}
+
 template <int G>
 __host__ __device__ __forceinline__ uint64_t morton(const uint32_t* c) {
   if constexpr (G == 1) return c[0];
   else if constexpr (G == 2) return spread2(c[0]) | (spread2(c[1]) << 1);
-  else return spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
+  else if constexpr (G == 3) return spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
+  else return spread4(c[0]) | (spread4(c[1]) << 1) | (spread4(c[2]) << 2) | (spread4(c[3]) << 3);
 }
 template <int G>
 __host__ __device__ __forceinline__ void unmorton(uint64_t code, uint32_t* c) {
   if constexpr (G == 1) c[0] = (uint32_t)code;
   else if constexpr (G == 2) { c[0] = compact2(code); c[1] = compact2(code >> 1); }
-  else { c[0] = compact3(code); c[1] = compact3(code >> 1); c[2] = compact3(code >> 2); }
+  else if constexpr (G == 3) { c[0] = compact3(code); c[1] = compact3(code >> 1); c[2] = compact3(code >> 2); }
+  else {
+    c[0] = compact4(code); c[1] = compact4(code >> 1);
+    c[2] = compact4(code >> 2); c[3] = compact4(code >> 3);
+  }
 }
 
 // ---------------------------------------------------------------------------

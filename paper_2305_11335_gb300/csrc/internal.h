@@ -38,6 +38,9 @@ void launch_bbox(const void* pts, int dtype, const ClassView& cv, int g, cudaStr
 // hc_dev ([ninst][ncut], device) or, when it is null, from hc_host (ncut <= kCutChunk)
 void launch_setup(const ClassView& cv, CutGeom* cuts, int ncut, const CutHost* hc_dev,
                   const CutHost* hc_host, cudaStream_t st);
+// level and block radius of one cutoff (cuts: [ninst]) again: rpref = 0 the
+// default rule, rpref > 0 the finest level whose block radius is <= rpref
+void launch_set_radius(const ClassView& cv, CutGeom* cuts, int rpref, cudaStream_t st);
 void launch_codes(const void* pts, int dtype, const ClassView& cv, int g, unsigned long long* codes,
                   uint32_t* ids, cudaStream_t st);
 void launch_gather(const void* pts, int dtype, const ClassView& cv, int dp,

@@ -116,7 +116,7 @@ extern "C" int dpc_density_static(const void* pts, int dtype, int64_t n, int32_t
   uint2* hvals = (uint2*)(base + kOffHvals);
 
   const uint32_t nn = (uint32_t)n;
-  const int g = d < 3 ? d : 3;
+  const int g = grid_dims(d);
   const int dp = d <= 2 ? 2 : (d <= 4 ? 4 : 8);
   const CutHost ch = make_cut_host(d_cut, dp);
   // the previous call's contents are still there: zero the words that

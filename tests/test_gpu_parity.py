@@ -220,3 +220,32 @@ def test_stats():
     s = dpc.dpc_get_stats()
     assert s["occupied_cells"] > 0 and s["bits_per_axis"] >= 1
     assert 0 < s["far_queries"] < 20000
+
+
+@pytest.mark.parametrize("radius", [1, 2, 3, 5])
+def test_block_radius_does_not_change_results(radius):
+    """Every block radius (grid level) gives the oracle's result, in 1, 2, 3
+    and 5 dimensions (radii above a dimension's maximum are clamped)."""
+    for d, n, dc in ((1, 3000, 0.004), (2, 4000, 0.03), (3, 4000, 0.06), (5, 2500, 0.12)):
+        pts = W.random_blobs(n, d, 900 + d)
+        refs = [oracle.run(pts, c, 2, 3, 0.1) for c in (dc, dc * 1.3)]
+        t = torch.from_numpy(pts).cuda()
+        out = dpc.run(t, [dc, dc * 1.3], 2, 3, 0.1, radius=radius)
+        for c, ref in enumerate(refs):
+            assert_same({k: v[c].cpu().numpy() for k, v in out.items()}, ref, "d=%d r=%d cut %d" % (d, radius, c))
+        st = dpc.dpc_get_stats()
+        assert 1 <= st["block_radius"] <= (5 if d <= 2 else (2 if d == 3 else 1))
+
+
+def test_autotune_keeps_results_and_caches():
+    pts = W.random_blobs(20000, 2, 4242)
+    dc = 0.01
+    ref = oracle.run(pts, dc, 2, 3, 0.1)
+    t = torch.from_numpy(pts).cuda()
+    first = dpc.run(t, [dc], 2, 3, 0.1, autotune=True)
+    r1 = dpc.dpc_get_stats()["block_radius"]
+    again = dpc.run(t, [dc], 2, 3, 0.1)
+    r2 = dpc.dpc_get_stats()["block_radius"]
+    assert r1 == r2 and 1 <= r1 <= 3
+    for out in (first, again):
+        assert_same({k: v[0].cpu().numpy() for k, v in out.items()}, ref)
