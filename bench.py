@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--fast", action="store_true", help="skip the fp64, e2e and CPU legs (profiling runs)")
     ap.add_argument("--cpu-sample", type=int, default=4096)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default grid-level rule")
+    ap.add_argument("--no-graph", action="store_true", help="time plain calls instead of graph replays")
     return ap.parse_args()
 
 
@@ -268,7 +269,11 @@ def run_ours(args, rank, world, dev):
     job = Job(load_workload(args.workload))
     batch = dpc.Batch(job.pt_offset, job.dims, job.d_cut, coord_offset=job.coord_offset)
     params = dpc.make_params(batch, job.rho_noise, job.rho_min, job.delta_min)
-    stream = torch.cuda.current_stream()
+    # one stream for every call (the library keeps one workspace, autotuning
+    # cache and captured graph per stream); graph capture needs a stream other
+    # than the legacy default one
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
     pts = torch.from_numpy(job.flat).to(dev)
     shape = (batch.n_dcut, job.N)
     out = {"rho": torch.empty(shape, dtype=torch.int32, device=dev),
@@ -278,14 +283,15 @@ def run_ours(args, rank, world, dev):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     units = job.N * batch.n_dcut
 
-    def timed_steps(k, precision, phase_times):
+    def timed_steps(k, precision, phase_times, graph=False):
         times, phases = [], {}
         for _ in range(k):
             flush.fill_(1)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            dpc.dpc_run(pts, batch, params, precision=precision, stream=stream, out=out, phase_times=phase_times)
+            dpc.dpc_run(pts, batch, params, precision=precision, stream=stream, out=out, phase_times=phase_times,
+                        graph=graph)
             b.record(stream)
             b.synchronize()
             times.append(a.elapsed_time(b))
@@ -307,16 +313,23 @@ def run_ours(args, rank, world, dev):
         dpc.dpc_run(pts, batch, params, precision=args.precision, stream=stream, out=out,
                     autotune=(steps == 0 and not args.no_autotune))
         steps += 1
-    dpc.dpc_run(pts, batch, params, precision=args.precision, stream=stream, out=out, sync=True)
+    use_graph = not args.no_graph
+    # capture (graph mode) or one more plain call, then synchronize
+    dpc.dpc_run(pts, batch, params, precision=args.precision, stream=stream, out=out, sync=True, graph=use_graph)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    times, phases = timed_steps(args.steps, args.precision, True)
+    times, _ = timed_steps(args.steps, args.precision, False, graph=use_graph)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop() if sampler else None
     stats = dpc.dpc_get_stats(stream)
+    # phase breakdown: a separate pass of plain (non-graph) calls with events
+    # around every phase on the same stream
+    k_ph = max(1, min(args.steps, 5))
+    _, phases = timed_steps(k_ph, args.precision, True)
+    phase_steps = k_ph
     total_ms, value = combine_ranks(sum(times), units, args.steps, world, dev)
     ms_per_step = total_ms / args.steps
 
@@ -330,7 +343,10 @@ def run_ours(args, rank, world, dev):
            "data": "synthetic (seeded generator standing in for the paper's data sets)",
            "config": config,
            "gpu_launches": int(stats["kernel_launches"]) * args.steps,
-           "phases_ms": {p: round(v[0] / args.steps, 5) for p, v in phases.items()},
+           "launch": ("one CUDA graph per step (DPC_FLAG_GRAPH: %d kernels captured once, replayed)"
+                      % int(stats["kernel_launches"])) if use_graph else "one launch per kernel",
+           "phases_ms": {p: round(v[0] / phase_steps, 5) for p, v in phases.items()},
+           "phases_from": "%d plain calls with events around every phase, after the timed steps" % phase_steps,
            "stats": {k: int(v) for k, v in stats.items()}}
     if rank != 0:
         return None
@@ -343,9 +359,9 @@ def run_ours(args, rank, world, dev):
     kernels = {"density": "k_density", "near": "k_dep_near"}
     model_phase = dom if dom in kernels else max(("density", "near"), key=lambda p: phases[p][0])
     work, mean_rho = block_work(job, out["rho"])
-    # phases[] holds the sums over the K timed steps; work is one step's
-    launches = phases[model_phase][1] // args.steps
-    step_ms = phases[model_phase][0] / args.steps
+    # phases[] holds the sums over the phase pass; work is one step's
+    launches = phases[model_phase][1] // phase_steps
+    step_ms = phases[model_phase][0] / phase_steps
     per_launch_ms = step_ms / launches
     achieved = work / (step_ms / 1e3) / 1e12
     clk = pk.get("sm_max_mhz", 2070.0)

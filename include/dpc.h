@@ -98,6 +98,16 @@ enum {
  * d <= 2, 2 for d = 3, 1 for d >= 4).  Results do not depend on it. */
 #define DPC_FLAG_RADIUS(r) ((uint32_t)(r) << 12)
 #define DPC_FLAG_RADIUS_MASK (0x7u << 12)
+/* dpc_run only: capture the call's kernels into a CUDA graph the first time a
+ * (pointers, batch, thresholds, precision, radius) combination is seen, and on
+ * later calls with the same combination launch that graph instead of one
+ * kernel at a time.  Each call still resets the status word and copies the
+ * instance tables (outside the graph), so the point coordinates may change
+ * between calls; a different combination, or a workspace that had to grow,
+ * captures anew.  Needs a stream other than the legacy default stream
+ * (DPC_ERR_UNSUPPORTED there).  Phase times are not recorded and autotuning is
+ * not done in this mode (autotune with a call without the flag first). */
+#define DPC_FLAG_GRAPH (1u << 11)
 
 /* A batch of independent point sets packed back to back.  n_inst = 1 for a
  * single point set.  All arrays are HOST arrays read during the call only. */

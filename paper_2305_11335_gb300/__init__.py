@@ -75,6 +75,7 @@ class _Stats(ctypes.Structure):
 PHASES = ["bin", "tree", "cells", "density", "maxkey", "near", "far", "labels"]
 DPC_FLAG_PHASE_TIMES = 1 << 9
 DPC_FLAG_AUTOTUNE = 1 << 10
+DPC_FLAG_GRAPH = 1 << 11
 
 
 def DPC_FLAG_RADIUS(r: int) -> int:
@@ -267,7 +268,7 @@ def dpc_cluster(batch: Batch, dcut_index: int, params, rho: torch.Tensor, lam: t
 
 def dpc_run(pts: torch.Tensor, batch: Batch, params, precision: str = "fp32", sync: bool = False, stream=None,
             out: dict | None = None, phase_times: bool = False, autotune: bool = False,
-            radius: int = 0) -> dict:
+            radius: int = 0, graph: bool = False) -> dict:
     lib = load()
     shape = (batch.n_dcut, batch.N)
     if out is None:
@@ -277,8 +278,8 @@ def dpc_run(pts: torch.Tensor, batch: Batch, params, precision: str = "fp32", sy
                "label": torch.empty(shape, dtype=torch.int32, device=pts.device)}
     _check(lib.dpc_run(_dev(pts, "pts"), _dtype_code(pts), batch.ptr, params, _dev(out["rho"], "rho"),
                        _dev(out["lam"], "lambda"), _dev(out["delta"], "delta"), _dev(out["label"], "label"),
-                       _flags(precision, sync, radius, autotune) | (DPC_FLAG_PHASE_TIMES if phase_times else 0),
-                       _stream(stream)),
+                       _flags(precision, sync, radius, autotune) | (DPC_FLAG_PHASE_TIMES if phase_times else 0)
+                       | (DPC_FLAG_GRAPH if graph else 0), _stream(stream)),
            "dpc_run")
     return out
 

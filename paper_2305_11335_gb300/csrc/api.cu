@@ -87,7 +87,7 @@ int check_batch(const dpc_batch* b, std::vector<Inst>* insts, uint64_t* total) {
 }
 
 constexpr uint32_t kKnownFlags = DPC_PREC_MASK | DPC_FLAG_SYNC_CHECK | DPC_FLAG_PHASE_TIMES |
-                                 DPC_FLAG_AUTOTUNE | DPC_FLAG_RADIUS_MASK;
+                                 DPC_FLAG_AUTOTUNE | DPC_FLAG_RADIUS_MASK | DPC_FLAG_GRAPH;
 
 int check_flags(uint32_t flags) {
   const uint32_t prec = flags & DPC_PREC_MASK;
@@ -200,6 +200,16 @@ struct Workspace {
   void* io = nullptr;
   size_t io_bytes = 0;
 
+  // the captured graph of DPC_FLAG_GRAPH calls and the key it was captured for
+  cudaGraphExec_t gexec = nullptr;
+  std::string gkey;
+  long long glaunches = 0;
+  void drop_graph() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+    gkey.clear();
+  }
+
   // autotuned block radius per (class shape, cutoff), see tune_radius
   std::map<std::string, int> tuned;
   cudaEvent_t tune_a = nullptr, tune_b = nullptr;
@@ -238,6 +248,7 @@ struct Workspace {
   void end_call() { launches_last = g_kernel_launches; }
 
   void release() {
+    drop_graph();
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     ev_pool.clear();
     ev_used = 0;
@@ -266,6 +277,7 @@ struct Workspace {
     int want_c = std::max(std::max(ncut, cap_ncut), 8);
     if (base) {
       cudaStreamSynchronize(stream);
+      drop_graph();  // it holds pointers into the old buffers
       cudaFree(base);
       base = nullptr;
     }
@@ -362,6 +374,7 @@ struct Workspace {
     if (b <= up_bytes && up_dev) return DPC_OK;
     if (up_dev) {
       cudaStreamSynchronize(stream);
+      drop_graph();
       cudaFree(up_dev);
       cudaFreeHost(up_host);
       up_dev = up_host = nullptr;
@@ -751,6 +764,7 @@ void reset_call(Workspace* w, uint32_t flags) {
 // Reserves the workspace for a plan and uploads its tables.
 int prepare(Workspace* w, CallPlan& P, const dpc_batch* b, const std::vector<Inst>& insts,
             const dpc_params* params, uint32_t flags) {
+  sort_init();
   int rc = w->reserve(P.max_n, P.max_inst, P.ncut);
   if (rc) return rc;
   reset_call(w, flags);
@@ -864,14 +878,12 @@ int dpc_cluster(const dpc_batch* b, int32_t dcut_index, const dpc_params* params
   return finish(w, flags);
 }
 
-static int run_device(Workspace* w, const void* pts, int dtype, const dpc_batch* b,
-                      const std::vector<Inst>& insts, uint64_t N, const dpc_params* params,
-                      int32_t* rho, int32_t* lambda, double* delta, int32_t* label,
-                      uint32_t flags) {
+// The kernels of every class and cutoff (the part of dpc_run a graph holds).
+static void run_classes(Workspace* w, const CallPlan& P, const void* pts, int dtype,
+                        const dpc_batch* b, const std::vector<Inst>& insts, uint64_t N,
+                        const dpc_params* params, int32_t* rho, int32_t* lambda, double* delta,
+                        int32_t* label, uint32_t flags) {
   const bool fp64 = (flags & DPC_PREC_MASK) == DPC_PREC_FP64;
-  CallPlan P = make_plan(b, insts, 0, b->n_dcut, false);
-  int rc = prepare(w, P, b, insts, params, flags);
-  if (rc) return rc;
   for (const ClassPlan& c : P.classes) {
     const ClassView cv = view_of(w, c, insts);
     bin_class(w, pts, dtype, P, c, cv, b, insts);
@@ -886,6 +898,84 @@ static int run_device(Workspace* w, const void* pts, int dtype, const dpc_batch*
       labels_step(w, c, cv, k, one_params(params, c, P.ncut_all, k), rho + o, lambda + o,
                   delta + o, label + o);
     }
+  }
+}
+
+static int run_device(Workspace* w, const void* pts, int dtype, const dpc_batch* b,
+                      const std::vector<Inst>& insts, uint64_t N, const dpc_params* params,
+                      int32_t* rho, int32_t* lambda, double* delta, int32_t* label,
+                      uint32_t flags) {
+  CallPlan P = make_plan(b, insts, 0, b->n_dcut, false);
+  int rc = prepare(w, P, b, insts, params, flags);
+  if (rc) return rc;
+  run_classes(w, P, pts, dtype, b, insts, N, params, rho, lambda, delta, label, flags);
+  return cudaGetLastError() == cudaSuccess ? DPC_OK : DPC_ERR_CUDA;
+}
+
+// Everything a captured graph depends on: the pointers, the batch, the
+// thresholds and the flags that change the kernel sequence.
+static std::string graph_key(const void* pts, int dtype, const dpc_batch* b,
+                             const dpc_params* params, const void* rho, const void* lambda,
+                             const void* delta, const void* label, uint32_t flags) {
+  std::string k;
+  auto put = [&](const void* p, size_t n) { k.append((const char*)p, n); };
+  const void* ptrs[5] = {pts, rho, lambda, delta, label};
+  put(ptrs, sizeof(ptrs));
+  const uint32_t f = flags & (DPC_PREC_MASK | DPC_FLAG_RADIUS_MASK);
+  put(&dtype, sizeof(dtype));
+  put(&f, sizeof(f));
+  put(&b->n_inst, sizeof(b->n_inst));
+  put(&b->n_dcut, sizeof(b->n_dcut));
+  put(b->pt_offset, sizeof(int64_t) * (b->n_inst + 1));
+  put(b->dim, sizeof(int32_t) * b->n_inst);
+  if (b->coord_offset) put(b->coord_offset, sizeof(int64_t) * b->n_inst);
+  put(b->d_cut, sizeof(double) * b->n_inst * b->n_dcut);
+  put(params, sizeof(dpc_params) * b->n_inst * b->n_dcut);
+  return k;
+}
+
+// dpc_run with DPC_FLAG_GRAPH: the kernels of a call are captured into a CUDA
+// graph on the first call with a new key and replayed afterwards.  The
+// per-call work outside the graph: status reset and the instance tables' copy.
+static int run_graph(Workspace* w, const void* pts, int dtype, const dpc_batch* b,
+                     const std::vector<Inst>& insts, uint64_t N, const dpc_params* params,
+                     int32_t* rho, int32_t* lambda, double* delta, int32_t* label, uint32_t flags) {
+  if (w->stream == nullptr) return DPC_ERR_UNSUPPORTED;  // the legacy stream cannot be captured
+  const uint32_t f = flags & ~(DPC_FLAG_PHASE_TIMES | DPC_FLAG_AUTOTUNE);
+  CallPlan P = make_plan(b, insts, 0, b->n_dcut, false);
+  int rc = prepare(w, P, b, insts, params, f);
+  if (rc) return rc;
+  std::string key = graph_key(pts, dtype, b, params, rho, lambda, delta, label, f);
+  if (!w->gexec || key != w->gkey) {
+    w->drop_graph();
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(w->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return DPC_ERR_CUDA;
+    }
+    const long long before = g_kernel_launches;
+    run_classes(w, P, pts, dtype, b, insts, N, params, rho, lambda, delta, label, f);
+    const cudaError_t e1 = cudaStreamEndCapture(w->stream, &g);
+    if (e1 != cudaSuccess || g == nullptr) {
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      return DPC_ERR_CUDA;
+    }
+    const cudaError_t e2 = cudaGraphInstantiate(&w->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+      cudaGetLastError();
+      w->gexec = nullptr;
+      return DPC_ERR_CUDA;
+    }
+    w->gkey.swap(key);
+    w->glaunches = g_kernel_launches - before;
+  } else {
+    g_kernel_launches += w->glaunches;
+  }
+  if (cudaGraphLaunch(w->gexec, w->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return DPC_ERR_CUDA;
   }
   return cudaGetLastError() == cudaSuccess ? DPC_OK : DPC_ERR_CUDA;
 }
@@ -913,7 +1003,11 @@ int dpc_run(const void* pts, int dtype, const dpc_batch* b, const dpc_params* pa
   Workspace* w = nullptr;
   if ((rc = get_workspace((cudaStream_t)stream, &w))) return rc;
   std::lock_guard<std::mutex> lk(g_mu);
-  if ((rc = run_device(w, pts, dtype, b, insts, N, params, rho, lambda, delta, label, flags))) return rc;
+  if (flags & DPC_FLAG_GRAPH)
+    rc = run_graph(w, pts, dtype, b, insts, N, params, rho, lambda, delta, label, flags);
+  else
+    rc = run_device(w, pts, dtype, b, insts, N, params, rho, lambda, delta, label, flags);
+  if (rc) return rc;
   return finish(w, flags);
 }
 

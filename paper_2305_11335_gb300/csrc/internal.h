@@ -54,6 +54,8 @@ void launch_cells(const unsigned long long* scode, const ClassView& cv, int g, c
 
 // ---- radix sort (sort.cu) ------------------------------------------------------
 size_t sort_hist_words(uint32_t n);
+// one-time kernel attribute setup (called before any stream capture)
+void sort_init();
 // Sorts (codes_a, ids_a) by code, LSD over the device-side pass count
 // sort_passes(cls->S, cls->ib); the result lands in the _a buffers if that
 // count is even, else in _b.

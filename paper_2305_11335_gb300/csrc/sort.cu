@@ -204,17 +204,21 @@ inline uint32_t tiles_for(uint32_t n) { return (n + kRsTile - 1) / kRsTile; }
 
 size_t sort_hist_words(uint32_t n) { return (size_t)257 * (tiles_for(n) ? tiles_for(n) : 1); }
 
-void launch_sort(unsigned long long* codes_a, unsigned long long* codes_b, uint32_t* ids_a,
-                 uint32_t* ids_b, uint32_t n, const ClassGeom* cls, uint32_t* hist,
-                 cudaStream_t st) {
-  if (n == 0) return;
-  const uint32_t nt = tiles_for(n);
+void sort_init() {
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(ScatterSmem));
     attr_set = true;
   }
+}
+
+void launch_sort(unsigned long long* codes_a, unsigned long long* codes_b, uint32_t* ids_a,
+                 uint32_t* ids_b, uint32_t n, const ClassGeom* cls, uint32_t* hist,
+                 cudaStream_t st) {
+  if (n == 0) return;
+  const uint32_t nt = tiles_for(n);
+  sort_init();
   unsigned long long* kb[2] = {codes_a, codes_b};
   uint32_t* vb[2] = {ids_a, ids_b};
   for (int pass = 0; pass < kMaxPasses; ++pass) {

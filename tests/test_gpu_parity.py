@@ -249,3 +249,52 @@ def test_autotune_keeps_results_and_caches():
     assert r1 == r2 and 1 <= r1 <= 3
     for out in (first, again):
         assert_same({k: v[0].cpu().numpy() for k, v in out.items()}, ref)
+
+
+def test_graph_mode_replays_and_recaptures():
+    """DPC_FLAG_GRAPH: capture on the first call, replay on identical calls
+    (new coordinates in the same buffer are picked up), capture again when
+    the batch changes; every result equals the oracle's."""
+    s = torch.cuda.Stream()
+    n, d = 6000, 2
+    sets = [W.random_blobs(n, d, 7100 + i) for i in range(3)]
+    t = torch.from_numpy(sets[0]).cuda()
+    torch.cuda.synchronize()
+    for cuts in ([0.02, 0.03], [0.025]):
+        batch = dpc.Batch.single(n, d, cuts)
+        params = dpc.make_params(batch, 2, 3, 0.1)
+        out = {"rho": torch.empty((len(cuts), n), dtype=torch.int32, device="cuda"),
+               "lam": torch.empty((len(cuts), n), dtype=torch.int32, device="cuda"),
+               "delta": torch.empty((len(cuts), n), dtype=torch.float64, device="cuda"),
+               "label": torch.empty((len(cuts), n), dtype=torch.int32, device="cuda")}
+        for rep, pts in enumerate(sets):
+            with torch.cuda.stream(s):
+                t.copy_(torch.from_numpy(pts))
+                dpc.dpc_run(t, batch, params, stream=s, out=out, graph=True, sync=True)
+            for c, dc in enumerate(cuts):
+                ref = oracle.run(pts, dc, 2, 3, 0.1)
+                assert_same({k: v[c].cpu().numpy() for k, v in out.items()}, ref,
+                            "cuts %r rep %d cut %d" % (cuts, rep, c))
+    assert dpc.dpc_get_stats(s)["kernel_launches"] > 10
+
+
+def test_graph_mode_batch():
+    """A multi-class batch in graph mode: the instance tables are copied before
+    every replay."""
+    s = torch.cuda.Stream()
+    sizes, dims = [300, 0, 1, 900, 45, 2000, 64], [2, 3, 3, 5, 2, 3, 7]
+    insts = [W.random_blobs(nn, dd, 7300 + i) if nn else np.zeros((0, dd), np.float32)
+             for i, (nn, dd) in enumerate(zip(sizes, dims))]
+    cuts = [[0.05 * (1 + 0.3 * (dd - 1))] for dd in dims]
+    batch = dpc.Batch.packed(sizes, dims, cuts)
+    params = dpc.make_params(batch, 2, 3, 0.1)
+    t = torch.from_numpy(np.concatenate([p.reshape(-1) for p in insts]).astype(np.float32)).cuda()
+    torch.cuda.synchronize()
+    for rep in range(3):
+        with torch.cuda.stream(s):
+            out = dpc.dpc_run(t, batch, params, stream=s, graph=True, sync=True)
+        out = {k: v.cpu().numpy() for k, v in out.items()}
+        for i, p in enumerate(insts):
+            lo, hi = batch.pt_offset[i], batch.pt_offset[i + 1]
+            ref = oracle.run(p, cuts[i][0], 2, 3, 0.1)
+            assert_same({k: v[0, lo:hi] for k, v in out.items()}, ref, "rep %d inst %d" % (rep, i))
