@@ -83,11 +83,12 @@ enum {
 #define DPC_FLAG_SYNC_CHECK (1u << 8)  /* synchronize and return the device status */
 #define DPC_FLAG_PHASE_TIMES (1u << 9) /* record CUDA events around every phase
                                           (read with dpc_get_phase_times)      */
-/* Autotune the grid level: the first dpc_run / dpc_density call that sees a
- * new (dimension class, instance count, point count, cutoff) shape runs the
- * cell-hash and density steps once per candidate block radius (R = 1, 2, 3
- * for d <= 2; R = 1, 2 for d = 3; d >= 4 has R = 1 only; the cells shrink as R
- * grows), timing each
+/* Autotune the grid level and the kernel layouts: the first dpc_run /
+ * dpc_density call that sees a new (dimension class, instance count, point
+ * count, cutoff) shape runs the cell-hash step, the density kernel and (for
+ * dpc_run) the near-dependent kernel in both layouts once per candidate block
+ * radius (R = 1, 2, 3 for d <= 2; R = 1, 2 for d = 3; d >= 4 has R = 1 only;
+ * the cells shrink as R grows), timing each
  * with CUDA events and synchronizing the stream, and keeps the fastest for
  * that shape in the workspace; later calls (with or without the flag) reuse
  * the choice without synchronizing.  Results do not depend on the choice.
@@ -98,6 +99,14 @@ enum {
  * d <= 2, 2 for d = 3, 1 for d >= 4).  Results do not depend on it. */
 #define DPC_FLAG_RADIUS(r) ((uint32_t)(r) << 12)
 #define DPC_FLAG_RADIUS_MASK (0x7u << 12)
+/* Fixed work layout of the density and near-dependent kernels instead of the
+ * default rule (segments for d = 3, union otherwise) or the autotuned choice:
+ * 1 = union (a warp's 32 consecutive points, one query per lane, the union of
+ * their blocks streamed as broadcast reads), 2 = segment (the block of one
+ * cell spread over the lanes, the cell's queries one at a time).  Results do
+ * not depend on it. */
+#define DPC_FLAG_LAYOUT(v) ((uint32_t)(v) << 16)
+#define DPC_FLAG_LAYOUT_MASK (0x3u << 16)
 /* dpc_run only: capture the call's kernels into a CUDA graph the first time a
  * (pointers, batch, thresholds, precision, radius) combination is seen, and on
  * later calls with the same combination launch that graph instead of one

@@ -82,6 +82,13 @@ def DPC_FLAG_RADIUS(r: int) -> int:
     return (int(r) & 7) << 12
 
 
+LAYOUTS = {"auto": 0, "union": 1, "segment": 2}
+
+
+def DPC_FLAG_LAYOUT(layout: str) -> int:
+    return LAYOUTS[layout] << 16
+
+
 class _PhaseTimes(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * len(PHASES)), ("launches", ctypes.c_int64 * len(PHASES))]
 
@@ -221,11 +228,12 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _flags(precision: str, sync: bool, radius: int = 0, autotune: bool = False) -> int:
+def _flags(precision: str, sync: bool, radius: int = 0, autotune: bool = False, layout: str = "auto") -> int:
     """Call flags: precision mode, synchronous status check, a fixed block
-    radius (0 = default rule or autotuned choice) and autotuning."""
+    radius (0 = default rule or autotuned choice), autotuning and a fixed
+    kernel layout ("auto" = default rule or autotuned choice)."""
     return (PREC[precision] | (DPC_FLAG_SYNC_CHECK if sync else 0) | DPC_FLAG_RADIUS(radius)
-            | (DPC_FLAG_AUTOTUNE if autotune else 0))
+            | (DPC_FLAG_AUTOTUNE if autotune else 0) | DPC_FLAG_LAYOUT(layout))
 
 
 def _check(rc: int, what: str):
@@ -235,16 +243,17 @@ def _check(rc: int, what: str):
 
 def dpc_density(pts: torch.Tensor, batch: Batch, precision: str = "fp32", sync: bool = False,
                 stream=None, out: torch.Tensor | None = None, autotune: bool = False,
-                radius: int = 0) -> torch.Tensor:
+                radius: int = 0, layout: str = "auto") -> torch.Tensor:
     lib = load()
     rho = out if out is not None else torch.empty((batch.n_dcut, batch.N), dtype=torch.int32, device=pts.device)
     _check(lib.dpc_density(_dev(pts, "pts"), _dtype_code(pts), batch.ptr, _dev(rho, "rho"),
-                           _flags(precision, sync, radius, autotune), _stream(stream)), "dpc_density")
+                           _flags(precision, sync, radius, autotune, layout), _stream(stream)), "dpc_density")
     return rho
 
 
 def dpc_dependent(pts: torch.Tensor, batch: Batch, dcut_index: int, rho: torch.Tensor, rho_skip: int = 0,
-                  precision: str = "fp32", sync: bool = False, stream=None, radius: int = 0):
+                  precision: str = "fp32", sync: bool = False, stream=None, radius: int = 0,
+                  layout: str = "auto"):
     lib = load()
     if rho.dtype != torch.int32 or rho.numel() != batch.N:
         raise ValueError("rho must be int32 [N]")
@@ -252,7 +261,7 @@ def dpc_dependent(pts: torch.Tensor, batch: Batch, dcut_index: int, rho: torch.T
     delta = torch.empty(batch.N, dtype=torch.float64, device=pts.device)
     _check(lib.dpc_dependent(_dev(pts, "pts"), _dtype_code(pts), batch.ptr, int(dcut_index), _dev(rho, "rho"),
                              int(rho_skip), _dev(lam, "lambda"), _dev(delta, "delta"),
-                             _flags(precision, sync, radius), _stream(stream)), "dpc_dependent")
+                             _flags(precision, sync, radius, False, layout), _stream(stream)), "dpc_dependent")
     return lam, delta
 
 
@@ -268,7 +277,7 @@ def dpc_cluster(batch: Batch, dcut_index: int, params, rho: torch.Tensor, lam: t
 
 def dpc_run(pts: torch.Tensor, batch: Batch, params, precision: str = "fp32", sync: bool = False, stream=None,
             out: dict | None = None, phase_times: bool = False, autotune: bool = False,
-            radius: int = 0, graph: bool = False) -> dict:
+            radius: int = 0, graph: bool = False, layout: str = "auto") -> dict:
     lib = load()
     shape = (batch.n_dcut, batch.N)
     if out is None:
@@ -278,7 +287,7 @@ def dpc_run(pts: torch.Tensor, batch: Batch, params, precision: str = "fp32", sy
                "label": torch.empty(shape, dtype=torch.int32, device=pts.device)}
     _check(lib.dpc_run(_dev(pts, "pts"), _dtype_code(pts), batch.ptr, params, _dev(out["rho"], "rho"),
                        _dev(out["lam"], "lambda"), _dev(out["delta"], "delta"), _dev(out["label"], "label"),
-                       _flags(precision, sync, radius, autotune) | (DPC_FLAG_PHASE_TIMES if phase_times else 0)
+                       _flags(precision, sync, radius, autotune, layout) | (DPC_FLAG_PHASE_TIMES if phase_times else 0)
                        | (DPC_FLAG_GRAPH if graph else 0), _stream(stream)),
            "dpc_run")
     return out
@@ -342,7 +351,7 @@ def dpc_last_status(stream=None) -> int:
 
 
 def run(pts: torch.Tensor, d_cut, rho_noise, rho_min, delta_min, precision: str = "fp32", sync: bool = True,
-        stream=None, autotune: bool = False, radius: int = 0) -> dict:
+        stream=None, autotune: bool = False, radius: int = 0, layout: str = "auto") -> dict:
     """DPC of one point set ``pts`` [n, d] (CUDA, int32/float32) for one or more cutoffs."""
     if pts.dim() == 1:
         pts = pts.reshape(-1, 1)
@@ -351,5 +360,5 @@ def run(pts: torch.Tensor, d_cut, rho_noise, rho_min, delta_min, precision: str 
     batch = Batch.single(n, d, cuts)
     params = make_params(batch, rho_noise, rho_min, delta_min)
     return dpc_run(pts.contiguous(), batch, params, precision=precision, sync=sync, stream=stream,
-                   autotune=autotune, radius=radius)
+                   autotune=autotune, radius=radius, layout=layout)
 

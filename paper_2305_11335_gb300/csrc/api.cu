@@ -87,13 +87,15 @@ int check_batch(const dpc_batch* b, std::vector<Inst>* insts, uint64_t* total) {
 }
 
 constexpr uint32_t kKnownFlags = DPC_PREC_MASK | DPC_FLAG_SYNC_CHECK | DPC_FLAG_PHASE_TIMES |
-                                 DPC_FLAG_AUTOTUNE | DPC_FLAG_RADIUS_MASK | DPC_FLAG_GRAPH;
+                                 DPC_FLAG_AUTOTUNE | DPC_FLAG_RADIUS_MASK | DPC_FLAG_GRAPH |
+                                 DPC_FLAG_LAYOUT_MASK;
 
 int check_flags(uint32_t flags) {
   const uint32_t prec = flags & DPC_PREC_MASK;
   if (prec != DPC_PREC_FP64 && prec != DPC_PREC_FP32_CERT) return DPC_ERR_UNSUPPORTED;
   if (flags & ~kKnownFlags) return DPC_ERR_ARG;
   if (((flags & DPC_FLAG_RADIUS_MASK) >> 12) > 5) return DPC_ERR_ARG;
+  if (((flags & DPC_FLAG_LAYOUT_MASK) >> 16) > 2) return DPC_ERR_ARG;
   return DPC_OK;
 }
 
@@ -148,6 +150,14 @@ std::vector<ClassPlan> plan_classes(const std::vector<Inst>& insts, bool all_one
   return out;
 }
 
+// Grid level and kernel layouts chosen for one (class, cutoff); r = 0: the
+// default rule.
+struct Choice {
+  int r = 0;
+  int dlay = 0;  // density layout (kLayout*)
+  int nlay = 0;  // near-phase layout
+};
+
 struct Workspace {
   int device = -1;
   cudaStream_t stream = nullptr;
@@ -162,6 +172,7 @@ struct Workspace {
   ClassGeom* cls = nullptr;
   HashInfo* hinfo = nullptr;
   Counters* ctr = nullptr;
+  Counters* ctr_save = nullptr;  // the counters during autotuning trials
   int* status = nullptr;
   int32_t* flags = nullptr;
   uint32_t* roots = nullptr;  // [cap_inst]
@@ -210,9 +221,9 @@ struct Workspace {
     gkey.clear();
   }
 
-  // autotuned block radius per (class shape, cutoff), see tune_radius
-  std::map<std::string, int> tuned;
-  cudaEvent_t tune_a = nullptr, tune_b = nullptr;
+  // autotuned radius and layouts per (class shape, cutoff), see choose()
+  std::map<std::string, Choice> tuned;
+  cudaEvent_t tune_ev[6] = {};
 
   // for dpc_get_stats: the last class and cutoff that ran
   const CutGeom* last_cut = nullptr;
@@ -258,10 +269,12 @@ struct Workspace {
     if (up_dev) cudaFree(up_dev);
     if (up_host) cudaFreeHost(up_host);
     if (up_done) cudaEventDestroy(up_done);
-    if (tune_a) cudaEventDestroy(tune_a);
-    if (tune_b) cudaEventDestroy(tune_b);
+    for (auto& e : tune_ev) {
+      if (e) cudaEventDestroy(e);
+      e = nullptr;
+    }
     base = io = up_dev = up_host = nullptr;
-    up_done = tune_a = tune_b = nullptr;
+    up_done = nullptr;
     tuned.clear();
     bytes = io_bytes = up_bytes = 0;
     cap_n = 0;
@@ -291,6 +304,7 @@ struct Workspace {
     const size_t o_cls = take(sizeof(ClassGeom));
     const size_t o_hi = take(sizeof(HashInfo));
     const size_t o_ctr = take(sizeof(Counters));
+    const size_t o_ctr2 = take(sizeof(Counters));
     const size_t o_status = take(sizeof(int));
     const size_t o_flags = take(sizeof(int32_t) * 80);
     const size_t o_roots = take(sizeof(uint32_t) * want_i);
@@ -323,6 +337,7 @@ struct Workspace {
     cls = (ClassGeom*)(b + o_cls);
     hinfo = (HashInfo*)(b + o_hi);
     ctr = (Counters*)(b + o_ctr);
+    ctr_save = (Counters*)(b + o_ctr2);
     status = (int*)(b + o_status);
     flags = (int32_t*)(b + o_flags);
     roots = (uint32_t*)(b + o_roots);
@@ -638,15 +653,15 @@ void cells_step(Workspace* w, const ClassPlan& c, const ClassView& cv, const Cut
 }
 
 void density_step(Workspace* w, const ClassPlan& c, const ClassView& cv, const CutGeom* cuts,
-                  bool fp64, int32_t* rho) {
+                  bool fp64, int layout, int32_t* rho) {
   Phase ph(w, DPC_PHASE_DENSITY);
-  launch_density(c.dp, c.g, fp64, w->spts, w->scode, w->sid, cv, cuts, w->hinfo, w->hkeys,
+  launch_density(c.dp, c.g, fp64, layout, w->spts, w->scode, w->sid, cv, cuts, w->hinfo, w->hkeys,
                  w->hvals, rho, w->skey, w->ctr, w->stream);
 }
 
 void dependent_step(Workspace* w, const ClassPlan& c, const ClassView& cv, const CutGeom* cuts,
-                    const void* pts, int dtype, int32_t rho_skip, bool fp64, int32_t* lambda,
-                    double* delta) {
+                    const void* pts, int dtype, int32_t rho_skip, bool fp64, int layout,
+                    int32_t* lambda, double* delta) {
   cudaStream_t st = w->stream;
   {
     Phase ph(w, DPC_PHASE_MAXKEY);
@@ -656,8 +671,8 @@ void dependent_step(Workspace* w, const ClassPlan& c, const ClassView& cv, const
   }
   {
     Phase ph(w, DPC_PHASE_NEAR);
-    launch_dep_near(c.dp, c.g, fp64, w->spts, w->scode, w->skey, cv, rho_skip, pts, dtype, cuts,
-                    w->hinfo, w->hkeys, w->hvals, lambda, delta, queue_of(w), w->ctr, st);
+    launch_dep_near(c.dp, c.g, fp64, layout, w->spts, w->scode, w->skey, cv, rho_skip, pts, dtype,
+                    cuts, w->hinfo, w->hkeys, w->hvals, lambda, delta, queue_of(w), w->ctr, st);
   }
   {
     Phase ph(w, DPC_PHASE_FAR);
@@ -707,52 +722,96 @@ std::string tune_key(const ClassPlan& c, const dpc_batch* b, int cut) {
   return buf;
 }
 
-// Applies the radius preference of (class, cutoff) to cuts ([ninst]),
-// measuring it first when the call asked for autotuning and the shape is new.
-// rho_scratch receives the densities of the trial runs.
-void apply_radius(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cuts,
-                  const dpc_batch* b, int cut, bool fp64, int32_t* rho_scratch, uint32_t flags) {
-  const int fixed = (int)((flags & DPC_FLAG_RADIUS_MASK) >> 12);
-  if (fixed > 0) {
-    launch_set_radius(cv, cuts, fixed, w->stream);
-    return;
-  }
-  const std::string key = tune_key(c, b, cut);
+// What a tuning trial of the dependent step needs (null: density only).
+struct NearTrial {
+  const void* pts;
+  int dtype;
+  int32_t* lambda;  // scratch outputs of the trial
+  double* delta;
+};
+
+inline int default_layout(int g) { return g == 3 ? kLayoutSegment : kLayoutUnion; }
+
+// The grid level and kernel layouts of one (class, cutoff): a fixed radius or
+// layout from the flags, else the autotuned choice (measured now when the
+// call asks for autotuning and the shape is new, cached otherwise), else the
+// default rule.  A trial, per radius, times cells, then density and the near
+// phase in both layouts (after one untimed pass that loads the kernels and
+// warms the caches); the radius with the least cells + best density + best near
+// wins, with its best layouts.  The counters are saved around the trials;
+// rho_scratch (and the NearTrial outputs) receive the trials' results.
+Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cuts,
+              const dpc_batch* b, int cut, bool fp64, int32_t* rho_scratch, uint32_t flags,
+              const NearTrial* near = nullptr) {
+  Choice ch;
+  ch.r = (int)((flags & DPC_FLAG_RADIUS_MASK) >> 12);
+  const int forced = (int)((flags & DPC_FLAG_LAYOUT_MASK) >> 16);
+  ch.dlay = ch.nlay = forced ? forced : default_layout(c.g);
+  const std::string key = (near ? "R/" : "D/") + tune_key(c, b, cut);
   auto it = w->tuned.find(key);
-  if (it == w->tuned.end() && (flags & DPC_FLAG_AUTOTUNE) && c.g >= 4) {
-    it = w->tuned.emplace(key, 1).first;  // (2R+1)^4 cells: only R = 1 fits a union
-  } else if (it == w->tuned.end() && (flags & DPC_FLAG_AUTOTUNE)) {
+  if (ch.r == 0 && !forced && it == w->tuned.end() && (flags & DPC_FLAG_AUTOTUNE)) {
     cudaStream_t st = w->stream;
-    if (!w->tune_a) {
-      cudaEventCreate(&w->tune_a);
-      cudaEventCreate(&w->tune_b);
-    }
-    const int rmax = c.g == 3 ? 2 : 3;
-    float best_ms = 0.f;
-    int best = 0;
-    for (int r = 1; r <= rmax; ++r) {
+    if (!w->tune_ev[0])
+      for (auto& e : w->tune_ev) cudaEventCreate(&e);
+    cudaMemcpyAsync(w->ctr_save, w->ctr, sizeof(Counters), cudaMemcpyDeviceToDevice, st);
+    const int lays[2] = {kLayoutUnion, kLayoutSegment};
+    auto trial = [&](int r, bool timed) {
+      if (timed) cudaEventRecord(w->tune_ev[0], st);
       launch_set_radius(cv, cuts, r, st);
-      cudaEventRecord(w->tune_a, st);
       launch_cells(w->scode, cv, c.g, cuts, w->hinfo, w->hkeys, w->hvals, w->hcap, st);
-      launch_density(c.dp, c.g, fp64, w->spts, w->scode, w->sid, cv, cuts, w->hinfo, w->hkeys,
-                     w->hvals, rho_scratch, w->skey, w->ctr, st);
-      cudaEventRecord(w->tune_b, st);
+      if (timed) cudaEventRecord(w->tune_ev[1], st);
+      for (int l = 0; l < 2; ++l) {
+        launch_density(c.dp, c.g, fp64, lays[l], w->spts, w->scode, w->sid, cv, cuts, w->hinfo,
+                       w->hkeys, w->hvals, rho_scratch, w->skey, w->ctr, st);
+        if (timed) cudaEventRecord(w->tune_ev[2 + l], st);
+      }
+      for (int l = 0; near && l < 2; ++l) {
+        launch_dep_near(c.dp, c.g, fp64, lays[l], w->spts, w->scode, w->skey, cv, 0, near->pts,
+                        near->dtype, cuts, w->hinfo, w->hkeys, w->hvals, near->lambda, near->delta,
+                        queue_of(w), w->ctr, st);
+        if (timed) cudaEventRecord(w->tune_ev[4 + l], st);
+      }
+    };
+    auto span = [&](int a, int z) {
       float ms = 0.f;
-      if (cudaEventSynchronize(w->tune_b) != cudaSuccess ||
-          cudaEventElapsedTime(&ms, w->tune_a, w->tune_b) != cudaSuccess) {
+      if (cudaEventElapsedTime(&ms, w->tune_ev[a], w->tune_ev[z]) != cudaSuccess) {
         cudaGetLastError();
-        best = 0;
+        return 1e30f;
+      }
+      return ms;
+    };
+    const int rmax = c.g >= 4 ? 1 : (c.g == 3 ? 2 : 3);
+    trial(1, false);  // untimed: module loading, caches
+    Choice best;
+    float best_ms = 0.f;
+    for (int r = 1; r <= rmax; ++r) {
+      trial(r, true);
+      if (cudaEventSynchronize(w->tune_ev[near ? 5 : 3]) != cudaSuccess) {
+        cudaGetLastError();
+        best = Choice();
         break;
       }
-      if (best == 0 || ms < best_ms) {
+      const float dU = span(1, 2), dS = span(2, 3);
+      float ms = span(0, 1) + fminf(dU, dS);
+      int nl = default_layout(c.g);
+      if (near) {
+        const float nU = span(3, 4), nS = span(4, 5);
+        ms += fminf(nU, nS);
+        nl = nU <= nS ? kLayoutUnion : kLayoutSegment;
+      }
+      if (best.r == 0 || ms < best_ms) {
         best_ms = ms;
-        best = r;
+        best.r = r;
+        best.dlay = dU <= dS ? kLayoutUnion : kLayoutSegment;
+        best.nlay = nl;
       }
     }
+    cudaMemcpyAsync(w->ctr, w->ctr_save, sizeof(Counters), cudaMemcpyDeviceToDevice, st);
     it = w->tuned.emplace(key, best).first;
   }
-  const int r = it == w->tuned.end() ? 0 : it->second;
-  if (r > 0) launch_set_radius(cv, cuts, r, w->stream);
+  if (ch.r == 0 && !forced && it != w->tuned.end() && it->second.r > 0) ch = it->second;
+  if (ch.r > 0) launch_set_radius(cv, cuts, ch.r, w->stream);
+  return ch;
 }
 
 void reset_call(Workspace* w, uint32_t flags) {
@@ -814,9 +873,9 @@ int dpc_density(const void* pts, int dtype, const dpc_batch* b, int32_t* rho, ui
     bin_class(w, pts, dtype, P, c, cv, b, insts);
     for (int k = 0; k < P.ncut; ++k) {
       CutGeom* cuts = w->cuts + (size_t)k * cv.ninst;
-      apply_radius(w, c, cv, cuts, b, k, fp64, rho + (size_t)k * N, flags);
+      const Choice ch = choose(w, c, cv, cuts, b, k, fp64, rho + (size_t)k * N, flags);
       cells_step(w, c, cv, cuts);
-      density_step(w, c, cv, cuts, fp64, rho + (size_t)k * N);
+      density_step(w, c, cv, cuts, fp64, ch.dlay, rho + (size_t)k * N);
     }
   }
   return finish(w, flags);
@@ -843,10 +902,11 @@ int dpc_dependent(const void* pts, int dtype, const dpc_batch* b, int32_t dcut_i
     const ClassView cv = view_of(w, c, insts);
     bin_class(w, pts, dtype, P, c, cv, b, insts);
     tree_step(w, cv);
-    apply_radius(w, c, cv, w->cuts, b, dcut_index, fp64, nullptr, flags & ~DPC_FLAG_AUTOTUNE);
+    const Choice ch = choose(w, c, cv, w->cuts, b, dcut_index, fp64, nullptr,
+                             flags & ~DPC_FLAG_AUTOTUNE, nullptr);
     cells_step(w, c, cv, w->cuts);
     launch_keys_from_rho(rho, w->sid, cv.N, w->skey, w->stream);
-    dependent_step(w, c, cv, w->cuts, pts, dtype, rho_skip, fp64, lambda, delta);
+    dependent_step(w, c, cv, w->cuts, pts, dtype, rho_skip, fp64, ch.nlay, lambda, delta);
   }
   return finish(w, flags);
 }
@@ -891,10 +951,11 @@ static void run_classes(Workspace* w, const CallPlan& P, const void* pts, int dt
     for (int k = 0; k < P.ncut; ++k) {
       const size_t o = (size_t)k * N;
       CutGeom* cuts = w->cuts + (size_t)k * cv.ninst;
-      apply_radius(w, c, cv, cuts, b, k, fp64, rho + o, flags);
+      const NearTrial nt{pts, dtype, lambda + o, delta + o};
+      const Choice ch = choose(w, c, cv, cuts, b, k, fp64, rho + o, flags, &nt);
       cells_step(w, c, cv, cuts);
-      density_step(w, c, cv, cuts, fp64, rho + o);
-      dependent_step(w, c, cv, cuts, pts, dtype, 0, fp64, lambda + o, delta + o);
+      density_step(w, c, cv, cuts, fp64, ch.dlay, rho + o);
+      dependent_step(w, c, cv, cuts, pts, dtype, 0, fp64, ch.nlay, lambda + o, delta + o);
       labels_step(w, c, cv, k, one_params(params, c, P.ncut_all, k), rho + o, lambda + o,
                   delta + o, label + o);
     }
@@ -921,7 +982,7 @@ static std::string graph_key(const void* pts, int dtype, const dpc_batch* b,
   auto put = [&](const void* p, size_t n) { k.append((const char*)p, n); };
   const void* ptrs[5] = {pts, rho, lambda, delta, label};
   put(ptrs, sizeof(ptrs));
-  const uint32_t f = flags & (DPC_PREC_MASK | DPC_FLAG_RADIUS_MASK);
+  const uint32_t f = flags & (DPC_PREC_MASK | DPC_FLAG_RADIUS_MASK | DPC_FLAG_LAYOUT_MASK);
   put(&dtype, sizeof(dtype));
   put(&f, sizeof(f));
   put(&b->n_inst, sizeof(b->n_inst));

@@ -222,6 +222,55 @@ __device__ __forceinline__ Pt<DP> window_pt(const float* __restrict__ wpts, uint
   return p;
 }
 
+// Block of radius R around cell c0, clipped to the grid.
+template <int G>
+__device__ __forceinline__ void block_union(const uint32_t* c0, int R, int cmax, Union<G>& u) {
+  int n = 1;
+#pragma unroll
+  for (int a = 0; a < G; ++a) {
+    const int lo = max((int)c0[a] - R, 0);
+    const int hi = min((int)c0[a] + R, cmax);
+    u.lo[a] = lo;
+    u.w[a] = hi - lo + 1;
+    u.inv[a] = (65536 + u.w[a] - 1) / u.w[a];
+    n *= u.w[a];
+  }
+  u.ncell = n;
+}
+
+// This lane's candidates w0 + lane + 32 v (v < V) of the run table, NaN
+// coordinates past the end (a NaN distance fails every comparison); with
+// KEYS also their order keys (0 past the end: below every query's key).
+template <int DP, int V, bool KEYS = false>
+__device__ __forceinline__ void load_window(const RunTable& rt, int nr, uint32_t w0, uint32_t total,
+                                            const float* __restrict__ spts, int lane, Pt<DP>* cand,
+                                            const unsigned long long* __restrict__ skey = nullptr,
+                                            unsigned long long* ck = nullptr) {
+  const uint32_t e0 = w0 + lane;
+  int lo = 0, hi = nr - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (rt.pre[mid] <= e0) lo = mid;
+    else hi = mid - 1;
+  }
+  int r = lo;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const uint32_t e = e0 + 32u * v;
+    if (w0 + 32u * v >= total) break;  // no lane has a candidate in this slot or later
+    if (e < total) {
+      while (r + 1 < nr && rt.pre[r + 1] <= e) ++r;
+      const uint32_t src = rt.start[r] + (e - rt.pre[r]);
+      cand[v] = load_pt<DP>(spts, src);
+      if constexpr (KEYS) ck[v] = __ldg(skey + src);
+    } else {
+#pragma unroll
+      for (int a = 0; a < DP; ++a) cand[v].x[a] = __int_as_float(0x7fffffff);
+      if constexpr (KEYS) ck[v] = 0ull;
+    }
+  }
+}
+
 // Does the block of radius R around cell c0 contain cell c?
 template <int G>
 __device__ __forceinline__ bool in_block(const uint32_t* c0, const uint32_t* c, int R) {

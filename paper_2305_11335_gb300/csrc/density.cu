@@ -143,6 +143,121 @@ k_density(const float* __restrict__ spts, const unsigned long long* __restrict__
   }
 }
 
+// ---------------------------------------------------------------------------
+// Segment form: the 32 points of a chunk are split into segments of equal
+// level-k cell; for each segment the warp looks up that cell's (2R+1)^g block
+// and spreads the block's candidates over the lanes (V per lane, held in
+// registers), then walks the segment's queries one by one: every lane
+// compares its V candidates with the query (read as a broadcast) and one warp
+// reduction gives the query's count.  No lane evaluates a candidate outside
+// the query's block, so the work is exactly the block's pairs.
+
+template <int DP>
+constexpr int seg_v() { return DP == 2 ? 16 : (DP == 4 ? 8 : 4); }
+
+template <int DP, int G, bool F64>
+__global__ void __launch_bounds__(kThreads, 5)
+k_density_seg(const float* __restrict__ spts, const unsigned long long* __restrict__ scode,
+              const uint32_t* __restrict__ sid, ClassView cv, const CutGeom* __restrict__ cuts,
+              const HashInfo* __restrict__ hi, const unsigned long long* __restrict__ hkeys,
+              const uint2* __restrict__ hvals, int32_t* __restrict__ rho_out,
+              unsigned long long* __restrict__ skey, Counters* ctr) {
+  constexpr int V = seg_v<DP>();
+  constexpr uint32_t W = 32u * V;
+  __shared__ RunTable s_rt[kWarps];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  RunTable& rt = s_rt[wib];
+  const int S = cv.cls->S, ib = cv.cls->ib;
+  const uint32_t hmask = hi->hmask;
+  const uint32_t n = cv.N;
+
+  unsigned long long band = 0;
+  for (uint32_t ch = blockIdx.x * kWarps + wib; ch < cv.nchunk; ch += gridDim.x * kWarps) {
+    uint32_t inst, p0, end;
+    cv.chunk(ch, inst, p0, end);
+    const CutGeom& C = cuts[inst];
+    const int k = C.k;
+    const int R = C.R;
+    const int shift = G * k;
+    const int cmax = (1 << (cv.geom[inst].B - k)) - 1;
+    const double dc2 = C.dc2;
+    const float t_in = C.t_in, t_out = C.t_out;
+    const unsigned long long hb = ib ? ((unsigned long long)inst << S) : 0ull;
+    const uint32_t p = p0 + lane;
+    const bool valid = p < end;
+    const unsigned long long mycell = valid ? (key_code(scode[p], S, ib) >> shift) : ~0ull;
+    const int nvalid = (int)min(32u, end - p0);
+    int32_t acc = 0;  // lane j: the count of query p0 + j
+    int s = 0;
+    while (s < nvalid) {
+      const unsigned long long cell = __shfl_sync(kFull, mycell, s);
+      const int e = s + __popc(__ballot_sync(kFull, valid && mycell == cell));  // queries s .. e-1
+      uint32_t c0[G];
+      unmorton<G>(cell, c0);
+      Union<G> u;
+      block_union<G>(c0, R, cmax, u);
+      const int nr = union_runs<G>(u, hkeys, hvals, hmask, hb, n, lane, rt);
+      const uint32_t total = rt.pre[nr];
+      for (uint32_t w0 = 0; w0 < total; w0 += W) {
+        Pt<DP> cand[V];
+        load_window<DP, V>(rt, nr, w0, total, spts, lane, cand);
+        // slots of this window that hold candidates (warp-uniform)
+        const int vn = (int)min((uint32_t)V, (total - w0 + 31u) / 32u);
+        for (int j = s; j < e; ++j) {
+          const Pt<DP> xq = load_pt<DP>(spts, p0 + j);
+          int32_t cnt;
+          if constexpr (F64) {
+            int c = 0;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              if (v >= vn) break;
+              c += dist64<DP>(xq, cand[v]) <= dc2;
+            }
+            cnt = (int32_t)__reduce_add_sync(kFull, (unsigned)c);
+          } else {
+            int ci = 0, co = 0;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              if (v >= vn) break;
+              const float s32 = dist32<DP>(xq, cand[v]);
+              ci += s32 <= t_in;
+              co += s32 <= t_out;
+            }
+            cnt = (int32_t)__reduce_add_sync(kFull, (unsigned)ci);
+            const int32_t cnt_out = (int32_t)__reduce_add_sync(kFull, (unsigned)co);
+            if (cnt_out != cnt) {  // band pairs: recount them in binary64
+              int in = 0, seen = 0;
+#pragma unroll
+              for (int v = 0; v < V; ++v) {
+                if (v >= vn) break;
+                const float s32 = dist32<DP>(xq, cand[v]);
+                if (s32 > t_in && s32 <= t_out) {
+                  ++seen;
+                  in += dist64<DP>(xq, cand[v]) <= dc2;
+                }
+              }
+              cnt += (int32_t)__reduce_add_sync(kFull, (unsigned)in);
+              const unsigned seen_all = __reduce_add_sync(kFull, (unsigned)seen);
+              if (lane == 0) band += seen_all;
+            }
+          }
+          if (lane == j) acc += cnt;
+        }
+      }
+      s = e;
+    }
+    if (valid) {
+      const uint32_t id = sid[p];
+      rho_out[id] = acc;
+      skey[p] = order_key(acc, id);
+    }
+  }
+  if constexpr (!F64) {
+    if (lane == 0 && band) atomicAdd(&ctr->band_pairs, band);
+  }
+}
+
 __global__ void k_keys_from_rho(const int32_t* __restrict__ rho, const uint32_t* __restrict__ sid,
                                 uint32_t n, unsigned long long* __restrict__ skey) {
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
@@ -159,32 +274,42 @@ inline unsigned grid_for(uint64_t items, int per_block, unsigned cap) {
 }
 
 template <int DP, int G>
-void density_dg(bool fp64, const float* spts, const unsigned long long* scode, const uint32_t* sid,
-                const ClassView& cv, const CutGeom* cuts, const HashInfo* hi,
+void density_dg(bool fp64, int layout, const float* spts, const unsigned long long* scode,
+                const uint32_t* sid, const ClassView& cv, const CutGeom* cuts, const HashInfo* hi,
                 const unsigned long long* hkeys, const uint2* hvals, int32_t* rho_out,
                 unsigned long long* skey, Counters* ctr, cudaStream_t st) {
   const unsigned grid = grid_for(cv.nchunk, kWarps, 152u * 64u);
-  if (fp64)
-    k_density<DP, G, true><<<grid, kThreads, 0, st>>>(spts, scode, sid, cv, cuts, hi, hkeys, hvals,
-                                                      rho_out, skey, ctr);
-  else
-    k_density<DP, G, false><<<grid, kThreads, 0, st>>>(spts, scode, sid, cv, cuts, hi, hkeys, hvals,
-                                                       rho_out, skey, ctr);
+  if (layout == kLayoutSegment) {
+    if (fp64)
+      k_density_seg<DP, G, true><<<grid, kThreads, 0, st>>>(spts, scode, sid, cv, cuts, hi, hkeys,
+                                                            hvals, rho_out, skey, ctr);
+    else
+      k_density_seg<DP, G, false><<<grid, kThreads, 0, st>>>(spts, scode, sid, cv, cuts, hi, hkeys,
+                                                             hvals, rho_out, skey, ctr);
+  } else {
+    if (fp64)
+      k_density<DP, G, true><<<grid, kThreads, 0, st>>>(spts, scode, sid, cv, cuts, hi, hkeys, hvals,
+                                                        rho_out, skey, ctr);
+    else
+      k_density<DP, G, false><<<grid, kThreads, 0, st>>>(spts, scode, sid, cv, cuts, hi, hkeys,
+                                                         hvals, rho_out, skey, ctr);
+  }
   count_launches(1);
 }
 
 }  // namespace
 
-void launch_density(int dp, int g, bool fp64, const float* spts, const unsigned long long* scode,
-                    const uint32_t* sid, const ClassView& cv, const CutGeom* cuts,
-                    const HashInfo* hi, const unsigned long long* hkeys, const uint2* hvals,
-                    int32_t* rho_out, unsigned long long* skey, Counters* ctr, cudaStream_t st) {
+void launch_density(int dp, int g, bool fp64, int layout, const float* spts,
+                    const unsigned long long* scode, const uint32_t* sid, const ClassView& cv,
+                    const CutGeom* cuts, const HashInfo* hi, const unsigned long long* hkeys,
+                    const uint2* hvals, int32_t* rho_out, unsigned long long* skey, Counters* ctr,
+                    cudaStream_t st) {
   if (cv.N == 0) return;
-  if (g == 1) density_dg<2, 1>(fp64, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
-  else if (g == 2) density_dg<2, 2>(fp64, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
-  else if (g == 3) density_dg<4, 3>(fp64, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
-  else if (dp == 4) density_dg<4, 4>(fp64, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
-  else density_dg<8, 4>(fp64, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
+  if (g == 1) density_dg<2, 1>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
+  else if (g == 2) density_dg<2, 2>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
+  else if (g == 3) density_dg<4, 3>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
+  else if (dp == 4) density_dg<4, 4>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
+  else density_dg<8, 4>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
 }
 
 void launch_keys_from_rho(const int32_t* rho, const uint32_t* sid, uint32_t n,

@@ -341,6 +341,169 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
   }
 }
 
+// Segment form of the near phase (the work layout of k_density_seg): the
+// chunk's points are split into segments of equal cell; for each segment the
+// block's candidates (and their order keys) are spread over the lanes, and for
+// every query of the segment each lane keeps the two smallest float32
+// distances among its higher candidates, merged over the warp with three
+// reductions.  Lane j collects the running best of the chunk's query j, then
+// settles it or queues it for the far phase exactly as k_dep_near does.
+
+template <int DP>
+constexpr int near_seg_v() { return DP == 8 ? 4 : 8; }
+
+// Merges the candidate summary (a1 smallest, a2 second smallest, ao an id at
+// a1) into a running one; equal smallest distances leave s2 == s1.
+__device__ __forceinline__ void min2_merge(Min2& m, float a1, float a2, uint32_t ao) {
+  const float hi1 = fmaxf(m.s1, a1);
+  m.s2 = fminf(fminf(m.s2, a2), hi1);
+  m.o1 = a1 < m.s1 ? ao : m.o1;
+  m.s1 = fminf(m.s1, a1);
+}
+
+template <int DP, int G, bool F64>
+__global__ void __launch_bounds__(kNearThreads, 4)
+k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restrict__ scode,
+               const unsigned long long* __restrict__ skey, ClassView cv, int32_t rho_skip,
+               const void* __restrict__ pts, int dtype, const CutGeom* __restrict__ cuts,
+               const HashInfo* __restrict__ hi, const unsigned long long* __restrict__ hkeys,
+               const uint2* __restrict__ hvals, int32_t* __restrict__ lambda,
+               double* __restrict__ delta, FarQueue q, Counters* ctr) {
+  constexpr int V = near_seg_v<DP>();
+  constexpr uint32_t W = 32u * V;
+  __shared__ RunTable s_rt[kNearWarps];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  RunTable& rt = s_rt[wib];
+  const int S = cv.cls->S, ib = cv.cls->ib;
+  const uint32_t hmask = hi->hmask;
+  const uint32_t n = cv.N;
+  const uint32_t lanemask_lt = (1u << lane) - 1u;
+
+  for (uint32_t ch = blockIdx.x * kNearWarps + wib; ch < cv.nchunk; ch += gridDim.x * kNearWarps) {
+    uint32_t inst, p0, end;
+    cv.chunk(ch, inst, p0, end);
+    const InstDev I = cv.instance(inst);
+    const CutGeom& C = cuts[inst];
+    const int k = C.k;
+    const int R = C.R;
+    const int shift = G * k;
+    const int cmax = (1 << (cv.geom[inst].B - k)) - 1;
+    const float bmul = C.band_mul, badd = C.band_add;
+    const float far32 = C.far32;
+    const double far64 = C.far64;
+    const unsigned long long hb = ib ? ((unsigned long long)inst << S) : 0ull;
+    const uint32_t p = p0 + lane;
+    const bool valid = p < end;
+    unsigned long long K = ~0ull;
+    if (valid) K = skey[p];
+    const unsigned long long mycell = valid ? (key_code(scode[p], S, ib) >> shift) : ~0ull;
+    const bool skip = valid && (int32_t)(K >> 32) < rho_skip;
+    const int nvalid = (int)min(32u, end - p0);
+    Min2 best;  // lane j: query p0 + j
+    best.init();
+    Exact best64;
+    best64.init();
+    int s = 0;
+    while (s < nvalid) {
+      const unsigned long long cell = __shfl_sync(kFull, mycell, s);
+      const unsigned seg = __ballot_sync(kFull, valid && mycell == cell);  // lanes s .. e-1
+      const int e = s + __popc(seg);
+      if (__ballot_sync(kFull, valid && !skip) & seg) {
+        uint32_t c0[G];
+        unmorton<G>(cell, c0);
+        Union<G> u;
+        block_union<G>(c0, R, cmax, u);
+        const int nr = union_runs<G>(u, hkeys, hvals, hmask, hb, n, lane, rt);
+        const uint32_t total = rt.pre[nr];
+        for (uint32_t w0 = 0; w0 < total; w0 += W) {
+          Pt<DP> cand[V];
+          unsigned long long ck[V];
+          load_window<DP, V, true>(rt, nr, w0, total, spts, lane, cand, skey, ck);
+          const int vn = (int)min((uint32_t)V, (total - w0 + 31u) / 32u);
+          for (int j = s; j < e; ++j) {
+            const unsigned long long Kj = __shfl_sync(kFull, K, j);
+            if (__shfl_sync(kFull, skip, j)) continue;
+            const Pt<DP> xq = load_pt<DP>(spts, p0 + j);
+            if constexpr (F64) {
+              Exact ex;
+              ex.init();
+#pragma unroll
+              for (int v = 0; v < V; ++v) {
+                if (v >= vn) break;
+                if (ck[v] > Kj) ex.add(dist64<DP>(xq, cand[v]), key_id(ck[v]));
+              }
+              ex.merge_warp();
+              if (lane == j) best64.add(ex.s, ex.o);
+            } else {
+              Min2 m;
+              m.init();
+#pragma unroll
+              for (int v = 0; v < V; ++v) {
+                if (v >= vn) break;
+                const float d32 = dist32<DP>(xq, cand[v]);
+                m.add(ck[v] > Kj ? d32 : INFINITY, key_id(ck[v]));
+              }
+              // the warp's two smallest and an id at the smallest
+              const float g1 = __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(m.s1)));
+              const unsigned at = __ballot_sync(kFull, m.s1 == g1);
+              const uint32_t go = __reduce_min_sync(kFull, m.s1 == g1 ? m.o1 : 0xffffffffu);
+              float g2;
+              if (__popc(at) > 1) {
+                g2 = g1;
+              } else {
+                g2 = __uint_as_float(
+                    __reduce_min_sync(kFull, __float_as_uint(m.s1 == g1 ? m.s2 : m.s1)));
+              }
+              if (lane == j) min2_merge(best, g1, g2, g1 < INFINITY ? go : 0xffffffffu);
+            }
+          }
+        }
+      }
+      s = e;
+    }
+
+    bool settled = false;
+    float s1 = INFINITY;
+    if (valid && !skip) {
+      const uint32_t id = key_id(K);
+      if constexpr (F64) {
+        settled = best64.o != 0xffffffffu && best64.s < far64;
+        if (settled) {
+          lambda[id] = (int32_t)(best64.o - (uint32_t)I.out);
+          delta[id] = sqrt(best64.s);
+        }
+      } else if (best.o1 != 0xffffffffu) {
+        s1 = best.s1;
+        const float bnd = band_of(s1, bmul, badd);
+        settled = bnd < far32 && best.s2 > bnd;
+        if (settled) {
+          const uint32_t o = best.o1 - (uint32_t)I.out;
+          const Pt<DP> me = load_pt<DP>(spts, p);
+          lambda[id] = (int32_t)o;
+          delta[id] = sqrt(dist64<DP>(me, input_pt<DP>(pts, dtype, I.coord, I.d, o)));
+        }
+      }
+    } else if (valid) {
+      const uint32_t id = key_id(K);
+      lambda[id] = -1;
+      delta[id] = __longlong_as_double(0x7ff8000000000000ll);  // NaN: skipped
+    }
+    // unsettled queries (nothing near, or a near tie) go to the far phase
+    const bool push = valid && !skip && !settled;
+    const unsigned pm = __ballot_sync(kFull, push);
+    uint32_t base = 0;
+    if (lane == 0 && pm) base = atomicAdd(&ctr->queue_n, (unsigned)__popc(pm));
+    base = __shfl_sync(kFull, base, 0);
+    if (push) {
+      const uint32_t slot = base + __popc(pm & lanemask_lt);
+      q.pos[slot] = p;
+      if constexpr (F64) q.s1d[slot] = best64.s;
+      else q.s1[slot] = s1;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // far phase: depth-first priority search of the radix tree
 
@@ -773,20 +936,31 @@ inline unsigned grid_for(uint64_t items, int per_block, unsigned cap) {
 }
 
 template <int DP, int G>
-void near_dg(bool fp64, const float* spts, const unsigned long long* scode,
+void near_dg(bool fp64, int layout, const float* spts, const unsigned long long* scode,
              const unsigned long long* skey, const ClassView& cv, int32_t rho_skip,
              const void* pts, int dtype, const CutGeom* cuts, const HashInfo* hi,
              const unsigned long long* hkeys, const uint2* hvals, int32_t* lambda, double* delta,
              FarQueue q, Counters* ctr, cudaStream_t st) {
   const unsigned grid = grid_for(cv.nchunk, kNearWarps, 152u * 64u);
-  if (fp64)
-    k_dep_near<DP, G, true><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, cv, rho_skip, pts,
-                                                           dtype, cuts, hi, hkeys, hvals, lambda,
-                                                           delta, q, ctr);
-  else
-    k_dep_near<DP, G, false><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, cv, rho_skip, pts,
-                                                            dtype, cuts, hi, hkeys, hvals, lambda,
-                                                            delta, q, ctr);
+  if (layout == kLayoutSegment) {
+    if (fp64)
+      k_dep_near_seg<DP, G, true><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, cv, rho_skip, pts,
+                                                                 dtype, cuts, hi, hkeys, hvals, lambda,
+                                                                 delta, q, ctr);
+    else
+      k_dep_near_seg<DP, G, false><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, cv, rho_skip, pts,
+                                                                  dtype, cuts, hi, hkeys, hvals, lambda,
+                                                                  delta, q, ctr);
+  } else {
+    if (fp64)
+      k_dep_near<DP, G, true><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, cv, rho_skip, pts,
+                                                             dtype, cuts, hi, hkeys, hvals, lambda,
+                                                             delta, q, ctr);
+    else
+      k_dep_near<DP, G, false><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, cv, rho_skip, pts,
+                                                              dtype, cuts, hi, hkeys, hvals, lambda,
+                                                              delta, q, ctr);
+  }
 }
 
 template <int DP>
@@ -813,19 +987,20 @@ void far_dp(bool fp64, const float* spts, const unsigned long long* scode,
 
 }  // namespace
 
-void launch_dep_near(int dp, int g, bool fp64, const float* spts, const unsigned long long* scode,
-                     const unsigned long long* skey, const ClassView& cv, int32_t rho_skip,
-                     const void* pts, int dtype, const CutGeom* cuts, const HashInfo* hi,
-                     const unsigned long long* hkeys, const uint2* hvals, int32_t* lambda,
-                     double* delta, FarQueue q, Counters* ctr, cudaStream_t st) {
+void launch_dep_near(int dp, int g, bool fp64, int layout, const float* spts,
+                     const unsigned long long* scode, const unsigned long long* skey,
+                     const ClassView& cv, int32_t rho_skip, const void* pts, int dtype,
+                     const CutGeom* cuts, const HashInfo* hi, const unsigned long long* hkeys,
+                     const uint2* hvals, int32_t* lambda, double* delta, FarQueue q, Counters* ctr,
+                     cudaStream_t st) {
   if (cv.N == 0) return;
   cudaMemsetAsync(&ctr->queue_n, 0, sizeof(unsigned int), st);
   cudaMemsetAsync(&ctr->queue2_n, 0, sizeof(unsigned int), st);
-  if (g == 1) near_dg<2, 1>(fp64, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
-  else if (g == 2) near_dg<2, 2>(fp64, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
-  else if (g == 3) near_dg<4, 3>(fp64, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
-  else if (dp == 4) near_dg<4, 4>(fp64, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
-  else near_dg<8, 4>(fp64, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
+  if (g == 1) near_dg<2, 1>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
+  else if (g == 2) near_dg<2, 2>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
+  else if (g == 3) near_dg<4, 3>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
+  else if (dp == 4) near_dg<4, 4>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
+  else near_dg<8, 4>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
   count_launches(1);
 }
 

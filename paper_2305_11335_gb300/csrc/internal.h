@@ -75,13 +75,23 @@ void launch_tree_maxkey(const unsigned long long* skey, const float* spts, int d
                         Node* nodes, const uint32_t* leaf_parent, uint32_t* visit, float* nbox,
                         bool boxes, cudaStream_t st);
 
+// Work layouts of the density and near-dependent kernels:
+//   union    a warp owns 32 consecutive sorted points (one query per lane) and
+//            streams the union of their blocks through shared memory, every
+//            candidate a broadcast read (block.cuh)
+//   segment  the 32 points are split into segments of equal cell; the block's
+//            candidates are spread over the lanes (in registers) and the
+//            segment's queries are taken one at a time, one warp reduction each
+enum { kLayoutUnion = 1, kLayoutSegment = 2 };
+
 // ---- density (density.cu) -------------------------------------------------------
 // rho of every point for one cutoff (cuts: [ninst]); rho_out is indexed by
 // output index (sid)
-void launch_density(int dp, int g, bool fp64, const float* spts, const unsigned long long* scode,
-                    const uint32_t* sid, const ClassView& cv, const CutGeom* cuts,
-                    const HashInfo* hi, const unsigned long long* hkeys, const uint2* hvals,
-                    int32_t* rho_out, unsigned long long* skey, Counters* ctr, cudaStream_t st);
+void launch_density(int dp, int g, bool fp64, int layout, const float* spts,
+                    const unsigned long long* scode, const uint32_t* sid, const ClassView& cv,
+                    const CutGeom* cuts, const HashInfo* hi, const unsigned long long* hkeys,
+                    const uint2* hvals, int32_t* rho_out, unsigned long long* skey, Counters* ctr,
+                    cudaStream_t st);
 // order keys of sorted points from densities given by output index
 void launch_keys_from_rho(const int32_t* rho, const uint32_t* sid, uint32_t n,
                           unsigned long long* skey, cudaStream_t st);
@@ -97,11 +107,12 @@ struct FarQueue {
 };
 // lambda and delta are indexed by output index; lambda values are
 // instance-local ids
-void launch_dep_near(int dp, int g, bool fp64, const float* spts, const unsigned long long* scode,
-                     const unsigned long long* skey, const ClassView& cv, int32_t rho_skip,
-                     const void* pts, int dtype, const CutGeom* cuts, const HashInfo* hi,
-                     const unsigned long long* hkeys, const uint2* hvals, int32_t* lambda,
-                     double* delta, FarQueue q, Counters* ctr, cudaStream_t st);
+void launch_dep_near(int dp, int g, bool fp64, int layout, const float* spts,
+                     const unsigned long long* scode, const unsigned long long* skey,
+                     const ClassView& cv, int32_t rho_skip, const void* pts, int dtype,
+                     const CutGeom* cuts, const HashInfo* hi, const unsigned long long* hkeys,
+                     const uint2* hvals, int32_t* lambda, double* delta, FarQueue q, Counters* ctr,
+                     cudaStream_t st);
 void launch_dep_far(int dp, bool fp64, const float* spts, const unsigned long long* scode,
                     const unsigned long long* skey, const ClassView& cv, const CutGeom* cuts,
                     const Node* nodes, const float* nbox, const uint32_t* root, FarQueue q,

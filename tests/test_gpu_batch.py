@@ -47,13 +47,13 @@ def thresholds(n_inst, seed):
     return rn, rm, dm
 
 
-def check_run(sizes, dims, insts, cuts, dtype, precision, seed):
+def check_run(sizes, dims, insts, cuts, dtype, precision, seed, layout="auto"):
     batch = dpc.Batch.packed(sizes, dims, cuts)
     flat = np.concatenate([p.reshape(-1) for p in insts]).astype(dtype)
     t = torch.from_numpy(flat).cuda()
     rn, rm, dm = thresholds(len(sizes), seed)
     params = dpc.make_params(batch, rn, rm, dm)
-    out = dpc.dpc_run(t, batch, params, precision=precision, sync=True)
+    out = dpc.dpc_run(t, batch, params, precision=precision, sync=True, layout=layout)
     out = {k: v.cpu().numpy() for k, v in out.items()}
     for i, p in enumerate(insts):
         lo, hi = batch.pt_offset[i], batch.pt_offset[i + 1]
@@ -64,15 +64,17 @@ def check_run(sizes, dims, insts, cuts, dtype, precision, seed):
                         "%s inst %d (n=%d d=%d) cut %d" % (precision, i, sizes[i], dims[i], c))
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_batch_mixed_dims_float(precision):
+@pytest.mark.parametrize("precision,layout", [("fp32", "auto"), ("fp64", "auto"), ("fp32", "union"),
+                                              ("fp32", "segment"), ("fp64", "segment")])
+def test_batch_mixed_dims_float(precision, layout):
     sizes, dims, insts, cuts = make_batch(1, 48, [2, 3, 5, 1, 4, 7, 8, 2, 3, 5])
-    check_run(sizes, dims, insts, cuts, np.float32, precision, 11)
+    check_run(sizes, dims, insts, cuts, np.float32, precision, 11, layout)
 
 
-def test_batch_int_ties():
+@pytest.mark.parametrize("layout", ["union", "segment"])
+def test_batch_int_ties(layout):
     sizes, dims, insts, cuts = make_batch(2, 30, [2, 3], dtype=np.int32, max_n=1500)
-    check_run(sizes, dims, insts, cuts, np.int32, "fp32", 12)
+    check_run(sizes, dims, insts, cuts, np.int32, "fp32", 12, layout)
 
 
 def test_batch_one_class_many_instances():

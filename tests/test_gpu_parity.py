@@ -222,15 +222,17 @@ def test_stats():
     assert 0 < s["far_queries"] < 20000
 
 
+@pytest.mark.parametrize("layout", ["union", "segment"])
 @pytest.mark.parametrize("radius", [1, 2, 3, 5])
-def test_block_radius_does_not_change_results(radius):
-    """Every block radius (grid level) gives the oracle's result, in 1, 2, 3
-    and 5 dimensions (radii above a dimension's maximum are clamped)."""
+def test_block_radius_does_not_change_results(radius, layout):
+    """Every block radius (grid level) and both kernel layouts give the
+    oracle's result, in 1, 2, 3 and 5 dimensions (radii above a dimension's
+    maximum are clamped)."""
     for d, n, dc in ((1, 3000, 0.004), (2, 4000, 0.03), (3, 4000, 0.06), (5, 2500, 0.12)):
         pts = W.random_blobs(n, d, 900 + d)
         refs = [oracle.run(pts, c, 2, 3, 0.1) for c in (dc, dc * 1.3)]
         t = torch.from_numpy(pts).cuda()
-        out = dpc.run(t, [dc, dc * 1.3], 2, 3, 0.1, radius=radius)
+        out = dpc.run(t, [dc, dc * 1.3], 2, 3, 0.1, radius=radius, layout=layout)
         for c, ref in enumerate(refs):
             assert_same({k: v[c].cpu().numpy() for k, v in out.items()}, ref, "d=%d r=%d cut %d" % (d, radius, c))
         st = dpc.dpc_get_stats()
