@@ -232,6 +232,9 @@ typedef struct {
   int64_t far_nodes_max;  /* most nodes expanded by a single far query       */
   int32_t block_radius;   /* block radius R of the last cutoff (cells per side
                              of the (2R+1)^g block around a query's cell)     */
+  int32_t density_layout; /* layout of the last density launch: 1 union,
+                             2 segment (see DPC_FLAG_LAYOUT)                  */
+  int32_t near_layout;    /* layout of the last near-dependent launch         */
   int32_t reserved;
 } dpc_stats;
 int dpc_get_stats(void* stream, dpc_stats* out);

@@ -69,6 +69,7 @@ class _Stats(ctypes.Structure):
                 ("grid_level", ctypes.c_int32), ("bits_per_axis", ctypes.c_int32),
                 ("kernel_launches", ctypes.c_int64), ("far_nodes", ctypes.c_int64),
                 ("far_nodes_max", ctypes.c_int64), ("block_radius", ctypes.c_int32),
+                ("density_layout", ctypes.c_int32), ("near_layout", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
 
 

@@ -226,6 +226,7 @@ struct Workspace {
   cudaEvent_t tune_ev[6] = {};
 
   // for dpc_get_stats: the last class and cutoff that ran
+  Choice last_choice;
   const CutGeom* last_cut = nullptr;
   const GridGeom* last_geom = nullptr;
   bool have_last = false;
@@ -784,33 +785,49 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
     trial(1, false);  // untimed: module loading, caches
     Choice best;
     float best_ms = 0.f;
-    for (int r = 1; r <= rmax; ++r) {
-      trial(r, true);
-      if (cudaEventSynchronize(w->tune_ev[near ? 5 : 3]) != cudaSuccess) {
-        cudaGetLastError();
-        best = Choice();
-        break;
+    bool failed = false;
+    for (int r = 1; r <= rmax && !failed; ++r) {
+      // each phase: the smaller of two timings
+      float cl = 1e30f, dU = 1e30f, dS = 1e30f, nU = 1e30f, nS = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        trial(r, true);
+        if (cudaEventSynchronize(w->tune_ev[near ? 5 : 3]) != cudaSuccess) {
+          cudaGetLastError();
+          failed = true;
+          break;
+        }
+        cl = fminf(cl, span(0, 1));
+        dU = fminf(dU, span(1, 2));
+        dS = fminf(dS, span(2, 3));
+        if (near) {
+          nU = fminf(nU, span(3, 4));
+          nS = fminf(nS, span(4, 5));
+        }
       }
-      const float dU = span(1, 2), dS = span(2, 3);
-      float ms = span(0, 1) + fminf(dU, dS);
-      int nl = default_layout(c.g);
-      if (near) {
-        const float nU = span(3, 4), nS = span(4, 5);
-        ms += fminf(nU, nS);
-        nl = nU <= nS ? kLayoutUnion : kLayoutSegment;
-      }
+      if (failed) break;
+      // a layout other than the default has to win by 3%
+      auto pick = [&](float u, float s) {
+        return default_layout(c.g) == kLayoutUnion ? (s < 0.97f * u ? kLayoutSegment : kLayoutUnion)
+                                                   : (u < 0.97f * s ? kLayoutUnion : kLayoutSegment);
+      };
+      const int dl = pick(dU, dS);
+      const int nl = near ? pick(nU, nS) : default_layout(c.g);
+      const float ms = cl + (dl == kLayoutUnion ? dU : dS) +
+                       (near ? (nl == kLayoutUnion ? nU : nS) : 0.f);
       if (best.r == 0 || ms < best_ms) {
         best_ms = ms;
         best.r = r;
-        best.dlay = dU <= dS ? kLayoutUnion : kLayoutSegment;
+        best.dlay = dl;
         best.nlay = nl;
       }
     }
+    if (failed) best = Choice();
     cudaMemcpyAsync(w->ctr, w->ctr_save, sizeof(Counters), cudaMemcpyDeviceToDevice, st);
     it = w->tuned.emplace(key, best).first;
   }
   if (ch.r == 0 && !forced && it != w->tuned.end() && it->second.r > 0) ch = it->second;
   if (ch.r > 0) launch_set_radius(cv, cuts, ch.r, w->stream);
+  w->last_choice = ch;
   return ch;
 }
 
@@ -1145,6 +1162,8 @@ int dpc_get_stats(void* stream, dpc_stats* out) {
     out->occupied_cells = hi.m;
     out->grid_level = cg.k;
     out->block_radius = cg.R;
+    out->density_layout = w->last_choice.dlay;
+    out->near_layout = w->last_choice.nlay;
     out->bits_per_axis = g.B;
   }
   return cudaGetLastError() == cudaSuccess ? DPC_OK : DPC_ERR_CUDA;

@@ -204,45 +204,64 @@ k_density_seg(const float* __restrict__ spts, const unsigned long long* __restri
         load_window<DP, V>(rt, nr, w0, total, spts, lane, cand);
         // slots of this window that hold candidates (warp-uniform)
         const int vn = (int)min((uint32_t)V, (total - w0 + 31u) / 32u);
-        for (int j = s; j < e; ++j) {
-          const Pt<DP> xq = load_pt<DP>(spts, p0 + j);
-          int32_t cnt;
+        // two queries per pass over the lane's candidates (independent
+        // chains); their per-lane counts (at most V each) share one 32-bit
+        // word per reduction
+        for (int j = s; j < e; j += 2) {
+          const bool two = j + 1 < e;
+          const Pt<DP> xa = load_pt<DP>(spts, p0 + j);
+          const Pt<DP> xb = load_pt<DP>(spts, p0 + (two ? j + 1 : j));
+          int32_t cnt_a, cnt_b;
           if constexpr (F64) {
-            int c = 0;
+            unsigned c = 0;
 #pragma unroll
             for (int v = 0; v < V; ++v) {
               if (v >= vn) break;
-              c += dist64<DP>(xq, cand[v]) <= dc2;
+              c += (dist64<DP>(xa, cand[v]) <= dc2) ? 1u : 0u;
+              c += (dist64<DP>(xb, cand[v]) <= dc2) ? 0x10000u : 0u;
             }
-            cnt = (int32_t)__reduce_add_sync(kFull, (unsigned)c);
+            c = __reduce_add_sync(kFull, c);
+            cnt_a = (int32_t)(c & 0xffffu);
+            cnt_b = (int32_t)(c >> 16);
           } else {
-            int ci = 0, co = 0;
+            unsigned ci = 0, co = 0;
 #pragma unroll
             for (int v = 0; v < V; ++v) {
               if (v >= vn) break;
-              const float s32 = dist32<DP>(xq, cand[v]);
-              ci += s32 <= t_in;
-              co += s32 <= t_out;
+              const float sa = dist32<DP>(xa, cand[v]);
+              const float sb = dist32<DP>(xb, cand[v]);
+              ci += (sa <= t_in ? 1u : 0u) + (sb <= t_in ? 0x10000u : 0u);
+              co += (sa <= t_out ? 1u : 0u) + (sb <= t_out ? 0x10000u : 0u);
             }
-            cnt = (int32_t)__reduce_add_sync(kFull, (unsigned)ci);
-            const int32_t cnt_out = (int32_t)__reduce_add_sync(kFull, (unsigned)co);
-            if (cnt_out != cnt) {  // band pairs: recount them in binary64
-              int in = 0, seen = 0;
+            ci = __reduce_add_sync(kFull, ci);
+            co = __reduce_add_sync(kFull, co);
+            cnt_a = (int32_t)(ci & 0xffffu);
+            cnt_b = (int32_t)(ci >> 16);
+            if (co != ci) {  // band pairs: recount them in binary64
+              unsigned in = 0, seen = 0;
 #pragma unroll
               for (int v = 0; v < V; ++v) {
                 if (v >= vn) break;
-                const float s32 = dist32<DP>(xq, cand[v]);
-                if (s32 > t_in && s32 <= t_out) {
+                const float sa = dist32<DP>(xa, cand[v]);
+                const float sb = dist32<DP>(xb, cand[v]);
+                if (sa > t_in && sa <= t_out) {
                   ++seen;
-                  in += dist64<DP>(xq, cand[v]) <= dc2;
+                  in += dist64<DP>(xa, cand[v]) <= dc2 ? 1u : 0u;
+                }
+                if (sb > t_in && sb <= t_out) {
+                  seen += 0x10000u;
+                  in += dist64<DP>(xb, cand[v]) <= dc2 ? 0x10000u : 0u;
                 }
               }
-              cnt += (int32_t)__reduce_add_sync(kFull, (unsigned)in);
-              const unsigned seen_all = __reduce_add_sync(kFull, (unsigned)seen);
-              if (lane == 0) band += seen_all;
+              in = __reduce_add_sync(kFull, in);
+              seen = __reduce_add_sync(kFull, seen);
+              cnt_a += (int32_t)(in & 0xffffu);
+              cnt_b += (int32_t)(in >> 16);
+              if (lane == 0) band += (seen & 0xffffu) + (two ? (seen >> 16) : 0u);
             }
           }
-          if (lane == j) acc += cnt;
+          if (lane == j) acc += cnt_a;
+          if (two && lane == j + 1) acc += cnt_b;
         }
       }
       s = e;

@@ -421,41 +421,61 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
           unsigned long long ck[V];
           load_window<DP, V, true>(rt, nr, w0, total, spts, lane, cand, skey, ck);
           const int vn = (int)min((uint32_t)V, (total - w0 + 31u) / 32u);
-          for (int j = s; j < e; ++j) {
-            const unsigned long long Kj = __shfl_sync(kFull, K, j);
-            if (__shfl_sync(kFull, skip, j)) continue;
-            const Pt<DP> xq = load_pt<DP>(spts, p0 + j);
+          // two queries per pass over the lane's candidates (independent chains)
+          for (int j = s; j < e; j += 2) {
+            const bool two = j + 1 < e;
+            const int jb = two ? j + 1 : j;
+            const unsigned long long Ka = __shfl_sync(kFull, K, j);
+            const unsigned long long Kb = __shfl_sync(kFull, K, jb);
+            const bool act_a = !__shfl_sync(kFull, skip, j);
+            const bool act_b = two && !__shfl_sync(kFull, skip, jb);
+            if (!act_a && !act_b) continue;
+            const Pt<DP> xa = load_pt<DP>(spts, p0 + j);
+            const Pt<DP> xb = load_pt<DP>(spts, p0 + jb);
             if constexpr (F64) {
-              Exact ex;
-              ex.init();
+              Exact ea, eb;
+              ea.init();
+              eb.init();
 #pragma unroll
               for (int v = 0; v < V; ++v) {
                 if (v >= vn) break;
-                if (ck[v] > Kj) ex.add(dist64<DP>(xq, cand[v]), key_id(ck[v]));
+                if (ck[v] > Ka) ea.add(dist64<DP>(xa, cand[v]), key_id(ck[v]));
+                if (ck[v] > Kb) eb.add(dist64<DP>(xb, cand[v]), key_id(ck[v]));
               }
-              ex.merge_warp();
-              if (lane == j) best64.add(ex.s, ex.o);
+              ea.merge_warp();
+              eb.merge_warp();
+              if (act_a && lane == j) best64.add(ea.s, ea.o);
+              if (act_b && lane == jb) best64.add(eb.s, eb.o);
             } else {
-              Min2 m;
-              m.init();
+              Min2 ma, mb;
+              ma.init();
+              mb.init();
 #pragma unroll
               for (int v = 0; v < V; ++v) {
                 if (v >= vn) break;
-                const float d32 = dist32<DP>(xq, cand[v]);
-                m.add(ck[v] > Kj ? d32 : INFINITY, key_id(ck[v]));
+                const float da = dist32<DP>(xa, cand[v]);
+                const float db = dist32<DP>(xb, cand[v]);
+                const uint32_t id = key_id(ck[v]);
+                ma.add(ck[v] > Ka ? da : INFINITY, id);
+                mb.add(ck[v] > Kb ? db : INFINITY, id);
               }
-              // the warp's two smallest and an id at the smallest
-              const float g1 = __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(m.s1)));
-              const unsigned at = __ballot_sync(kFull, m.s1 == g1);
-              const uint32_t go = __reduce_min_sync(kFull, m.s1 == g1 ? m.o1 : 0xffffffffu);
-              float g2;
-              if (__popc(at) > 1) {
-                g2 = g1;
-              } else {
-                g2 = __uint_as_float(
-                    __reduce_min_sync(kFull, __float_as_uint(m.s1 == g1 ? m.s2 : m.s1)));
-              }
-              if (lane == j) min2_merge(best, g1, g2, g1 < INFINITY ? go : 0xffffffffu);
+              // per query: the warp's two smallest and an id at the smallest
+              auto warp_min2 = [&](const Min2& m, float& g1, float& g2, uint32_t& go) {
+                g1 = __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(m.s1)));
+                const unsigned at = __ballot_sync(kFull, m.s1 == g1);
+                go = __reduce_min_sync(kFull, m.s1 == g1 ? m.o1 : 0xffffffffu);
+                g2 = __popc(at) > 1
+                         ? g1
+                         : __uint_as_float(
+                               __reduce_min_sync(kFull, __float_as_uint(m.s1 == g1 ? m.s2 : m.s1)));
+                if (!(g1 < INFINITY)) go = 0xffffffffu;
+              };
+              float a1, a2, b1, b2;
+              uint32_t ao, bo;
+              warp_min2(ma, a1, a2, ao);
+              warp_min2(mb, b1, b2, bo);
+              if (act_a && lane == j) min2_merge(best, a1, a2, ao);
+              if (act_b && lane == jb) min2_merge(best, b1, b2, bo);
             }
           }
         }
