@@ -372,9 +372,11 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
   constexpr int V = near_seg_v<DP>();
   constexpr uint32_t W = 32u * V;
   __shared__ RunTable s_rt[kNearWarps];
+  __shared__ RunTable s_rt2[kNearWarps];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   RunTable& rt = s_rt[wib];
+  RunTable& rt2 = s_rt2[wib];
   const int S = cv.cls->S, ib = cv.cls->ib;
   const uint32_t hmask = hi->hmask;
   const uint32_t n = cv.N;
@@ -400,6 +402,17 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
     const unsigned long long mycell = valid ? (key_code(scode[p], S, ib) >> shift) : ~0ull;
     const bool skip = valid && (int32_t)(K >> 32) < rho_skip;
     const int nvalid = (int)min(32u, end - p0);
+    // this lane's query in fine units, for the cell lower bounds of pass 2
+    const GridGeom* geom = cv.geom + inst;
+    const float f2lo = geom->f2 * (1.f - 1e-5f);
+    const float cell_fine = (float)(1u << k);
+    float uq[G];
+    {
+      const Pt<DP> me = valid ? load_pt<DP>(spts, p) : Pt<DP>{};
+#pragma unroll
+      for (int a = 0; a < G; ++a)
+        uq[a] = valid ? (float)(((double)me.x[a] - geom->org[a]) * geom->inv_f) : 0.f;
+    }
     Min2 best;  // lane j: query p0 + j
     best.init();
     Exact best64;
@@ -415,11 +428,13 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
         Union<G> u;
         block_union<G>(c0, R, cmax, u);
         const int nr = union_runs<G>(u, hkeys, hvals, hmask, hb, n, lane, rt);
-        const uint32_t total = rt.pre[nr];
+        // every candidate of a run table, window by window
+        auto scan = [&](const RunTable& tab, int ntab) {
+        const uint32_t total = tab.pre[ntab];
         for (uint32_t w0 = 0; w0 < total; w0 += W) {
           Pt<DP> cand[V];
           unsigned long long ck[V];
-          load_window<DP, V, true>(rt, nr, w0, total, spts, lane, cand, skey, ck);
+          load_window<DP, V, true>(tab, ntab, w0, total, spts, lane, cand, skey, ck);
           const int vn = (int)min((uint32_t)V, (total - w0 + 31u) / 32u);
           // two queries per pass over the lane's candidates (independent chains)
           for (int j = s; j < e; j += 2) {
@@ -478,6 +493,47 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
               if (act_b && lane == jb) min2_merge(best, b1, b2, bo);
             }
           }
+        }
+        };
+        // Dense blocks (more than 8 windows): pass 1 scans the segment's own
+        // cell, pass 2 only the other cells that can still hold a point
+        // closer than some query's best (a conservative lower bound decides).
+        // Otherwise one pass over everything (the second pass's filtering and
+        // short windows cost more than the cells it skips).
+        auto own = [&](const uint32_t* cc) {
+          bool same = true;
+#pragma unroll
+          for (int a = 0; a < G; ++a) same &= cc[a] == c0[a];
+          return same;
+        };
+        const bool mine = ((seg >> lane) & 1u) && !skip;
+        const int npass = rt.pre[nr] <= 8u * W ? 1 : 2;
+        for (int pass = 0; pass < npass; ++pass) {
+          int ntab;
+          if (npass == 1) {
+            ntab = nr;
+          } else if (pass == 0) {
+            ntab = filter_runs<G>(rt, nr, u, rt2, lane, own);
+          } else {
+            ntab = filter_runs<G>(rt, nr, u, rt2, lane, [&](const uint32_t* cc) {
+              if (own(cc)) return false;
+              bool need = mine;
+              if (need) {
+                float lb2 = 0.f;
+#pragma unroll
+                for (int a = 0; a < G; ++a) {
+                  const float lo = (float)cc[a] * cell_fine;
+                  const float l = lb_axis(lo, lo + cell_fine - 1.f, uq[a]);
+                  lb2 = fmaf(l, l, lb2);
+                }
+                const float lbs = lb2 * f2lo;
+                if constexpr (F64) need = (double)lbs <= best64.s;
+                else need = !beyond(lbs, band_of(best.s1, bmul, badd));
+              }
+              return __any_sync(kFull, need) != 0;
+            });
+          }
+          scan(npass == 1 ? rt : rt2, ntab);
         }
       }
       s = e;

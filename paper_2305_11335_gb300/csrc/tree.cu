@@ -101,6 +101,15 @@ __device__ __forceinline__ void child_box(uint32_t c, const float* __restrict__ 
   }
 }
 
+// Arrival counter with acquire-release semantics at GPU scope: the first
+// child to arrive publishes its subtree's results (release), the second reads
+// them after its own increment (acquire), without full fences.
+__device__ __forceinline__ uint32_t arrive(uint32_t* counter) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(counter) : "memory");
+  return old;
+}
+
 template <int DP, bool BOX>
 __global__ void k_tree_up(const unsigned long long* __restrict__ skey,
                           const float* __restrict__ spts, uint32_t n, Node* nodes,
@@ -108,9 +117,7 @@ __global__ void k_tree_up(const unsigned long long* __restrict__ skey,
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     uint32_t node = leaf_parent[t];
     for (uint32_t depth = 0; depth < 2u * n + 64u; ++depth) {
-      __threadfence();
-      if (atomicAdd(&visit[node], 1u) == 0u) break;  // first arrival: the sibling continues
-      __threadfence();
+      if (arrive(&visit[node]) == 0u) break;  // first arrival: the sibling continues
       const uint32_t l = nodes[node].left, r = nodes[node].right;
       const unsigned long long kl =
           (l & kLeafBit) ? skey[l & ~kLeafBit] : __ldcg(&nodes[l].maxkey);
