@@ -103,8 +103,9 @@ enum {
  * default rule (segments for d = 3, union otherwise) or the autotuned choice:
  * 1 = union (a warp's 32 consecutive points, one query per lane, the union of
  * their blocks streamed as broadcast reads), 2 = segment (the block of one
- * cell spread over the lanes, the cell's queries one at a time).  Results do
- * not depend on it. */
+ * cell spread over the lanes, the cell's queries one at a time), 3 = tree
+ * (near phase only, density keeps its default: no block scan, every query goes
+ * to the tree search of the far phase).  Results do not depend on it. */
 #define DPC_FLAG_LAYOUT(v) ((uint32_t)(v) << 16)
 #define DPC_FLAG_LAYOUT_MASK (0x3u << 16)
 /* dpc_run only: capture the call's kernels into a CUDA graph the first time a
@@ -234,7 +235,7 @@ typedef struct {
                              of the (2R+1)^g block around a query's cell)     */
   int32_t density_layout; /* layout of the last density launch: 1 union,
                              2 segment (see DPC_FLAG_LAYOUT)                  */
-  int32_t near_layout;    /* layout of the last near-dependent launch         */
+  int32_t near_layout;    /* layout of the last near-dependent launch (3 = tree) */
   int32_t reserved;
 } dpc_stats;
 int dpc_get_stats(void* stream, dpc_stats* out);

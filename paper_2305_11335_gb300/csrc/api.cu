@@ -95,7 +95,7 @@ int check_flags(uint32_t flags) {
   if (prec != DPC_PREC_FP64 && prec != DPC_PREC_FP32_CERT) return DPC_ERR_UNSUPPORTED;
   if (flags & ~kKnownFlags) return DPC_ERR_ARG;
   if (((flags & DPC_FLAG_RADIUS_MASK) >> 12) > 5) return DPC_ERR_ARG;
-  if (((flags & DPC_FLAG_LAYOUT_MASK) >> 16) > 2) return DPC_ERR_ARG;
+  if (((flags & DPC_FLAG_LAYOUT_MASK) >> 16) > 3) return DPC_ERR_ARG;
   return DPC_OK;
 }
 
@@ -223,7 +223,7 @@ struct Workspace {
 
   // autotuned radius and layouts per (class shape, cutoff), see choose()
   std::map<std::string, Choice> tuned;
-  cudaEvent_t tune_ev[6] = {};
+  cudaEvent_t tune_ev[8] = {};
 
   // for dpc_get_stats: the last class and cutoff that ran
   Choice last_choice;
@@ -736,10 +736,11 @@ inline int default_layout(int g) { return g == 3 ? kLayoutSegment : kLayoutUnion
 // The grid level and kernel layouts of one (class, cutoff): a fixed radius or
 // layout from the flags, else the autotuned choice (measured now when the
 // call asks for autotuning and the shape is new, cached otherwise), else the
-// default rule.  A trial, per radius, times cells, then density and the near
-// phase in both layouts (after one untimed pass that loads the kernels and
-// warms the caches); the radius with the least cells + best density + best near
-// wins, with its best layouts.  The counters are saved around the trials;
+// default rule.  A trial, per radius, times cells, then density in both
+// layouts and the dependent search (near phase + far phase) with each near
+// layout (after one untimed pass that loads the kernels and warms the caches);
+// the radius with the least cells + best density + best dependent search wins,
+// with its best layouts.  The counters are saved around the trials;
 // rho_scratch (and the NearTrial outputs) receive the trials' results.
 Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cuts,
               const dpc_batch* b, int cut, bool fp64, int32_t* rho_scratch, uint32_t flags,
@@ -747,7 +748,8 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
   Choice ch;
   ch.r = (int)((flags & DPC_FLAG_RADIUS_MASK) >> 12);
   const int forced = (int)((flags & DPC_FLAG_LAYOUT_MASK) >> 16);
-  ch.dlay = ch.nlay = forced ? forced : default_layout(c.g);
+  ch.dlay = (forced && forced != kLayoutTree) ? forced : default_layout(c.g);
+  ch.nlay = forced ? forced : default_layout(c.g);
   const std::string key = (near ? "R/" : "D/") + tune_key(c, b, cut);
   auto it = w->tuned.find(key);
   if (ch.r == 0 && !forced && it == w->tuned.end() && (flags & DPC_FLAG_AUTOTUNE)) {
@@ -755,22 +757,33 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
     if (!w->tune_ev[0])
       for (auto& e : w->tune_ev) cudaEventCreate(&e);
     cudaMemcpyAsync(w->ctr_save, w->ctr, sizeof(Counters), cudaMemcpyDeviceToDevice, st);
-    const int lays[2] = {kLayoutUnion, kLayoutSegment};
+    const int dlays[2] = {kLayoutUnion, kLayoutSegment};
+    const int nlays[3] = {kLayoutUnion, kLayoutSegment, kLayoutTree};
+    // events: 0 start, 1 after cells, 2-3 after each density layout, 4 after
+    // the subtree keys, 5-7 after each near layout (each followed by the far
+    // search, which finishes what the near phase leaves)
     auto trial = [&](int r, bool timed) {
       if (timed) cudaEventRecord(w->tune_ev[0], st);
       launch_set_radius(cv, cuts, r, st);
       launch_cells(w->scode, cv, c.g, cuts, w->hinfo, w->hkeys, w->hvals, w->hcap, st);
       if (timed) cudaEventRecord(w->tune_ev[1], st);
       for (int l = 0; l < 2; ++l) {
-        launch_density(c.dp, c.g, fp64, lays[l], w->spts, w->scode, w->sid, cv, cuts, w->hinfo,
+        launch_density(c.dp, c.g, fp64, dlays[l], w->spts, w->scode, w->sid, cv, cuts, w->hinfo,
                        w->hkeys, w->hvals, rho_scratch, w->skey, w->ctr, st);
         if (timed) cudaEventRecord(w->tune_ev[2 + l], st);
       }
-      for (int l = 0; near && l < 2; ++l) {
-        launch_dep_near(c.dp, c.g, fp64, lays[l], w->spts, w->scode, w->skey, cv, 0, near->pts,
+      if (!near) return;
+      launch_tree_maxkey(w->skey, w->spts, c.dp, cv.N, w->nodes, w->leaf_parent, w->visit, w->nbox,
+                         !w->boxes_ready, st);
+      w->boxes_ready = true;
+      if (timed) cudaEventRecord(w->tune_ev[4], st);
+      for (int l = 0; l < 3; ++l) {
+        launch_dep_near(c.dp, c.g, fp64, nlays[l], w->spts, w->scode, w->skey, cv, 0, near->pts,
                         near->dtype, cuts, w->hinfo, w->hkeys, w->hvals, near->lambda, near->delta,
                         queue_of(w), w->ctr, st);
-        if (timed) cudaEventRecord(w->tune_ev[4 + l], st);
+        launch_dep_far(c.dp, fp64, w->spts, w->scode, w->skey, cv, cuts, w->nodes, w->nbox, w->roots,
+                       queue_of(w), near->lambda, near->delta, w->ctr, st);
+        if (timed) cudaEventRecord(w->tune_ev[5 + l], st);
       }
     };
     auto span = [&](int a, int z) {
@@ -788,37 +801,39 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
     bool failed = false;
     for (int r = 1; r <= rmax && !failed; ++r) {
       // each phase: the smaller of two timings
-      float cl = 1e30f, dU = 1e30f, dS = 1e30f, nU = 1e30f, nS = 1e30f;
+      float cl = 1e30f, dt[2] = {1e30f, 1e30f}, nt[3] = {1e30f, 1e30f, 1e30f};
       for (int rep = 0; rep < 2; ++rep) {
         trial(r, true);
-        if (cudaEventSynchronize(w->tune_ev[near ? 5 : 3]) != cudaSuccess) {
+        if (cudaEventSynchronize(w->tune_ev[near ? 7 : 3]) != cudaSuccess) {
           cudaGetLastError();
           failed = true;
           break;
         }
         cl = fminf(cl, span(0, 1));
-        dU = fminf(dU, span(1, 2));
-        dS = fminf(dS, span(2, 3));
-        if (near) {
-          nU = fminf(nU, span(3, 4));
-          nS = fminf(nS, span(4, 5));
-        }
+        dt[0] = fminf(dt[0], span(1, 2));
+        dt[1] = fminf(dt[1], span(2, 3));
+        if (near)
+          for (int l = 0; l < 3; ++l) nt[l] = fminf(nt[l], span(4 + l, 5 + l));
       }
       if (failed) break;
       // a layout other than the default has to win by 3%
-      auto pick = [&](float u, float s) {
-        return default_layout(c.g) == kLayoutUnion ? (s < 0.97f * u ? kLayoutSegment : kLayoutUnion)
-                                                   : (u < 0.97f * s ? kLayoutUnion : kLayoutSegment);
+      const int def = default_layout(c.g);
+      auto pick = [&](const float* t, const int* lays, int m) {
+        int bi = 0;
+        for (int l = 0; l < m; ++l)
+          if (lays[l] == def) bi = l;
+        for (int l = 0; l < m; ++l)
+          if (t[l] < 0.97f * t[bi]) bi = l;
+        return bi;
       };
-      const int dl = pick(dU, dS);
-      const int nl = near ? pick(nU, nS) : default_layout(c.g);
-      const float ms = cl + (dl == kLayoutUnion ? dU : dS) +
-                       (near ? (nl == kLayoutUnion ? nU : nS) : 0.f);
+      const int di = pick(dt, dlays, 2);
+      const int ni = near ? pick(nt, nlays, 3) : -1;
+      const float ms = cl + dt[di] + (near ? nt[ni] : 0.f);
       if (best.r == 0 || ms < best_ms) {
         best_ms = ms;
         best.r = r;
-        best.dlay = dl;
-        best.nlay = nl;
+        best.dlay = dlays[di];
+        best.nlay = near ? nlays[ni] : def;
       }
     }
     if (failed) best = Choice();

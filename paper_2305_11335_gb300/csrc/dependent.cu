@@ -580,6 +580,39 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
   }
 }
 
+// Tree layout of the near phase: no block scan; every query (but the skipped
+// ones) goes to the tree search with no bound.  Pays off where blocks are
+// dense enough that a best-first search of the tree, pruned by maximum key and
+// by box distance, visits far fewer points than the block holds.
+__global__ void k_near_to_far(const unsigned long long* __restrict__ skey, uint32_t n,
+                              int32_t rho_skip, int32_t* __restrict__ lambda,
+                              double* __restrict__ delta, FarQueue q, Counters* ctr) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lanemask_lt = (1u << lane) - 1u;
+  const uint32_t n_pad = (n + 31) & ~31u;
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n_pad; p += gridDim.x * blockDim.x) {
+    const bool valid = p < n;
+    const unsigned long long K = valid ? skey[p] : 0ull;
+    const bool skip = valid && (int32_t)(K >> 32) < rho_skip;
+    if (skip) {
+      const uint32_t id = key_id(K);
+      lambda[id] = -1;
+      delta[id] = __longlong_as_double(0x7ff8000000000000ll);  // NaN: skipped
+    }
+    const bool push = valid && !skip;
+    const unsigned pm = __ballot_sync(kFull, push);
+    uint32_t base = 0;
+    if (lane == 0 && pm) base = atomicAdd(&ctr->queue_n, (unsigned)__popc(pm));
+    base = __shfl_sync(kFull, base, 0);
+    if (push) {
+      const uint32_t slot = base + __popc(pm & lanemask_lt);
+      q.pos[slot] = p;
+      q.s1[slot] = INFINITY;
+      q.s1d[slot] = INFINITY;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // far phase: depth-first priority search of the radix tree
 
@@ -1072,7 +1105,10 @@ void launch_dep_near(int dp, int g, bool fp64, int layout, const float* spts,
   if (cv.N == 0) return;
   cudaMemsetAsync(&ctr->queue_n, 0, sizeof(unsigned int), st);
   cudaMemsetAsync(&ctr->queue2_n, 0, sizeof(unsigned int), st);
-  if (g == 1) near_dg<2, 1>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
+  if (layout == kLayoutTree) {
+    k_near_to_far<<<grid_for(cv.N, 256, 152u * 16u), 256, 0, st>>>(skey, cv.N, rho_skip, lambda,
+                                                                     delta, q, ctr);
+  } else if (g == 1) near_dg<2, 1>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
   else if (g == 2) near_dg<2, 2>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
   else if (g == 3) near_dg<4, 3>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
   else if (dp == 4) near_dg<4, 4>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);

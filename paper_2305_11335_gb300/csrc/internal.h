@@ -82,7 +82,9 @@ void launch_tree_maxkey(const unsigned long long* skey, const float* spts, int d
 //   segment  the 32 points are split into segments of equal cell; the block's
 //            candidates are spread over the lanes (in registers) and the
 //            segment's queries are taken one at a time, one warp reduction each
-enum { kLayoutUnion = 1, kLayoutSegment = 2 };
+//   tree     (near phase only) no block scan: every query goes to the tree
+//            search of the far phase
+enum { kLayoutUnion = 1, kLayoutSegment = 2, kLayoutTree = 3 };
 
 // ---- density (density.cu) -------------------------------------------------------
 // rho of every point for one cutoff (cuts: [ninst]); rho_out is indexed by

@@ -222,7 +222,7 @@ def test_stats():
     assert 0 < s["far_queries"] < 20000
 
 
-@pytest.mark.parametrize("layout", ["union", "segment"])
+@pytest.mark.parametrize("layout", ["union", "segment", "tree"])
 @pytest.mark.parametrize("radius", [1, 2, 3, 5])
 def test_block_radius_does_not_change_results(radius, layout):
     """Every block radius (grid level) and both kernel layouts give the
