@@ -337,8 +337,8 @@ def run_ours(args, rank, world, dev):
     config.update({"precision": args.precision, "l2": "flushed between steps (512 MiB write)",
                    "grid_level": "autotuned in the first warm-up call" if not args.no_autotune else "default rule",
                    "block_radius": int(stats.get("block_radius", 0)),
-                   "layouts": {"density": ["?", "union", "segment", "tree"][int(stats.get("density_layout", 0))],
-                               "near": ["?", "union", "segment", "tree"][int(stats.get("near_layout", 0))]},
+                   "layouts": {"density": ["?", "union", "segment", "tree", "tensor"][int(stats.get("density_layout", 0))],
+                               "near": ["?", "union", "segment", "tree", "tensor"][int(stats.get("near_layout", 0))]},
                    "parallelism": "replicas" if world > 1 else "1 GPU"})
     res = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -359,7 +359,7 @@ def run_ours(args, rank, world, dev):
     pk, pk_kind = peaks()
     single = {p: v for p, v in phases.items() if p in ("density", "near", "far", "tree", "maxkey")}
     dom = max(single, key=lambda p: single[p][0]) if single else None
-    kernels = {"density": {2: "k_density_seg"}.get(stats.get("density_layout"), "k_density"),
+    kernels = {"density": {2: "k_density_seg", 4: "k_density_tc"}.get(stats.get("density_layout"), "k_density"),
                "near": {2: "k_dep_near_seg", 3: "k_near_to_far"}.get(stats.get("near_layout"), "k_dep_near")}
     model_phase = dom if dom in kernels else max(("density", "near"), key=lambda p: phases[p][0])
     work, mean_rho = block_work(job, out["rho"])

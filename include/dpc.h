@@ -105,9 +105,12 @@ enum {
  * their blocks streamed as broadcast reads), 2 = segment (the block of one
  * cell spread over the lanes, the cell's queries one at a time), 3 = tree
  * (near phase only, density keeps its default: no block scan, every query goes
- * to the tree search of the far phase).  Results do not depend on it. */
+ * to the tree search of the far phase), 4 = tensor (density only, 5-8
+ * dimensions with DPC_PREC_FP32_CERT: distance tiles on the tensor cores with a
+ * certified error band; other cases use segment).  Results do not depend on
+ * it. */
 #define DPC_FLAG_LAYOUT(v) ((uint32_t)(v) << 16)
-#define DPC_FLAG_LAYOUT_MASK (0x3u << 16)
+#define DPC_FLAG_LAYOUT_MASK (0x7u << 16)
 /* dpc_run only: capture the call's kernels into a CUDA graph the first time a
  * (pointers, batch, thresholds, precision, radius) combination is seen, and on
  * later calls with the same combination launch that graph instead of one

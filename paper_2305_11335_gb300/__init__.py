@@ -83,7 +83,7 @@ def DPC_FLAG_RADIUS(r: int) -> int:
     return (int(r) & 7) << 12
 
 
-LAYOUTS = {"auto": 0, "union": 1, "segment": 2, "tree": 3}
+LAYOUTS = {"auto": 0, "union": 1, "segment": 2, "tree": 3, "tensor": 4}
 
 
 def DPC_FLAG_LAYOUT(layout: str) -> int:

@@ -95,7 +95,7 @@ int check_flags(uint32_t flags) {
   if (prec != DPC_PREC_FP64 && prec != DPC_PREC_FP32_CERT) return DPC_ERR_UNSUPPORTED;
   if (flags & ~kKnownFlags) return DPC_ERR_ARG;
   if (((flags & DPC_FLAG_RADIUS_MASK) >> 12) > 5) return DPC_ERR_ARG;
-  if (((flags & DPC_FLAG_LAYOUT_MASK) >> 16) > 3) return DPC_ERR_ARG;
+  if (((flags & DPC_FLAG_LAYOUT_MASK) >> 16) > 4) return DPC_ERR_ARG;
   return DPC_OK;
 }
 
@@ -103,6 +103,7 @@ int status_to_code(int s) {
   if (s == 0) return DPC_OK;
   if (s & (kStatusBadCoord | kStatusCycle)) return DPC_ERR_DATA;
   if (s & kStatusStack) return DPC_ERR_UNSUPPORTED;
+  if (s & kStatusTimeout) return DPC_ERR_TIMEOUT;
   return DPC_ERR_CUDA;
 }
 
@@ -193,6 +194,7 @@ struct Workspace {
   bool boxes_ready = false; // nbox matches the current binning
   uint32_t* leaf_parent = nullptr;
   uint32_t* visit = nullptr;
+  uint2* pieces = nullptr;        // 128-point pieces of the cells (tensor-core density)
   uint32_t* qpos = nullptr;
   float* qs1 = nullptr;
   double* qs1d = nullptr;
@@ -223,7 +225,7 @@ struct Workspace {
 
   // autotuned radius and layouts per (class shape, cutoff), see choose()
   std::map<std::string, Choice> tuned;
-  cudaEvent_t tune_ev[8] = {};
+  cudaEvent_t tune_ev[9] = {};
 
   // for dpc_get_stats: the last class and cutoff that ran
   Choice last_choice;
@@ -321,6 +323,7 @@ struct Workspace {
     const size_t o_nodes = take(sizeof(Node) * N);
     const size_t o_nbox = take(4 * 16 * N);
     const size_t o_lp = take(4 * N), o_visit = take(4 * N);
+    const size_t o_pieces = take(8 * N);
     const size_t o_qpos = take(4 * N), o_qs1 = take(4 * N), o_qs1d = take(8 * N);
     const size_t o_qpos2 = take(4 * N), o_qs1_2 = take(4 * N), o_qs1d2 = take(8 * N);
     void* p = nullptr;
@@ -360,6 +363,7 @@ struct Workspace {
     nbox = (float*)(b + o_nbox);
     leaf_parent = (uint32_t*)(b + o_lp);
     visit = (uint32_t*)(b + o_visit);
+    pieces = (uint2*)(b + o_pieces);
     qpos = (uint32_t*)(b + o_qpos);
     qs1 = (float*)(b + o_qs1);
     qs1d = (double*)(b + o_qs1d);
@@ -657,7 +661,7 @@ void density_step(Workspace* w, const ClassPlan& c, const ClassView& cv, const C
                   bool fp64, int layout, int32_t* rho) {
   Phase ph(w, DPC_PHASE_DENSITY);
   launch_density(c.dp, c.g, fp64, layout, w->spts, w->scode, w->sid, cv, cuts, w->hinfo, w->hkeys,
-                 w->hvals, rho, w->skey, w->ctr, w->stream);
+                 w->hvals, w->pieces, rho, w->skey, w->ctr, w->stream);
 }
 
 void dependent_step(Workspace* w, const ClassPlan& c, const ClassView& cv, const CutGeom* cuts,
@@ -749,7 +753,7 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
   ch.r = (int)((flags & DPC_FLAG_RADIUS_MASK) >> 12);
   const int forced = (int)((flags & DPC_FLAG_LAYOUT_MASK) >> 16);
   ch.dlay = (forced && forced != kLayoutTree) ? forced : default_layout(c.g);
-  ch.nlay = forced ? forced : default_layout(c.g);
+  ch.nlay = (forced && forced != kLayoutTensor) ? forced : default_layout(c.g);
   const std::string key = (near ? "R/" : "D/") + tune_key(c, b, cut);
   auto it = w->tuned.find(key);
   if (ch.r == 0 && !forced && it == w->tuned.end() && (flags & DPC_FLAG_AUTOTUNE)) {
@@ -757,33 +761,36 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
     if (!w->tune_ev[0])
       for (auto& e : w->tune_ev) cudaEventCreate(&e);
     cudaMemcpyAsync(w->ctr_save, w->ctr, sizeof(Counters), cudaMemcpyDeviceToDevice, st);
-    const int dlays[2] = {kLayoutUnion, kLayoutSegment};
+    // the tensor layout exists for 5-8 dimensions with the float32 filter
+    const int ndl = (c.dp == 8 && !fp64) ? 3 : 2;
+    const int dlays[3] = {kLayoutUnion, kLayoutSegment, kLayoutTensor};
     const int nlays[3] = {kLayoutUnion, kLayoutSegment, kLayoutTree};
-    // events: 0 start, 1 after cells, 2-3 after each density layout, 4 after
-    // the subtree keys, 5-7 after each near layout (each followed by the far
+    // events: 0 start, 1 after cells, 2-4 after each density layout, 5 after
+    // the subtree keys, 6-8 after each near layout (each followed by the far
     // search, which finishes what the near phase leaves)
     auto trial = [&](int r, bool timed) {
       if (timed) cudaEventRecord(w->tune_ev[0], st);
       launch_set_radius(cv, cuts, r, st);
       launch_cells(w->scode, cv, c.g, cuts, w->hinfo, w->hkeys, w->hvals, w->hcap, st);
       if (timed) cudaEventRecord(w->tune_ev[1], st);
-      for (int l = 0; l < 2; ++l) {
-        launch_density(c.dp, c.g, fp64, dlays[l], w->spts, w->scode, w->sid, cv, cuts, w->hinfo,
-                       w->hkeys, w->hvals, rho_scratch, w->skey, w->ctr, st);
+      for (int l = 0; l < 3; ++l) {
+        if (l < ndl)
+          launch_density(c.dp, c.g, fp64, dlays[l], w->spts, w->scode, w->sid, cv, cuts, w->hinfo,
+                         w->hkeys, w->hvals, w->pieces, rho_scratch, w->skey, w->ctr, st);
         if (timed) cudaEventRecord(w->tune_ev[2 + l], st);
       }
       if (!near) return;
       launch_tree_maxkey(w->skey, w->spts, c.dp, cv.N, w->nodes, w->leaf_parent, w->visit, w->nbox,
                          !w->boxes_ready, st);
       w->boxes_ready = true;
-      if (timed) cudaEventRecord(w->tune_ev[4], st);
+      if (timed) cudaEventRecord(w->tune_ev[5], st);
       for (int l = 0; l < 3; ++l) {
         launch_dep_near(c.dp, c.g, fp64, nlays[l], w->spts, w->scode, w->skey, cv, 0, near->pts,
                         near->dtype, cuts, w->hinfo, w->hkeys, w->hvals, near->lambda, near->delta,
                         queue_of(w), w->ctr, st);
         launch_dep_far(c.dp, fp64, w->spts, w->scode, w->skey, cv, cuts, w->nodes, w->nbox, w->roots,
                        queue_of(w), near->lambda, near->delta, w->ctr, st);
-        if (timed) cudaEventRecord(w->tune_ev[5 + l], st);
+        if (timed) cudaEventRecord(w->tune_ev[6 + l], st);
       }
     };
     auto span = [&](int a, int z) {
@@ -801,19 +808,18 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
     bool failed = false;
     for (int r = 1; r <= rmax && !failed; ++r) {
       // each phase: the smaller of two timings
-      float cl = 1e30f, dt[2] = {1e30f, 1e30f}, nt[3] = {1e30f, 1e30f, 1e30f};
+      float cl = 1e30f, dt[3] = {1e30f, 1e30f, 1e30f}, nt[3] = {1e30f, 1e30f, 1e30f};
       for (int rep = 0; rep < 2; ++rep) {
         trial(r, true);
-        if (cudaEventSynchronize(w->tune_ev[near ? 7 : 3]) != cudaSuccess) {
+        if (cudaEventSynchronize(w->tune_ev[near ? 8 : 4]) != cudaSuccess) {
           cudaGetLastError();
           failed = true;
           break;
         }
         cl = fminf(cl, span(0, 1));
-        dt[0] = fminf(dt[0], span(1, 2));
-        dt[1] = fminf(dt[1], span(2, 3));
+        for (int l = 0; l < ndl; ++l) dt[l] = fminf(dt[l], span(1 + l, 2 + l));
         if (near)
-          for (int l = 0; l < 3; ++l) nt[l] = fminf(nt[l], span(4 + l, 5 + l));
+          for (int l = 0; l < 3; ++l) nt[l] = fminf(nt[l], span(5 + l, 6 + l));
       }
       if (failed) break;
       // a layout other than the default has to win by 3%
@@ -826,7 +832,7 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
           if (t[l] < 0.97f * t[bi]) bi = l;
         return bi;
       };
-      const int di = pick(dt, dlays, 2);
+      const int di = pick(dt, dlays, ndl);
       const int ni = near ? pick(nt, nlays, 3) : -1;
       const float ms = cl + dt[di] + (near ? nt[ni] : 0.f);
       if (best.r == 0 || ms < best_ms) {

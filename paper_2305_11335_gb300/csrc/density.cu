@@ -320,10 +320,17 @@ void density_dg(bool fp64, int layout, const float* spts, const unsigned long lo
 
 void launch_density(int dp, int g, bool fp64, int layout, const float* spts,
                     const unsigned long long* scode, const uint32_t* sid, const ClassView& cv,
-                    const CutGeom* cuts, const HashInfo* hi, const unsigned long long* hkeys,
-                    const uint2* hvals, int32_t* rho_out, unsigned long long* skey, Counters* ctr,
-                    cudaStream_t st) {
+                    const CutGeom* cuts, HashInfo* hi, const unsigned long long* hkeys,
+                    const uint2* hvals, uint2* pieces, int32_t* rho_out,
+                    unsigned long long* skey, Counters* ctr, cudaStream_t st) {
   if (cv.N == 0) return;
+  if (layout == kLayoutTensor) {
+    if (dp == 8 && !fp64 && pieces) {
+      launch_density_tc(g, spts, sid, cv, cuts, hi, hkeys, hvals, pieces, rho_out, skey, ctr, st);
+      return;
+    }
+    layout = kLayoutSegment;
+  }
   if (g == 1) density_dg<2, 1>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
   else if (g == 2) density_dg<2, 2>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
   else if (g == 3) density_dg<4, 3>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);

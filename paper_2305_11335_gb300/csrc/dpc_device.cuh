@@ -48,7 +48,8 @@ enum : int {
   kStatusHashFull = 2,   // hash probe limit reached (cannot happen at load <= 1/2)
   kStatusStack = 4,      // tree traversal stack overflow
   kStatusCycle = 8,      // dependent pointers did not converge to roots
-  kStatusIndex = 16      // an internal index failed its bounds check (a bug)
+  kStatusIndex = 16,     // an internal index failed its bounds check (a bug)
+  kStatusTimeout = 32    // a bounded wait for the tensor core gave up
 };
 
 // Per-instance grid geometry, written by the setup kernel from the bounding box.
@@ -96,6 +97,8 @@ constexpr uint32_t kNoNode = 0xffffffffu;  // no internal node (instance of one 
 struct HashInfo {
   uint32_t m;          // occupied cells (all instances)
   uint32_t hmask;      // table size - 1
+  uint32_t work;       // work counter of kernels that take items one by one
+  uint32_t npieces;    // entries of the piece list (tensor-core density)
 };
 
 // What a kernel needs to know about the class it works on.  A chunk is up to

@@ -84,16 +84,24 @@ void launch_tree_maxkey(const unsigned long long* skey, const float* spts, int d
 //            segment's queries are taken one at a time, one warp reduction each
 //   tree     (near phase only) no block scan: every query goes to the tree
 //            search of the far phase
-enum { kLayoutUnion = 1, kLayoutSegment = 2, kLayoutTree = 3 };
+//   tensor   (density, 5-8 dimensions, float32 filter) the distance tiles on the
+//            tensor cores (tc_density.cu); other cases fall back to segment
+enum { kLayoutUnion = 1, kLayoutSegment = 2, kLayoutTree = 3, kLayoutTensor = 4 };
 
 // ---- density (density.cu) -------------------------------------------------------
 // rho of every point for one cutoff (cuts: [ninst]); rho_out is indexed by
 // output index (sid)
 void launch_density(int dp, int g, bool fp64, int layout, const float* spts,
                     const unsigned long long* scode, const uint32_t* sid, const ClassView& cv,
-                    const CutGeom* cuts, const HashInfo* hi, const unsigned long long* hkeys,
-                    const uint2* hvals, int32_t* rho_out, unsigned long long* skey, Counters* ctr,
-                    cudaStream_t st);
+                    const CutGeom* cuts, HashInfo* hi, const unsigned long long* hkeys,
+                    const uint2* hvals, uint2* pieces, int32_t* rho_out,
+                    unsigned long long* skey, Counters* ctr, cudaStream_t st);
+// the tensor-core form of the density step (dp = 8, float32 filter only)
+// (pieces: scratch for the piece list, at least N / 128 + occupied cells entries)
+void launch_density_tc(int g, const float* spts, const uint32_t* sid, const ClassView& cv,
+                       const CutGeom* cuts, HashInfo* hi, const unsigned long long* hkeys,
+                       const uint2* hvals, uint2* pieces, int32_t* rho_out,
+                       unsigned long long* skey, Counters* ctr, cudaStream_t st);
 // order keys of sorted points from densities given by output index
 void launch_keys_from_rho(const int32_t* rho, const uint32_t* sid, uint32_t n,
                           unsigned long long* skey, cudaStream_t st);

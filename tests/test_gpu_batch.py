@@ -66,13 +66,13 @@ def check_run(sizes, dims, insts, cuts, dtype, precision, seed, layout="auto"):
 
 @pytest.mark.parametrize("precision,layout", [("fp32", "auto"), ("fp64", "auto"), ("fp32", "union"),
                                               ("fp32", "segment"), ("fp64", "segment"), ("fp32", "tree"),
-                                              ("fp64", "tree")])
+                                              ("fp64", "tree"), ("fp32", "tensor"), ("fp64", "tensor")])
 def test_batch_mixed_dims_float(precision, layout):
     sizes, dims, insts, cuts = make_batch(1, 48, [2, 3, 5, 1, 4, 7, 8, 2, 3, 5])
     check_run(sizes, dims, insts, cuts, np.float32, precision, 11, layout)
 
 
-@pytest.mark.parametrize("layout", ["union", "segment", "tree"])
+@pytest.mark.parametrize("layout", ["union", "segment", "tree", "tensor"])
 def test_batch_int_ties(layout):
     sizes, dims, insts, cuts = make_batch(2, 30, [2, 3], dtype=np.int32, max_n=1500)
     check_run(sizes, dims, insts, cuts, np.int32, "fp32", 12, layout)

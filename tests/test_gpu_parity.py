@@ -222,7 +222,7 @@ def test_stats():
     assert 0 < s["far_queries"] < 20000
 
 
-@pytest.mark.parametrize("layout", ["union", "segment", "tree"])
+@pytest.mark.parametrize("layout", ["union", "segment", "tree", "tensor"])
 @pytest.mark.parametrize("radius", [1, 2, 3, 5])
 def test_block_radius_does_not_change_results(radius, layout):
     """Every block radius (grid level) and both kernel layouts give the
@@ -300,3 +300,27 @@ def test_graph_mode_batch():
             lo, hi = batch.pt_offset[i], batch.pt_offset[i + 1]
             ref = oracle.run(p, cuts[i][0], 2, 3, 0.1)
             assert_same({k: v[0, lo:hi] for k, v in out.items()}, ref, "rep %d inst %d" % (rep, i))
+
+
+@pytest.mark.parametrize("d,dtype", [(5, np.float32), (6, np.float32), (8, np.float32), (5, np.int32)])
+def test_tensor_density_dense_blocks(d, dtype):
+    """The tensor-core density in 5-8 dimensions on dense blocks (many 256-
+    candidate tiles per segment, 128-point items over several cells) and, for
+    integer coordinates, many pairs exactly at the cutoff (the error band and
+    its binary64 recount decide them)."""
+    rng = np.random.default_rng(300 + d)
+    if dtype == np.int32:
+        pts = rng.integers(0, 12, (12000, d)).astype(np.int32)
+        cuts = [3.0, 4.0]
+    else:
+        pts = W.random_blobs(12000, d, 310 + d, n_blobs=3)
+        cuts = [0.15, 0.25]
+    t = torch.from_numpy(pts).cuda()
+    for c in cuts:
+        ref = oracle.density(pts, c)
+        for prec in ("fp32", "fp64"):
+            got = dpc.dpc_density(t, dpc.Batch.single(len(pts), d, [c]), precision=prec, sync=True,
+                                  layout="tensor")
+            assert np.array_equal(got[0].cpu().numpy(), ref), (d, c, prec)
+    st = dpc.dpc_get_stats()
+    assert st["density_layout"] in (2, 4)
