@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=4096)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default grid-level rule")
     ap.add_argument("--no-graph", action="store_true", help="time plain calls instead of graph replays")
+    ap.add_argument("--layout", default="auto", choices=["auto", "union", "segment", "tree", "tensor"],
+                    help="fixed kernel layout (auto: the autotuned choice)")
     return ap.parse_args()
 
 
@@ -291,7 +293,7 @@ def run_ours(args, rank, world, dev):
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
             dpc.dpc_run(pts, batch, params, precision=precision, stream=stream, out=out, phase_times=phase_times,
-                        graph=graph)
+                        graph=graph, layout=args.layout)
             b.record(stream)
             b.synchronize()
             times.append(a.elapsed_time(b))
@@ -310,12 +312,13 @@ def run_ours(args, rank, world, dev):
     steps = 0
     while steps < args.warmup or time.time() < t_end:
         # the first warm-up call autotunes the grid level (cached for the rest)
-        dpc.dpc_run(pts, batch, params, precision=args.precision, stream=stream, out=out,
-                    autotune=(steps == 0 and not args.no_autotune))
+        dpc.dpc_run(pts, batch, params, precision=args.precision, stream=stream, out=out, layout=args.layout,
+                    autotune=(steps == 0 and not args.no_autotune and args.layout == "auto"))
         steps += 1
     use_graph = not args.no_graph
     # capture (graph mode) or one more plain call, then synchronize
-    dpc.dpc_run(pts, batch, params, precision=args.precision, stream=stream, out=out, sync=True, graph=use_graph)
+    dpc.dpc_run(pts, batch, params, precision=args.precision, stream=stream, out=out, sync=True, graph=use_graph,
+                layout=args.layout)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -363,6 +366,12 @@ def run_ours(args, rank, world, dev):
                "near": {2: "k_dep_near_seg", 3: "k_near_to_far"}.get(stats.get("near_layout"), "k_dep_near")}
     model_phase = dom if dom in kernels else max(("density", "near"), key=lambda p: phases[p][0])
     work, mean_rho = block_work(job, out["rho"])
+    high_d = max(job.dims) > 3
+    if high_d:
+        # the ideal all-coordinate grid overestimates clustered data above
+        # 3 dimensions: count the pairs the density step actually scanned
+        d_mean = float(np.dot(job.sizes, job.dims)) / max(1, job.N)
+        work = float(stats.get("density_pairs", 0)) * 3.0 * d_mean
     # phases[] holds the sums over the phase pass; work is one step's
     launches = phases[model_phase][1] // phase_steps
     step_ms = phases[model_phase][0] / phase_steps
@@ -375,8 +384,11 @@ def run_ours(args, rank, world, dev):
         "frac": achieved / peak, "traffic": load_traffic(kernels[model_phase], job.name),
         "peak_source": "derived (no FP32 figure is measured): 152 SMs x 128 FP32 lanes x 2 flops x "
                        "%.0f MHz max SM clock" % clk,
-        "work": "%.4g flops per step over %d launches: per point rho x 3^d / V_d block candidates x 3d flops "
-                "(mean rho %.1f at the first cutoff)" % (work, launches, mean_rho),
+        "work": ("%.4g flops per step over %d launches: the %d (query, candidate) pairs the density step "
+                 "scanned x 3d flops (d > 3: the ideal-grid count rho x 3^d / V_d overestimates clustered "
+                 "data)" % (work, launches, int(stats.get("density_pairs", 0)))) if high_d else
+                ("%.4g flops per step over %d launches: per point rho x 3^d / V_d block candidates x 3d flops "
+                 "(mean rho %.1f at the first cutoff)" % (work, launches, mean_rho)),
         "ms_per_launch": per_launch_ms}
     res["dominant_phase"] = dom
 

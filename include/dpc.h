@@ -100,7 +100,8 @@ enum {
 #define DPC_FLAG_RADIUS(r) ((uint32_t)(r) << 12)
 #define DPC_FLAG_RADIUS_MASK (0x7u << 12)
 /* Fixed work layout of the density and near-dependent kernels instead of the
- * default rule (segments for d = 3, union otherwise) or the autotuned choice:
+ * default rule (density in segments for d >= 2; the near phase in segments for
+ * d = 3, union otherwise) or the autotuned choice:
  * 1 = union (a warp's 32 consecutive points, one query per lane, the union of
  * their blocks streamed as broadcast reads), 2 = segment (the block of one
  * cell spread over the lanes, the cell's queries one at a time), 3 = tree
@@ -240,6 +241,8 @@ typedef struct {
                              2 segment (see DPC_FLAG_LAYOUT)                  */
   int32_t near_layout;    /* layout of the last near-dependent launch (3 = tree) */
   int32_t reserved;
+  int64_t density_pairs;  /* (query, candidate) pairs the density step scanned
+                             (every cutoff and instance of the last call)    */
 } dpc_stats;
 int dpc_get_stats(void* stream, dpc_stats* out);
 

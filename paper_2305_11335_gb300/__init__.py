@@ -70,7 +70,7 @@ class _Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("far_nodes", ctypes.c_int64),
                 ("far_nodes_max", ctypes.c_int64), ("block_radius", ctypes.c_int32),
                 ("density_layout", ctypes.c_int32), ("near_layout", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("density_pairs", ctypes.c_int64)]
 
 
 PHASES = ["bin", "tree", "cells", "density", "maxkey", "near", "far", "labels"]

@@ -735,7 +735,10 @@ struct NearTrial {
   double* delta;
 };
 
-inline int default_layout(int g) { return g == 3 ? kLayoutSegment : kLayoutUnion; }
+// Default layouts (measured on the GB300): density in segments from 2 gridded
+// dimensions up; the near phase in segments in 3, union otherwise.
+inline int default_dlayout(int g) { return g >= 2 ? kLayoutSegment : kLayoutUnion; }
+inline int default_nlayout(int g) { return g == 3 ? kLayoutSegment : kLayoutUnion; }
 
 // The grid level and kernel layouts of one (class, cutoff): a fixed radius or
 // layout from the flags, else the autotuned choice (measured now when the
@@ -752,8 +755,8 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
   Choice ch;
   ch.r = (int)((flags & DPC_FLAG_RADIUS_MASK) >> 12);
   const int forced = (int)((flags & DPC_FLAG_LAYOUT_MASK) >> 16);
-  ch.dlay = (forced && forced != kLayoutTree) ? forced : default_layout(c.g);
-  ch.nlay = (forced && forced != kLayoutTensor) ? forced : default_layout(c.g);
+  ch.dlay = (forced && forced != kLayoutTree) ? forced : default_dlayout(c.g);
+  ch.nlay = (forced && forced != kLayoutTensor) ? forced : default_nlayout(c.g);
   const std::string key = (near ? "R/" : "D/") + tune_key(c, b, cut);
   auto it = w->tuned.find(key);
   if (ch.r == 0 && !forced && it == w->tuned.end() && (flags & DPC_FLAG_AUTOTUNE)) {
@@ -823,8 +826,7 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
       }
       if (failed) break;
       // a layout other than the default has to win by 3%
-      const int def = default_layout(c.g);
-      auto pick = [&](const float* t, const int* lays, int m) {
+      auto pick = [&](const float* t, const int* lays, int m, int def) {
         int bi = 0;
         for (int l = 0; l < m; ++l)
           if (lays[l] == def) bi = l;
@@ -832,14 +834,14 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
           if (t[l] < 0.97f * t[bi]) bi = l;
         return bi;
       };
-      const int di = pick(dt, dlays, ndl);
-      const int ni = near ? pick(nt, nlays, 3) : -1;
+      const int di = pick(dt, dlays, ndl, default_dlayout(c.g));
+      const int ni = near ? pick(nt, nlays, 3, default_nlayout(c.g)) : -1;
       const float ms = cl + dt[di] + (near ? nt[ni] : 0.f);
       if (best.r == 0 || ms < best_ms) {
         best_ms = ms;
         best.r = r;
         best.dlay = dlays[di];
-        best.nlay = near ? nlays[ni] : def;
+        best.nlay = near ? nlays[ni] : default_nlayout(c.g);
       }
     }
     if (failed) best = Choice();
@@ -1173,6 +1175,7 @@ int dpc_get_stats(void* stream, dpc_stats* out) {
   out->kernel_launches = w->launches_last;
   out->far_nodes = (int64_t)c.far_nodes;
   out->far_nodes_max = (int64_t)c.far_nodes_max;
+  out->density_pairs = (int64_t)c.pairs;
   if (w->have_last) {
     CutGeom cg;
     GridGeom g;

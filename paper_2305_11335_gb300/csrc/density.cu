@@ -69,7 +69,7 @@ k_density(const float* __restrict__ spts, const unsigned long long* __restrict__
   const uint32_t hmask = hi->hmask;
   const uint32_t n = cv.N;
 
-  unsigned long long band = 0;
+  unsigned long long band = 0, pairs = 0;
   for (uint32_t ch = blockIdx.x * kWarps + wib; ch < cv.nchunk; ch += gridDim.x * kWarps) {
     uint32_t inst, p0, end;
     cv.chunk(ch, inst, p0, end);
@@ -104,6 +104,7 @@ k_density(const float* __restrict__ spts, const unsigned long long* __restrict__
         for_window_runs<G>(rt, nr, u, w0, w1, [&](uint32_t i0, uint32_t i1, const uint32_t* cc) {
           const bool need = act && in_block<G>(c0, cc, R);
           if (!__any_sync(kFull, need)) return;
+          if (need) pairs += i1 - i0;
           // a lane outside this cell's block compares against -1: never counts
           const float ti = need ? t_in : -1.f, to = need ? t_out : -1.f;
           const double dl = need ? dc2 : -1.0;
@@ -137,6 +138,8 @@ k_density(const float* __restrict__ spts, const unsigned long long* __restrict__
       skey[p] = order_key(count, id);
     }
   }
+  for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(kFull, pairs, o);
+  if (lane == 0 && pairs) atomicAdd(&ctr->pairs, pairs);
   if constexpr (!F64) {
     for (int o = 16; o > 0; o >>= 1) band += __shfl_xor_sync(kFull, band, o);
     if (lane == 0 && band) atomicAdd(&ctr->band_pairs, band);
@@ -172,7 +175,7 @@ k_density_seg(const float* __restrict__ spts, const unsigned long long* __restri
   const uint32_t hmask = hi->hmask;
   const uint32_t n = cv.N;
 
-  unsigned long long band = 0;
+  unsigned long long band = 0, pairs = 0;
   for (uint32_t ch = blockIdx.x * kWarps + wib; ch < cv.nchunk; ch += gridDim.x * kWarps) {
     uint32_t inst, p0, end;
     cv.chunk(ch, inst, p0, end);
@@ -199,6 +202,7 @@ k_density_seg(const float* __restrict__ spts, const unsigned long long* __restri
       block_union<G>(c0, R, cmax, u);
       const int nr = union_runs<G>(u, hkeys, hvals, hmask, hb, n, lane, rt);
       const uint32_t total = rt.pre[nr];
+      pairs += (unsigned long long)(e - s) * total;
       for (uint32_t w0 = 0; w0 < total; w0 += W) {
         Pt<DP> cand[V];
         load_window<DP, V>(rt, nr, w0, total, spts, lane, cand);
@@ -272,6 +276,7 @@ k_density_seg(const float* __restrict__ spts, const unsigned long long* __restri
       skey[p] = order_key(acc, id);
     }
   }
+  if (lane == 0 && pairs) atomicAdd(&ctr->pairs, pairs);
   if constexpr (!F64) {
     if (lane == 0 && band) atomicAdd(&ctr->band_pairs, band);
   }

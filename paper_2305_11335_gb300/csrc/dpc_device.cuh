@@ -167,6 +167,7 @@ struct Counters {
   unsigned long long exact_rescans;
   unsigned long long far_nodes;   // tree nodes expanded by far queries
   unsigned long long far_wide_queries;  // far queries that needed the second round
+  unsigned long long pairs;       // density: (query, candidate) pairs evaluated
   unsigned int far_nodes_max;     // most tree nodes expanded by one far query
   unsigned int queue_n;           // dependent far-query queue length
   unsigned int queue2_n;          // far queries passed to the second round

@@ -140,7 +140,7 @@ extern "C" int dpc_density_static(const void* pts, int dtype, int64_t n, int32_t
   launch_sort(codes_a, codes_b, ids_a, ids_b, nn, cls, hist, st);
   launch_gather(pts, dtype, cv, dp, codes_a, codes_b, ids_a, ids_b, spts, scode, sid, st);
   launch_cells(scode, cv, g, cut, hinfo, hkeys, hvals, kStaticHash, st);
-  launch_density(dp, g, prec == DPC_PREC_FP64, g == 3 ? kLayoutSegment : kLayoutUnion, spts, scode,
+  launch_density(dp, g, prec == DPC_PREC_FP64, g >= 2 ? kLayoutSegment : kLayoutUnion, spts, scode,
                  sid, cv, cut, hinfo, hkeys, hvals, nullptr, rho,
                  skey, ctr, st);
   if (cudaGetLastError() != cudaSuccess) return DPC_ERR_CUDA;

@@ -187,7 +187,7 @@ k_density_tc(const float* __restrict__ spts, const uint32_t* __restrict__ sid, C
   const int chalf = warp >> 2;
   const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(chalf * (kTcN / 2));
   uint32_t phase = 0;
-  unsigned long long band = 0;
+  unsigned long long band = 0, pairs = 0;
   bool stop = false;
 
   while (!stop) {
@@ -221,6 +221,10 @@ k_density_tc(const float* __restrict__ spts, const uint32_t* __restrict__ sid, C
     __syncthreads();
     const int nr = sm.nr;
     const uint32_t total = sm.rt.pre[nr];
+    if (tid == 0) {
+      const uint32_t q0p = pc.y < run.x ? run.x : pc.y;
+      pairs += (unsigned long long)min((uint32_t)kTcM, run.y - q0p) * total;
+    }
     {
       const uint32_t q0 = pc.y < run.x ? run.x : pc.y;
       // query rows: this thread's point, relative to the piece's first point
@@ -377,6 +381,7 @@ k_density_tc(const float* __restrict__ spts, const uint32_t* __restrict__ sid, C
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcN) : "memory");
   for (int o = 16; o > 0; o >>= 1) band += __shfl_xor_sync(kFull, band, o);
   if (lane == 0 && band) atomicAdd(&ctr->band_pairs, band);
+  if (tid == 0 && pairs) atomicAdd(&ctr->pairs, pairs);
 }
 
 // Dynamic shared memory per CTA: at least the layout, and enough that no
