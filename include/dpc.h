@@ -178,6 +178,37 @@ int dpc_cluster(const dpc_batch* b, int32_t dcut_index, const dpc_params* params
                 const int32_t* rho, const int32_t* lambda, const double* delta, int32_t* label,
                 uint32_t flags, void* stream);
 
+/* Decision-graph summaries of one cutoff's (rho, delta) arrays (Section 3:
+ * d_cut, rho_min and delta_min are picked from the graph of delta against
+ * rho).  Two products per instance, both computed on the device:
+ *   top, gamma  device, int32 / double [n_inst][k]: the k points with the
+ *               largest gamma = fl64(rho * delta) -- the center score of
+ *               Rodriguez and Laio, unrelated to the priority value of the
+ *               priority search kd-tree -- in descending gamma, equal gamma
+ *               by the smaller instance-local id; the top point's gamma is
+ *               +inf.  Points whose product is NaN (delta NaN: a point
+ *               skipped with rho_skip) or negative take no part.  Rows of
+ *               instances with fewer than k such points end in (-1, NaN).
+ *               k in [0, 1024]; k = 0 skips this product (top, gamma unused).
+ *   hist        device, int64 [n_inst][rho_bins][delta_bins]: counts of the
+ *               points with rho >= 1 and a non-NaN delta by
+ *                 rho bin   = floor(log2 rho)
+ *                 delta bin = 0 if delta <= delta_lo, else the binary
+ *                             exponent of fl64(delta / delta_lo)
+ *               each clipped to its last bin (+inf delta lands in the last
+ *               delta bin).  rho_bins in [0, 32], delta_bins in [0, 2048],
+ *               both 0 (skip, hist unused) or both positive; delta_lo finite
+ *               and > 0 when used.
+ *   rho, delta  device, [N] for one cutoff (slices of dpc_run's outputs or
+ *               what dpc_density / dpc_dependent wrote).
+ * Only the point counts and offsets of `b` are read; its coordinates and
+ * cutoffs are not.  Flags: DPC_FLAG_SYNC_CHECK only.  All outputs are
+ * written in stream order; a bad argument returns DPC_ERR_ARG with nothing
+ * launched. */
+int dpc_decision_graph(const dpc_batch* b, const int32_t* rho, const double* delta, int32_t k,
+                       int32_t* top, double* gamma, int32_t rho_bins, int32_t delta_bins,
+                       double delta_lo, int64_t* hist, uint32_t flags, void* stream);
+
 /* The whole pipeline for every cutoff: one binning per instance, then for each
  * cutoff density, dependent points and labels.  The instances of a batch are
  * processed together in at most four groups of equal padded dimension

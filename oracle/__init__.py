@@ -15,6 +15,7 @@ Points are ``(n, d)`` C-contiguous numpy arrays of ``int32`` or ``float32``.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -160,6 +161,74 @@ def cluster(rho, lam, delta, rho_noise: int, rho_min: int, delta_min: float) -> 
                              float(delta_min), _ptr(out))
     if rc:
         raise RuntimeError("orc_cluster: dependent pointers do not form a valid forest (%d)" % rc)
+    return out
+
+
+# planted deviations of decision_graph, used only by the pin tests
+DG_TIE_LARGER_ID = 1
+DG_DROP_INF = 2
+DG_DELTA_BIN_UP = 4
+DG_SUM_NOT_PRODUCT = 8
+
+
+def decision_graph(rho, delta, k: int, rho_bins: int = 0, delta_bins: int = 0, delta_lo: float = 1.0,
+                   variant: int = 0):
+    """Decision-graph summaries of one instance (Section 3: the hyper-parameters
+    are read off the graph of delta against rho).
+
+    top/gamma: the k points with the largest center score gamma = rho * delta
+    (one binary64 product), descending, equal scores by the smaller id; a
+    point whose score is NaN (delta NaN) or negative takes no part; the row is
+    padded with (-1, NaN).  hist[a][b] counts the points with rho >= 1 and a
+    non-NaN delta, a = floor(log2 rho), b = the binary exponent of the
+    quotient delta / delta_lo (0 when delta <= delta_lo), both clipped to the
+    last bin.  Plain numpy and Python loops; the rule is written out point by
+    point.
+    """
+    rho = np.asarray(rho, dtype=np.int32)
+    delta = np.asarray(delta, dtype=np.float64)
+    n = rho.shape[0]
+    score = []
+    for i in range(n):
+        r = float(rho[i])
+        dl = float(delta[i])
+        g = r + dl if variant & DG_SUM_NOT_PRODUCT else r * dl
+        if math.isnan(g) or g < 0.0:
+            continue
+        if variant & DG_DROP_INF and math.isinf(g):
+            continue
+        score.append((g, i))
+    if variant & DG_TIE_LARGER_ID:
+        score.sort(key=lambda t: (-t[0], -t[1]))
+    else:
+        score.sort(key=lambda t: (-t[0], t[1]))
+    top = np.full(k, -1, dtype=np.int32)
+    gamma = np.full(k, np.nan, dtype=np.float64)
+    for j, (g, i) in enumerate(score[:k]):
+        top[j] = i
+        gamma[j] = g
+    out = {"top": top, "gamma": gamma}
+    if rho_bins > 0 and delta_bins > 0:
+        hist = np.zeros((rho_bins, delta_bins), dtype=np.int64)
+        for i in range(n):
+            r = int(rho[i])
+            dl = float(delta[i])
+            if r < 1 or math.isnan(dl):
+                continue
+            a = min(r.bit_length() - 1, rho_bins - 1)  # 2^a <= r < 2^(a+1)
+            if not dl > delta_lo:
+                b = 0
+            else:
+                q = dl / delta_lo
+                if math.isinf(q):
+                    b = delta_bins - 1
+                else:
+                    b = math.frexp(q)[1] - 1  # q = m * 2^(b+1), 0.5 <= m < 1
+                    if variant & DG_DELTA_BIN_UP:
+                        b += 1
+                    b = min(max(b, 0), delta_bins - 1)
+            hist[a, b] += 1
+        out["hist"] = hist
     return out
 
 

@@ -41,7 +41,8 @@ DPC_F32 = 1
 PREC = {"fp64": 0, "fp32": 1}
 DPC_FLAG_SYNC_CHECK = 1 << 8
 
-EXPORTS = ["dpc_density", "dpc_dependent", "dpc_cluster", "dpc_run", "dpc_run_host", "dpc_density_static",
+EXPORTS = ["dpc_density", "dpc_dependent", "dpc_cluster", "dpc_decision_graph", "dpc_run", "dpc_run_host",
+           "dpc_density_static",
            "dpc_get_stats", "dpc_get_phase_times", "dpc_last_status", "dpc_strerror", "dpc_version",
            "dpc_release"]
 DPC_STATIC_MAX_POINTS = 65536
@@ -112,6 +113,7 @@ def load(path: str = LIB_PATH):
     lib.dpc_density.argtypes = [vp, ctypes.c_int, bp, vp, u32, vp]
     lib.dpc_dependent.argtypes = [vp, ctypes.c_int, bp, i32, vp, i32, vp, vp, u32, vp]
     lib.dpc_cluster.argtypes = [bp, i32, pp, vp, vp, vp, vp, u32, vp]
+    lib.dpc_decision_graph.argtypes = [bp, vp, vp, i32, vp, vp, i32, i32, ctypes.c_double, vp, u32, vp]
     lib.dpc_run.argtypes = [vp, ctypes.c_int, bp, pp, vp, vp, vp, vp, u32, vp]
     lib.dpc_run_host.argtypes = [vp, ctypes.c_int, bp, pp, vp, vp, vp, vp, u32, vp]
     lib.dpc_density_static.argtypes = [vp, ctypes.c_int, ctypes.c_int64, i32, ctypes.c_double, vp, u32, vp]
@@ -274,6 +276,34 @@ def dpc_cluster(batch: Batch, dcut_index: int, params, rho: torch.Tensor, lam: t
                            _dev(delta, "delta"), _dev(label, "label"), DPC_FLAG_SYNC_CHECK if sync else 0,
                            _stream(stream)), "dpc_cluster")
     return label
+
+
+def dpc_decision_graph(batch: Batch, rho: torch.Tensor, delta: torch.Tensor, k: int = 16, rho_bins: int = 0,
+                       delta_bins: int = 0, delta_lo: float = 1.0, sync: bool = False, stream=None) -> dict:
+    """Decision-graph summaries of one cutoff: the top-k points by
+    gamma = rho * delta per instance ("top" int32 [n_inst, k], "gamma" float64
+    [n_inst, k]) and, with rho_bins/delta_bins > 0, the log2-binned (rho, delta)
+    counts ("hist" int64 [n_inst, rho_bins, delta_bins])."""
+    lib = load()
+    if rho.dtype != torch.int32 or delta.dtype != torch.float64:
+        raise ValueError("rho must be int32 and delta float64")
+    dev = rho.device
+    out = {}
+    top = torch.empty((batch.n_inst, k), dtype=torch.int32, device=dev) if k > 0 else None
+    gamma = torch.empty((batch.n_inst, k), dtype=torch.float64, device=dev) if k > 0 else None
+    hist = (torch.empty((batch.n_inst, rho_bins, delta_bins), dtype=torch.int64, device=dev)
+            if rho_bins > 0 and delta_bins > 0 else None)
+    _check(lib.dpc_decision_graph(batch.ptr, _dev(rho, "rho"), _dev(delta, "delta"), int(k),
+                                  _dev(top, "top") if top is not None else None,
+                                  _dev(gamma, "gamma") if gamma is not None else None,
+                                  int(rho_bins), int(delta_bins), float(delta_lo),
+                                  _dev(hist, "hist") if hist is not None else None,
+                                  DPC_FLAG_SYNC_CHECK if sync else 0, _stream(stream)), "dpc_decision_graph")
+    if top is not None:
+        out["top"], out["gamma"] = top, gamma
+    if hist is not None:
+        out["hist"] = hist
+    return out
 
 
 def dpc_run(pts: torch.Tensor, batch: Batch, params, precision: str = "fp32", sync: bool = False, stream=None,

@@ -560,6 +560,8 @@ int upload_tables(Workspace* w, CallPlan& P, const dpc_batch* b, const std::vect
       id[j].coord = in.coord_off;
       id[j].d = in.d;
       id[j].chunk0 = chunk;
+      id[j].row = (uint32_t)bi;
+      id[j].pad = 0;
       start += (uint32_t)in.n;
       chunk += (uint32_t)((in.n + 31) / 32);
       for (int k = 0; k < P.ncut; ++k) {
@@ -602,6 +604,7 @@ ClassView view_of(Workspace* w, const ClassPlan& c, const std::vector<Inst>& ins
     v.one.coord = in.coord_off;
     v.one.d = in.d;
     v.one.chunk0 = 0;
+    v.one.row = (uint32_t)c.members[0];
   }
   return v;
 }
@@ -1000,6 +1003,39 @@ static void run_classes(Workspace* w, const CallPlan& P, const void* pts, int dt
                   delta + o, label + o);
     }
   }
+}
+
+int dpc_decision_graph(const dpc_batch* b, const int32_t* rho, const double* delta, int32_t k,
+                       int32_t* top, double* gamma, int32_t rho_bins, int32_t delta_bins,
+                       double delta_lo, int64_t* hist, uint32_t flags, void* stream) {
+  std::vector<Inst> insts;
+  uint64_t N = 0;
+  int rc = check_batch(b, &insts, &N);
+  if (rc) return rc;
+  if (flags & ~(DPC_FLAG_SYNC_CHECK)) return DPC_ERR_ARG;
+  if (k < 0 || k > decision_max_topk()) return DPC_ERR_ARG;
+  if (rho_bins < 0 || rho_bins > 32 || delta_bins < 0 || delta_bins > 2048) return DPC_ERR_ARG;
+  if ((rho_bins > 0) != (delta_bins > 0)) return DPC_ERR_ARG;
+  if (k > 0 && (!top || !gamma)) return DPC_ERR_ARG;
+  if (rho_bins > 0 && (!hist || !(delta_lo > 0.0) || !std::isfinite(delta_lo))) return DPC_ERR_ARG;
+  if (N > 0 && (!rho || !delta)) return DPC_ERR_ARG;
+  Workspace* w = nullptr;
+  if ((rc = get_workspace((cudaStream_t)stream, &w))) return rc;
+  std::lock_guard<std::mutex> lk(g_mu);
+  // every non-empty instance in one class (the summaries do not depend on the
+  // dimension); rows of empty instances keep the padding written first
+  CallPlan P = make_plan(b, insts, 0, 1, true);
+  if ((rc = prepare(w, P, b, insts, nullptr, flags))) return rc;
+  launch_decision_init(b->n_inst, k, top, gamma, rho_bins, delta_bins,
+                       (unsigned long long*)hist, w->stream);
+  for (const ClassPlan& c : P.classes) {
+    const ClassView cv = view_of(w, c, insts);
+    launch_class_init(cv, c.g, c.ib, c.bcap, w->status, w->stream);
+    launch_chunks(cv, w->chunk_inst, w->chunk_pos, w->stream);
+    launch_decision(rho, delta, cv, k, top, gamma, rho_bins, delta_bins, delta_lo,
+                    (unsigned long long*)hist, w->stream);
+  }
+  return finish(w, flags);
 }
 
 static int run_device(Workspace* w, const void* pts, int dtype, const dpc_batch* b,

@@ -82,6 +82,8 @@ struct InstDev {
   uint64_t coord;      // element offset of its coordinates in the caller's pts
   int32_t d;           // dimension
   uint32_t chunk0;     // first 32-point chunk of the instance
+  uint32_t row;        // the instance's index in the caller's batch
+  uint32_t pad;
 };
 
 // Labelling thresholds of one (instance, cutoff) (same layout as dpc_params).

@@ -128,6 +128,18 @@ void launch_dep_far(int dp, bool fp64, const float* spts, const unsigned long lo
                     const Node* nodes, const float* nbox, const uint32_t* root, FarQueue q,
                     int32_t* lambda, double* delta, Counters* ctr, cudaStream_t st);
 
+// ---- decision graph (decision.cu) -------------------------------------------------
+// top-k by gamma = rho * delta and the (rho, delta) histogram of every instance
+// of the class (rho, delta indexed by output index; top/gamma [n_inst][k] and
+// hist [n_inst][rho_bins][delta_bins] by batch row, InstDev::row)
+void launch_decision(const int32_t* rho, const double* delta, const ClassView& cv, int k,
+                     int32_t* top, double* gamma, int rho_bins, int delta_bins, double delta_lo,
+                     unsigned long long* hist, cudaStream_t st);
+int decision_max_topk();
+// padding of every top-k row (-1, NaN) and zero histograms for n_inst rows
+void launch_decision_init(int n_inst, int k, int32_t* top, double* gamma, int rho_bins,
+                          int delta_bins, unsigned long long* hist, cudaStream_t st);
+
 // ---- labels (labels.cu) -------------------------------------------------------------
 int label_rounds(uint32_t n);
 // Labels of every point of the class for one cutoff (arrays indexed by output

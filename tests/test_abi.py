@@ -81,6 +81,18 @@ def test_argument_errors_are_host_side(lib):
     assert lib.dpc_dependent(p, 1, b.ptr, 1, p, 0, p, p, 1, None) == dpc.DPC_ERR_ARG  # cutoff index
     assert lib.dpc_cluster(b.ptr, 0, None, p, p, p, p, 0, None) == dpc.DPC_ERR_ARG    # no params
     assert lib.dpc_get_stats(None, None) == dpc.DPC_ERR_ARG
+    dg = lib.dpc_decision_graph
+    assert dg(None, p, p, 4, p, p, 0, 0, 1.0, None, 0, None) == dpc.DPC_ERR_ARG
+    assert dg(b.ptr, p, p, -1, p, p, 0, 0, 1.0, None, 0, None) == dpc.DPC_ERR_ARG     # k < 0
+    assert dg(b.ptr, p, p, 1025, p, p, 0, 0, 1.0, None, 0, None) == dpc.DPC_ERR_ARG   # k > 1024
+    assert dg(b.ptr, p, p, 4, None, p, 0, 0, 1.0, None, 0, None) == dpc.DPC_ERR_ARG  # no top
+    assert dg(b.ptr, p, p, 0, None, None, 4, 0, 1.0, p, 0, None) == dpc.DPC_ERR_ARG  # one bin count 0
+    assert dg(b.ptr, p, p, 0, None, None, 33, 4, 1.0, p, 0, None) == dpc.DPC_ERR_ARG  # rho bins > 32
+    assert dg(b.ptr, p, p, 0, None, None, 4, 4, 0.0, p, 0, None) == dpc.DPC_ERR_ARG   # delta_lo 0
+    assert dg(b.ptr, p, p, 0, None, None, 4, 4, math.inf, p, 0, None) == dpc.DPC_ERR_ARG
+    assert dg(b.ptr, p, p, 0, None, None, 4, 4, 1.0, None, 0, None) == dpc.DPC_ERR_ARG  # no hist
+    assert dg(b.ptr, None, p, 4, p, p, 0, 0, 1.0, None, 0, None) == dpc.DPC_ERR_ARG  # no rho
+    assert dg(b.ptr, p, p, 4, p, p, 0, 0, 1.0, None, 1 << 10, None) == dpc.DPC_ERR_ARG  # flag
 
 
 def test_no_device_is_an_error_not_a_fallback(lib):
