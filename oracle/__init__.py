@@ -232,6 +232,36 @@ def decision_graph(rho, delta, k: int, rho_bins: int = 0, delta_bins: int = 0, d
     return out
 
 
+# planted deviations of priority_range, used only by the pin tests
+PR_GE = 1          # rho >= rho_q instead of rho > rho_q
+PR_OPEN_BOX = 2    # lo < x < hi instead of lo <= x <= hi
+PR_DROP_LAST = 4   # the last coordinate not tested
+
+
+def priority_range(pts, rho, lo, hi, rho_q, variant: int = 0):
+    """Priority range search (the appendix on range queries): the ids of the
+    points x_i with x_i in the closed axis-parallel box [lo, hi] and priority
+    rho_i > rho_q, in ascending order.  The priority is the density.  One query
+    (lo, hi: length-d sequences); coordinates compared in binary64, where the
+    int32 and float32 inputs are exact.  Written out point by point with numpy
+    comparisons."""
+    x = np.asarray(pts).astype(np.float64)
+    if x.ndim == 1:
+        x = x.reshape(-1, 1)
+    n, d = x.shape
+    rho = np.asarray(rho, dtype=np.int64)
+    lo = np.asarray(lo, dtype=np.float64)[:d]
+    hi = np.asarray(hi, dtype=np.float64)[:d]
+    keep = rho >= rho_q if variant & PR_GE else rho > rho_q
+    dims = d - 1 if variant & PR_DROP_LAST else d
+    for a in range(dims):
+        if variant & PR_OPEN_BOX:
+            keep &= (x[:, a] > lo[a]) & (x[:, a] < hi[a])
+        else:
+            keep &= (x[:, a] >= lo[a]) & (x[:, a] <= hi[a])
+    return np.flatnonzero(keep).astype(np.int32)
+
+
 def kth_sqdist(pts, idx, k: int, nthreads: int = 0) -> np.ndarray:
     """k-th smallest squared distance from each point ``idx`` (self counted first)."""
     pts, dtype, n, d = _points(pts)
