@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="time plain calls instead of graph replays")
     ap.add_argument("--layout", default="auto", choices=["auto", "union", "segment", "tree", "tensor"],
                     help="fixed kernel layout (auto: the autotuned choice)")
+    ap.add_argument("--study", default="none", choices=["none", "scaling", "dcut"],
+                    help="scaling: time over n = 1e3..1e7 on the seed-spreader family in 2-D and 3-D; "
+                         "dcut: phase times over a d_cut sweep on c2 and c3 (one JSON line per point)")
     return ap.parse_args()
 
 
@@ -437,6 +440,92 @@ def run_ours(args, rank, world, dev):
     return res
 
 
+# ---------------------------------------------------------------------------
+# studies (not the bench line): running time against n and against d_cut
+
+
+def _study_point(dpc, torch, dev, stream, flush, w, steps, warmup, skip_noise=False):
+    """Median graph-replay time of dpc_run on workload ``w`` (one cutoff),
+    the phase times of one plain call, and the mean density."""
+    job = Job(w)
+    batch = dpc.Batch(job.pt_offset, job.dims, job.d_cut, coord_offset=job.coord_offset)
+    params = dpc.make_params(batch, job.rho_noise, job.rho_min, job.delta_min)
+    pts = torch.from_numpy(job.flat).to(dev)
+    shape = (batch.n_dcut, job.N)
+    out = {"rho": torch.empty(shape, dtype=torch.int32, device=dev),
+           "lam": torch.empty(shape, dtype=torch.int32, device=dev),
+           "delta": torch.empty(shape, dtype=torch.float64, device=dev),
+           "label": torch.empty(shape, dtype=torch.int32, device=dev)}
+    for i in range(max(3, warmup)):
+        dpc.dpc_run(pts, batch, params, stream=stream, out=out, autotune=(i == 0), skip_noise=skip_noise)
+    dpc.dpc_run(pts, batch, params, stream=stream, out=out, sync=True, graph=True, skip_noise=skip_noise)
+    times = []
+    for _ in range(steps):
+        flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dpc.dpc_run(pts, batch, params, stream=stream, out=out, graph=True, skip_noise=skip_noise)
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    dpc.dpc_run(pts, batch, params, stream=stream, out=out, sync=True, phase_times=True, skip_noise=skip_noise)
+    ph = {p: round(v[0], 5) for p, v in dpc.dpc_get_phase_times(stream).items()}
+    rho = out["rho"][0].double()
+    mean_rho = float(rho.mean()) if job.N else 0.0
+    noise = float((out["rho"][0] < int(job.rho_noise[0])).double().mean()) if job.N else 0.0
+    del pts, out
+    return job, statistics.median(times), ph, mean_rho, noise
+
+
+def run_study(args, dev):
+    import torch
+    import paper_2305_11335_gb300 as dpc
+    from paper_2305_11335_gb300 import _build
+
+    _build.build()
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    steps = max(3, args.steps)
+    if args.study == "scaling":
+        # Section 7's scalability over n (1e3..1e7), d_cut = 30, rho_min = 0,
+        # delta_min = 100, on the seed-spreader family (2-D stands in for simden)
+        for d in (2, 3):
+            ns, ms = [], []
+            for e in range(3, 8):
+                n = 10 ** e
+                job, t, ph, mean_rho, _ = _study_point(dpc, torch, dev, stream, flush, W.spreader(n, d), steps,
+                                                       args.warmup)
+                ns.append(n)
+                ms.append(t)
+                print(json.dumps({"study": "scaling", "workload": job.name, "n": n, "d": d, "ms": t,
+                                  "points_per_s": n / (t / 1e3), "mean_rho": mean_rho, "phases_ms": ph}),
+                      flush=True)
+            x, y = np.log10(ns), np.log10(ms)
+            print(json.dumps({"study": "scaling", "d": d, "summary": True,
+                              "slope_log_time_vs_log_n": float(np.polyfit(x, y, 1)[0]),
+                              "slope_n_ge_1e5": float(np.polyfit(x[2:], y[2:], 1)[0]),
+                              "paper_slope_dpc_priority": 0.94}), flush=True)
+    else:
+        # the d_cut study (the paper's appendix on d_cut): with the noise
+        # threshold fixed, sweep d_cut and split the time into density and
+        # dependent-point finding; noise points skip the dependent search
+        for name in ("c2", "c3"):
+            base = load_workload(name)
+            for f in (0.25, 0.5, 1.0, 2.0, 4.0):
+                w = W.Workload(base.name, base.pts, [base.d_cut[0] * f], base.rho_noise[:1], base.rho_min[:1],
+                               base.delta_min[:1])
+                job, t, ph, mean_rho, noise = _study_point(dpc, torch, dev, stream, flush, w, steps,
+                                                           args.warmup, skip_noise=True)
+                dep = ph["maxkey"] + ph["near"] + ph["far"]
+                print(json.dumps({"study": "dcut", "workload": base.name, "d_cut": base.d_cut[0] * f,
+                                  "d_cut_factor": f, "avg_pct_within_d_cut": 100.0 * mean_rho / job.N,
+                                  "mean_rho": mean_rho, "noise_fraction": noise, "rho_noise": int(job.rho_noise[0]),
+                                  "ms": t, "density_ms": ph["density"], "dependent_ms": dep,
+                                  "phases_ms": ph}), flush=True)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -478,6 +567,11 @@ def main():
     torch.cuda.set_device(dev)
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=dev)
+    if args.study != "none":
+        if world > 1:
+            raise SystemExit("--study runs on one GPU")
+        run_study(args, dev)
+        return
     res = run_ours(args, rank, world, dev)
     if res is not None:
         print(json.dumps(res))

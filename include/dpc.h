@@ -122,6 +122,13 @@ enum {
  * (DPC_ERR_UNSUPPORTED there).  Phase times are not recorded and autotuning is
  * not done in this mode (autotune with a call without the flag first). */
 #define DPC_FLAG_GRAPH (1u << 11)
+/* dpc_run / dpc_run_host only: skip the dependent-point search of the noise
+ * points, as Algorithm 1 queries only the points at or above the density
+ * threshold.  A point of instance i with rho < rho_noise of (i, cutoff) gets
+ * lambda = -1 and delta = NaN; it is noise, so its label is -1 either way.
+ * Every other output is unchanged: the points a non-noise point can depend on
+ * are denser than it, hence never noise. */
+#define DPC_FLAG_SKIP_NOISE (1u << 15)
 
 /* A batch of independent point sets packed back to back.  n_inst = 1 for a
  * single point set.  All arrays are HOST arrays read during the call only. */
@@ -208,6 +215,39 @@ int dpc_cluster(const dpc_batch* b, int32_t dcut_index, const dpc_params* params
 int dpc_decision_graph(const dpc_batch* b, const int32_t* rho, const double* delta, int32_t k,
                        int32_t* top, double* gamma, int32_t rho_bins, int32_t delta_bins,
                        double delta_lo, int64_t* hist, uint32_t flags, void* stream);
+
+/* Priority range search (the appendix on range queries of the priority
+ * search kd-tree): for each query, the points of one instance inside a closed
+ * axis-parallel box whose priority -- the density rho -- is above a
+ * threshold:  { i : lo[a] <= x_i[a] <= hi[a] for a < d, and rho_i > rho_q }.
+ * The search runs on the same radix tree as the dependent-point step,
+ * entering a subtree only if its largest density is above rho_q and its
+ * bounding box meets the query box.
+ *   pts, dtype, b  the points, as for dpc_density (the first cutoff of every
+ *                  instance sizes the search grid; results do not depend on it)
+ *   rho       device, int32 [N]: the priorities (normally one cutoff's rho)
+ *   n_query   number of queries (0: nothing is done)
+ *   q_inst    device, int32 [n_query]: the batch row of each query's instance
+ *   q_box     device, double [n_query][2][8]: lo[0..7] then hi[0..7]; only
+ *             the first dim[q_inst] entries of each are read; coordinates are
+ *             compared exactly (a NaN bound matches nothing)
+ *   q_rho     device, int32 [n_query]: the thresholds rho_q
+ *   count     device, int64 [n_query]: number of matching points
+ *   ids       device, int32 [n_query][max_out]: the min(count, max_out)
+ *             smallest matching instance-local ids, ascending, then -1;
+ *             max_out = 0 computes the counts only (ids unused)
+ * A q_inst outside [0, n_inst) leaves count 0 and sets the device status
+ * (DPC_ERR_DATA with DPC_FLAG_SYNC_CHECK).  With max_out > 0 the call reads
+ * the number of matches back once per dimension class, so it synchronizes
+ * `stream`; more than 2^32 - 1 matches in one class returns DPC_ERR_OVERFLOW.
+ * Flags: DPC_FLAG_SYNC_CHECK only.  The environment variable
+ * DPC_RANGE_STACK (1..2048) caps the per-warp node stack; a smaller cap sends
+ * more subtrees to the per-lane walk (for testing that path; results do not
+ * depend on it). */
+int dpc_priority_range(const void* pts, int dtype, const dpc_batch* b, const int32_t* rho,
+                       int32_t n_query, const int32_t* q_inst, const double* q_box,
+                       const int32_t* q_rho, int32_t max_out, int64_t* count, int32_t* ids,
+                       uint32_t flags, void* stream);
 
 /* The whole pipeline for every cutoff: one binning per instance, then for each
  * cutoff density, dependent points and labels.  The instances of a batch are

@@ -41,8 +41,8 @@ DPC_F32 = 1
 PREC = {"fp64": 0, "fp32": 1}
 DPC_FLAG_SYNC_CHECK = 1 << 8
 
-EXPORTS = ["dpc_density", "dpc_dependent", "dpc_cluster", "dpc_decision_graph", "dpc_run", "dpc_run_host",
-           "dpc_density_static",
+EXPORTS = ["dpc_density", "dpc_dependent", "dpc_cluster", "dpc_decision_graph", "dpc_priority_range", "dpc_run",
+           "dpc_run_host", "dpc_density_static",
            "dpc_get_stats", "dpc_get_phase_times", "dpc_last_status", "dpc_strerror", "dpc_version",
            "dpc_release"]
 DPC_STATIC_MAX_POINTS = 65536
@@ -78,6 +78,7 @@ PHASES = ["bin", "tree", "cells", "density", "maxkey", "near", "far", "labels"]
 DPC_FLAG_PHASE_TIMES = 1 << 9
 DPC_FLAG_AUTOTUNE = 1 << 10
 DPC_FLAG_GRAPH = 1 << 11
+DPC_FLAG_SKIP_NOISE = 1 << 15
 
 
 def DPC_FLAG_RADIUS(r: int) -> int:
@@ -114,6 +115,7 @@ def load(path: str = LIB_PATH):
     lib.dpc_dependent.argtypes = [vp, ctypes.c_int, bp, i32, vp, i32, vp, vp, u32, vp]
     lib.dpc_cluster.argtypes = [bp, i32, pp, vp, vp, vp, vp, u32, vp]
     lib.dpc_decision_graph.argtypes = [bp, vp, vp, i32, vp, vp, i32, i32, ctypes.c_double, vp, u32, vp]
+    lib.dpc_priority_range.argtypes = [vp, ctypes.c_int, bp, vp, i32, vp, vp, vp, i32, vp, vp, u32, vp]
     lib.dpc_run.argtypes = [vp, ctypes.c_int, bp, pp, vp, vp, vp, vp, u32, vp]
     lib.dpc_run_host.argtypes = [vp, ctypes.c_int, bp, pp, vp, vp, vp, vp, u32, vp]
     lib.dpc_density_static.argtypes = [vp, ctypes.c_int, ctypes.c_int64, i32, ctypes.c_double, vp, u32, vp]
@@ -306,9 +308,49 @@ def dpc_decision_graph(batch: Batch, rho: torch.Tensor, delta: torch.Tensor, k: 
     return out
 
 
+def range_boxes(lo, hi, device="cuda") -> torch.Tensor:
+    """Query boxes [n, 2, 8] (float64) from lo, hi of shape [n, d] (d <= 8)."""
+    lo = torch.as_tensor(lo, dtype=torch.float64)
+    hi = torch.as_tensor(hi, dtype=torch.float64)
+    if lo.dim() == 1:
+        lo, hi = lo.reshape(-1, 1), hi.reshape(-1, 1)
+    box = torch.zeros((lo.shape[0], 2, 8), dtype=torch.float64)
+    box[:, 0, :lo.shape[1]] = lo
+    box[:, 1, :hi.shape[1]] = hi
+    return box.to(device)
+
+
+def dpc_priority_range(pts: torch.Tensor, batch: Batch, rho: torch.Tensor, q_inst: torch.Tensor,
+                       q_box: torch.Tensor, q_rho: torch.Tensor, max_out: int = 0, sync: bool = False,
+                       stream=None) -> dict:
+    """Priority range search: per query (instance q_inst, closed box q_box
+    [n, 2, 8], threshold q_rho), "count" (int64 [n]) of the instance's points
+    in the box with rho > q_rho and "ids" (int32 [n, max_out]): the smallest
+    matching instance-local ids, ascending, padded with -1."""
+    lib = load()
+    if q_inst.dtype != torch.int32 or q_rho.dtype != torch.int32 or q_box.dtype != torch.float64:
+        raise ValueError("q_inst and q_rho must be int32, q_box float64")
+    nq = int(q_inst.numel())
+    if tuple(q_box.shape) != (nq, 2, 8) or q_rho.numel() != nq:
+        raise ValueError("q_box must be [n_query, 2, 8] and q_rho [n_query]")
+    dev = rho.device
+    count = torch.empty(nq, dtype=torch.int64, device=dev)
+    ids = torch.empty((nq, max_out), dtype=torch.int32, device=dev) if max_out > 0 else None
+    if nq:
+        _check(lib.dpc_priority_range(_dev(pts, "pts"), _dtype_code(pts), batch.ptr, _dev(rho, "rho"), nq,
+                                      _dev(q_inst, "q_inst"), _dev(q_box, "q_box"), _dev(q_rho, "q_rho"),
+                                      int(max_out), _dev(count, "count"),
+                                      _dev(ids, "ids") if ids is not None else None,
+                                      DPC_FLAG_SYNC_CHECK if sync else 0, _stream(stream)), "dpc_priority_range")
+    out = {"count": count}
+    if ids is not None:
+        out["ids"] = ids
+    return out
+
+
 def dpc_run(pts: torch.Tensor, batch: Batch, params, precision: str = "fp32", sync: bool = False, stream=None,
             out: dict | None = None, phase_times: bool = False, autotune: bool = False,
-            radius: int = 0, graph: bool = False, layout: str = "auto") -> dict:
+            radius: int = 0, graph: bool = False, layout: str = "auto", skip_noise: bool = False) -> dict:
     lib = load()
     shape = (batch.n_dcut, batch.N)
     if out is None:
@@ -319,13 +361,14 @@ def dpc_run(pts: torch.Tensor, batch: Batch, params, precision: str = "fp32", sy
     _check(lib.dpc_run(_dev(pts, "pts"), _dtype_code(pts), batch.ptr, params, _dev(out["rho"], "rho"),
                        _dev(out["lam"], "lambda"), _dev(out["delta"], "delta"), _dev(out["label"], "label"),
                        _flags(precision, sync, radius, autotune, layout) | (DPC_FLAG_PHASE_TIMES if phase_times else 0)
-                       | (DPC_FLAG_GRAPH if graph else 0), _stream(stream)),
+                       | (DPC_FLAG_GRAPH if graph else 0) | (DPC_FLAG_SKIP_NOISE if skip_noise else 0),
+                       _stream(stream)),
            "dpc_run")
     return out
 
 
 def dpc_run_host(pts: torch.Tensor, batch: Batch, params, precision: str = "fp32", stream=None,
-                 out: dict | None = None) -> dict:
+                 out: dict | None = None, skip_noise: bool = False) -> dict:
     """Host-buffer form: `pts` and the results are CPU tensors (pin them for
     faster copies); the call returns after the results are on the host."""
     lib = load()
@@ -339,7 +382,8 @@ def dpc_run_host(pts: torch.Tensor, batch: Batch, params, precision: str = "fp32
     def hp(t):
         return ctypes.c_void_p(t.data_ptr())
     _check(lib.dpc_run_host(hp(pts), _dtype_code(pts), batch.ptr, params, hp(out["rho"]), hp(out["lam"]),
-                            hp(out["delta"]), hp(out["label"]), _flags(precision, True), _stream(stream)),
+                            hp(out["delta"]), hp(out["label"]),
+                            _flags(precision, True) | (DPC_FLAG_SKIP_NOISE if skip_noise else 0), _stream(stream)),
            "dpc_run_host")
     return out
 
@@ -382,7 +426,8 @@ def dpc_last_status(stream=None) -> int:
 
 
 def run(pts: torch.Tensor, d_cut, rho_noise, rho_min, delta_min, precision: str = "fp32", sync: bool = True,
-        stream=None, autotune: bool = False, radius: int = 0, layout: str = "auto") -> dict:
+        stream=None, autotune: bool = False, radius: int = 0, layout: str = "auto",
+        skip_noise: bool = False) -> dict:
     """DPC of one point set ``pts`` [n, d] (CUDA, int32/float32) for one or more cutoffs."""
     if pts.dim() == 1:
         pts = pts.reshape(-1, 1)
@@ -391,5 +436,5 @@ def run(pts: torch.Tensor, d_cut, rho_noise, rho_min, delta_min, precision: str 
     batch = Batch.single(n, d, cuts)
     params = make_params(batch, rho_noise, rho_min, delta_min)
     return dpc_run(pts.contiguous(), batch, params, precision=precision, sync=sync, stream=stream,
-                   autotune=autotune, radius=radius, layout=layout)
+                   autotune=autotune, radius=radius, layout=layout, skip_noise=skip_noise)
 

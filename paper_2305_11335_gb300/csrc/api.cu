@@ -88,7 +88,7 @@ int check_batch(const dpc_batch* b, std::vector<Inst>* insts, uint64_t* total) {
 
 constexpr uint32_t kKnownFlags = DPC_PREC_MASK | DPC_FLAG_SYNC_CHECK | DPC_FLAG_PHASE_TIMES |
                                  DPC_FLAG_AUTOTUNE | DPC_FLAG_RADIUS_MASK | DPC_FLAG_GRAPH |
-                                 DPC_FLAG_LAYOUT_MASK;
+                                 DPC_FLAG_LAYOUT_MASK | DPC_FLAG_SKIP_NOISE;
 
 int check_flags(uint32_t flags) {
   const uint32_t prec = flags & DPC_PREC_MASK;
@@ -101,7 +101,7 @@ int check_flags(uint32_t flags) {
 
 int status_to_code(int s) {
   if (s == 0) return DPC_OK;
-  if (s & (kStatusBadCoord | kStatusCycle)) return DPC_ERR_DATA;
+  if (s & (kStatusBadCoord | kStatusCycle | kStatusQuery)) return DPC_ERR_DATA;
   if (s & kStatusStack) return DPC_ERR_UNSUPPORTED;
   if (s & kStatusTimeout) return DPC_ERR_TIMEOUT;
   return DPC_ERR_CUDA;
@@ -213,6 +213,12 @@ struct Workspace {
   void* io = nullptr;
   size_t io_bytes = 0;
 
+  // priority range search: per-query arrays (scr) and the match keys (scr2)
+  void* scr = nullptr;
+  size_t scr_bytes = 0;
+  void* scr2 = nullptr;
+  size_t scr2_bytes = 0;
+
   // the captured graph of DPC_FLAG_GRAPH calls and the key it was captured for
   cudaGraphExec_t gexec = nullptr;
   std::string gkey;
@@ -269,6 +275,10 @@ struct Workspace {
     recs.clear();
     if (base) cudaFree(base);
     if (io) cudaFree(io);
+    if (scr) cudaFree(scr);
+    if (scr2) cudaFree(scr2);
+    scr = scr2 = nullptr;
+    scr_bytes = scr2_bytes = 0;
     if (up_dev) cudaFree(up_dev);
     if (up_host) cudaFreeHost(up_host);
     if (up_done) cudaEventDestroy(up_done);
@@ -415,6 +425,24 @@ struct Workspace {
     return DPC_OK;
   }
 
+  // grow-only device scratch (contents not kept across growth)
+  int reserve_buf(void** p, size_t* have, size_t b) {
+    if (b <= *have && *p) return DPC_OK;
+    if (*p) {
+      cudaStreamSynchronize(stream);
+      cudaFree(*p);
+      *p = nullptr;
+    }
+    if (cudaMalloc(p, b) != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      *have = 0;
+      return DPC_ERR_OOM;
+    }
+    *have = b;
+    return DPC_OK;
+  }
+
   int reserve_io(size_t b) {
     if (b <= io_bytes && io) return DPC_OK;
     if (io) {
@@ -508,6 +536,8 @@ struct CallPlan {
   int ncut = 1;       // cutoffs this call uses
   uint32_t max_inst = 0;
   uint64_t max_n = 0;
+  const dpc_params* params = nullptr;  // thresholds of the call (dpc_run, dpc_cluster)
+  bool skip_noise = false;             // DPC_FLAG_SKIP_NOISE
 };
 
 CallPlan make_plan(const dpc_batch* b, const std::vector<Inst>& insts, int cut_first, int ncut,
@@ -523,6 +553,14 @@ CallPlan make_plan(const dpc_batch* b, const std::vector<Inst>& insts, int cut_f
     P.max_n = std::max<uint64_t>(P.max_n, c.N);
   }
   return P;
+}
+
+// The cutoff constants of (instance bi, cutoff cut); with DPC_FLAG_SKIP_NOISE
+// the dependent search skips that pair's noise points.
+CutHost cut_host(const CallPlan& P, const dpc_batch* b, int bi, int cut, int dp) {
+  CutHost h = make_cut_host(b->d_cut[(size_t)bi * P.ncut_all + cut], dp);
+  if (P.skip_noise && P.params) h.skip = P.params[(size_t)bi * P.ncut_all + cut].rho_noise;
+  return h;
 }
 
 // Fills and copies the tables of every multi-instance class (instance
@@ -566,7 +604,7 @@ int upload_tables(Workspace* w, CallPlan& P, const dpc_batch* b, const std::vect
       chunk += (uint32_t)((in.n + 31) / 32);
       for (int k = 0; k < P.ncut; ++k) {
         const int cut = P.cut_first + k;
-        ch[j * P.ncut + k] = make_cut_host(b->d_cut[(size_t)bi * P.ncut_all + cut], c.dp);
+        ch[j * P.ncut + k] = cut_host(P, b, bi, cut, c.dp);
         LabelParams L{0, 0, 0.0};
         if (params) {
           const dpc_params& q = params[(size_t)bi * P.ncut_all + cut];
@@ -626,7 +664,7 @@ void bin_class(Workspace* w, const void* pts, int dtype, const CallPlan& P, cons
   if (!c.uploaded()) {
     const int bi = c.members[0];
     for (int k = 0; k < P.ncut && k < kCutChunk; ++k)
-      hc.push_back(make_cut_host(b->d_cut[(size_t)bi * P.ncut_all + P.cut_first + k], c.dp));
+      hc.push_back(cut_host(P, b, bi, P.cut_first + k, c.dp));
   }
   launch_setup(cv, w->cuts, P.ncut, cut_table(w, c), hc.data(), st);
   launch_codes(pts, dtype, cv, c.g, w->codes_a, w->ids_a, st);
@@ -867,6 +905,8 @@ void reset_call(Workspace* w, uint32_t flags) {
 int prepare(Workspace* w, CallPlan& P, const dpc_batch* b, const std::vector<Inst>& insts,
             const dpc_params* params, uint32_t flags) {
   sort_init();
+  P.params = params;
+  P.skip_noise = (flags & DPC_FLAG_SKIP_NOISE) != 0;
   int rc = w->reserve(P.max_n, P.max_inst, P.ncut);
   if (rc) return rc;
   reset_call(w, flags);
@@ -903,6 +943,7 @@ int dpc_density(const void* pts, int dtype, const dpc_batch* b, int32_t* rho, ui
   int rc = check_batch(b, &insts, &N);
   if (rc) return rc;
   if ((rc = check_flags(flags))) return rc;
+  if (flags & DPC_FLAG_SKIP_NOISE) return DPC_ERR_ARG;  // no thresholds here
   if (dtype != DPC_I32 && dtype != DPC_F32) return DPC_ERR_ARG;
   if (N > 0 && (!pts || !rho)) return DPC_ERR_ARG;
   Workspace* w = nullptr;
@@ -932,6 +973,7 @@ int dpc_dependent(const void* pts, int dtype, const dpc_batch* b, int32_t dcut_i
   int rc = check_batch(b, &insts, &N);
   if (rc) return rc;
   if ((rc = check_flags(flags))) return rc;
+  if (flags & DPC_FLAG_SKIP_NOISE) return DPC_ERR_ARG;  // rho_skip is the argument here
   if (dtype != DPC_I32 && dtype != DPC_F32) return DPC_ERR_ARG;
   if (dcut_index < 0 || dcut_index >= b->n_dcut) return DPC_ERR_ARG;
   if (N > 0 && (!pts || !rho || !lambda || !delta)) return DPC_ERR_ARG;
@@ -1034,6 +1076,112 @@ int dpc_decision_graph(const dpc_batch* b, const int32_t* rho, const double* del
     launch_chunks(cv, w->chunk_inst, w->chunk_pos, w->stream);
     launch_decision(rho, delta, cv, k, top, gamma, rho_bins, delta_bins, delta_lo,
                     (unsigned long long*)hist, w->stream);
+  }
+  return finish(w, flags);
+}
+
+int dpc_priority_range(const void* pts, int dtype, const dpc_batch* b, const int32_t* rho,
+                       int32_t n_query, const int32_t* q_inst, const double* q_box,
+                       const int32_t* q_rho, int32_t max_out, int64_t* count, int32_t* ids,
+                       uint32_t flags, void* stream) {
+  std::vector<Inst> insts;
+  uint64_t N = 0;
+  int rc = check_batch(b, &insts, &N);
+  if (rc) return rc;
+  if (flags & ~(DPC_FLAG_SYNC_CHECK)) return DPC_ERR_ARG;
+  if (dtype != DPC_I32 && dtype != DPC_F32) return DPC_ERR_ARG;
+  if (n_query < 0 || max_out < 0) return DPC_ERR_ARG;
+  if (n_query == 0) return DPC_OK;
+  if (!q_inst || !q_box || !q_rho || !count || (max_out > 0 && !ids)) return DPC_ERR_ARG;
+  if (N > 0 && (!pts || !rho)) return DPC_ERR_ARG;
+  Workspace* w = nullptr;
+  if ((rc = get_workspace((cudaStream_t)stream, &w))) return rc;
+  std::lock_guard<std::mutex> lk(g_mu);
+  // classes by dimension; the first cutoff of every instance sizes its grid
+  // (the tree does not depend on it)
+  CallPlan P = make_plan(b, insts, 0, 1, false);
+  if ((rc = prepare(w, P, b, insts, nullptr, flags))) return rc;
+  cudaStream_t st = w->stream;
+  const uint32_t nq = (uint32_t)n_query;
+  const size_t o_cnt = 0;
+  const size_t o_off = align_up(sizeof(uint32_t) * nq);
+  const size_t o_map = o_off + align_up(sizeof(unsigned long long) * (nq + 1));
+  const size_t bytes = o_map + align_up(sizeof(int32_t) * (size_t)b->n_inst);
+  if ((rc = w->reserve_buf(&w->scr, &w->scr_bytes, bytes))) return rc;
+  uint32_t* cnt = (uint32_t*)((char*)w->scr + o_cnt);
+  unsigned long long* off = (unsigned long long*)((char*)w->scr + o_off);
+  int32_t* rowmap = (int32_t*)((char*)w->scr + o_map);
+  PrangeArgs a;
+  a.nq = nq;
+  a.n_inst = b->n_inst;
+  a.q_inst = q_inst;
+  a.q_box = q_box;
+  a.q_rho = q_rho;
+  a.rowmap = nullptr;
+  a.one_row = -1;
+  a.count = (long long*)count;
+  a.stack_cap = 0;
+  if (const char* e = std::getenv("DPC_RANGE_STACK")) a.stack_cap = std::atoi(e);
+  launch_prange_init(a, ids, max_out, w->status, st);
+  std::vector<int32_t> map_host((size_t)b->n_inst);
+  for (const ClassPlan& c : P.classes) {
+    const ClassView cv = view_of(w, c, insts);
+    bin_class(w, pts, dtype, P, c, cv, b, insts);
+    tree_step(w, cv);
+    launch_keys_from_rho(rho, w->sid, cv.N, w->skey, st);
+    launch_tree_maxkey(w->skey, w->spts, c.dp, cv.N, w->nodes, w->leaf_parent, w->visit, w->nbox,
+                       true, st);
+    w->boxes_ready = true;
+    if (c.uploaded()) {
+      std::fill(map_host.begin(), map_host.end(), -1);
+      for (size_t j = 0; j < c.members.size(); ++j) map_host[c.members[j]] = (int32_t)j;
+      // pageable source: staged before the call returns
+      cudaMemcpyAsync(rowmap, map_host.data(), sizeof(int32_t) * map_host.size(),
+                      cudaMemcpyHostToDevice, st);
+      a.rowmap = rowmap;
+      a.one_row = -1;
+    } else {
+      a.rowmap = nullptr;
+      a.one_row = c.members[0];
+    }
+    launch_prange(c.dp, false, w->spts, w->sid, w->skey, cv, w->nodes, w->nbox, w->roots, a, cnt,
+                  nullptr, nullptr, w->status, st);
+    if (max_out == 0) continue;
+    launch_prange_scan(cnt, nq, off, st);
+    unsigned long long total = 0;
+    if (cudaMemcpyAsync(&total, off + nq, sizeof(total), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      cudaGetLastError();
+      return DPC_ERR_CUDA;
+    }
+    if (total == 0) continue;
+    if (total >= (1ull << 32)) return DPC_ERR_OVERFLOW;
+    const uint32_t tn = (uint32_t)total;
+    const size_t k_a = 0;
+    const size_t k_b = align_up(sizeof(unsigned long long) * tn);
+    const size_t v_a = 2 * k_b;
+    const size_t v_b = v_a + align_up(sizeof(uint32_t) * tn);
+    const size_t h_o = v_b + align_up(sizeof(uint32_t) * tn);
+    const size_t need = h_o + align_up(sizeof(uint32_t) * sort_hist_words(tn));
+    if ((rc = w->reserve_buf(&w->scr2, &w->scr2_bytes, need))) return rc;
+    char* s2 = (char*)w->scr2;
+    unsigned long long* keys_a = (unsigned long long*)(s2 + k_a);
+    unsigned long long* keys_b = (unsigned long long*)(s2 + k_b);
+    launch_prange(c.dp, true, w->spts, w->sid, w->skey, cv, w->nodes, w->nbox, w->roots, a, cnt, off,
+                  keys_a, w->status, st);
+    // sort the keys (query << 31 | id): 31 id bits under ib query bits
+    int ib = 0;
+    while (ib < 32 && (1ull << ib) < nq) ++ib;
+    ClassGeom g;
+    std::memset(&g, 0, sizeof(g));
+    g.S = 31;
+    g.ib = ib;
+    g.status = w->status;
+    cudaMemcpyAsync(w->cls, &g, sizeof(g), cudaMemcpyHostToDevice, st);
+    launch_sort(keys_a, keys_b, (uint32_t*)(s2 + v_a), (uint32_t*)(s2 + v_b), tn, w->cls,
+                (uint32_t*)(s2 + h_o), st);
+    const int passes = sort_passes(31, ib);
+    launch_prange_scatter((passes & 1) ? keys_b : keys_a, total, off, nq, max_out, ids, w->status, st);
   }
   return finish(w, flags);
 }

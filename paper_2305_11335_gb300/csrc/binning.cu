@@ -228,6 +228,7 @@ __global__ void k_setup_cuts(ClassView cv, CutGeom* cuts, int ncut, const CutHos
   C.t_out = H.t_out;
   C.band_mul = H.band_mul;
   C.band_add = H.band_add;
+  C.skip = H.skip;
   choose_level(C, cv.geom + i, 0);
 }
 
@@ -440,6 +441,8 @@ CutHost make_cut_host(double d_cut, int dp) {
   double rho_band = (1.0 + g32) * (1.0 + g64) / ((1.0 - g32) * (1.0 - g64)) * (1.0 + safety);
   h.band_mul = round_up_f(rho_band);
   h.band_add = round_up_f(eta * (rho_band + 1.0) * (1.0 + safety));
+  h.skip = 0;
+  h.pad = 0;
   return h;
 }
 

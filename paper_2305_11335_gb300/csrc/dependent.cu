@@ -220,7 +220,7 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
     const unsigned long long mycell = valid ? (key_code(scode[p], S, ib) >> shift) : ~0ull;
     uint32_t c0[G];
     unmorton<G>(valid ? mycell : 0ull, c0);
-    const bool skip = valid && (int32_t)(K >> 32) < rho_skip;
+    const bool skip = valid && (int32_t)(K >> 32) < max(rho_skip, C.skip);
     const int nvalid = (int)min(32u, end - p0);
     Min2 acc;
     acc.init();
@@ -400,7 +400,7 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
     unsigned long long K = ~0ull;
     if (valid) K = skey[p];
     const unsigned long long mycell = valid ? (key_code(scode[p], S, ib) >> shift) : ~0ull;
-    const bool skip = valid && (int32_t)(K >> 32) < rho_skip;
+    const bool skip = valid && (int32_t)(K >> 32) < max(rho_skip, C.skip);
     const int nvalid = (int)min(32u, end - p0);
     // this lane's query in fine units, for the cell lower bounds of pass 2
     const GridGeom* geom = cv.geom + inst;
@@ -584,16 +584,23 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
 // ones) goes to the tree search with no bound.  Pays off where blocks are
 // dense enough that a best-first search of the tree, pruned by maximum key and
 // by box distance, visits far fewer points than the block holds.
-__global__ void k_near_to_far(const unsigned long long* __restrict__ skey, uint32_t n,
-                              int32_t rho_skip, int32_t* __restrict__ lambda,
-                              double* __restrict__ delta, FarQueue q, Counters* ctr) {
+// One warp per 32-point chunk (the chunk gives the instance, hence its skip
+// threshold).
+__global__ void k_near_to_far(const unsigned long long* __restrict__ skey, ClassView cv,
+                              const CutGeom* __restrict__ cuts, int32_t rho_skip,
+                              int32_t* __restrict__ lambda, double* __restrict__ delta, FarQueue q,
+                              Counters* ctr) {
   const int lane = threadIdx.x & 31;
   const uint32_t lanemask_lt = (1u << lane) - 1u;
-  const uint32_t n_pad = (n + 31) & ~31u;
-  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n_pad; p += gridDim.x * blockDim.x) {
-    const bool valid = p < n;
+  const uint64_t total = (uint64_t)cv.nchunk * 32u;
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < total;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t inst, p0, end;
+    cv.chunk((uint32_t)(e >> 5), inst, p0, end);
+    const uint32_t p = p0 + lane;
+    const bool valid = p < end;
     const unsigned long long K = valid ? skey[p] : 0ull;
-    const bool skip = valid && (int32_t)(K >> 32) < rho_skip;
+    const bool skip = valid && (int32_t)(K >> 32) < max(rho_skip, cuts[inst].skip);
     if (skip) {
       const uint32_t id = key_id(K);
       lambda[id] = -1;
@@ -1106,8 +1113,8 @@ void launch_dep_near(int dp, int g, bool fp64, int layout, const float* spts,
   cudaMemsetAsync(&ctr->queue_n, 0, sizeof(unsigned int), st);
   cudaMemsetAsync(&ctr->queue2_n, 0, sizeof(unsigned int), st);
   if (layout == kLayoutTree) {
-    k_near_to_far<<<grid_for(cv.N, 256, 152u * 16u), 256, 0, st>>>(skey, cv.N, rho_skip, lambda,
-                                                                     delta, q, ctr);
+    k_near_to_far<<<grid_for((uint64_t)cv.nchunk * 32u, 256, 152u * 16u), 256, 0, st>>>(
+        skey, cv, cuts, rho_skip, lambda, delta, q, ctr);
   } else if (g == 1) near_dg<2, 1>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
   else if (g == 2) near_dg<2, 2>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
   else if (g == 3) near_dg<4, 3>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);

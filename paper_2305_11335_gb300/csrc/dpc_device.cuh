@@ -49,7 +49,8 @@ enum : int {
   kStatusStack = 4,      // tree traversal stack overflow
   kStatusCycle = 8,      // dependent pointers did not converge to roots
   kStatusIndex = 16,     // an internal index failed its bounds check (a bug)
-  kStatusTimeout = 32    // a bounded wait for the tensor core gave up
+  kStatusTimeout = 32,   // a bounded wait for the tensor core gave up
+  kStatusQuery = 64      // a query names an instance outside the batch
 };
 
 // Per-instance grid geometry, written by the setup kernel from the bounding box.
@@ -160,6 +161,8 @@ struct CutGeom {
   double far64;       //   settled by the (2R+1)^g block (float / double forms)
   uint32_t m;         // occupied level-k cells
   uint32_t hmask;     // hash table size - 1
+  int32_t skip;       // dependent: points with rho < skip are skipped   [host]
+  int32_t pad;
 };
 
 // Counters for dpc_get_stats.

@@ -20,6 +20,8 @@ inline void count_launches(int k) { g_kernel_launches += k; }
 struct CutHost {
   double dc, dc2;
   float t_in, t_out, band_mul, band_add;
+  int32_t skip;  // dependent search: points with rho < skip are skipped
+  int32_t pad;
 };
 CutHost make_cut_host(double d_cut, int dp);
 
@@ -135,6 +137,33 @@ void launch_dep_far(int dp, bool fp64, const float* spts, const unsigned long lo
 void launch_decision(const int32_t* rho, const double* delta, const ClassView& cv, int k,
                      int32_t* top, double* gamma, int rho_bins, int delta_bins, double delta_lo,
                      unsigned long long* hist, cudaStream_t st);
+// ---- priority range search (range.cu) -------------------------------------------
+struct PrangeArgs {
+  uint32_t nq;              // queries
+  int32_t n_inst;           // instances of the batch
+  const int32_t* q_inst;    // [nq] batch row of each query (device)
+  const double* q_box;      // [nq][2][kMaxDim] lo then hi (device)
+  const int32_t* q_rho;     // [nq] thresholds (device)
+  const int32_t* rowmap;    // [n_inst] class-local index or -1; null: one_row only
+  int32_t one_row;          // the batch row of a single-instance class
+  long long* count;         // [nq] matches (device output)
+  int stack_cap;            // shared stack entries per warp (0: all); smaller
+                            //   values send more subtrees to the per-lane walk
+};
+void launch_prange_init(const PrangeArgs& a, int32_t* ids, int max_out, int* status,
+                        cudaStream_t st);
+// one class: count (fill = false: cnt[q] for the class's queries, 0 for the
+// others, and count[q]) or fill (keys (q << 31 | id) at off[q]..)
+void launch_prange(int dp, bool fill, const float* spts, const uint32_t* sid,
+                   const unsigned long long* skey, const ClassView& cv, const Node* nodes,
+                   const float* nbox, const uint32_t* roots, const PrangeArgs& a, uint32_t* cnt,
+                   const unsigned long long* off, unsigned long long* keys, int* status,
+                   cudaStream_t st);
+void launch_prange_scan(const uint32_t* cnt, uint32_t nq, unsigned long long* off, cudaStream_t st);
+void launch_prange_scatter(const unsigned long long* keys, uint64_t total,
+                           const unsigned long long* off, uint32_t nq, int max_out, int32_t* ids,
+                           int* status, cudaStream_t st);
+
 int decision_max_topk();
 // padding of every top-k row (-1, NaN) and zero histograms for n_inst rows
 void launch_decision_init(int n_inst, int k, int32_t* top, double* gamma, int rho_bins,

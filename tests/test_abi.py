@@ -80,6 +80,9 @@ def test_argument_errors_are_host_side(lib):
     p = ctypes.c_void_p(1)
     assert lib.dpc_dependent(p, 1, b.ptr, 1, p, 0, p, p, 1, None) == dpc.DPC_ERR_ARG  # cutoff index
     assert lib.dpc_cluster(b.ptr, 0, None, p, p, p, p, 0, None) == dpc.DPC_ERR_ARG    # no params
+    skip = 1 | dpc.DPC_FLAG_SKIP_NOISE  # dpc_run only
+    assert lib.dpc_density(p, 1, b.ptr, p, skip, None) == dpc.DPC_ERR_ARG
+    assert lib.dpc_dependent(p, 1, b.ptr, 0, p, 0, p, p, skip, None) == dpc.DPC_ERR_ARG
     assert lib.dpc_get_stats(None, None) == dpc.DPC_ERR_ARG
     dg = lib.dpc_decision_graph
     assert dg(None, p, p, 4, p, p, 0, 0, 1.0, None, 0, None) == dpc.DPC_ERR_ARG
@@ -93,6 +96,16 @@ def test_argument_errors_are_host_side(lib):
     assert dg(b.ptr, p, p, 0, None, None, 4, 4, 1.0, None, 0, None) == dpc.DPC_ERR_ARG  # no hist
     assert dg(b.ptr, None, p, 4, p, p, 0, 0, 1.0, None, 0, None) == dpc.DPC_ERR_ARG  # no rho
     assert dg(b.ptr, p, p, 4, p, p, 0, 0, 1.0, None, 1 << 10, None) == dpc.DPC_ERR_ARG  # flag
+    pr = lib.dpc_priority_range
+    assert pr(p, 1, None, p, 1, p, p, p, 0, p, None, 0, None) == dpc.DPC_ERR_ARG      # no batch
+    assert pr(p, 7, b.ptr, p, 1, p, p, p, 0, p, None, 0, None) == dpc.DPC_ERR_ARG     # dtype
+    assert pr(p, 1, b.ptr, p, -1, p, p, p, 0, p, None, 0, None) == dpc.DPC_ERR_ARG    # n_query < 0
+    assert pr(p, 1, b.ptr, p, 1, p, p, p, -1, p, None, 0, None) == dpc.DPC_ERR_ARG    # max_out < 0
+    assert pr(p, 1, b.ptr, p, 1, None, p, p, 0, p, None, 0, None) == dpc.DPC_ERR_ARG  # no q_inst
+    assert pr(p, 1, b.ptr, p, 1, p, p, p, 4, p, None, 0, None) == dpc.DPC_ERR_ARG     # no ids
+    assert pr(p, 1, b.ptr, p, 1, p, p, p, 0, None, None, 0, None) == dpc.DPC_ERR_ARG  # no count
+    assert pr(p, 1, b.ptr, p, 1, p, p, p, 0, p, None, 1 << 15, None) == dpc.DPC_ERR_ARG  # flag
+    assert pr(p, 1, b.ptr, p, 0, None, None, None, 0, None, None, 0, None) == dpc.DPC_OK  # no queries
 
 
 def test_no_device_is_an_error_not_a_fallback(lib):

@@ -47,19 +47,25 @@ def thresholds(n_inst, seed):
     return rn, rm, dm
 
 
-def check_run(sizes, dims, insts, cuts, dtype, precision, seed, layout="auto"):
+def check_run(sizes, dims, insts, cuts, dtype, precision, seed, layout="auto", skip_noise=False, graph=False):
     batch = dpc.Batch.packed(sizes, dims, cuts)
     flat = np.concatenate([p.reshape(-1) for p in insts]).astype(dtype)
     t = torch.from_numpy(flat).cuda()
     rn, rm, dm = thresholds(len(sizes), seed)
     params = dpc.make_params(batch, rn, rm, dm)
-    out = dpc.dpc_run(t, batch, params, precision=precision, sync=True, layout=layout)
+    if graph:
+        with torch.cuda.stream(torch.cuda.Stream()):
+            for _ in range(2):
+                out = dpc.dpc_run(t, batch, params, precision=precision, sync=True, layout=layout,
+                                  skip_noise=skip_noise, graph=True)
+    else:
+        out = dpc.dpc_run(t, batch, params, precision=precision, sync=True, layout=layout, skip_noise=skip_noise)
     out = {k: v.cpu().numpy() for k, v in out.items()}
     for i, p in enumerate(insts):
         lo, hi = batch.pt_offset[i], batch.pt_offset[i + 1]
         for c in range(NCUT):
             j = i * NCUT + c
-            ref = oracle.run(p, cuts[i][c], rn[j], rm[j], dm[j])
+            ref = oracle.run(p, cuts[i][c], rn[j], rm[j], dm[j], rho_skip=rn[j] if skip_noise else 0)
             assert_same({k: v[c, lo:hi] for k, v in out.items()}, ref,
                         "%s inst %d (n=%d d=%d) cut %d" % (precision, i, sizes[i], dims[i], c))
 
@@ -87,6 +93,26 @@ def test_batch_one_class_many_instances():
     dims = [2] * len(sizes)
     cuts = [[0.03, 0.04, 0.05] for _ in sizes]
     check_run(sizes, dims, insts, cuts, np.float32, "fp32", 13)
+
+
+@pytest.mark.parametrize("layout,graph", [("auto", False), ("tree", False), ("segment", False), ("auto", True)])
+def test_batch_skip_noise(layout, graph):
+    """Noise points skip the dependent search (lambda -1, delta NaN); every
+    instance and cutoff has its own noise threshold."""
+    sizes, dims, insts, cuts = make_batch(21, 30, [1, 2, 3, 4, 6])
+    check_run(sizes, dims, insts, cuts, np.float32, "fp32", 22, layout=layout, skip_noise=True, graph=graph)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_single_skip_noise(precision):
+    pts = W.random_blobs(20000, 2, 77)
+    cuts = [0.01, 0.02]
+    t = torch.from_numpy(pts).cuda()
+    out = dpc.run(t, cuts, 4, 6, 0.05, precision=precision, skip_noise=True)
+    for c, dc in enumerate(cuts):
+        ref = oracle.run(pts, dc, 4, 6, 0.05, rho_skip=4)
+        assert_same({k: v[c].cpu().numpy() for k, v in out.items()}, ref, "cut %d" % c)
+        assert np.isnan(ref["delta"]).sum() == (ref["rho"] < 4).sum() > 0
 
 
 def test_batch_split_entry_points():

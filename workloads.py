@@ -120,31 +120,32 @@ def c2(seed: int = 2) -> Workload:
 
 def c3_points(seed: int = 3, steps: int = 99_900, per_step: int = 100, n_noise: int = 10_000,
               box: float = 1e5, step_len: float = 50.0, radius: float = 100.0,
-              restart_p: float = 1e-4) -> tuple:
+              restart_p: float = 1e-4, d: int = 3) -> tuple:
     rng = np.random.default_rng(seed)
-    dirs = rng.standard_normal((steps, 3))
+    dirs = rng.standard_normal((steps, d))
     dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
     restart = rng.random(steps) < restart_p
-    restart_pos = rng.uniform(0.0, box, (steps, 3))
-    pos = rng.uniform(0.0, box, 3).tolist()
-    centers = np.empty((steps, 3))
+    restart_pos = rng.uniform(0.0, box, (steps, d))
+    pos = rng.uniform(0.0, box, d).tolist()
+    centers = np.empty((steps, d))
     dl = dirs.tolist()
     rl = restart.tolist()
     rp = restart_pos.tolist()
     for t in range(steps):
         dx = dl[t]
-        pos = [min(max(pos[k] + step_len * dx[k], 0.0), box) for k in range(3)]
+        pos = [min(max(pos[k] + step_len * dx[k], 0.0), box) for k in range(d)]
         centers[t] = pos
         if rl[t]:
             pos = rp[t]
     # per_step points uniform in the ball of `radius` around each walk position
     m = steps * per_step
-    u = rng.standard_normal((m, 3))
+    u = rng.standard_normal((m, d))
     u /= np.linalg.norm(u, axis=1, keepdims=True)
-    r = radius * np.cbrt(rng.random(m))
+    v = rng.random(m)
+    r = radius * (np.cbrt(v) if d == 3 else v ** (1.0 / d))
     cloud = np.repeat(centers, per_step, axis=0) + u * r[:, None]
     del u, r
-    noise = rng.uniform(0.0, box, (n_noise, 3))
+    noise = rng.uniform(0.0, box, (n_noise, d))
     pts, noise_ids = _shuffle(rng, np.concatenate([cloud, noise]), n_noise)
     return pts.astype(np.float32), noise_ids
 
@@ -154,6 +155,20 @@ def c3(seed: int = 3) -> Workload:
     p = load_params().get("c3", {})
     rmin = p.get("rho_min", 0)
     return Workload("c3_seedspreader_f32_n1e7_d3", pts, [30.0], [rmin], [rmin], [1000.0], noise_ids)
+
+
+def spreader(n: int, d: int, seed: int = 3) -> Workload:
+    """The seed-spreader family at any size: the walk of ``c3_points`` in d
+    dimensions with 100 points per step and about 0.1% uniform noise in the
+    [0, 1e5]^d box, with the paper's synthetic hyper-parameters (d_cut = 30,
+    rho_min = 0, delta_min = 100).  n = 1e7, d = 3 is exactly ``c3``'s point
+    set; d = 2 stands in for simden."""
+    steps = max(1, int(round(0.999 * n / 100)))
+    n_noise = max(0, n - 100 * steps)
+    pts, noise_ids = c3_points(seed, steps=steps, per_step=100, n_noise=n_noise, d=d)
+    pts = pts[:n] if pts.shape[0] > n else pts
+    return Workload("spreader_f32_n%d_d%d" % (n, d), np.ascontiguousarray(pts), [30.0], [0], [0], [100.0],
+                    noise_ids[noise_ids < n])
 
 
 def c5_points(seed: int = 5, n_blob_pts: int = 1_960_000, n_blobs: int = 30, n_noise: int = 40_000,
