@@ -63,9 +63,10 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="time plain calls instead of graph replays")
     ap.add_argument("--layout", default="auto", choices=["auto", "union", "segment", "tree", "tensor"],
                     help="fixed kernel layout (auto: the autotuned choice)")
-    ap.add_argument("--study", default="none", choices=["none", "scaling", "dcut"],
+    ap.add_argument("--study", default="none", choices=["none", "scaling", "dcut", "next"],
                     help="scaling: time over n = 1e3..1e7 on the seed-spreader family in 2-D and 3-D; "
-                         "dcut: phase times over a d_cut sweep on c2 and c3 (one JSON line per point)")
+                         "dcut: phase times over a d_cut sweep on c2 and c3; next: the decision-graph "
+                         "summaries and the priority range search on c3 and c4 (one JSON line per point)")
     return ap.parse_args()
 
 
@@ -507,6 +508,8 @@ def run_study(args, dev):
                               "slope_log_time_vs_log_n": float(np.polyfit(x, y, 1)[0]),
                               "slope_n_ge_1e5": float(np.polyfit(x[2:], y[2:], 1)[0]),
                               "paper_slope_dpc_priority": 0.94}), flush=True)
+    elif args.study == "next":
+        run_next(args, dev, dpc, torch, stream, flush, steps)
     else:
         # the d_cut study (the paper's appendix on d_cut): with the noise
         # threshold fixed, sweep d_cut and split the time into density and
@@ -524,6 +527,85 @@ def run_study(args, dev):
                                   "mean_rho": mean_rho, "noise_fraction": noise, "rho_noise": int(job.rho_noise[0]),
                                   "ms": t, "density_ms": ph["density"], "dependent_ms": dep,
                                   "phases_ms": ph}), flush=True)
+
+
+def _events_ms(torch, stream, flush, fn, steps):
+    """Median CUDA-event time of fn() on `stream` (L2 flushed before each)."""
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def run_next(args, dev, dpc, torch, stream, flush, steps):
+    """Throughput of the decision-graph summaries and the priority range
+    search on the outputs of a full run (c3: one 1e7-point set; c4: the
+    4096-instance batch, first cutoff)."""
+    pk, pk_kind = peaks()
+    for name in ("c3", "c4"):
+        job = Job(load_workload(name))
+        batch = dpc.Batch(job.pt_offset, job.dims, job.d_cut, coord_offset=job.coord_offset)
+        params = dpc.make_params(batch, job.rho_noise, job.rho_min, job.delta_min)
+        pts = torch.from_numpy(job.flat).to(dev)
+        out = dpc.dpc_run(pts, batch, params, stream=stream, sync=True)
+        rho, delta = out["rho"][0].contiguous(), out["delta"][0].contiguous()
+        for k, rb, db in ((16, 0, 0), (1024, 0, 0), (0, 24, 48)):
+            ms = _events_ms(torch, stream, flush, lambda: dpc.dpc_decision_graph(
+                batch, rho, delta, k=k, rho_bins=rb, delta_bins=db, delta_lo=1e-3 * job.d_cut[0][0],
+                stream=stream), steps)
+            nbytes = 12.0 * job.N  # rho + delta read once: the algorithmic minimum
+            gbs = nbytes / (ms / 1e3) / 1e9
+            print(json.dumps({"study": "next", "op": "dpc_decision_graph", "workload": job.name,
+                              "k": k, "rho_bins": rb, "delta_bins": db, "points": job.N, "ms": ms,
+                              "points_per_s": job.N / (ms / 1e3),
+                              "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"],
+                                           "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+                                           "peak_source": pk_kind,
+                                           "work": "12 B per point (rho, delta read once)"}}), flush=True)
+        # priority range: boxes of 2 d_cut around random points, threshold = the
+        # point's own density (the points that could be its dependent point)
+        rng = np.random.default_rng(7)
+        nq = 100_000
+        rows = rng.integers(0, len(job.sizes), nq)
+        rows = rows[np.asarray(job.sizes)[rows] > 0]
+        nq = len(rows)
+        lo = np.zeros((nq, 8))
+        hi = np.zeros((nq, 8))
+        rq = np.zeros(nq, np.int32)
+        rho_h = rho.cpu().numpy()
+        for t, r in enumerate(rows.tolist()):
+            j = int(rng.integers(0, job.sizes[r]))
+            x = job.instance(r)[j].astype(np.float64)
+            w = 2.0 * job.d_cut[r][0]
+            lo[t, :len(x)], hi[t, :len(x)] = x - w, x + w
+            rq[t] = rho_h[job.pt_offset[r] + j]
+        q_inst = torch.from_numpy(rows.astype(np.int32)).to(dev)
+        box = torch.from_numpy(np.stack([lo, hi], axis=1)).to(dev)
+        q_rho = torch.from_numpy(rq).to(dev)
+        for max_out in (0, 64):
+            res = {}
+
+            def call():
+                res["o"] = dpc.dpc_priority_range(pts, batch, rho, q_inst, box, q_rho, max_out=max_out,
+                                                  stream=stream)
+            ms = _events_ms(torch, stream, flush, call, steps)
+            cnt = res["o"]["count"].double()
+            print(json.dumps({"study": "next", "op": "dpc_priority_range", "workload": job.name,
+                              "queries": nq, "max_out": max_out, "ms": ms, "queries_per_s": nq / (ms / 1e3),
+                              "mean_matches": float(cnt.mean()), "box": "2 d_cut half-width around a point",
+                              "threshold": "the point's own density",
+                              "includes": "binning and tree of every class (the call builds them)"}),
+                  flush=True)
+        del pts, out, rho, delta
 
 
 def run_reference(args, rank, world):

@@ -1072,10 +1072,13 @@ int dpc_decision_graph(const dpc_batch* b, const int32_t* rho, const double* del
                        (unsigned long long*)hist, w->stream);
   for (const ClassPlan& c : P.classes) {
     const ClassView cv = view_of(w, c, insts);
+    if (k > 0 &&
+        (rc = w->reserve_buf(&w->scr, &w->scr_bytes, decision_scratch_bytes(cv.ninst, k))))
+      return rc;
     launch_class_init(cv, c.g, c.ib, c.bcap, w->status, w->stream);
     launch_chunks(cv, w->chunk_inst, w->chunk_pos, w->stream);
     launch_decision(rho, delta, cv, k, top, gamma, rho_bins, delta_bins, delta_lo,
-                    (unsigned long long*)hist, w->stream);
+                    (unsigned long long*)hist, w->scr, w->stream);
   }
   return finish(w, flags);
 }

@@ -136,7 +136,9 @@ void launch_dep_far(int dp, bool fp64, const float* spts, const unsigned long lo
 // hist [n_inst][rho_bins][delta_bins] by batch row, InstDev::row)
 void launch_decision(const int32_t* rho, const double* delta, const ClassView& cv, int k,
                      int32_t* top, double* gamma, int rho_bins, int delta_bins, double delta_lo,
-                     unsigned long long* hist, cudaStream_t st);
+                     unsigned long long* hist, void* scratch, cudaStream_t st);
+// device scratch launch_decision needs for a class of ninst instances
+size_t decision_scratch_bytes(uint32_t ninst, int k);
 // ---- priority range search (range.cu) -------------------------------------------
 struct PrangeArgs {
   uint32_t nq;              // queries
