@@ -61,8 +61,10 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=4096)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default grid-level rule")
     ap.add_argument("--no-graph", action="store_true", help="time plain calls instead of graph replays")
-    ap.add_argument("--layout", default="auto", choices=["auto", "union", "segment", "tree", "tensor"],
+    ap.add_argument("--layout", default="auto", choices=["auto", "union", "segment", "tree", "tensor", "pairs"],
                     help="fixed kernel layout (auto: the autotuned choice)")
+    ap.add_argument("--near-shift", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="fixed near-phase grid level below the density's (-1: the autotuned choice)")
     ap.add_argument("--study", default="none", choices=["none", "scaling", "dcut", "next"],
                     help="scaling: time over n = 1e3..1e7 on the seed-spreader family in 2-D and 3-D; "
                          "dcut: phase times over a d_cut sweep on c2 and c3; next: the decision-graph "
@@ -297,7 +299,7 @@ def run_ours(args, rank, world, dev):
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
             dpc.dpc_run(pts, batch, params, precision=precision, stream=stream, out=out, phase_times=phase_times,
-                        graph=graph, layout=args.layout)
+                        graph=graph, layout=args.layout, near_shift=args.near_shift)
             b.record(stream)
             b.synchronize()
             times.append(a.elapsed_time(b))
@@ -317,12 +319,14 @@ def run_ours(args, rank, world, dev):
     while steps < args.warmup or time.time() < t_end:
         # the first warm-up call autotunes the grid level (cached for the rest)
         dpc.dpc_run(pts, batch, params, precision=args.precision, stream=stream, out=out, layout=args.layout,
-                    autotune=(steps == 0 and not args.no_autotune and args.layout == "auto"))
+                    near_shift=args.near_shift,
+                    autotune=(steps == 0 and not args.no_autotune and args.layout == "auto"
+                              and args.near_shift < 0))
         steps += 1
     use_graph = not args.no_graph
     # capture (graph mode) or one more plain call, then synchronize
     dpc.dpc_run(pts, batch, params, precision=args.precision, stream=stream, out=out, sync=True, graph=use_graph,
-                layout=args.layout)
+                layout=args.layout, near_shift=args.near_shift)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -344,8 +348,9 @@ def run_ours(args, rank, world, dev):
     config.update({"precision": args.precision, "l2": "flushed between steps (512 MiB write)",
                    "grid_level": "autotuned in the first warm-up call" if not args.no_autotune else "default rule",
                    "block_radius": int(stats.get("block_radius", 0)),
-                   "layouts": {"density": ["?", "union", "segment", "tree", "tensor"][int(stats.get("density_layout", 0))],
-                               "near": ["?", "union", "segment", "tree", "tensor"][int(stats.get("near_layout", 0))]},
+                   "near_shift": int(stats.get("near_shift", 0)),
+                   "layouts": {"density": ["?", "union", "segment", "tree", "tensor", "pairs"][int(stats.get("density_layout", 0))],
+                               "near": ["?", "union", "segment", "tree", "tensor", "pairs"][int(stats.get("near_layout", 0))]},
                    "parallelism": "replicas" if world > 1 else "1 GPU"})
     res = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -366,7 +371,8 @@ def run_ours(args, rank, world, dev):
     pk, pk_kind = peaks()
     single = {p: v for p, v in phases.items() if p in ("density", "near", "far", "tree", "maxkey")}
     dom = max(single, key=lambda p: single[p][0]) if single else None
-    kernels = {"density": {2: "k_density_seg", 4: "k_density_tc"}.get(stats.get("density_layout"), "k_density"),
+    kernels = {"density": {2: "k_density_seg", 4: "k_density_tc", 5: "k_density_pairs"}.get(
+        stats.get("density_layout"), "k_density"),
                "near": {2: "k_dep_near_seg", 3: "k_near_to_far"}.get(stats.get("near_layout"), "k_dep_near")}
     model_phase = dom if dom in kernels else max(("density", "near"), key=lambda p: phases[p][0])
     work, mean_rho = block_work(job, out["rho"])
@@ -376,6 +382,9 @@ def run_ours(args, rank, world, dev):
         # 3 dimensions: count the pairs the density step actually scanned
         d_mean = float(np.dot(job.sizes, job.dims)) / max(1, job.N)
         work = float(stats.get("density_pairs", 0)) * 3.0 * d_mean
+    pairs_layout = model_phase == "density" and int(stats.get("density_layout", 0)) == 5
+    if pairs_layout and not high_d:
+        work *= 0.5  # the pair layout evaluates each unordered pair once
     # phases[] holds the sums over the phase pass; work is one step's
     launches = phases[model_phase][1] // phase_steps
     step_ms = phases[model_phase][0] / phase_steps
@@ -392,7 +401,9 @@ def run_ours(args, rank, world, dev):
                  "scanned x 3d flops (d > 3: the ideal-grid count rho x 3^d / V_d overestimates clustered "
                  "data)" % (work, launches, int(stats.get("density_pairs", 0)))) if high_d else
                 ("%.4g flops per step over %d launches: per point rho x 3^d / V_d block candidates x 3d flops "
-                 "(mean rho %.1f at the first cutoff)" % (work, launches, mean_rho)),
+                 "(mean rho %.1f at the first cutoff)%s" % (work, launches, mean_rho,
+                                                             ", halved: each unordered pair once"
+                                                             if pairs_layout else "")),
         "ms_per_launch": per_launch_ms}
     res["dominant_phase"] = dom
 

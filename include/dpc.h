@@ -108,8 +108,9 @@ enum {
  * (near phase only, density keeps its default: no block scan, every query goes
  * to the tree search of the far phase), 4 = tensor (density only, 5-8
  * dimensions with DPC_PREC_FP32_CERT: distance tiles on the tensor cores with a
- * certified error band; other cases use segment).  Results do not depend on
- * it. */
+ * certified error band; other cases use segment), 5 = pairs (density only:
+ * the segment layout evaluating every unordered pair once and counting it for
+ * both points).  Results do not depend on it. */
 #define DPC_FLAG_LAYOUT(v) ((uint32_t)(v) << 16)
 #define DPC_FLAG_LAYOUT_MASK (0x7u << 16)
 /* dpc_run only: capture the call's kernels into a CUDA graph the first time a
@@ -129,6 +130,13 @@ enum {
  * Every other output is unchanged: the points a non-noise point can depend on
  * are denser than it, hence never noise. */
 #define DPC_FLAG_SKIP_NOISE (1u << 15)
+/* Fixed grid level of the near-dependent phase: DPC_FLAG_NEAR_SHIFT(j), j =
+ * 0..2, searches the (2R+1)^g block of cells j levels finer than the density
+ * step's (a block 2^j times narrower: fewer candidates per query, more queries
+ * left to the tree search); without it the default (j = 0) or the autotuned
+ * choice.  Results do not depend on it. */
+#define DPC_FLAG_NEAR_SHIFT(j) (((uint32_t)(j) + 1u) << 20)
+#define DPC_FLAG_NEAR_SHIFT_MASK (0x3u << 20)
 
 /* A batch of independent point sets packed back to back.  n_inst = 1 for a
  * single point set.  All arrays are HOST arrays read during the call only. */
@@ -311,7 +319,7 @@ typedef struct {
   int32_t density_layout; /* layout of the last density launch: 1 union,
                              2 segment (see DPC_FLAG_LAYOUT)                  */
   int32_t near_layout;    /* layout of the last near-dependent launch (3 = tree) */
-  int32_t reserved;
+  int32_t near_shift;     /* grid levels the near phase ran below the density's */
   int64_t density_pairs;  /* (query, candidate) pairs the density step scanned
                              (every cutoff and instance of the last call)    */
 } dpc_stats;

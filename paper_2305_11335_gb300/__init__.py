@@ -71,7 +71,7 @@ class _Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("far_nodes", ctypes.c_int64),
                 ("far_nodes_max", ctypes.c_int64), ("block_radius", ctypes.c_int32),
                 ("density_layout", ctypes.c_int32), ("near_layout", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("density_pairs", ctypes.c_int64)]
+                ("near_shift", ctypes.c_int32), ("density_pairs", ctypes.c_int64)]
 
 
 PHASES = ["bin", "tree", "cells", "density", "maxkey", "near", "far", "labels"]
@@ -81,11 +81,20 @@ DPC_FLAG_GRAPH = 1 << 11
 DPC_FLAG_SKIP_NOISE = 1 << 15
 
 
+def DPC_FLAG_NEAR_SHIFT(j: int) -> int:
+    """Near-dependent phase j = 0..2 grid levels below the density's; -1 = auto."""
+    if j < 0:
+        return 0
+    if j > 2:
+        raise ValueError("near shift must be 0..2")
+    return (j + 1) << 20
+
+
 def DPC_FLAG_RADIUS(r: int) -> int:
     return (int(r) & 7) << 12
 
 
-LAYOUTS = {"auto": 0, "union": 1, "segment": 2, "tree": 3, "tensor": 4}
+LAYOUTS = {"auto": 0, "union": 1, "segment": 2, "tree": 3, "tensor": 4, "pairs": 5}
 
 
 def DPC_FLAG_LAYOUT(layout: str) -> int:
@@ -350,7 +359,8 @@ def dpc_priority_range(pts: torch.Tensor, batch: Batch, rho: torch.Tensor, q_ins
 
 def dpc_run(pts: torch.Tensor, batch: Batch, params, precision: str = "fp32", sync: bool = False, stream=None,
             out: dict | None = None, phase_times: bool = False, autotune: bool = False,
-            radius: int = 0, graph: bool = False, layout: str = "auto", skip_noise: bool = False) -> dict:
+            radius: int = 0, graph: bool = False, layout: str = "auto", skip_noise: bool = False,
+            near_shift: int = -1) -> dict:
     lib = load()
     shape = (batch.n_dcut, batch.N)
     if out is None:
@@ -361,7 +371,8 @@ def dpc_run(pts: torch.Tensor, batch: Batch, params, precision: str = "fp32", sy
     _check(lib.dpc_run(_dev(pts, "pts"), _dtype_code(pts), batch.ptr, params, _dev(out["rho"], "rho"),
                        _dev(out["lam"], "lambda"), _dev(out["delta"], "delta"), _dev(out["label"], "label"),
                        _flags(precision, sync, radius, autotune, layout) | (DPC_FLAG_PHASE_TIMES if phase_times else 0)
-                       | (DPC_FLAG_GRAPH if graph else 0) | (DPC_FLAG_SKIP_NOISE if skip_noise else 0),
+                       | (DPC_FLAG_GRAPH if graph else 0) | (DPC_FLAG_SKIP_NOISE if skip_noise else 0)
+                       | DPC_FLAG_NEAR_SHIFT(near_shift),
                        _stream(stream)),
            "dpc_run")
     return out
@@ -427,7 +438,7 @@ def dpc_last_status(stream=None) -> int:
 
 def run(pts: torch.Tensor, d_cut, rho_noise, rho_min, delta_min, precision: str = "fp32", sync: bool = True,
         stream=None, autotune: bool = False, radius: int = 0, layout: str = "auto",
-        skip_noise: bool = False) -> dict:
+        skip_noise: bool = False, near_shift: int = -1) -> dict:
     """DPC of one point set ``pts`` [n, d] (CUDA, int32/float32) for one or more cutoffs."""
     if pts.dim() == 1:
         pts = pts.reshape(-1, 1)
@@ -436,5 +447,6 @@ def run(pts: torch.Tensor, d_cut, rho_noise, rho_min, delta_min, precision: str 
     batch = Batch.single(n, d, cuts)
     params = make_params(batch, rho_noise, rho_min, delta_min)
     return dpc_run(pts.contiguous(), batch, params, precision=precision, sync=sync, stream=stream,
-                   autotune=autotune, radius=radius, layout=layout, skip_noise=skip_noise)
+                   autotune=autotune, radius=radius, layout=layout, skip_noise=skip_noise,
+                   near_shift=near_shift)
 

@@ -88,14 +88,16 @@ int check_batch(const dpc_batch* b, std::vector<Inst>* insts, uint64_t* total) {
 
 constexpr uint32_t kKnownFlags = DPC_PREC_MASK | DPC_FLAG_SYNC_CHECK | DPC_FLAG_PHASE_TIMES |
                                  DPC_FLAG_AUTOTUNE | DPC_FLAG_RADIUS_MASK | DPC_FLAG_GRAPH |
-                                 DPC_FLAG_LAYOUT_MASK | DPC_FLAG_SKIP_NOISE;
+                                 DPC_FLAG_LAYOUT_MASK | DPC_FLAG_SKIP_NOISE |
+                                 DPC_FLAG_NEAR_SHIFT_MASK;
 
 int check_flags(uint32_t flags) {
   const uint32_t prec = flags & DPC_PREC_MASK;
   if (prec != DPC_PREC_FP64 && prec != DPC_PREC_FP32_CERT) return DPC_ERR_UNSUPPORTED;
   if (flags & ~kKnownFlags) return DPC_ERR_ARG;
   if (((flags & DPC_FLAG_RADIUS_MASK) >> 12) > 5) return DPC_ERR_ARG;
-  if (((flags & DPC_FLAG_LAYOUT_MASK) >> 16) > 4) return DPC_ERR_ARG;
+  if (((flags & DPC_FLAG_LAYOUT_MASK) >> 16) > 5) return DPC_ERR_ARG;
+  if (((flags & DPC_FLAG_NEAR_SHIFT_MASK) >> 20) > 3) return DPC_ERR_ARG;
   return DPC_OK;
 }
 
@@ -157,6 +159,7 @@ struct Choice {
   int r = 0;
   int dlay = 0;  // density layout (kLayout*)
   int nlay = 0;  // near-phase layout
+  int ns = 0;    // near-phase grid levels below the density's
 };
 
 struct Workspace {
@@ -231,7 +234,7 @@ struct Workspace {
 
   // autotuned radius and layouts per (class shape, cutoff), see choose()
   std::map<std::string, Choice> tuned;
-  cudaEvent_t tune_ev[9] = {};
+  cudaEvent_t tune_ev[20] = {};
 
   // for dpc_get_stats: the last class and cutoff that ran
   Choice last_choice;
@@ -705,8 +708,8 @@ void density_step(Workspace* w, const ClassPlan& c, const ClassView& cv, const C
                  w->hvals, w->pieces, rho, w->skey, w->ctr, w->stream);
 }
 
-void dependent_step(Workspace* w, const ClassPlan& c, const ClassView& cv, const CutGeom* cuts,
-                    const void* pts, int dtype, int32_t rho_skip, bool fp64, int layout,
+void dependent_step(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cuts,
+                    const void* pts, int dtype, int32_t rho_skip, bool fp64, int layout, int nshift,
                     int32_t* lambda, double* delta) {
   cudaStream_t st = w->stream;
   {
@@ -714,6 +717,10 @@ void dependent_step(Workspace* w, const ClassPlan& c, const ClassView& cv, const
     launch_tree_maxkey(w->skey, w->spts, c.dp, cv.N, w->nodes, w->leaf_parent, w->visit, w->nbox,
                        !w->boxes_ready, st);
     w->boxes_ready = true;
+  }
+  if (nshift > 0 && layout != kLayoutTree) {  // the near phase on finer cells
+    launch_near_level(cv, cuts, nshift, st);
+    cells_step(w, c, cv, cuts);
   }
   {
     Phase ph(w, DPC_PHASE_NEAR);
@@ -796,28 +803,35 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
   Choice ch;
   ch.r = (int)((flags & DPC_FLAG_RADIUS_MASK) >> 12);
   const int forced = (int)((flags & DPC_FLAG_LAYOUT_MASK) >> 16);
+  const int forced_ns = (int)((flags & DPC_FLAG_NEAR_SHIFT_MASK) >> 20);
   ch.dlay = (forced && forced != kLayoutTree) ? forced : default_dlayout(c.g);
-  ch.nlay = (forced && forced != kLayoutTensor) ? forced : default_nlayout(c.g);
+  ch.nlay = (forced && forced != kLayoutTensor && forced != kLayoutPairs) ? forced
+                                                                          : default_nlayout(c.g);
+  ch.ns = forced_ns ? forced_ns - 1 : 0;
   const std::string key = (near ? "R/" : "D/") + tune_key(c, b, cut);
   auto it = w->tuned.find(key);
-  if (ch.r == 0 && !forced && it == w->tuned.end() && (flags & DPC_FLAG_AUTOTUNE)) {
+  const bool fixed = ch.r != 0 || forced || forced_ns;
+  if (!fixed && it == w->tuned.end() && (flags & DPC_FLAG_AUTOTUNE)) {
     cudaStream_t st = w->stream;
     if (!w->tune_ev[0])
       for (auto& e : w->tune_ev) cudaEventCreate(&e);
     cudaMemcpyAsync(w->ctr_save, w->ctr, sizeof(Counters), cudaMemcpyDeviceToDevice, st);
     // the tensor layout exists for 5-8 dimensions with the float32 filter
-    const int ndl = (c.dp == 8 && !fp64) ? 3 : 2;
-    const int dlays[3] = {kLayoutUnion, kLayoutSegment, kLayoutTensor};
+    const int ndl = (c.dp == 8 && !fp64) ? 4 : 3;
+    const int dlays[4] = {kLayoutUnion, kLayoutSegment, kLayoutPairs, kLayoutTensor};
     const int nlays[3] = {kLayoutUnion, kLayoutSegment, kLayoutTree};
-    // events: 0 start, 1 after cells, 2-4 after each density layout, 5 after
-    // the subtree keys, 6-8 after each near layout (each followed by the far
-    // search, which finishes what the near phase leaves)
+    constexpr int kShifts = 3;  // near phase 0, 1 or 2 levels below the density's
+    // events: 0 start, 1 after cells, 2-5 after each density layout, 6 after
+    // the subtree keys; per near shift s, 7 + 4s after its level change and
+    // cells, then one after each near layout (each followed by the far search,
+    // which finishes what the near phase leaves; the tree layout, which uses
+    // no cells, only at s = 0)
     auto trial = [&](int r, bool timed) {
       if (timed) cudaEventRecord(w->tune_ev[0], st);
       launch_set_radius(cv, cuts, r, st);
       launch_cells(w->scode, cv, c.g, cuts, w->hinfo, w->hkeys, w->hvals, w->hcap, st);
       if (timed) cudaEventRecord(w->tune_ev[1], st);
-      for (int l = 0; l < 3; ++l) {
+      for (int l = 0; l < 4; ++l) {
         if (l < ndl)
           launch_density(c.dp, c.g, fp64, dlays[l], w->spts, w->scode, w->sid, cv, cuts, w->hinfo,
                          w->hkeys, w->hvals, w->pieces, rho_scratch, w->skey, w->ctr, st);
@@ -827,14 +841,24 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
       launch_tree_maxkey(w->skey, w->spts, c.dp, cv.N, w->nodes, w->leaf_parent, w->visit, w->nbox,
                          !w->boxes_ready, st);
       w->boxes_ready = true;
-      if (timed) cudaEventRecord(w->tune_ev[5], st);
-      for (int l = 0; l < 3; ++l) {
-        launch_dep_near(c.dp, c.g, fp64, nlays[l], w->spts, w->scode, w->skey, cv, 0, near->pts,
-                        near->dtype, cuts, w->hinfo, w->hkeys, w->hvals, near->lambda, near->delta,
-                        queue_of(w), w->ctr, st);
-        launch_dep_far(c.dp, fp64, w->spts, w->scode, w->skey, cv, cuts, w->nodes, w->nbox, w->roots,
-                       queue_of(w), near->lambda, near->delta, w->ctr, st);
-        if (timed) cudaEventRecord(w->tune_ev[6 + l], st);
+      if (timed) cudaEventRecord(w->tune_ev[6], st);
+      for (int sh = 0; sh < kShifts; ++sh) {
+        if (sh > 0) {
+          launch_set_radius(cv, cuts, r, st);
+          launch_near_level(cv, cuts, sh, st);
+          launch_cells(w->scode, cv, c.g, cuts, w->hinfo, w->hkeys, w->hvals, w->hcap, st);
+        }
+        if (timed) cudaEventRecord(w->tune_ev[7 + 4 * sh], st);
+        for (int l = 0; l < 3; ++l) {
+          if (sh == 0 || nlays[l] != kLayoutTree) {
+            launch_dep_near(c.dp, c.g, fp64, nlays[l], w->spts, w->scode, w->skey, cv, 0, near->pts,
+                            near->dtype, cuts, w->hinfo, w->hkeys, w->hvals, near->lambda,
+                            near->delta, queue_of(w), w->ctr, st);
+            launch_dep_far(c.dp, fp64, w->spts, w->scode, w->skey, cv, cuts, w->nodes, w->nbox,
+                           w->roots, queue_of(w), near->lambda, near->delta, w->ctr, st);
+          }
+          if (timed) cudaEventRecord(w->tune_ev[8 + 4 * sh + l], st);
+        }
       }
     };
     auto span = [&](int a, int z) {
@@ -852,10 +876,15 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
     bool failed = false;
     for (int r = 1; r <= rmax && !failed; ++r) {
       // each phase: the smaller of two timings
-      float cl = 1e30f, dt[3] = {1e30f, 1e30f, 1e30f}, nt[3] = {1e30f, 1e30f, 1e30f};
+      float cl = 1e30f, dt[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+      float nt[kShifts][3], lv[kShifts];
+      for (int sh = 0; sh < kShifts; ++sh) {
+        lv[sh] = 1e30f;
+        for (int l = 0; l < 3; ++l) nt[sh][l] = 1e30f;
+      }
       for (int rep = 0; rep < 2; ++rep) {
         trial(r, true);
-        if (cudaEventSynchronize(w->tune_ev[near ? 8 : 4]) != cudaSuccess) {
+        if (cudaEventSynchronize(w->tune_ev[near ? 7 + 4 * (kShifts - 1) + 3 : 5]) != cudaSuccess) {
           cudaGetLastError();
           failed = true;
           break;
@@ -863,7 +892,13 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
         cl = fminf(cl, span(0, 1));
         for (int l = 0; l < ndl; ++l) dt[l] = fminf(dt[l], span(1 + l, 2 + l));
         if (near)
-          for (int l = 0; l < 3; ++l) nt[l] = fminf(nt[l], span(5 + l, 6 + l));
+          for (int sh = 0; sh < kShifts; ++sh) {
+            // the level change and cells of a shift count against it
+            lv[sh] = sh == 0 ? 0.f : fminf(lv[sh], span(7 + 4 * (sh - 1) + 3, 7 + 4 * sh));
+            for (int l = 0; l < 3; ++l)
+              if (sh == 0 || nlays[l] != kLayoutTree)
+                nt[sh][l] = fminf(nt[sh][l], span(7 + 4 * sh + l, 8 + 4 * sh + l));
+          }
       }
       if (failed) break;
       // a layout other than the default has to win by 3%
@@ -876,20 +911,37 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
         return bi;
       };
       const int di = pick(dt, dlays, ndl, default_dlayout(c.g));
-      const int ni = near ? pick(nt, nlays, 3, default_nlayout(c.g)) : -1;
-      const float ms = cl + dt[di] + (near ? nt[ni] : 0.f);
+      int nsi = 0, ni = -1;
+      float nms = 0.f;
+      if (near) {
+        ni = pick(nt[0], nlays, 3, default_nlayout(c.g));
+        nms = nt[0][ni];
+        for (int sh = 1; sh < kShifts; ++sh) {
+          const int l = pick(nt[sh], nlays, 3, default_nlayout(c.g));
+          const float t = lv[sh] + nt[sh][l];
+          if (t < 0.97f * nms) {
+            nms = t;
+            nsi = sh;
+            ni = l;
+          }
+        }
+      }
+      const float ms = cl + dt[di] + nms;
       if (best.r == 0 || ms < best_ms) {
         best_ms = ms;
         best.r = r;
         best.dlay = dlays[di];
         best.nlay = near ? nlays[ni] : default_nlayout(c.g);
+        best.ns = near ? nsi : 0;
       }
     }
     if (failed) best = Choice();
+    // back to the default level (the trials left a shifted one behind)
+    launch_set_radius(cv, cuts, 0, st);
     cudaMemcpyAsync(w->ctr, w->ctr_save, sizeof(Counters), cudaMemcpyDeviceToDevice, st);
     it = w->tuned.emplace(key, best).first;
   }
-  if (ch.r == 0 && !forced && it != w->tuned.end() && it->second.r > 0) ch = it->second;
+  if (!fixed && it != w->tuned.end() && it->second.r > 0) ch = it->second;
   if (ch.r > 0) launch_set_radius(cv, cuts, ch.r, w->stream);
   w->last_choice = ch;
   return ch;
@@ -991,7 +1043,7 @@ int dpc_dependent(const void* pts, int dtype, const dpc_batch* b, int32_t dcut_i
                              flags & ~DPC_FLAG_AUTOTUNE, nullptr);
     cells_step(w, c, cv, w->cuts);
     launch_keys_from_rho(rho, w->sid, cv.N, w->skey, w->stream);
-    dependent_step(w, c, cv, w->cuts, pts, dtype, rho_skip, fp64, ch.nlay, lambda, delta);
+    dependent_step(w, c, cv, w->cuts, pts, dtype, rho_skip, fp64, ch.nlay, ch.ns, lambda, delta);
   }
   return finish(w, flags);
 }
@@ -1040,7 +1092,7 @@ static void run_classes(Workspace* w, const CallPlan& P, const void* pts, int dt
       const Choice ch = choose(w, c, cv, cuts, b, k, fp64, rho + o, flags, &nt);
       cells_step(w, c, cv, cuts);
       density_step(w, c, cv, cuts, fp64, ch.dlay, rho + o);
-      dependent_step(w, c, cv, cuts, pts, dtype, 0, fp64, ch.nlay, lambda + o, delta + o);
+      dependent_step(w, c, cv, cuts, pts, dtype, 0, fp64, ch.nlay, ch.ns, lambda + o, delta + o);
       labels_step(w, c, cv, k, one_params(params, c, P.ncut_all, k), rho + o, lambda + o,
                   delta + o, label + o);
     }
@@ -1375,6 +1427,7 @@ int dpc_get_stats(void* stream, dpc_stats* out) {
     out->block_radius = cg.R;
     out->density_layout = w->last_choice.dlay;
     out->near_layout = w->last_choice.nlay;
+    out->near_shift = w->last_choice.ns;
     out->bits_per_axis = g.B;
   }
   return cudaGetLastError() == cudaSuccess ? DPC_OK : DPC_ERR_CUDA;

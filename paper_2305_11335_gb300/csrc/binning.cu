@@ -171,6 +171,17 @@ __global__ void k_setup_geom(ClassView cv, int ncut, const CutHost* __restrict__
 // power-of-two multiple of the fine cell, e.g. the larger cutoffs of a sweep).
 // rpref > 0: the finest level whose block radius is at most rpref (the
 // autotuner's choice, see api.cu).
+// Points outside the (2R+1)^g block of level-k cells around a query are at
+// least (R*2^k - 1) fine units away: the bound below which a near-phase
+// winner is final.
+__device__ void set_far(CutGeom& C, double f) {
+  const double gap = ldexp((double)C.R, C.k) - 1.0;
+  const double lb2 = gap > 0.0 ? gap * gap * f * f : 0.0;
+  C.far64 = lb2 * (1.0 - 1e-9);
+  const double l32 = lb2 * (1.0 - 1e-5) - 0x1p-100;
+  C.far32 = l32 <= 0.0 ? 0.0f : (l32 >= 3.0e38 ? 3.0e38f : __double2float_rd(l32));
+}
+
 __device__ void choose_level(CutGeom& C, const GridGeom* geom, int rpref) {
   const double f = geom->f;
   const int B = geom->B;
@@ -204,12 +215,18 @@ __device__ void choose_level(CutGeom& C, const GridGeom* geom, int rpref) {
   // density prune: squared lower bound in fine units vs d_cut^2 / f^2
   double pf = C.dc2 * (1.0 + 1e-6) / (f * f) * (1.0 + 1e-6);
   C.prune_fine = pf >= 3.0e38 ? INFINITY : __double2float_ru(pf);
-  // points outside the (2R+1)^g block are at least (R*2^k - 1) fine units away
-  double gap = ldexp((double)R, k) - 1.0;
-  double lb2 = gap > 0.0 ? gap * gap * f * f : 0.0;
-  C.far64 = lb2 * (1.0 - 1e-9);
-  double l32 = lb2 * (1.0 - 1e-5) - 0x1p-100;
-  C.far32 = l32 <= 0.0 ? 0.0f : (l32 >= 3.0e38 ? 3.0e38f : __double2float_rd(l32));
+  set_far(C, f);
+}
+
+// The near-dependent search on cells `shift` levels finer than the density's,
+// with the same block radius: a block 2^shift times narrower, so fewer
+// candidates per query and more queries left to the tree search.
+__global__ void k_near_level(ClassView cv, CutGeom* cuts, int shift) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cv.ninst) return;
+  CutGeom& C = cuts[i];
+  C.k = C.k > shift ? C.k - shift : 0;
+  set_far(C, cv.geom[i].f);
 }
 
 // Per (instance, cutoff) search parameters, one thread each.  cuts is
@@ -454,6 +471,12 @@ void launch_class_init(const ClassView& cv, int g, int ib, int bcap, int* status
 void launch_chunks(const ClassView& cv, uint32_t* chunk_inst, uint32_t* chunk_pos, cudaStream_t st) {
   if (!cv.inst || cv.ninst == 0) return;
   k_chunks<<<grid_for(cv.ninst, 1, 152u * 16u), 128, 0, st>>>(cv.inst, cv.ninst, chunk_inst, chunk_pos);
+  count_launches(1);
+}
+
+void launch_near_level(const ClassView& cv, CutGeom* cuts, int shift, cudaStream_t st) {
+  if (shift <= 0) return;
+  k_near_level<<<grid_for(cv.ninst), kThreads, 0, st>>>(cv, cuts, shift);
   count_launches(1);
 }
 

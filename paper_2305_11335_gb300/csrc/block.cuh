@@ -271,6 +271,37 @@ __device__ __forceinline__ void load_window(const RunTable& rt, int nr, uint32_t
   }
 }
 
+// load_window with the sorted position of every candidate (0xffffffff past
+// the end).
+template <int DP, int V>
+__device__ __forceinline__ void load_window_pos(const RunTable& rt, int nr, uint32_t w0, uint32_t total,
+                                                const float* __restrict__ spts, int lane, Pt<DP>* cand,
+                                                uint32_t* pos) {
+  const uint32_t e0 = w0 + lane;
+  int lo = 0, hi = nr - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (rt.pre[mid] <= e0) lo = mid;
+    else hi = mid - 1;
+  }
+  int r = lo;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const uint32_t e = e0 + 32u * v;
+    pos[v] = 0xffffffffu;
+    if (w0 + 32u * v >= total) break;
+    if (e < total) {
+      while (r + 1 < nr && rt.pre[r + 1] <= e) ++r;
+      const uint32_t src = rt.start[r] + (e - rt.pre[r]);
+      cand[v] = load_pt<DP>(spts, src);
+      pos[v] = src;
+    } else {
+#pragma unroll
+      for (int a = 0; a < DP; ++a) cand[v].x[a] = __int_as_float(0x7fffffff);
+    }
+  }
+}
+
 // Does the block of radius R around cell c0 contain cell c?
 template <int G>
 __device__ __forceinline__ bool in_block(const uint32_t* c0, const uint32_t* c, int R) {

@@ -11,6 +11,8 @@
 //   FP64:      every pair is evaluated in binary64.
 // Both give exactly the binary64 count.  The kernel also writes the order key
 // of every sorted point, (rho << 32) | ~id.
+#include <type_traits>
+
 #include "block.cuh"
 #include "internal.h"
 
@@ -58,6 +60,7 @@ k_density(const float* __restrict__ spts, const unsigned long long* __restrict__
           const HashInfo* __restrict__ hi, const unsigned long long* __restrict__ hkeys,
           const uint2* __restrict__ hvals, int32_t* __restrict__ rho_out,
           unsigned long long* __restrict__ skey, Counters* ctr) {
+  constexpr int ND = real_dims<DP, G>();
   constexpr int kCap = density_cap<DP>();
   __shared__ __align__(16) float s_pts[kWarps * kCap * DP];
   __shared__ RunTable s_rt[kWarps];
@@ -112,9 +115,9 @@ k_density(const float* __restrict__ spts, const unsigned long long* __restrict__
           for (uint32_t i = i0; i < i1; ++i) {
             const Pt<DP> x = window_pt<DP>(wpts, i);
             if constexpr (F64) {
-              c += dist64<DP>(me, x) <= dl;
+              c += dist64<DP, ND>(me, x) <= dl;
             } else {
-              const float s32 = dist32<DP>(me, x);
+              const float s32 = dist32<DP, ND>(me, x);
               c += s32 <= ti;
               c2 += s32 <= to;
             }
@@ -165,6 +168,7 @@ k_density_seg(const float* __restrict__ spts, const unsigned long long* __restri
               const HashInfo* __restrict__ hi, const unsigned long long* __restrict__ hkeys,
               const uint2* __restrict__ hvals, int32_t* __restrict__ rho_out,
               unsigned long long* __restrict__ skey, Counters* ctr) {
+  constexpr int ND = real_dims<DP, G>();
   constexpr int V = seg_v<DP>();
   constexpr uint32_t W = 32u * V;
   __shared__ RunTable s_rt[kWarps];
@@ -221,8 +225,8 @@ k_density_seg(const float* __restrict__ spts, const unsigned long long* __restri
 #pragma unroll
             for (int v = 0; v < V; ++v) {
               if (v >= vn) break;
-              c += (dist64<DP>(xa, cand[v]) <= dc2) ? 1u : 0u;
-              c += (dist64<DP>(xb, cand[v]) <= dc2) ? 0x10000u : 0u;
+              c += (dist64<DP, ND>(xa, cand[v]) <= dc2) ? 1u : 0u;
+              c += (dist64<DP, ND>(xb, cand[v]) <= dc2) ? 0x10000u : 0u;
             }
             c = __reduce_add_sync(kFull, c);
             cnt_a = (int32_t)(c & 0xffffu);
@@ -232,8 +236,8 @@ k_density_seg(const float* __restrict__ spts, const unsigned long long* __restri
 #pragma unroll
             for (int v = 0; v < V; ++v) {
               if (v >= vn) break;
-              const float sa = dist32<DP>(xa, cand[v]);
-              const float sb = dist32<DP>(xb, cand[v]);
+              const float sa = dist32<DP, ND>(xa, cand[v]);
+              const float sb = dist32<DP, ND>(xb, cand[v]);
               ci += (sa <= t_in ? 1u : 0u) + (sb <= t_in ? 0x10000u : 0u);
               co += (sa <= t_out ? 1u : 0u) + (sb <= t_out ? 0x10000u : 0u);
             }
@@ -246,15 +250,15 @@ k_density_seg(const float* __restrict__ spts, const unsigned long long* __restri
 #pragma unroll
               for (int v = 0; v < V; ++v) {
                 if (v >= vn) break;
-                const float sa = dist32<DP>(xa, cand[v]);
-                const float sb = dist32<DP>(xb, cand[v]);
+                const float sa = dist32<DP, ND>(xa, cand[v]);
+                const float sb = dist32<DP, ND>(xb, cand[v]);
                 if (sa > t_in && sa <= t_out) {
                   ++seen;
-                  in += dist64<DP>(xa, cand[v]) <= dc2 ? 1u : 0u;
+                  in += dist64<DP, ND>(xa, cand[v]) <= dc2 ? 1u : 0u;
                 }
                 if (sb > t_in && sb <= t_out) {
                   seen += 0x10000u;
-                  in += dist64<DP>(xb, cand[v]) <= dc2 ? 0x10000u : 0u;
+                  in += dist64<DP, ND>(xb, cand[v]) <= dc2 ? 0x10000u : 0u;
                 }
               }
               in = __reduce_add_sync(kFull, in);
@@ -282,6 +286,215 @@ k_density_seg(const float* __restrict__ spts, const unsigned long long* __restri
   }
 }
 
+// candidate slots per lane of the pair layout (its per-slot counts need
+// registers of their own)
+template <int DP>
+constexpr int pairs_v() { return DP == 2 ? 8 : (DP == 4 ? 8 : 4); }
+
+// Pair layout (symmetric): every unordered pair within d_cut is evaluated
+// once and counted for both points.  The work layout is k_density_seg's
+// (segments of equal cell, the block's candidates spread over the lanes, two
+// queries per pass), but a segment in cell A only takes the cells B of its
+// block that follow A in Morton order, plus the points of A itself that
+// follow the query in sorted order.  A query's count stays in a register and
+// each candidate's in a register per slot; both go to a position-indexed
+// counter with one atomic add per window (candidates) or per chunk (queries).
+// cnt2 is the low 32-bit word of each sorted point's 64-bit order key slot
+// (index 2p), zeroed before; k_pairs_finish turns it into rho and the key.
+template <int DP, int G, bool F64>
+__global__ void __launch_bounds__(kThreads, DP == 2 ? 5 : 4)
+k_density_pairs(const float* __restrict__ spts, const unsigned long long* __restrict__ scode,
+                ClassView cv, const CutGeom* __restrict__ cuts, const HashInfo* __restrict__ hi,
+                const unsigned long long* __restrict__ hkeys, const uint2* __restrict__ hvals,
+                uint32_t* __restrict__ cnt2, Counters* ctr) {
+  constexpr int ND = real_dims<DP, G>();
+  constexpr int V = pairs_v<DP>();
+  constexpr uint32_t W = 32u * V;
+  __shared__ RunTable s_rt[kWarps];
+  __shared__ RunTable s_rt2[kWarps];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  RunTable& rt = s_rt[wib];
+  RunTable& rt2 = s_rt2[wib];
+  const int S = cv.cls->S, ib = cv.cls->ib;
+  const uint32_t hmask = hi->hmask;
+  const uint32_t n = cv.N;
+
+  unsigned long long band = 0, pairs = 0;
+  for (uint32_t ch = blockIdx.x * kWarps + wib; ch < cv.nchunk; ch += gridDim.x * kWarps) {
+    uint32_t inst, p0, end;
+    cv.chunk(ch, inst, p0, end);
+    const CutGeom& C = cuts[inst];
+    const int k = C.k;
+    const int R = C.R;
+    const int shift = G * k;
+    const int cmax = (1 << (cv.geom[inst].B - k)) - 1;
+    const double dc2 = C.dc2;
+    const float t_in = C.t_in, t_out = C.t_out;
+    const unsigned long long hb = ib ? ((unsigned long long)inst << S) : 0ull;
+    const uint32_t p = p0 + lane;
+    const bool valid = p < end;
+    const unsigned long long mycell = valid ? (key_code(scode[p], S, ib) >> shift) : ~0ull;
+    const int nvalid = (int)min(32u, end - p0);
+    int32_t acc = valid ? 1 : 0;  // lane j: query p0 + j (itself, then its pairs)
+    int s = 0;
+    while (s < nvalid) {
+      const unsigned long long cell = __shfl_sync(kFull, mycell, s);
+      const int e = s + __popc(__ballot_sync(kFull, valid && mycell == cell));  // queries s .. e-1
+      uint32_t c0[G];
+      unmorton<G>(cell, c0);
+      Union<G> u;
+      block_union<G>(c0, R, cmax, u);
+      const int nr = union_runs<G>(u, hkeys, hvals, hmask, hb, n, lane, rt);
+      // OWN = false: the cells after A; OWN = true: A's points after the
+      // segment's first query (a pair counts only if the candidate follows
+      // the query)
+      auto scan = [&](const RunTable& tab, int ntab, auto own_tag) {
+        constexpr bool OWN = decltype(own_tag)::value;
+        const uint32_t total = tab.pre[ntab];
+        pairs += (unsigned long long)(e - s) * total;
+        for (uint32_t w0 = 0; w0 < total; w0 += W) {
+          Pt<DP> cand[V];
+          load_window<DP, V>(tab, ntab, w0, total, spts, lane, cand);
+          const int vn = (int)min((uint32_t)V, (total - w0 + 31u) / 32u);
+          // OWN: one run, so slot v of this lane holds position pbase + 32 v
+          const uint32_t pbase = OWN ? tab.start[0] + w0 + lane : 0u;
+          // this lane's candidates' counts, two 16-bit halves per word
+          uint32_t cc[(V + 1) / 2];
+#pragma unroll
+          for (int v = 0; v < (V + 1) / 2; ++v) cc[v] = 0u;
+          for (int j = s; j < e; j += 2) {
+            const bool two = j + 1 < e;
+            const uint32_t qa = p0 + j, qb = p0 + (two ? j + 1 : j);
+            const Pt<DP> xa = load_pt<DP>(spts, qa);
+            const Pt<DP> xb = load_pt<DP>(spts, qb);
+            int32_t cnt_a, cnt_b;
+            if constexpr (F64) {
+              unsigned c = 0;
+#pragma unroll
+              for (int v = 0; v < V; ++v) {
+                if (v >= vn) break;
+                const uint32_t pv = pbase + 32u * v;
+                const bool ea = (!OWN || pv > qa) && dist64<DP, ND>(xa, cand[v]) <= dc2;
+                const bool eb = two && (!OWN || pv > qb) && dist64<DP, ND>(xb, cand[v]) <= dc2;
+                c += (ea ? 1u : 0u) + (eb ? 0x10000u : 0u);
+                cc[v >> 1] += ((ea ? 1u : 0u) + (eb ? 1u : 0u)) << (16 * (v & 1));
+              }
+              c = __reduce_add_sync(kFull, c);
+              cnt_a = (int32_t)(c & 0xffffu);
+              cnt_b = (int32_t)(c >> 16);
+            } else {
+              unsigned ci = 0, co = 0;
+#pragma unroll
+              for (int v = 0; v < V; ++v) {
+                if (v >= vn) break;
+                const uint32_t pv = pbase + 32u * v;
+                const float sa0 = dist32<DP, ND>(xa, cand[v]);
+                const float sb0 = dist32<DP, ND>(xb, cand[v]);
+                // a pair that does not count is moved past every threshold
+                const float sa = (!OWN || pv > qa) ? sa0 : INFINITY;
+                const float sb = (two && (!OWN || pv > qb)) ? sb0 : INFINITY;
+                const bool ia = sa <= t_in, ib2 = sb <= t_in;
+                ci += (ia ? 1u : 0u) + (ib2 ? 0x10000u : 0u);
+                co += (sa <= t_out ? 1u : 0u) + (sb <= t_out ? 0x10000u : 0u);
+                cc[v >> 1] += ((ia ? 1u : 0u) + (ib2 ? 1u : 0u)) << (16 * (v & 1));
+              }
+              ci = __reduce_add_sync(kFull, ci);
+              co = __reduce_add_sync(kFull, co);
+              cnt_a = (int32_t)(ci & 0xffffu);
+              cnt_b = (int32_t)(ci >> 16);
+              if (co != ci) {  // band pairs: recount them in binary64
+                unsigned in = 0, seen = 0;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                  if (v >= vn) break;
+                  const uint32_t pv = pbase + 32u * v;
+                  const float sa = (!OWN || pv > qa) ? dist32<DP, ND>(xa, cand[v]) : INFINITY;
+                  const float sb = (two && (!OWN || pv > qb)) ? dist32<DP, ND>(xb, cand[v]) : INFINITY;
+                  if (sa > t_in && sa <= t_out) {
+                    ++seen;
+                    const bool x = dist64<DP, ND>(xa, cand[v]) <= dc2;
+                    in += x ? 1u : 0u;
+                    cc[v >> 1] += (x ? 1u : 0u) << (16 * (v & 1));
+                  }
+                  if (sb > t_in && sb <= t_out) {
+                    seen += 0x10000u;
+                    const bool x = dist64<DP, ND>(xb, cand[v]) <= dc2;
+                    in += x ? 0x10000u : 0u;
+                    cc[v >> 1] += (x ? 1u : 0u) << (16 * (v & 1));
+                  }
+                }
+                in = __reduce_add_sync(kFull, in);
+                seen = __reduce_add_sync(kFull, seen);
+                cnt_a += (int32_t)(in & 0xffffu);
+                cnt_b += (int32_t)(in >> 16);
+                if (lane == 0) band += (seen & 0xffffu) + (seen >> 16);
+              }
+            }
+            if (lane == j) acc += cnt_a;
+            if (two && lane == j + 1) acc += cnt_b;
+          }
+          // the candidates' counts, at their positions (found again in the run table)
+          {
+            const uint32_t e0 = w0 + lane;
+            int lo = 0, hi = ntab - 1;
+            while (lo < hi) {
+              const int mid = (lo + hi + 1) >> 1;
+              if (tab.pre[mid] <= e0) lo = mid;
+              else hi = mid - 1;
+            }
+            int r = lo;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+              const uint32_t c = (cc[v >> 1] >> (16 * (v & 1))) & 0xffffu;
+              const uint32_t ev = e0 + 32u * v;
+              if (ev >= total) break;
+              while (r + 1 < ntab && tab.pre[r + 1] <= ev) ++r;
+              if (c) atomicAdd(&cnt2[2 * (size_t)(tab.start[r] + (ev - tab.pre[r]))], c);
+            }
+          }
+        }
+      };
+      // the block's cells after A (Morton order)
+      const int nb = filter_runs<G>(rt, nr, u, rt2, lane, [&](const uint32_t* cc) {
+        return morton<G>(cc) > cell;
+      });
+      scan(rt2, nb, std::false_type());
+      // A itself: its points after the segment's first query
+      {
+        const uint2 run = clip_run(hash_find(hkeys, hvals, hmask, hb | cell), n);
+        const uint32_t a0 = max(run.x, p0 + (uint32_t)s + 1u);
+        __syncwarp();
+        if (lane == 0) {
+          rt2.pre[0] = 0u;
+          rt2.start[0] = a0;
+          rt2.cell[0] = 0u;
+          rt2.pre[1] = run.y > a0 ? run.y - a0 : 0u;
+        }
+        __syncwarp();
+        scan(rt2, 1, std::true_type());
+      }
+      s = e;
+    }
+    if (valid) atomicAdd(&cnt2[2 * (size_t)p], (uint32_t)acc);
+  }
+  if (lane == 0 && pairs) atomicAdd(&ctr->pairs, pairs);
+  if constexpr (!F64) {
+    if (lane == 0 && band) atomicAdd(&ctr->band_pairs, band);
+  }
+}
+
+// Counts of the pair layout -> rho (by output id) and the order keys.
+__global__ void k_pairs_finish(const uint32_t* __restrict__ sid, uint32_t n, int32_t* __restrict__ rho_out,
+                               unsigned long long* __restrict__ skey) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const uint32_t c = reinterpret_cast<const uint32_t*>(skey)[2 * (size_t)p];
+    const uint32_t id = sid[p];
+    rho_out[id] = (int32_t)c;
+    skey[p] = order_key((int32_t)c, id);
+  }
+}
+
 __global__ void k_keys_from_rho(const int32_t* __restrict__ rho, const uint32_t* __restrict__ sid,
                                 uint32_t n, unsigned long long* __restrict__ skey) {
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
@@ -303,7 +516,18 @@ void density_dg(bool fp64, int layout, const float* spts, const unsigned long lo
                 const unsigned long long* hkeys, const uint2* hvals, int32_t* rho_out,
                 unsigned long long* skey, Counters* ctr, cudaStream_t st) {
   const unsigned grid = grid_for(cv.nchunk, kWarps, 152u * 64u);
-  if (layout == kLayoutSegment) {
+  if (layout == kLayoutPairs) {
+    cudaMemsetAsync(skey, 0, sizeof(unsigned long long) * cv.N, st);
+    uint32_t* cnt2 = reinterpret_cast<uint32_t*>(skey);
+    if (fp64)
+      k_density_pairs<DP, G, true><<<grid, kThreads, 0, st>>>(spts, scode, cv, cuts, hi, hkeys, hvals,
+                                                              cnt2, ctr);
+    else
+      k_density_pairs<DP, G, false><<<grid, kThreads, 0, st>>>(spts, scode, cv, cuts, hi, hkeys, hvals,
+                                                               cnt2, ctr);
+    k_pairs_finish<<<grid_for(cv.N, 256, 152u * 16u), 256, 0, st>>>(sid, cv.N, rho_out, skey);
+    count_launches(1);
+  } else if (layout == kLayoutSegment) {
     if (fp64)
       k_density_seg<DP, G, true><<<grid, kThreads, 0, st>>>(spts, scode, sid, cv, cuts, hi, hkeys,
                                                             hvals, rho_out, skey, ctr);

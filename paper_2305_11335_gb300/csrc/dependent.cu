@@ -171,6 +171,7 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
            const HashInfo* __restrict__ hi, const unsigned long long* __restrict__ hkeys,
            const uint2* __restrict__ hvals, int32_t* __restrict__ lambda,
            double* __restrict__ delta, FarQueue q, Counters* ctr) {
+  constexpr int ND = real_dims<DP, G>();
   constexpr int kNearCap = DP == 8 ? 128 : 256;
   __shared__ __align__(16) float s_pts[kNearWarps * kNearCap * DP];
   __shared__ unsigned long long s_key[kNearWarps * kNearCap];
@@ -251,9 +252,9 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
               const unsigned long long kt = wkey[i];
               const Pt<DP> x = window_pt<DP>(wpts, i);
               if constexpr (F64) {
-                if (kt > Kl) acc64.add(dist64<DP>(me, x), key_id(kt));
+                if (kt > Kl) acc64.add(dist64<DP, ND>(me, x), key_id(kt));
               } else {
-                const float d32 = dist32<DP>(me, x);
+                const float d32 = dist32<DP, ND>(me, x);
                 acc.add(kt > Kl ? d32 : INFINITY, key_id(kt));
               }
             }
@@ -318,7 +319,7 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
         if (settled) {
           const uint32_t o = acc.o1 - (uint32_t)I.out;
           lambda[id] = (int32_t)o;
-          delta[id] = sqrt(dist64<DP>(me, input_pt<DP>(pts, dtype, I.coord, I.d, o)));
+          delta[id] = sqrt(dist64<DP, ND>(me, input_pt<DP>(pts, dtype, I.coord, I.d, o)));
         }
       }
     } else if (valid) {
@@ -369,6 +370,7 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
                const HashInfo* __restrict__ hi, const unsigned long long* __restrict__ hkeys,
                const uint2* __restrict__ hvals, int32_t* __restrict__ lambda,
                double* __restrict__ delta, FarQueue q, Counters* ctr) {
+  constexpr int ND = real_dims<DP, G>();
   constexpr int V = near_seg_v<DP>();
   constexpr uint32_t W = 32u * V;
   __shared__ RunTable s_rt[kNearWarps];
@@ -454,8 +456,8 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
 #pragma unroll
               for (int v = 0; v < V; ++v) {
                 if (v >= vn) break;
-                if (ck[v] > Ka) ea.add(dist64<DP>(xa, cand[v]), key_id(ck[v]));
-                if (ck[v] > Kb) eb.add(dist64<DP>(xb, cand[v]), key_id(ck[v]));
+                if (ck[v] > Ka) ea.add(dist64<DP, ND>(xa, cand[v]), key_id(ck[v]));
+                if (ck[v] > Kb) eb.add(dist64<DP, ND>(xb, cand[v]), key_id(ck[v]));
               }
               ea.merge_warp();
               eb.merge_warp();
@@ -468,8 +470,8 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
 #pragma unroll
               for (int v = 0; v < V; ++v) {
                 if (v >= vn) break;
-                const float da = dist32<DP>(xa, cand[v]);
-                const float db = dist32<DP>(xb, cand[v]);
+                const float da = dist32<DP, ND>(xa, cand[v]);
+                const float db = dist32<DP, ND>(xb, cand[v]);
                 const uint32_t id = key_id(ck[v]);
                 ma.add(ck[v] > Ka ? da : INFINITY, id);
                 mb.add(ck[v] > Kb ? db : INFINITY, id);
@@ -557,7 +559,7 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
           const uint32_t o = best.o1 - (uint32_t)I.out;
           const Pt<DP> me = load_pt<DP>(spts, p);
           lambda[id] = (int32_t)o;
-          delta[id] = sqrt(dist64<DP>(me, input_pt<DP>(pts, dtype, I.coord, I.d, o)));
+          delta[id] = sqrt(dist64<DP, ND>(me, input_pt<DP>(pts, dtype, I.coord, I.d, o)));
         }
       }
     } else if (valid) {

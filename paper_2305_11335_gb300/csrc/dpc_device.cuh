@@ -325,11 +325,18 @@ __device__ __forceinline__ Pt<DP> load_pt(const float* __restrict__ spts, uint32
 
 // float32 filter value: any evaluation order, contraction allowed; its error
 // against the exact squared distance is covered by the bands in CutGeom.
-template <int DP>
+// Coordinates that can be nonzero in a class of padded dimension DP with G
+// gridded axes: every instance of a class with fewer than 4 gridded axes has
+// d = G (the rest is zero padding); from 4 gridded axes on, up to DP.
+template <int DP, int G>
+constexpr int real_dims() { return G < 4 ? G : DP; }
+
+// ND <= DP leading coordinates (the others are padding zeros that add 0).
+template <int DP, int ND = DP>
 __device__ __forceinline__ float dist32(const Pt<DP>& a, const Pt<DP>& b) {
   float s = 0.f;
 #pragma unroll
-  for (int k = 0; k < DP; ++k) {
+  for (int k = 0; k < ND; ++k) {
     float t = a.x[k] - b.x[k];
     s = fmaf(t, t, s);
   }
@@ -339,11 +346,11 @@ __device__ __forceinline__ float dist32(const Pt<DP>& a, const Pt<DP>& b) {
 // The canonical binary64 squared distance: t_k = x_k - y_k, s = ((t0*t0 + t1*t1) + ...)
 // in increasing k, each step rounded to nearest, never contracted.  Padding
 // coordinates are zero and add exactly 0.
-template <int DP>
+template <int DP, int ND = DP>
 __device__ __forceinline__ double dist64(const Pt<DP>& a, const Pt<DP>& b) {
   double s = 0.0;
 #pragma unroll
-  for (int k = 0; k < DP; ++k) {
+  for (int k = 0; k < ND; ++k) {
     double t = __dsub_rn((double)a.x[k], (double)b.x[k]);
     s = __dadd_rn(s, __dmul_rn(t, t));
   }

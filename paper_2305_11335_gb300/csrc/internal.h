@@ -43,6 +43,8 @@ void launch_setup(const ClassView& cv, CutGeom* cuts, int ncut, const CutHost* h
 // level and block radius of one cutoff (cuts: [ninst]) again: rpref = 0 the
 // default rule, rpref > 0 the finest level whose block radius is <= rpref
 void launch_set_radius(const ClassView& cv, CutGeom* cuts, int rpref, cudaStream_t st);
+// near-dependent search `shift` grid levels finer than the density's (0: same)
+void launch_near_level(const ClassView& cv, CutGeom* cuts, int shift, cudaStream_t st);
 void launch_codes(const void* pts, int dtype, const ClassView& cv, int g, unsigned long long* codes,
                   uint32_t* ids, cudaStream_t st);
 void launch_gather(const void* pts, int dtype, const ClassView& cv, int dp,
@@ -88,7 +90,9 @@ void launch_tree_maxkey(const unsigned long long* skey, const float* spts, int d
 //            search of the far phase
 //   tensor   (density, 5-8 dimensions, float32 filter) the distance tiles on the
 //            tensor cores (tc_density.cu); other cases fall back to segment
-enum { kLayoutUnion = 1, kLayoutSegment = 2, kLayoutTree = 3, kLayoutTensor = 4 };
+//   pairs    (density only) the segment layout counting every unordered pair
+//            once, for both of its points (density.cu, k_density_pairs)
+enum { kLayoutUnion = 1, kLayoutSegment = 2, kLayoutTree = 3, kLayoutTensor = 4, kLayoutPairs = 5 };
 
 // ---- density (density.cu) -------------------------------------------------------
 // rho of every point for one cutoff (cuts: [ninst]); rho_out is indexed by

@@ -67,7 +67,7 @@ def test_argument_errors_are_host_side(lib):
     assert _call_run(lib, _batch(cuts=(math.inf,))) == dpc.DPC_ERR_ARG
     assert _call_run(lib, _batch(), dtype=7) == dpc.DPC_ERR_ARG
     assert _call_run(lib, _batch(), flags=0xF) == dpc.DPC_ERR_UNSUPPORTED
-    assert _call_run(lib, _batch(), flags=1 << 20) == dpc.DPC_ERR_ARG
+    assert _call_run(lib, _batch(), flags=1 << 24) == dpc.DPC_ERR_ARG
     assert _call_run(lib, _batch(), ptr=0) == dpc.DPC_ERR_ARG
     b = _batch()
     assert _call_run(lib, b, params=dpc.make_params(b, 1, 1, math.nan)) == dpc.DPC_ERR_ARG

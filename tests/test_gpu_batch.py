@@ -78,7 +78,7 @@ def test_batch_mixed_dims_float(precision, layout):
     check_run(sizes, dims, insts, cuts, np.float32, precision, 11, layout)
 
 
-@pytest.mark.parametrize("layout", ["union", "segment", "tree", "tensor"])
+@pytest.mark.parametrize("layout", ["union", "segment", "tree", "tensor", "pairs"])
 def test_batch_int_ties(layout):
     sizes, dims, insts, cuts = make_batch(2, 30, [2, 3], dtype=np.int32, max_n=1500)
     check_run(sizes, dims, insts, cuts, np.int32, "fp32", 12, layout)

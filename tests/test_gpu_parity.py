@@ -222,7 +222,7 @@ def test_stats():
     assert 0 < s["far_queries"] < 20000
 
 
-@pytest.mark.parametrize("layout", ["union", "segment", "tree", "tensor"])
+@pytest.mark.parametrize("layout", ["union", "segment", "tree", "tensor", "pairs"])
 @pytest.mark.parametrize("radius", [1, 2, 3, 5])
 def test_block_radius_does_not_change_results(radius, layout):
     """Every block radius (grid level) and both kernel layouts give the
@@ -237,6 +237,25 @@ def test_block_radius_does_not_change_results(radius, layout):
             assert_same({k: v[c].cpu().numpy() for k, v in out.items()}, ref, "d=%d r=%d cut %d" % (d, radius, c))
         st = dpc.dpc_get_stats()
         assert 1 <= st["block_radius"] <= (5 if d <= 2 else (2 if d == 3 else 1))
+
+
+@pytest.mark.parametrize("layout", ["union", "segment"])
+@pytest.mark.parametrize("shift", [0, 1, 2])
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_near_shift_does_not_change_results(shift, layout, precision):
+    """The near phase on cells one or two levels finer than the density's
+    (more queries left to the tree search) gives the oracle's result."""
+    rng = np.random.default_rng(77)
+    cases = [(W.random_blobs(4000, 2, 950), 0.03), (W.random_blobs(4000, 3, 951), 0.06),
+             (W.random_blobs(2500, 5, 952), 0.12), (rng.integers(0, 40, (3000, 2)).astype(np.int32), 2.0)]
+    for pts, dc in cases:
+        refs = [oracle.run(pts, c, 2, 3, 0.1) for c in (dc, dc * 1.3)]
+        t = torch.from_numpy(pts).cuda()
+        out = dpc.run(t, [dc, dc * 1.3], 2, 3, 0.1, layout=layout, near_shift=shift, precision=precision)
+        for c, ref in enumerate(refs):
+            assert_same({k: v[c].cpu().numpy() for k, v in out.items()}, ref,
+                        "d=%d shift=%d cut %d" % (pts.shape[1], shift, c))
+        assert dpc.dpc_get_stats()["near_shift"] == shift
 
 
 def test_autotune_keeps_results_and_caches():
