@@ -160,6 +160,7 @@ struct Choice {
   int dlay = 0;  // density layout (kLayout*)
   int nlay = 0;  // near-phase layout
   int ns = 0;    // near-phase grid levels below the density's
+  int sc = 0;    // segment layouts: cells a segment's union may hold (0: one cell)
 };
 
 struct Workspace {
@@ -702,15 +703,15 @@ void cells_step(Workspace* w, const ClassPlan& c, const ClassView& cv, const Cut
 }
 
 void density_step(Workspace* w, const ClassPlan& c, const ClassView& cv, const CutGeom* cuts,
-                  bool fp64, int layout, int32_t* rho) {
+                  bool fp64, int layout, int seg_cells, int32_t* rho) {
   Phase ph(w, DPC_PHASE_DENSITY);
   launch_density(c.dp, c.g, fp64, layout, w->spts, w->scode, w->sid, cv, cuts, w->hinfo, w->hkeys,
-                 w->hvals, w->pieces, rho, w->skey, w->ctr, w->stream);
+                 w->hvals, w->pieces, rho, w->skey, w->ctr, w->stream, seg_cells);
 }
 
 void dependent_step(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cuts,
                     const void* pts, int dtype, int32_t rho_skip, bool fp64, int layout, int nshift,
-                    int32_t* lambda, double* delta) {
+                    int seg_cells, int32_t* lambda, double* delta) {
   cudaStream_t st = w->stream;
   {
     Phase ph(w, DPC_PHASE_MAXKEY);
@@ -725,7 +726,8 @@ void dependent_step(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGe
   {
     Phase ph(w, DPC_PHASE_NEAR);
     launch_dep_near(c.dp, c.g, fp64, layout, w->spts, w->scode, w->skey, cv, rho_skip, pts, dtype,
-                    cuts, w->hinfo, w->hkeys, w->hvals, lambda, delta, queue_of(w), w->ctr, st);
+                    cuts, w->hinfo, w->hkeys, w->hvals, lambda, delta, queue_of(w), w->ctr, st,
+                    seg_cells);
   }
   {
     Phase ph(w, DPC_PHASE_FAR);
@@ -787,6 +789,8 @@ struct NearTrial {
 // dimensions up; the near phase in segments in 3, union otherwise.
 inline int default_dlayout(int g) { return g >= 2 ? kLayoutSegment : kLayoutUnion; }
 inline int default_nlayout(int g) { return g == 3 ? kLayoutSegment : kLayoutUnion; }
+// segments of the segment layouts span cells while their union fits this
+inline int default_seg_cells(int g) { return g == 3 ? 48 : 0; }
 
 // The grid level and kernel layouts of one (class, cutoff): a fixed radius or
 // layout from the flags, else the autotuned choice (measured now when the
@@ -808,6 +812,7 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
   ch.nlay = (forced && forced != kLayoutTensor && forced != kLayoutPairs) ? forced
                                                                           : default_nlayout(c.g);
   ch.ns = forced_ns ? forced_ns - 1 : 0;
+  ch.sc = default_seg_cells(c.g);
   const std::string key = (near ? "R/" : "D/") + tune_key(c, b, cut);
   auto it = w->tuned.find(key);
   const bool fixed = ch.r != 0 || forced || forced_ns;
@@ -834,7 +839,8 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
       for (int l = 0; l < 4; ++l) {
         if (l < ndl)
           launch_density(c.dp, c.g, fp64, dlays[l], w->spts, w->scode, w->sid, cv, cuts, w->hinfo,
-                         w->hkeys, w->hvals, w->pieces, rho_scratch, w->skey, w->ctr, st);
+                         w->hkeys, w->hvals, w->pieces, rho_scratch, w->skey, w->ctr, st,
+                         default_seg_cells(c.g));
         if (timed) cudaEventRecord(w->tune_ev[2 + l], st);
       }
       if (!near) return;
@@ -853,7 +859,7 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
           if (sh == 0 || nlays[l] != kLayoutTree) {
             launch_dep_near(c.dp, c.g, fp64, nlays[l], w->spts, w->scode, w->skey, cv, 0, near->pts,
                             near->dtype, cuts, w->hinfo, w->hkeys, w->hvals, near->lambda,
-                            near->delta, queue_of(w), w->ctr, st);
+                            near->delta, queue_of(w), w->ctr, st, default_seg_cells(c.g));
             launch_dep_far(c.dp, fp64, w->spts, w->scode, w->skey, cv, cuts, w->nodes, w->nbox,
                            w->roots, queue_of(w), near->lambda, near->delta, w->ctr, st);
           }
@@ -1011,7 +1017,7 @@ int dpc_density(const void* pts, int dtype, const dpc_batch* b, int32_t* rho, ui
       CutGeom* cuts = w->cuts + (size_t)k * cv.ninst;
       const Choice ch = choose(w, c, cv, cuts, b, k, fp64, rho + (size_t)k * N, flags);
       cells_step(w, c, cv, cuts);
-      density_step(w, c, cv, cuts, fp64, ch.dlay, rho + (size_t)k * N);
+      density_step(w, c, cv, cuts, fp64, ch.dlay, ch.sc, rho + (size_t)k * N);
     }
   }
   return finish(w, flags);
@@ -1043,7 +1049,8 @@ int dpc_dependent(const void* pts, int dtype, const dpc_batch* b, int32_t dcut_i
                              flags & ~DPC_FLAG_AUTOTUNE, nullptr);
     cells_step(w, c, cv, w->cuts);
     launch_keys_from_rho(rho, w->sid, cv.N, w->skey, w->stream);
-    dependent_step(w, c, cv, w->cuts, pts, dtype, rho_skip, fp64, ch.nlay, ch.ns, lambda, delta);
+    dependent_step(w, c, cv, w->cuts, pts, dtype, rho_skip, fp64, ch.nlay, ch.ns, ch.sc, lambda,
+                   delta);
   }
   return finish(w, flags);
 }
@@ -1091,8 +1098,9 @@ static void run_classes(Workspace* w, const CallPlan& P, const void* pts, int dt
       const NearTrial nt{pts, dtype, lambda + o, delta + o};
       const Choice ch = choose(w, c, cv, cuts, b, k, fp64, rho + o, flags, &nt);
       cells_step(w, c, cv, cuts);
-      density_step(w, c, cv, cuts, fp64, ch.dlay, rho + o);
-      dependent_step(w, c, cv, cuts, pts, dtype, 0, fp64, ch.nlay, ch.ns, lambda + o, delta + o);
+      density_step(w, c, cv, cuts, fp64, ch.dlay, ch.sc, rho + o);
+      dependent_step(w, c, cv, cuts, pts, dtype, 0, fp64, ch.nlay, ch.ns, ch.sc, lambda + o,
+                     delta + o);
       labels_step(w, c, cv, k, one_params(params, c, P.ncut_all, k), rho + o, lambda + o,
                   delta + o, label + o);
     }

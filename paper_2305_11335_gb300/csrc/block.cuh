@@ -311,6 +311,69 @@ __device__ __forceinline__ bool in_block(const uint32_t* c0, const uint32_t* c, 
   return in;
 }
 
+// A segment of the chunk for the segment layouts: from lane s, the longest
+// run of whole cells (at least the first cell's lanes) whose bounding box,
+// grown by R and clipped to the grid, holds at most max_cells cells; u is set
+// to that union (it contains the block of every query of the segment, so a
+// search over it sees every point a query's own block holds).  max_cells <= 0
+// or a first block larger than max_cells: the first cell alone and its block.
+// The union only grows with the segment, so the ends that fit form a prefix.
+template <int G>
+__device__ __forceinline__ int super_segment(unsigned long long mycell, bool valid, int s, int nvalid,
+                                             int R, int cmax, int max_cells, int lane, Union<G>& u) {
+  const unsigned long long cell = __shfl_sync(kFull, mycell, s);
+  const int e1 = s + __popc(__ballot_sync(kFull, valid && mycell == cell));
+  int last = e1 - 1;
+  int lo[G], hi[G];
+  if (max_cells > 0 && e1 < nvalid) {
+    uint32_t mc[G];
+    unmorton<G>(valid ? mycell : cell, mc);
+    const bool in = valid && lane >= s;
+#pragma unroll
+    for (int a = 0; a < G; ++a) {
+      lo[a] = in ? (int)mc[a] : 0x7fffffff;
+      hi[a] = in ? (int)mc[a] : -1;
+    }
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+      for (int a = 0; a < G; ++a) {
+        const int tl = __shfl_up_sync(kFull, lo[a], d);
+        const int th = __shfl_up_sync(kFull, hi[a], d);
+        if (lane >= d) {
+          lo[a] = min(lo[a], tl);
+          hi[a] = max(hi[a], th);
+        }
+      }
+    }
+    long long size = 1;
+#pragma unroll
+    for (int a = 0; a < G; ++a) size *= (long long)(min(hi[a] + R, cmax) - max(lo[a] - R, 0) + 1);
+    const unsigned long long next = __shfl_down_sync(kFull, mycell, 1);
+    const bool cell_end = valid && lane >= e1 - 1 && (lane + 1 >= nvalid || next != mycell);
+    const unsigned ok = __ballot_sync(kFull, cell_end && size <= (long long)max_cells);
+    if (ok & (1u << (e1 - 1))) last = 31 - __clz((int)ok);
+  }
+  if (last == e1 - 1) {  // the first cell and its block
+    uint32_t c0[G];
+    unmorton<G>(cell, c0);
+    block_union<G>(c0, R, cmax, u);
+    return e1;
+  }
+  int n = 1;
+#pragma unroll
+  for (int a = 0; a < G; ++a) {
+    const int l = max(__shfl_sync(kFull, lo[a], last) - R, 0);
+    const int h = min(__shfl_sync(kFull, hi[a], last) + R, cmax);
+    u.lo[a] = l;
+    u.w[a] = h - l + 1;
+    u.inv[a] = (65536 + u.w[a] - 1) / u.w[a];
+    n *= u.w[a];
+  }
+  u.ncell = n;
+  return last + 1;
+}
+
 // The warp's groups of lanes: the whole chunk if its union is small enough,
 // else one group per cell.  group(active, union) is called for each group.
 // `valid` marks lanes holding a point (a prefix of the warp), `active` the

@@ -167,7 +167,7 @@ k_density_seg(const float* __restrict__ spts, const unsigned long long* __restri
               const uint32_t* __restrict__ sid, ClassView cv, const CutGeom* __restrict__ cuts,
               const HashInfo* __restrict__ hi, const unsigned long long* __restrict__ hkeys,
               const uint2* __restrict__ hvals, int32_t* __restrict__ rho_out,
-              unsigned long long* __restrict__ skey, Counters* ctr) {
+              unsigned long long* __restrict__ skey, Counters* ctr, int seg_cells) {
   constexpr int ND = real_dims<DP, G>();
   constexpr int V = seg_v<DP>();
   constexpr uint32_t W = 32u * V;
@@ -198,12 +198,8 @@ k_density_seg(const float* __restrict__ spts, const unsigned long long* __restri
     int32_t acc = 0;  // lane j: the count of query p0 + j
     int s = 0;
     while (s < nvalid) {
-      const unsigned long long cell = __shfl_sync(kFull, mycell, s);
-      const int e = s + __popc(__ballot_sync(kFull, valid && mycell == cell));  // queries s .. e-1
-      uint32_t c0[G];
-      unmorton<G>(cell, c0);
       Union<G> u;
-      block_union<G>(c0, R, cmax, u);
+      const int e = super_segment<G>(mycell, valid, s, nvalid, R, cmax, seg_cells, lane, u);  // queries s .. e-1
       const int nr = union_runs<G>(u, hkeys, hvals, hmask, hb, n, lane, rt);
       const uint32_t total = rt.pre[nr];
       pairs += (unsigned long long)(e - s) * total;
@@ -514,7 +510,7 @@ template <int DP, int G>
 void density_dg(bool fp64, int layout, const float* spts, const unsigned long long* scode,
                 const uint32_t* sid, const ClassView& cv, const CutGeom* cuts, const HashInfo* hi,
                 const unsigned long long* hkeys, const uint2* hvals, int32_t* rho_out,
-                unsigned long long* skey, Counters* ctr, cudaStream_t st) {
+                unsigned long long* skey, Counters* ctr, int seg_cells, cudaStream_t st) {
   const unsigned grid = grid_for(cv.nchunk, kWarps, 152u * 64u);
   if (layout == kLayoutPairs) {
     cudaMemsetAsync(skey, 0, sizeof(unsigned long long) * cv.N, st);
@@ -530,10 +526,10 @@ void density_dg(bool fp64, int layout, const float* spts, const unsigned long lo
   } else if (layout == kLayoutSegment) {
     if (fp64)
       k_density_seg<DP, G, true><<<grid, kThreads, 0, st>>>(spts, scode, sid, cv, cuts, hi, hkeys,
-                                                            hvals, rho_out, skey, ctr);
+                                                            hvals, rho_out, skey, ctr, seg_cells);
     else
       k_density_seg<DP, G, false><<<grid, kThreads, 0, st>>>(spts, scode, sid, cv, cuts, hi, hkeys,
-                                                             hvals, rho_out, skey, ctr);
+                                                             hvals, rho_out, skey, ctr, seg_cells);
   } else {
     if (fp64)
       k_density<DP, G, true><<<grid, kThreads, 0, st>>>(spts, scode, sid, cv, cuts, hi, hkeys, hvals,
@@ -551,7 +547,7 @@ void launch_density(int dp, int g, bool fp64, int layout, const float* spts,
                     const unsigned long long* scode, const uint32_t* sid, const ClassView& cv,
                     const CutGeom* cuts, HashInfo* hi, const unsigned long long* hkeys,
                     const uint2* hvals, uint2* pieces, int32_t* rho_out,
-                    unsigned long long* skey, Counters* ctr, cudaStream_t st) {
+                    unsigned long long* skey, Counters* ctr, cudaStream_t st, int seg_cells) {
   if (cv.N == 0) return;
   if (layout == kLayoutTensor) {
     if (dp == 8 && !fp64 && pieces) {
@@ -560,11 +556,11 @@ void launch_density(int dp, int g, bool fp64, int layout, const float* spts,
     }
     layout = kLayoutSegment;
   }
-  if (g == 1) density_dg<2, 1>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
-  else if (g == 2) density_dg<2, 2>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
-  else if (g == 3) density_dg<4, 3>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
-  else if (dp == 4) density_dg<4, 4>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
-  else density_dg<8, 4>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, st);
+  if (g == 1) density_dg<2, 1>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, seg_cells, st);
+  else if (g == 2) density_dg<2, 2>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, seg_cells, st);
+  else if (g == 3) density_dg<4, 3>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, seg_cells, st);
+  else if (dp == 4) density_dg<4, 4>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, seg_cells, st);
+  else density_dg<8, 4>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, seg_cells, st);
 }
 
 void launch_keys_from_rho(const int32_t* rho, const uint32_t* sid, uint32_t n,

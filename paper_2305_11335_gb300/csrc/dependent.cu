@@ -171,7 +171,6 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
            const HashInfo* __restrict__ hi, const unsigned long long* __restrict__ hkeys,
            const uint2* __restrict__ hvals, int32_t* __restrict__ lambda,
            double* __restrict__ delta, FarQueue q, Counters* ctr) {
-  constexpr int ND = real_dims<DP, G>();
   constexpr int kNearCap = DP == 8 ? 128 : 256;
   __shared__ __align__(16) float s_pts[kNearWarps * kNearCap * DP];
   __shared__ unsigned long long s_key[kNearWarps * kNearCap];
@@ -252,9 +251,9 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
               const unsigned long long kt = wkey[i];
               const Pt<DP> x = window_pt<DP>(wpts, i);
               if constexpr (F64) {
-                if (kt > Kl) acc64.add(dist64<DP, ND>(me, x), key_id(kt));
+                if (kt > Kl) acc64.add(dist64<DP>(me, x), key_id(kt));
               } else {
-                const float d32 = dist32<DP, ND>(me, x);
+                const float d32 = dist32<DP>(me, x);
                 acc.add(kt > Kl ? d32 : INFINITY, key_id(kt));
               }
             }
@@ -319,7 +318,7 @@ k_dep_near(const float* __restrict__ spts, const unsigned long long* __restrict_
         if (settled) {
           const uint32_t o = acc.o1 - (uint32_t)I.out;
           lambda[id] = (int32_t)o;
-          delta[id] = sqrt(dist64<DP, ND>(me, input_pt<DP>(pts, dtype, I.coord, I.d, o)));
+          delta[id] = sqrt(dist64<DP>(me, input_pt<DP>(pts, dtype, I.coord, I.d, o)));
         }
       }
     } else if (valid) {
@@ -369,8 +368,7 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
                const void* __restrict__ pts, int dtype, const CutGeom* __restrict__ cuts,
                const HashInfo* __restrict__ hi, const unsigned long long* __restrict__ hkeys,
                const uint2* __restrict__ hvals, int32_t* __restrict__ lambda,
-               double* __restrict__ delta, FarQueue q, Counters* ctr) {
-  constexpr int ND = real_dims<DP, G>();
+               double* __restrict__ delta, FarQueue q, Counters* ctr, int seg_cells) {
   constexpr int V = near_seg_v<DP>();
   constexpr uint32_t W = 32u * V;
   __shared__ RunTable s_rt[kNearWarps];
@@ -422,13 +420,14 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
     int s = 0;
     while (s < nvalid) {
       const unsigned long long cell = __shfl_sync(kFull, mycell, s);
-      const unsigned seg = __ballot_sync(kFull, valid && mycell == cell);  // lanes s .. e-1
-      const int e = s + __popc(seg);
+      Union<G> u;
+      const int e = super_segment<G>(mycell, valid, s, nvalid, R, cmax, seg_cells, lane, u);
+      const unsigned seg = (e >= 32 ? 0xffffffffu : ((1u << e) - 1u)) & ~((1u << s) - 1u);  // lanes s .. e-1
+      // one cell only: the own-cell-first passes below apply
+      const bool single = (__ballot_sync(kFull, valid && mycell == cell) & seg) == seg;
       if (__ballot_sync(kFull, valid && !skip) & seg) {
         uint32_t c0[G];
         unmorton<G>(cell, c0);
-        Union<G> u;
-        block_union<G>(c0, R, cmax, u);
         const int nr = union_runs<G>(u, hkeys, hvals, hmask, hb, n, lane, rt);
         // every candidate of a run table, window by window
         auto scan = [&](const RunTable& tab, int ntab) {
@@ -456,8 +455,8 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
 #pragma unroll
               for (int v = 0; v < V; ++v) {
                 if (v >= vn) break;
-                if (ck[v] > Ka) ea.add(dist64<DP, ND>(xa, cand[v]), key_id(ck[v]));
-                if (ck[v] > Kb) eb.add(dist64<DP, ND>(xb, cand[v]), key_id(ck[v]));
+                if (ck[v] > Ka) ea.add(dist64<DP>(xa, cand[v]), key_id(ck[v]));
+                if (ck[v] > Kb) eb.add(dist64<DP>(xb, cand[v]), key_id(ck[v]));
               }
               ea.merge_warp();
               eb.merge_warp();
@@ -470,8 +469,8 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
 #pragma unroll
               for (int v = 0; v < V; ++v) {
                 if (v >= vn) break;
-                const float da = dist32<DP, ND>(xa, cand[v]);
-                const float db = dist32<DP, ND>(xb, cand[v]);
+                const float da = dist32<DP>(xa, cand[v]);
+                const float db = dist32<DP>(xb, cand[v]);
                 const uint32_t id = key_id(ck[v]);
                 ma.add(ck[v] > Ka ? da : INFINITY, id);
                 mb.add(ck[v] > Kb ? db : INFINITY, id);
@@ -509,7 +508,7 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
           return same;
         };
         const bool mine = ((seg >> lane) & 1u) && !skip;
-        const int npass = rt.pre[nr] <= 8u * W ? 1 : 2;
+        const int npass = (!single || rt.pre[nr] <= 8u * W) ? 1 : 2;
         for (int pass = 0; pass < npass; ++pass) {
           int ntab;
           if (npass == 1) {
@@ -559,7 +558,7 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
           const uint32_t o = best.o1 - (uint32_t)I.out;
           const Pt<DP> me = load_pt<DP>(spts, p);
           lambda[id] = (int32_t)o;
-          delta[id] = sqrt(dist64<DP, ND>(me, input_pt<DP>(pts, dtype, I.coord, I.d, o)));
+          delta[id] = sqrt(dist64<DP>(me, input_pt<DP>(pts, dtype, I.coord, I.d, o)));
         }
       }
     } else if (valid) {
@@ -1058,17 +1057,17 @@ void near_dg(bool fp64, int layout, const float* spts, const unsigned long long*
              const unsigned long long* skey, const ClassView& cv, int32_t rho_skip,
              const void* pts, int dtype, const CutGeom* cuts, const HashInfo* hi,
              const unsigned long long* hkeys, const uint2* hvals, int32_t* lambda, double* delta,
-             FarQueue q, Counters* ctr, cudaStream_t st) {
+             FarQueue q, Counters* ctr, int seg_cells, cudaStream_t st) {
   const unsigned grid = grid_for(cv.nchunk, kNearWarps, 152u * 64u);
   if (layout == kLayoutSegment) {
     if (fp64)
       k_dep_near_seg<DP, G, true><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, cv, rho_skip, pts,
                                                                  dtype, cuts, hi, hkeys, hvals, lambda,
-                                                                 delta, q, ctr);
+                                                                 delta, q, ctr, seg_cells);
     else
       k_dep_near_seg<DP, G, false><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, cv, rho_skip, pts,
                                                                   dtype, cuts, hi, hkeys, hvals, lambda,
-                                                                  delta, q, ctr);
+                                                                  delta, q, ctr, seg_cells);
   } else {
     if (fp64)
       k_dep_near<DP, G, true><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, cv, rho_skip, pts,
@@ -1110,18 +1109,18 @@ void launch_dep_near(int dp, int g, bool fp64, int layout, const float* spts,
                      const ClassView& cv, int32_t rho_skip, const void* pts, int dtype,
                      const CutGeom* cuts, const HashInfo* hi, const unsigned long long* hkeys,
                      const uint2* hvals, int32_t* lambda, double* delta, FarQueue q, Counters* ctr,
-                     cudaStream_t st) {
+                     cudaStream_t st, int seg_cells) {
   if (cv.N == 0) return;
   cudaMemsetAsync(&ctr->queue_n, 0, sizeof(unsigned int), st);
   cudaMemsetAsync(&ctr->queue2_n, 0, sizeof(unsigned int), st);
   if (layout == kLayoutTree) {
     k_near_to_far<<<grid_for((uint64_t)cv.nchunk * 32u, 256, 152u * 16u), 256, 0, st>>>(
         skey, cv, cuts, rho_skip, lambda, delta, q, ctr);
-  } else if (g == 1) near_dg<2, 1>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
-  else if (g == 2) near_dg<2, 2>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
-  else if (g == 3) near_dg<4, 3>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
-  else if (dp == 4) near_dg<4, 4>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
-  else near_dg<8, 4>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, st);
+  } else if (g == 1) near_dg<2, 1>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, seg_cells, st);
+  else if (g == 2) near_dg<2, 2>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, seg_cells, st);
+  else if (g == 3) near_dg<4, 3>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, seg_cells, st);
+  else if (dp == 4) near_dg<4, 4>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, seg_cells, st);
+  else near_dg<8, 4>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, seg_cells, st);
   count_launches(1);
 }
 

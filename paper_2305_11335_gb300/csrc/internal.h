@@ -92,6 +92,9 @@ void launch_tree_maxkey(const unsigned long long* skey, const float* spts, int d
 //            tensor cores (tc_density.cu); other cases fall back to segment
 //   pairs    (density only) the segment layout counting every unordered pair
 //            once, for both of its points (density.cu, k_density_pairs)
+// seg_cells (segment layouts): a segment may span several consecutive cells
+// while their bounding box grown by R holds at most seg_cells cells (0: one
+// cell per segment)
 enum { kLayoutUnion = 1, kLayoutSegment = 2, kLayoutTree = 3, kLayoutTensor = 4, kLayoutPairs = 5 };
 
 // ---- density (density.cu) -------------------------------------------------------
@@ -101,7 +104,8 @@ void launch_density(int dp, int g, bool fp64, int layout, const float* spts,
                     const unsigned long long* scode, const uint32_t* sid, const ClassView& cv,
                     const CutGeom* cuts, HashInfo* hi, const unsigned long long* hkeys,
                     const uint2* hvals, uint2* pieces, int32_t* rho_out,
-                    unsigned long long* skey, Counters* ctr, cudaStream_t st);
+                    unsigned long long* skey, Counters* ctr, cudaStream_t st,
+                    int seg_cells = 0);
 // the tensor-core form of the density step (dp = 8, float32 filter only)
 // (pieces: scratch for the piece list, at least N / 128 + occupied cells entries)
 void launch_density_tc(int g, const float* spts, const uint32_t* sid, const ClassView& cv,
@@ -128,7 +132,8 @@ void launch_dep_near(int dp, int g, bool fp64, int layout, const float* spts,
                      const ClassView& cv, int32_t rho_skip, const void* pts, int dtype,
                      const CutGeom* cuts, const HashInfo* hi, const unsigned long long* hkeys,
                      const uint2* hvals, int32_t* lambda, double* delta, FarQueue q, Counters* ctr,
-                     cudaStream_t st);
+                     cudaStream_t st,
+                     int seg_cells = 0);
 void launch_dep_far(int dp, bool fp64, const float* spts, const unsigned long long* scode,
                     const unsigned long long* skey, const ClassView& cv, const CutGeom* cuts,
                     const Node* nodes, const float* nbox, const uint32_t* root, FarQueue q,
