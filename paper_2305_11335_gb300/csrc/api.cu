@@ -939,6 +939,7 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
         best.dlay = dlays[di];
         best.nlay = near ? nlays[ni] : default_nlayout(c.g);
         best.ns = near ? nsi : 0;
+        best.sc = default_seg_cells(c.g);
       }
     }
     if (failed) best = Choice();
