@@ -110,37 +110,69 @@ __device__ __forceinline__ uint32_t arrive(uint32_t* counter) {
   return old;
 }
 
+// One thread per internal node whose two children are both leaves (the
+// bottom of the tree: about a third of the nodes).  It computes that node and
+// walks up, carrying the node's results in registers.  A parent whose other
+// child is a leaf is computed at once; only at a parent with two internal
+// children do the two walks meet, and the second to arrive (an acq_rel atomic
+// counter) continues with the first's published results.
 template <int DP, bool BOX>
 __global__ void k_tree_up(const unsigned long long* __restrict__ skey,
                           const float* __restrict__ spts, uint32_t n, Node* nodes,
-                          const uint32_t* __restrict__ leaf_parent, uint32_t* visit, float* nbox) {
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-    uint32_t node = leaf_parent[t];
-    for (uint32_t depth = 0; depth < 2u * n + 64u; ++depth) {
-      if (arrive(&visit[node]) == 0u) break;  // first arrival: the sibling continues
-      const uint32_t l = nodes[node].left, r = nodes[node].right;
-      const unsigned long long kl =
-          (l & kLeafBit) ? skey[l & ~kLeafBit] : __ldcg(&nodes[l].maxkey);
-      const unsigned long long kr =
-          (r & kLeafBit) ? skey[r & ~kLeafBit] : __ldcg(&nodes[r].maxkey);
-      __stcg(&nodes[node].maxkey, kl > kr ? kl : kr);
+                          uint32_t* visit, float* nbox) {
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t + 1 < n; t += gridDim.x * blockDim.x) {
+    uint32_t node = t;
+    const uint32_t l0 = nodes[node].left, r0 = nodes[node].right;
+    if (!((l0 & kLeafBit) && (r0 & kLeafBit))) continue;
+    // this node from its two leaves
+    unsigned long long key;
+    float lo[DP], hi[DP];
+    {
+      const unsigned long long kl = skey[l0 & ~kLeafBit], kr = skey[r0 & ~kLeafBit];
+      key = kl > kr ? kl : kr;
       if constexpr (BOX) {
-        float lo[DP], hi[DP], lo2[DP], hi2[DP];
-        child_box<DP>(l, spts, nbox, lo, hi);
-        child_box<DP>(r, spts, nbox, lo2, hi2);
-        float v[2 * DP];
+        float lo2[DP], hi2[DP];
+        child_box<DP>(l0, spts, nbox, lo, hi);
+        child_box<DP>(r0, spts, nbox, lo2, hi2);
 #pragma unroll
         for (int a = 0; a < DP; ++a) {
-          v[a] = fminf(lo[a], lo2[a]);
-          v[DP + a] = fmaxf(hi[a], hi2[a]);
+          lo[a] = fminf(lo[a], lo2[a]);
+          hi[a] = fmaxf(hi[a], hi2[a]);
         }
+      }
+    }
+    for (uint32_t depth = 0; depth < 2u * n + 64u; ++depth) {
+      __stcg(&nodes[node].maxkey, key);
+      if constexpr (BOX) {
         float4* b = reinterpret_cast<float4*>(nbox) + (size_t)node * (DP / 2);
 #pragma unroll
-        for (int k = 0; k < DP / 2; ++k)
-          __stcg(b + k, make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
+        for (int k = 0; k < DP / 2; ++k) {
+          const float v0 = (4 * k < DP) ? lo[4 * k] : hi[4 * k - DP];
+          const float v1 = (4 * k + 1 < DP) ? lo[4 * k + 1] : hi[4 * k + 1 - DP];
+          const float v2 = (4 * k + 2 < DP) ? lo[4 * k + 2] : hi[4 * k + 2 - DP];
+          const float v3 = (4 * k + 3 < DP) ? lo[4 * k + 3] : hi[4 * k + 3 - DP];
+          __stcg(b + k, make_float4(v0, v1, v2, v3));
+        }
       }
       if (node == 0u) break;
-      node = nodes[node].parent;
+      const uint32_t par = nodes[node].parent;
+      const uint32_t pl = nodes[par].left, pr = nodes[par].right;
+      const uint32_t sib = (pl == node) ? pr : pl;
+      if (!(sib & kLeafBit) && arrive(&visit[par]) == 0u) break;  // the sibling's walk continues
+      // the parent from this node (registers) and its sibling
+      const unsigned long long ks =
+          (sib & kLeafBit) ? skey[sib & ~kLeafBit] : __ldcg(&nodes[sib].maxkey);
+      key = key > ks ? key : ks;
+      if constexpr (BOX) {
+        float lo2[DP], hi2[DP];
+        child_box<DP>(sib, spts, nbox, lo2, hi2);
+#pragma unroll
+        for (int a = 0; a < DP; ++a) {
+          lo[a] = fminf(lo[a], lo2[a]);
+          hi[a] = fmaxf(hi[a], hi2[a]);
+        }
+      }
+      node = par;
     }
   }
 }
@@ -167,10 +199,11 @@ template <int DP>
 void tree_up_dp(const unsigned long long* skey, const float* spts, uint32_t n, Node* nodes,
                 const uint32_t* leaf_parent, uint32_t* visit, float* nbox, bool boxes,
                 cudaStream_t st) {
+  (void)leaf_parent;
   if (boxes)
-    k_tree_up<DP, true><<<grid_for(n), kThreads, 0, st>>>(skey, spts, n, nodes, leaf_parent, visit, nbox);
+    k_tree_up<DP, true><<<grid_for(n - 1), kThreads, 0, st>>>(skey, spts, n, nodes, visit, nbox);
   else
-    k_tree_up<DP, false><<<grid_for(n), kThreads, 0, st>>>(skey, spts, n, nodes, leaf_parent, visit, nbox);
+    k_tree_up<DP, false><<<grid_for(n - 1), kThreads, 0, st>>>(skey, spts, n, nodes, visit, nbox);
 }
 
 void launch_tree_maxkey(const unsigned long long* skey, const float* spts, int dp, uint32_t n,
