@@ -1,16 +1,22 @@
 // sort.cu -- LSD radix sort of (64-bit code, 32-bit id) pairs by code.
 //
 // The radix-sort primitive of Section 3.2, used here to put the points in
-// Morton order.  Each 8-bit pass has three kernels:
-//   hist    per-tile digit counts, written digit-major [256][ntiles]
-//   scan    per digit, an exclusive scan over tiles + the digit total
-//   scatter stable rank of every item inside its tile (warp multi-split with
-//           __match_any_sync, warps in tile order), a shared-memory reorder,
-//           then coalesced runs to the global position
-// The number of passes (ceil((S + ib) / 8) for keys of S + ib bits, see
-// ClassGeom) is known only on the device: passes beyond it return at once,
-// so the launch sequence is fixed and the result lands in buffer
-// (passes & 1).
+// Morton order.  One read of the keys counts the digits of every pass
+// (k_rs_hist_all) and a small kernel turns those counts into each digit's
+// global start (k_rs_scan_all).  Then one kernel per 8-bit pass
+// (k_rs_onesweep): a CTA takes the next tile of 4096 items (an atomic tile
+// counter, so tiles start in order), ranks every item inside the tile (warp
+// multi-split with __match_any_sync, warps in tile order), publishes its digit
+// counts, and finds the count of every digit in all earlier tiles by looking
+// back over their published counts (decoupled look-back, after Merrill and
+// Garland's single-pass prefix scan: a tile that has its inclusive prefix
+// publishes it, so a look-back stops at the first such tile); then a
+// shared-memory reorder and coalesced runs to the global positions.  Every
+// wait on an earlier tile is bounded; a wait that gives up records
+// kStatusTimeout.  The number of passes (ceil((S + ib) / 8) for keys of
+// S + ib bits, see ClassGeom) is known only on the device: passes beyond it
+// return at once, so the launch sequence is fixed and the result lands in
+// buffer (passes & 1).
 #include "internal.h"
 
 namespace dpc {
@@ -24,59 +30,74 @@ constexpr int kRsTile = kRsThreads * kRsIpt;        // 4096 items per tile
 constexpr int kRsWarpItems = 32 * kRsIpt;           // 512 items per warp
 constexpr int kMaxPasses = 8;
 
+constexpr unsigned long long kFlagAgg = 1ull << 62;     // the tile's own counts
+constexpr unsigned long long kFlagPrefix = 2ull << 62;  // counts of this and every earlier tile
+constexpr unsigned long long kFlagMask = 3ull << 62;
+constexpr uint32_t kSpinLimit = 1u << 20;  // ld.acquire polls of one earlier tile
+
+// The sort's scratch: status[ntiles][256] (u64, reused by every pass), the
+// digit counts and starts of every pass [kMaxPasses][256], a tile counter per
+// pass.
+struct SortScratch {
+  unsigned long long* status;
+  uint32_t* count;
+  uint32_t* start;
+  uint32_t* tiles;
+};
+
+__host__ __device__ inline SortScratch sort_scratch(uint32_t* base, uint32_t ntiles) {
+  SortScratch z;
+  z.status = reinterpret_cast<unsigned long long*>(base);
+  z.count = base + (size_t)ntiles * 256u * 2u;
+  z.start = z.count + kMaxPasses * 256;
+  z.tiles = z.start + kMaxPasses * 256;
+  return z;
+}
+
+// Digit counts of every pass in one read of the keys.
 __global__ void __launch_bounds__(kRsThreads)
-k_rs_hist(const unsigned long long* __restrict__ keys, uint32_t n, int pass,
-          const ClassGeom* __restrict__ cls, uint32_t* __restrict__ hist, uint32_t ntiles) {
-  if (pass >= sort_passes(cls->S, cls->ib)) return;
-  __shared__ uint32_t cnt[kRsWarps][256];
-  for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&cnt[0][0])[i] = 0;
+k_rs_hist_all(const unsigned long long* __restrict__ keys, uint32_t n,
+              const ClassGeom* __restrict__ cls, uint32_t* __restrict__ count) {
+  __shared__ uint32_t cnt[kMaxPasses][256];
+  const int npass = sort_passes(cls->S, cls->ib);
+  for (int i = threadIdx.x; i < kMaxPasses * 256; i += kRsThreads) (&cnt[0][0])[i] = 0;
   __syncthreads();
-  const int shift = 8 * pass;
-  const int w = threadIdx.x >> 5;
-  const uint32_t base = blockIdx.x * kRsTile;
-#pragma unroll 4
-  for (int r = 0; r < kRsIpt; ++r) {
-    uint32_t i = base + r * kRsThreads + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[w][(keys[i] >> shift) & 255u], 1u);
+  for (uint32_t i = blockIdx.x * kRsThreads + threadIdx.x; i < n; i += gridDim.x * kRsThreads) {
+    const unsigned long long k = keys[i];
+    for (int p = 0; p < npass && p < kMaxPasses; ++p) atomicAdd(&cnt[p][(k >> (8 * p)) & 255u], 1u);
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < 256; d += kRsThreads) {
-    uint32_t s = 0;
-#pragma unroll
-    for (int k = 0; k < kRsWarps; ++k) s += cnt[k][d];
-    hist[(size_t)d * ntiles + blockIdx.x] = s;
+  for (int i = threadIdx.x; i < kMaxPasses * 256; i += kRsThreads) {
+    const uint32_t v = (&cnt[0][0])[i];
+    if (v) atomicAdd(&count[i], v);
   }
 }
 
-// One block per digit: exclusive scan of that digit's per-tile counts; the
-// digit total goes to hist[256 * ntiles + digit].
-__global__ void __launch_bounds__(kRsThreads)
-k_rs_scan(uint32_t* __restrict__ hist, uint32_t ntiles, int pass, const ClassGeom* __restrict__ cls) {
-  if (pass >= sort_passes(cls->S, cls->ib)) return;
-  __shared__ uint32_t part[kRsThreads];
-  const int d = blockIdx.x;
-  uint32_t* row = hist + (size_t)d * ntiles;
-  const uint32_t per = (ntiles + kRsThreads - 1) / kRsThreads;
-  const uint32_t lo = threadIdx.x * per;
-  const uint32_t hi = min(lo + per, ntiles);
-  uint32_t s = 0;
-  for (uint32_t t = lo; t < hi; ++t) s += row[t];
-  part[threadIdx.x] = s;
+// Exclusive scan of every pass's 256 digit counts (one CTA per pass).
+__global__ void __launch_bounds__(256) k_rs_scan_all(const uint32_t* __restrict__ count,
+                                                     uint32_t* __restrict__ start) {
+  __shared__ uint32_t part[256];
+  const int p = blockIdx.x;
+  const uint32_t v = count[p * 256 + threadIdx.x];
+  part[threadIdx.x] = v;
   __syncthreads();
-  // inclusive scan of the per-thread sums (Hillis-Steele)
-  for (int o = 1; o < kRsThreads; o <<= 1) {
-    uint32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
+  for (int o = 1; o < 256; o <<= 1) {
+    const uint32_t t = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
     __syncthreads();
-    part[threadIdx.x] += v;
+    part[threadIdx.x] += t;
     __syncthreads();
   }
-  uint32_t run = part[threadIdx.x] - s;  // exclusive
-  for (uint32_t t = lo; t < hi; ++t) {
-    uint32_t c = row[t];
-    row[t] = run;
-    run += c;
-  }
-  if (threadIdx.x == kRsThreads - 1) hist[(size_t)256 * ntiles + d] = part[kRsThreads - 1];
+  start[p * 256 + threadIdx.x] = part[threadIdx.x] - v;
+}
+
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
 }
 
 struct ScatterSmem {
@@ -84,14 +105,14 @@ struct ScatterSmem {
   uint32_t vals[kRsTile];
   uint32_t whist[kRsWarps][256];  // per-warp digit counts, then warp prefixes
   uint32_t tstart[256];           // tile-local start of each digit
-  uint32_t gbase[256];            // global start of each digit (over all tiles)
+  uint32_t gbase[256];            // global start of each digit in this tile
+  uint32_t tile;
 };
 
 __global__ void __launch_bounds__(kRsThreads)
-k_rs_scatter(const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin,
-             unsigned long long* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t n,
-             int pass, const ClassGeom* __restrict__ cls, const uint32_t* __restrict__ hist,
-             uint32_t ntiles) {
+k_rs_onesweep(const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin,
+              unsigned long long* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t n,
+              int pass, const ClassGeom* __restrict__ cls, SortScratch z) {
   if (pass >= sort_passes(cls->S, cls->ib)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ScatterSmem& S = *reinterpret_cast<ScatterSmem*>(smem_raw);
@@ -101,28 +122,13 @@ k_rs_scatter(const unsigned long long* __restrict__ kin, const uint32_t* __restr
   const uint32_t lanemask_lt = (1u << lane) - 1u;
 
   for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&S.whist[0][0])[i] = 0;
-  // digit base over all tiles: exclusive scan of the digit totals
-  {
-    const uint32_t* tot = hist + (size_t)256 * ntiles;
-    uint32_t v = tot[threadIdx.x];  // kRsThreads == 256
-    S.gbase[threadIdx.x] = v;
-  }
+  // tiles are taken in launch order, so every earlier tile has started
+  if (threadIdx.x == 0) S.tile = atomicAdd(&z.tiles[pass], 1u);
   __syncthreads();
-  for (int o = 1; o < 256; o <<= 1) {
-    uint32_t v = threadIdx.x >= o ? S.gbase[threadIdx.x - o] : 0u;
-    __syncthreads();
-    S.gbase[threadIdx.x] += v;
-    __syncthreads();
-  }
-  {
-    uint32_t incl = S.gbase[threadIdx.x];
-    __syncthreads();
-    S.gbase[threadIdx.x] = incl - hist[(size_t)256 * ntiles + threadIdx.x];
-  }
-  __syncthreads();
+  const uint32_t tile = S.tile;
 
   // pass 1: warp-local stable ranks
-  const uint32_t wbase = blockIdx.x * kRsTile + w * kRsWarpItems;
+  const uint32_t wbase = tile * kRsTile + w * kRsWarpItems;
   unsigned long long key[kRsIpt];
   uint32_t val[kRsIpt];
   uint32_t rank[kRsIpt];
@@ -143,7 +149,8 @@ k_rs_scatter(const unsigned long long* __restrict__ kin, const uint32_t* __restr
     rank[r] = valid ? pre + __popc(peers & lanemask_lt) : 0xffffffffu;
   }
   __syncthreads();
-  // per digit: prefix over warps (tile order), then the tile-local digit start
+  // per digit: prefix over warps (tile order), the tile's count, then the
+  // count of the digit in every earlier tile (look-back)
   uint32_t my_total;
   {
     const int d = threadIdx.x;
@@ -156,6 +163,31 @@ k_rs_scatter(const unsigned long long* __restrict__ kin, const uint32_t* __restr
     }
     my_total = run;
     S.tstart[d] = run;
+    unsigned long long* st = z.status + (size_t)tile * 256u + d;
+    uint32_t before = 0;
+    if (tile == 0) {
+      st_release(st, kFlagPrefix | my_total);
+    } else {
+      st_release(st, kFlagAgg | my_total);
+      uint32_t t = tile - 1;
+      uint32_t spins = 0;
+      for (;;) {
+        const unsigned long long v = ld_acquire(z.status + (size_t)t * 256u + d);
+        const unsigned long long f = v & kFlagMask;
+        if (f == 0ull) {
+          if (++spins > kSpinLimit) {  // an earlier tile never published: give up
+            set_status(cls->status, kStatusTimeout);
+            break;
+          }
+          continue;
+        }
+        before += (uint32_t)v;
+        if (f == kFlagPrefix || t == 0) break;
+        --t;
+      }
+      st_release(st, kFlagPrefix | (before + my_total));
+    }
+    S.gbase[d] = z.start[pass * 256 + d] + before;
   }
   __syncthreads();
   for (int o = 1; o < 256; o <<= 1) {
@@ -182,13 +214,12 @@ k_rs_scatter(const unsigned long long* __restrict__ kin, const uint32_t* __restr
   }
   __syncthreads();
   // pass 3: coalesced runs to global memory
-  const uint32_t tbase = blockIdx.x * kRsTile;
-  const uint32_t tcount = min((uint32_t)kRsTile, n - tbase);
-  const uint32_t* __restrict__ toff = hist;  // scanned [digit][tile]
+  const uint32_t tbase = tile * kRsTile;
+  const uint32_t tcount = tbase < n ? min((uint32_t)kRsTile, n - tbase) : 0u;
   for (uint32_t pos = threadIdx.x; pos < tcount; pos += kRsThreads) {
     const unsigned long long k = S.keys[pos];
     const uint32_t dg = (uint32_t)(k >> shift) & 255u;
-    const uint32_t dst = S.gbase[dg] + toff[(size_t)dg * ntiles + blockIdx.x] + (pos - S.tstart[dg]);
+    const uint32_t dst = S.gbase[dg] + (pos - S.tstart[dg]);
     if (dst < n) {
       kout[dst] = k;
       vout[dst] = S.vals[pos];
@@ -202,12 +233,15 @@ inline uint32_t tiles_for(uint32_t n) { return (n + kRsTile - 1) / kRsTile; }
 
 }  // namespace
 
-size_t sort_hist_words(uint32_t n) { return (size_t)257 * (tiles_for(n) ? tiles_for(n) : 1); }
+size_t sort_hist_words(uint32_t n) {
+  const uint32_t nt = tiles_for(n) ? tiles_for(n) : 1;
+  return (size_t)nt * 256u * 2u + 2u * kMaxPasses * 256u + kMaxPasses + 8u;
+}
 
 void sort_init() {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_rs_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(ScatterSmem));
     attr_set = true;
   }
@@ -219,16 +253,21 @@ void launch_sort(unsigned long long* codes_a, unsigned long long* codes_b, uint3
   if (n == 0) return;
   const uint32_t nt = tiles_for(n);
   sort_init();
+  const SortScratch z = sort_scratch(hist, nt);
+  // counts, starts and tile counters of every pass
+  cudaMemsetAsync(z.count, 0, sizeof(uint32_t) * (2 * kMaxPasses * 256 + kMaxPasses), st);
+  unsigned hb = nt < 152u * 4u ? nt : 152u * 4u;
+  k_rs_hist_all<<<hb, kRsThreads, 0, st>>>(codes_a, n, cls, z.count);
+  k_rs_scan_all<<<kMaxPasses, 256, 0, st>>>(z.count, z.start);
   unsigned long long* kb[2] = {codes_a, codes_b};
   uint32_t* vb[2] = {ids_a, ids_b};
   for (int pass = 0; pass < kMaxPasses; ++pass) {
     const int i = pass & 1, o = (pass + 1) & 1;
-    k_rs_hist<<<nt, kRsThreads, 0, st>>>(kb[i], n, pass, cls, hist, nt);
-    k_rs_scan<<<256, kRsThreads, 0, st>>>(hist, nt, pass, cls);
-    k_rs_scatter<<<nt, kRsThreads, sizeof(ScatterSmem), st>>>(kb[i], vb[i], kb[o], vb[o], n, pass,
-                                                              cls, hist, nt);
+    cudaMemsetAsync(z.status, 0, sizeof(unsigned long long) * 256u * nt, st);
+    k_rs_onesweep<<<nt, kRsThreads, sizeof(ScatterSmem), st>>>(kb[i], vb[i], kb[o], vb[o], n, pass,
+                                                               cls, z);
   }
-  count_launches(3 * kMaxPasses);
+  count_launches(2 + kMaxPasses);
 }
 
 }  // namespace dpc
