@@ -232,6 +232,35 @@ def block_work(job, rho_dev):
     return total, mean_rho
 
 
+def phase_rooflines(job, stats, phase_ms, hbm_gbs, peak_kind):
+    """HBM rooflines of the two streaming phases of one step, from their
+    algorithmic bytes per point and cutoff:
+      binning  bbox (read the coordinates), keys (read them, write a 64-bit key
+               and a 32-bit id), radix sort (one 8-byte read for the digit
+               counts, then 24 bytes read and written per pass), gather (read
+               the id and the coordinates, write the padded float point, key
+               and id): 12 d + 48 + 24 passes + 4 DP bytes per point;
+      labels   read rho, lambda and delta, write the label: 20 bytes per point
+               and cutoff.
+    Single point sets only (a batch mixes dimensions and pass counts)."""
+    if len(job.sizes) != 1 or not phase_ms:
+        return None
+    d = job.dims[0]
+    g = min(d, 4)
+    dp = 2 if d <= 2 else (4 if d <= 4 else 8)
+    passes = (g * int(stats.get("bits_per_axis", 0)) + 7) // 8
+    out = {}
+    for name, per_pt in (("bin", 12 * d + 48 + 24 * passes + 4 * dp), ("labels", 20 * job.n_dcut)):
+        ms = phase_ms.get(name)
+        if not ms:
+            continue
+        gbs = per_pt * job.N / (ms / 1e3) / 1e9
+        out[name] = {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s", "frac": gbs / hbm_gbs,
+                     "bytes_per_point": per_pt, "ms": ms, "peak_source": peak_kind,
+                     "passes": passes if name == "bin" else None}
+    return out
+
+
 def combine_ranks(total_ms, units_per_rank, steps, world, device=None):
     """Whole-job timing over replicas: the slowest rank's time bounds the job.
     Returns (max total ms over ranks, points/s of all ranks together)."""
@@ -406,6 +435,8 @@ def run_ours(args, rank, world, dev):
                                                              if pairs_layout else "")),
         "ms_per_launch": per_launch_ms}
     res["dominant_phase"] = dom
+    res["phase_rooflines"] = phase_rooflines(job, stats, res["phases_ms"], pk.get("hbm_gbs", 6800.0),
+                                             "measured" if pk_kind == "measured" else "fallback")
 
     if not args.fast:
         # the plain FP64 path on the same workload (binary64 costs 10-50x more
