@@ -85,14 +85,15 @@ enum {
                                           (read with dpc_get_phase_times)      */
 /* Autotune the grid level and the kernel layouts: the first dpc_run /
  * dpc_density call that sees a new (dimension class, instance count, point
- * count, cutoff) shape runs the cell-hash step, the density kernel and (for
- * dpc_run) the near-dependent kernel in both layouts once per candidate block
- * radius (R = 1, 2, 3 for d <= 2; R = 1, 2 for d = 3; d >= 4 has R = 1 only;
- * the cells shrink as R grows), timing each
- * with CUDA events and synchronizing the stream, and keeps the fastest for
- * that shape in the workspace; later calls (with or without the flag) reuse
- * the choice without synchronizing.  Results do not depend on the choice.
- * Do not set it on a call that is being captured into a CUDA graph. */
+ * count, cutoff) shape runs, once per candidate block radius (R = 1, 2, 3 for
+ * d <= 2; R = 1, 2 for d = 3; d >= 4 has R = 1 only; the cells shrink as R
+ * grows), the cell-hash step, the density kernel in every density layout and
+ * (for dpc_run) the near-dependent and far search for every near layout at
+ * 0, 1 and 2 grid levels below the density's, timing each with CUDA events
+ * and synchronizing the stream, and keeps the fastest for that shape in the
+ * workspace; later calls (with or without the flag) reuse the choice without
+ * synchronizing.  Results do not depend on the choice.  Do not set it on a
+ * call that is being captured into a CUDA graph. */
 #define DPC_FLAG_AUTOTUNE (1u << 10)
 /* Fixed block radius r = 1..5 instead of the default rule or the autotuned
  * choice (larger radii are clamped to the largest the dimension allows: 5 for
