@@ -72,7 +72,8 @@ def check_run(sizes, dims, insts, cuts, dtype, precision, seed, layout="auto", s
 
 @pytest.mark.parametrize("precision,layout", [("fp32", "auto"), ("fp64", "auto"), ("fp32", "union"),
                                               ("fp32", "segment"), ("fp64", "segment"), ("fp32", "tree"),
-                                              ("fp64", "tree"), ("fp32", "tensor"), ("fp64", "tensor")])
+                                              ("fp64", "tree"), ("fp32", "tensor"), ("fp64", "tensor"),
+                                              ("fp32", "pairs"), ("fp64", "pairs")])
 def test_batch_mixed_dims_float(precision, layout):
     sizes, dims, insts, cuts = make_batch(1, 48, [2, 3, 5, 1, 4, 7, 8, 2, 3, 5])
     check_run(sizes, dims, insts, cuts, np.float32, precision, 11, layout)
