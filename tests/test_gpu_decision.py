@@ -81,6 +81,14 @@ def test_decision_graph_of_clustered_points():
     check(sizes, arrays, 32, 12, 24, 1e-3)
 
 
+def test_decision_graph_many_bins():
+    """More (rho, delta) bins than fit in shared memory: counted with global
+    atomics only."""
+    sizes = [40000, 3000]
+    arrays = [synthetic(n, 110 + i, ties=False) for i, n in enumerate(sizes)]
+    check(sizes, arrays, 0, 32, 200, 1e-7)
+
+
 def test_decision_graph_products_only_one_kind():
     sizes = [500, 800]
     arrays = [synthetic(n, 90 + i) for i, n in enumerate(sizes)]
