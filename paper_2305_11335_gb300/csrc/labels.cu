@@ -62,7 +62,7 @@ __global__ void k_label_init(const int32_t* __restrict__ rho, const int32_t* __r
 // harmless.  If every pointer covered at least L steps before a round, the
 // first jump covers 2L and each further one at least L more, so a round
 // multiplies the covered distance by at least kJumps + 1.
-constexpr int kJumps = 8;
+constexpr int kJumps = 32;
 __global__ void k_label_jump(int32_t* par, ClassView cv, int32_t* flags, int r) {
   if (flags[r - 1] == 0) return;  // the previous round changed nothing
   int changed = 0;
