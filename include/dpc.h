@@ -277,28 +277,30 @@ int dpc_run_host(const void* pts_host, int dtype, const dpc_batch* b, const dpc_
                  int32_t* label_host, uint32_t flags, void* stream);
 
 /* dpc_density for ONE point set without allocating device memory.  The paper
- * has no counterpart: this entry point exists for callers that cannot let a
- * library call cudaMalloc -- work enqueued while a stream is being captured
- * into a CUDA graph (allocation is not allowed during capture), hosts that
- * budget device memory through their own allocator, and paths that cannot
- * afford the device synchronization an allocation may cause.
+ * has no counterpart.  It is for callers that cannot let a library call
+ * cudaMalloc: a host application that hands out all device memory through its
+ * own allocator or budget (an allocation behind its back can fail or push it
+ * over that budget), and latency-critical paths, where cudaMalloc and cudaFree
+ * may synchronize the device.
  *   pts     device, [n][d] row-major, int32 or float32 (dtype), same range
  *           rules as every other entry point
  *   n       0 .. DPC_STATIC_MAX_POINTS; larger n fails with DPC_ERR_OVERFLOW
  *           before any work is queued
  *   d       1..8; d_cut finite and >= 0
- *   rho     device, int32 [n]: rho[i] = density of point i (Definition 1),
- *           identical to dpc_density's result
+ *   rho     device, int32 [n]: the same densities dpc_density writes for this
+ *           point set and cutoff
  *   flags   precision (DPC_PREC_*) and DPC_FLAG_SYNC_CHECK as for dpc_density
  * All scratch memory is one fixed array of about 7 MB compiled into the
  * library, so every GPU that loads the library holds it until the process
- * exits.  The first call on a device looks up that array's device address;
- * make that first call before any stream capture.  The call never allocates
- * (no cudaMalloc, cudaFree or allocating library routine) and issues only
- * kernels and memsets on `stream`.  All calls share the one array: calls
+ * exits.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  The call never allocates (no cudaMalloc,
+ * cudaFree or allocating library routine) and issues only kernels and
+ * memsets on `stream`; it clears the words that must start at zero itself.
+ * All calls share the one array, which keeps the last call's contents: calls
  * that overlap on the GPU (on different streams, or from several threads
- * without ordering) race and corrupt each other's results; order them on
- * one stream. */
+ * without ordering) race and corrupt each other's results; order them on one
+ * stream. */
 #define DPC_STATIC_MAX_POINTS 65536
 int dpc_density_static(const void* pts, int dtype, int64_t n, int32_t d, double d_cut,
                        int32_t* rho, uint32_t flags, void* stream);

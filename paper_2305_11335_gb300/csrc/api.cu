@@ -33,6 +33,25 @@ namespace dpc {
 
 long long g_kernel_launches = 0;
 
+unsigned sm_count() {
+  constexpr int kDevs = 64;
+  static int cached[kDevs] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevs) {
+    cudaGetLastError();
+    return 1u;  // the launch that follows reports the error
+  }
+  if (cached[dev] <= 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      return 1u;
+    }
+    cached[dev] = v;
+  }
+  return (unsigned)cached[dev];
+}
+
 namespace {
 
 constexpr size_t kAlign = 256;

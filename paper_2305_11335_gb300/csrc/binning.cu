@@ -18,7 +18,7 @@ namespace {
 
 constexpr int kThreads = 256;
 
-inline unsigned grid_for(uint64_t n, int threads = kThreads, unsigned cap = 152u * 16u) {
+inline unsigned grid_for(uint64_t n, int threads = kThreads, unsigned cap = sm_count() * 16u) {
   uint64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
   if (b > cap) b = cap;
@@ -470,7 +470,7 @@ void launch_class_init(const ClassView& cv, int g, int ib, int bcap, int* status
 
 void launch_chunks(const ClassView& cv, uint32_t* chunk_inst, uint32_t* chunk_pos, cudaStream_t st) {
   if (!cv.inst || cv.ninst == 0) return;
-  k_chunks<<<grid_for(cv.ninst, 1, 152u * 16u), 128, 0, st>>>(cv.inst, cv.ninst, chunk_inst, chunk_pos);
+  k_chunks<<<grid_for(cv.ninst, 1, sm_count() * 16u), 128, 0, st>>>(cv.inst, cv.ninst, chunk_inst, chunk_pos);
   count_launches(1);
 }
 
@@ -487,7 +487,7 @@ void launch_set_radius(const ClassView& cv, CutGeom* cuts, int rpref, cudaStream
 
 void launch_bbox(const void* pts, int dtype, const ClassView& cv, int g, cudaStream_t st) {
   if (cv.N == 0) return;
-  const unsigned grid = grid_for((uint64_t)cv.nchunk * 32u, kThreads, 152u * 4u);
+  const unsigned grid = grid_for((uint64_t)cv.nchunk * 32u, kThreads, sm_count() * 4u);
   if (dtype == 0)
     k_bbox<int32_t><<<grid, kThreads, 0, st>>>((const int32_t*)pts, cv, g);
   else

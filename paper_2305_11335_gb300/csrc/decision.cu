@@ -388,7 +388,7 @@ void launch_decision_init(int n_inst, int k, int32_t* top, double* gamma, int rh
     const size_t m = (size_t)n_inst * k;
     uint64_t blocks = (m + 255) / 256;
     if (blocks < 1) blocks = 1;
-    if (blocks > 152u * 16u) blocks = 152u * 16u;
+    if (blocks > sm_count() * 16u) blocks = sm_count() * 16u;
     k_decision_pad<<<(unsigned)blocks, 256, 0, st>>>(top, gamma, m);
     count_launches(1);
   }
@@ -417,9 +417,9 @@ void launch_decision(const int32_t* rho, const double* delta, const ClassView& c
     unsigned long long* ck = (unsigned long long*)(b + a + h);
     uint32_t* ci = (uint32_t*)(b + a + h + c);
     uint64_t cb = ((uint64_t)cv.nchunk + 31) / 32;  // at least 32 chunks per CTA
-    const unsigned chunk_blocks = (unsigned)(cb < 1 ? 1 : (cb > 152u * 8u ? 152u * 8u : cb));
+    const unsigned chunk_blocks = (unsigned)(cb < 1 ? 1 : (cb > sm_count() * 8u ? sm_count() * 8u : cb));
     uint64_t ib = ((uint64_t)cv.ninst + 7) / 8;
-    const unsigned inst_blocks = (unsigned)(ib < 1 ? 1 : (ib > 152u * 16u ? 152u * 16u : ib));
+    const unsigned inst_blocks = (unsigned)(ib < 1 ? 1 : (ib > sm_count() * 16u ? sm_count() * 16u : ib));
     k_dg_init<<<inst_blocks, 256, 0, st>>>(S, H, cv.ninst, k);
     for (int dg = 7; dg >= 0; --dg) {
       k_dg_hist<false><<<chunk_blocks, 256, 0, st>>>(rho, delta, cv, S, H, dg);
@@ -430,14 +430,14 @@ void launch_decision(const int32_t* rho, const double* delta, const ClassView& c
       k_dg_pick<true><<<inst_blocks, 256, 0, st>>>(S, H, cv.ninst, dg);
     }
     k_dg_gather<<<chunk_blocks, 256, 0, st>>>(rho, delta, cv, S, k, ck, ci);
-    const unsigned grid = cv.ninst < 152u * 2u ? cv.ninst : 152u * 2u;
+    const unsigned grid = cv.ninst < sm_count() * 2u ? cv.ninst : sm_count() * 2u;
     k_dg_sort<<<grid, kDgThreads, 0, st>>>(cv, S, k, ck, ci, top, gamma);
     count_launches(1 + 2 * 12 + 2);
   }
   if (hist && rho_bins > 0 && delta_bins > 0) {
     uint64_t blocks = ((uint64_t)cv.nchunk + 31) / 32;  // at least 32 chunks per CTA
     if (blocks < 1) blocks = 1;
-    if (blocks > 152u * 8u) blocks = 152u * 8u;
+    if (blocks > sm_count() * 8u) blocks = sm_count() * 8u;
     if (rho_bins * delta_bins <= kHistSmemBins)
       k_decision_hist<true><<<(unsigned)blocks, 256, 0, st>>>(rho, delta, cv, rho_bins, delta_bins,
                                                               delta_lo, hist);

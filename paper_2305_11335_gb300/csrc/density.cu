@@ -511,7 +511,7 @@ void density_dg(bool fp64, int layout, const float* spts, const unsigned long lo
                 const uint32_t* sid, const ClassView& cv, const CutGeom* cuts, const HashInfo* hi,
                 const unsigned long long* hkeys, const uint2* hvals, int32_t* rho_out,
                 unsigned long long* skey, Counters* ctr, int seg_cells, cudaStream_t st) {
-  const unsigned grid = grid_for(cv.nchunk, kWarps, 152u * 64u);
+  const unsigned grid = grid_for(cv.nchunk, kWarps, sm_count() * 64u);
   if (layout == kLayoutPairs) {
     cudaMemsetAsync(skey, 0, sizeof(unsigned long long) * cv.N, st);
     uint32_t* cnt2 = reinterpret_cast<uint32_t*>(skey);
@@ -521,7 +521,7 @@ void density_dg(bool fp64, int layout, const float* spts, const unsigned long lo
     else
       k_density_pairs<DP, G, false><<<grid, kThreads, 0, st>>>(spts, scode, cv, cuts, hi, hkeys, hvals,
                                                                cnt2, ctr);
-    k_pairs_finish<<<grid_for(cv.N, 256, 152u * 16u), 256, 0, st>>>(sid, cv.N, rho_out, skey);
+    k_pairs_finish<<<grid_for(cv.N, 256, sm_count() * 16u), 256, 0, st>>>(sid, cv.N, rho_out, skey);
     count_launches(1);
   } else if (layout == kLayoutSegment) {
     if (fp64)
@@ -566,7 +566,7 @@ void launch_density(int dp, int g, bool fp64, int layout, const float* spts,
 void launch_keys_from_rho(const int32_t* rho, const uint32_t* sid, uint32_t n,
                           unsigned long long* skey, cudaStream_t st) {
   if (n == 0) return;
-  k_keys_from_rho<<<grid_for(n, 256, 152u * 16u), 256, 0, st>>>(rho, sid, n, skey);
+  k_keys_from_rho<<<grid_for(n, 256, sm_count() * 16u), 256, 0, st>>>(rho, sid, n, skey);
   count_launches(1);
 }
 

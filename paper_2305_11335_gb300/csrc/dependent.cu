@@ -1058,7 +1058,7 @@ void near_dg(bool fp64, int layout, const float* spts, const unsigned long long*
              const void* pts, int dtype, const CutGeom* cuts, const HashInfo* hi,
              const unsigned long long* hkeys, const uint2* hvals, int32_t* lambda, double* delta,
              FarQueue q, Counters* ctr, int seg_cells, cudaStream_t st) {
-  const unsigned grid = grid_for(cv.nchunk, kNearWarps, 152u * 64u);
+  const unsigned grid = grid_for(cv.nchunk, kNearWarps, sm_count() * 64u);
   if (layout == kLayoutSegment) {
     if (fp64)
       k_dep_near_seg<DP, G, true><<<grid, kNearThreads, 0, st>>>(spts, scode, skey, cv, rho_skip, pts,
@@ -1087,8 +1087,8 @@ void far_dp(bool fp64, const float* spts, const unsigned long long* scode,
             int32_t* lambda, double* delta, Counters* ctr, cudaStream_t st) {
   // the queue length is known only on the device: launch enough threads for
   // a full SM load and let them stride over it
-  const unsigned grid = grid_for(cv.N, kFarThreads, 152u * 8u);
-  const unsigned grid2 = grid_for(cv.N, kFarThreads / 32, 152u * 16u);
+  const unsigned grid = grid_for(cv.N, kFarThreads, sm_count() * 8u);
+  const unsigned grid2 = grid_for(cv.N, kFarThreads / 32, sm_count() * 16u);
   if (fp64) {
     k_dep_far<DP, true><<<grid, kFarThreads, 0, st>>>(spts, scode, skey, cv, cuts, nodes, nbox,
                                                       root, q, lambda, delta, ctr);
@@ -1114,7 +1114,7 @@ void launch_dep_near(int dp, int g, bool fp64, int layout, const float* spts,
   cudaMemsetAsync(&ctr->queue_n, 0, sizeof(unsigned int), st);
   cudaMemsetAsync(&ctr->queue2_n, 0, sizeof(unsigned int), st);
   if (layout == kLayoutTree) {
-    k_near_to_far<<<grid_for((uint64_t)cv.nchunk * 32u, 256, 152u * 16u), 256, 0, st>>>(
+    k_near_to_far<<<grid_for((uint64_t)cv.nchunk * 32u, 256, sm_count() * 16u), 256, 0, st>>>(
         skey, cv, cuts, rho_skip, lambda, delta, q, ctr);
   } else if (g == 1) near_dg<2, 1>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, seg_cells, st);
   else if (g == 2) near_dg<2, 2>(fp64, layout, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys, hvals, lambda, delta, q, ctr, seg_cells, st);

@@ -11,6 +11,10 @@
 
 namespace dpc {
 
+// Streaming multiprocessors of the current device (grid caps are multiples
+// of it); queried once per device.
+unsigned sm_count();
+
 // Kernels enqueued by the current call (the entry points hold the library
 // lock while enqueueing, so a plain counter suffices).
 extern long long g_kernel_launches;
@@ -57,6 +61,15 @@ void launch_cells(const unsigned long long* scode, const ClassView& cv, int g, c
                   cudaStream_t st);
 
 // ---- radix sort (sort.cu) ------------------------------------------------------
+constexpr uint32_t kSortTile = 4096;    // items per tile of one pass
+constexpr uint32_t kSortMaxPasses = 8;  // 8-bit digits of a 64-bit key
+// 32-bit words of sort scratch for n items: per tile and digit a published
+// 64-bit count, the digit counts and starts of every pass, a tile counter per
+// pass (and slack)
+constexpr size_t sort_hist_words_for(uint64_t n) {
+  return (size_t)(n ? (n + kSortTile - 1) / kSortTile : 1) * 256u * 2u +
+         2u * kSortMaxPasses * 256u + kSortMaxPasses + 8u;
+}
 size_t sort_hist_words(uint32_t n);
 // one-time kernel attribute setup (called before any stream capture)
 void sort_init();

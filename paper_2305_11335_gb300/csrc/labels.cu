@@ -102,7 +102,7 @@ __global__ void k_label_check(const int32_t* __restrict__ flags, int last, Class
 inline unsigned grid_for(uint64_t n) {
   uint64_t b = (n + kThreads - 1) / kThreads;
   if (b < 1) b = 1;
-  if (b > 152u * 16u) b = 152u * 16u;
+  if (b > sm_count() * 16u) b = sm_count() * 16u;
   return (unsigned)b;
 }
 

@@ -328,7 +328,7 @@ void prange_dp(const float* spts, const uint32_t* sid, const unsigned long long*
                const ClassView& cv, const Node* nodes, const float* nbox, const uint32_t* roots,
                const PrangeArgs& a, uint32_t* cnt, const unsigned long long* off,
                unsigned long long* keys, int* status, cudaStream_t st) {
-  k_prange<DP, FILL><<<grid_cap(a.nq, kPrWarps, 152u * 8u), kPrThreads, 0, st>>>(
+  k_prange<DP, FILL><<<grid_cap(a.nq, kPrWarps, sm_count() * 8u), kPrThreads, 0, st>>>(
       spts, sid, skey, cv, nodes, nbox, roots, a.nq, a.n_inst, a.q_inst, a.q_box, a.q_rho,
       a.rowmap, a.one_row, cnt, a.count, off, keys,
       a.stack_cap > 0 && a.stack_cap < kPrStack ? a.stack_cap : kPrStack, status);
@@ -339,7 +339,7 @@ void prange_dp(const float* spts, const uint32_t* sid, const unsigned long long*
 void launch_prange_init(const PrangeArgs& a, int32_t* ids, int max_out, int* status,
                         cudaStream_t st) {
   const uint64_t items = (uint64_t)a.nq * (uint64_t)(max_out > 0 ? max_out : 1);
-  k_prange_init<<<grid_cap(items, 256, 152u * 16u), 256, 0, st>>>(a.nq, a.n_inst, a.q_inst, a.count,
+  k_prange_init<<<grid_cap(items, 256, sm_count() * 16u), 256, 0, st>>>(a.nq, a.n_inst, a.q_inst, a.count,
                                                                  ids, max_out, status);
   count_launches(1);
 }
@@ -373,7 +373,7 @@ void launch_prange_scatter(const unsigned long long* keys, uint64_t total,
                            const unsigned long long* off, uint32_t nq, int max_out, int32_t* ids,
                            int* status, cudaStream_t st) {
   if (total == 0 || max_out <= 0) return;
-  k_prange_scatter<<<grid_cap(total, 256, 152u * 16u), 256, 0, st>>>(keys, total, off, nq, max_out,
+  k_prange_scatter<<<grid_cap(total, 256, sm_count() * 16u), 256, 0, st>>>(keys, total, off, nq, max_out,
                                                                      ids, status);
   count_launches(1);
 }

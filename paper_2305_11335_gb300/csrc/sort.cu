@@ -28,7 +28,8 @@ constexpr int kRsWarps = kRsThreads / 32;
 constexpr int kRsIpt = 16;                          // items per thread
 constexpr int kRsTile = kRsThreads * kRsIpt;        // 4096 items per tile
 constexpr int kRsWarpItems = 32 * kRsIpt;           // 512 items per warp
-constexpr int kMaxPasses = 8;
+constexpr int kMaxPasses = (int)kSortMaxPasses;
+static_assert(kRsTile == (int)kSortTile, "tile size of the scratch formula");
 
 constexpr unsigned long long kFlagAgg = 1ull << 62;     // the tile's own counts
 constexpr unsigned long long kFlagPrefix = 2ull << 62;  // counts of this and every earlier tile
@@ -233,10 +234,7 @@ inline uint32_t tiles_for(uint32_t n) { return (n + kRsTile - 1) / kRsTile; }
 
 }  // namespace
 
-size_t sort_hist_words(uint32_t n) {
-  const uint32_t nt = tiles_for(n) ? tiles_for(n) : 1;
-  return (size_t)nt * 256u * 2u + 2u * kMaxPasses * 256u + kMaxPasses + 8u;
-}
+size_t sort_hist_words(uint32_t n) { return sort_hist_words_for(n); }
 
 void sort_init() {
   static bool attr_set = false;
@@ -256,7 +254,7 @@ void launch_sort(unsigned long long* codes_a, unsigned long long* codes_b, uint3
   const SortScratch z = sort_scratch(hist, nt);
   // counts, starts and tile counters of every pass
   cudaMemsetAsync(z.count, 0, sizeof(uint32_t) * (2 * kMaxPasses * 256 + kMaxPasses), st);
-  unsigned hb = nt < 152u * 4u ? nt : 152u * 4u;
+  unsigned hb = nt < sm_count() * 4u ? nt : sm_count() * 4u;
   k_rs_hist_all<<<hb, kRsThreads, 0, st>>>(codes_a, n, cls, z.count);
   k_rs_scan_all<<<kMaxPasses, 256, 0, st>>>(z.count, z.start);
   unsigned long long* kb[2] = {codes_a, codes_b};

@@ -1,11 +1,11 @@
 // static_density.cu -- dpc_density for one point set without any device
 // allocation: every scratch buffer lives in one file-scope __device__ array.
 //
-// For callers that must not allocate device memory: code enqueued while a
-// stream is being captured into a CUDA graph (cudaMalloc is not allowed
-// there), hosts whose device memory is budgeted by their own allocator, and
-// latency-critical paths (cudaMalloc may synchronize the device).  The price
-// is a fixed maximum size and a single shared scratch area (see dpc.h).
+// For callers that must not allocate device memory: hosts whose device memory
+// is handed out by their own allocator or budget, and latency-critical paths
+// (cudaMalloc and cudaFree may synchronize the device).  The price is a fixed
+// maximum size and a single shared scratch area (see dpc.h).
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -25,7 +25,6 @@ constexpr uint32_t pow2_at_least(uint64_t x) {
   return (uint32_t)t;
 }
 constexpr uint32_t kStaticHash = pow2_at_least(2 * kStaticN);
-constexpr size_t kTiles = (kStaticN + 4095) / 4096;
 
 // Layout of the scratch array (byte offsets).
 constexpr size_t kOffGeom = 0;
@@ -39,7 +38,7 @@ constexpr size_t kOffCodesB = kOffCodesA + al(8 * kStaticN);
 constexpr size_t kOffIdsA = kOffCodesB + al(8 * kStaticN);
 constexpr size_t kOffIdsB = kOffIdsA + al(4 * kStaticN);
 constexpr size_t kOffHist = kOffIdsB + al(4 * kStaticN);
-constexpr size_t kOffSpts = kOffHist + al(4 * 257 * kTiles);
+constexpr size_t kOffSpts = kOffHist + al(4 * sort_hist_words_for(kStaticN));
 constexpr size_t kOffScode = kOffSpts + al(4 * 8 * kStaticN);
 constexpr size_t kOffSid = kOffScode + al(8 * kStaticN);
 constexpr size_t kOffSkey = kOffSid + al(4 * kStaticN);
@@ -50,6 +49,8 @@ constexpr size_t kStaticBytes = kOffHvals + al(8 * (size_t)kStaticHash);
 // The scratch area.  In host code this name is only a handle; its device
 // address comes from cudaGetSymbolAddress (once per device, below).
 static __device__ __align__(256) unsigned char g_scratch[kStaticBytes];
+// the sort's scratch for the largest accepted set fits its region
+static_assert(kOffSpts - kOffHist >= 4 * sort_hist_words_for(kStaticN), "sort scratch region");
 
 std::mutex g_static_mu;
 constexpr int kMaxDevices = 64;
@@ -133,7 +134,9 @@ extern "C" int dpc_density_static(const void* pts, int dtype, int64_t n, int32_t
   cv.one.d = d;
   cv.geom = geom;
   cv.cls = cls;
-  launch_class_init(cv, g, 0, kMaxBits, status, st);
+  // one instance: no instance bits, and g * B <= 63 keeps every cell code
+  // below 2^63 (the allocating path's rule with ib = 0)
+  launch_class_init(cv, g, 0, std::min(kMaxBits, 63 / g), status, st);
   launch_bbox(pts, dtype, cv, g, st);
   launch_setup(cv, cut, 1, nullptr, &ch, st);
   launch_codes(pts, dtype, cv, g, codes_a, ids_a, st);

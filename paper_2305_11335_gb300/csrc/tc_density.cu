@@ -407,8 +407,8 @@ void launch_density_tc(int g, const float* spts, const uint32_t* sid, const Clas
   }
   cudaMemsetAsync(&hi->work, 0, sizeof(uint32_t), st);
   cudaMemsetAsync(&hi->npieces, 0, sizeof(uint32_t), st);
-  k_tc_pieces<<<152u * 8u, 256, 0, st>>>(hi, hkeys, hvals, cv.N, pieces);
-  const unsigned grid = 152u * 2u;  // two resident CTAs per SM take the pieces one by one
+  k_tc_pieces<<<sm_count() * 8u, 256, 0, st>>>(hi, hkeys, hvals, cv.N, pieces);
+  const unsigned grid = sm_count() * 2u;  // two resident CTAs per SM take the pieces one by one
   if (g == 3)
     k_density_tc<3><<<grid, kTcThreads, kTcSmemBytes, st>>>(spts, sid, cv, cuts, hi, hkeys, hvals,
                                                             pieces, rho_out, skey, ctr);

@@ -180,7 +180,7 @@ __global__ void k_tree_up(const unsigned long long* __restrict__ skey,
 inline unsigned grid_for(uint64_t n) {
   uint64_t b = (n + kThreads - 1) / kThreads;
   if (b < 1) b = 1;
-  if (b > 152u * 16u) b = 152u * 16u;
+  if (b > sm_count() * 16u) b = sm_count() * 16u;
   return (unsigned)b;
 }
 

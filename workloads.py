@@ -305,3 +305,18 @@ def random_blobs(n: int, d: int, seed: int, dtype=np.float32, n_blobs: int = 4, 
     if np.issubdtype(np.dtype(dtype), np.integer):
         return np.rint(pts).astype(dtype)
     return pts.astype(dtype)
+
+
+def wide_clusters(n: int, d: int, seed: int, extent: float = 2.0e6, sigma: float = 20.0,
+                  n_centers: int = 64, dtype=np.int32) -> np.ndarray:
+    """Tight isotropic clusters (sigma) around n_centers centers drawn
+    uniformly in [0, extent)^d: a bounding box many thousand cutoffs wide with
+    non-trivial densities inside the clusters."""
+    rng = np.random.default_rng(seed)
+    centers = rng.random((n_centers, d)) * extent
+    which = rng.integers(0, n_centers, n)
+    pts = centers[which] + rng.normal(0.0, sigma, (n, d))
+    pts, _ = _shuffle(rng, pts, 0)
+    if np.issubdtype(np.dtype(dtype), np.integer):
+        return np.rint(pts).astype(dtype)
+    return pts.astype(dtype)
