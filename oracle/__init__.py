@@ -24,6 +24,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dpc_oracle.c")
+_SRC_TREE = os.path.join(_HERE, "dpc_oracle_tree.c")
 _LIB_PATH = os.path.join(_HERE, "_liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -38,15 +39,18 @@ VAR_TIE_LARGER_ID = 4
 VAR_DIST_TIE_LARGER = 8
 VAR_SQRT_COMPARE = 16
 VAR_DROP_LAST_DIM = 32
+VAR_CENTER_NO_RHO_MIN = 64  # labels only: a center need not reach rho_min
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc into ``oracle/_liboracle.so``."""
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+    srcs = (_SRC, _SRC_TREE)
+    if not force and os.path.exists(_LIB_PATH) and \
+            all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(s) for s in srcs):
         return _LIB_PATH
     tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-pthread", "-o", tmp, _SRC, "-lm"]
+           "-pthread", "-o", tmp, *srcs, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -62,9 +66,14 @@ def _load():
         lib.orc_density.argtypes = [vp, i32, i64, i32, dbl, vp, i64, i32, i32, vp]
         lib.orc_dependent.argtypes = [vp, i32, i64, i32, vp, ctypes.c_int32, i32, i32, vp, vp]
         lib.orc_dependent_at.argtypes = [vp, i32, i64, i32, dbl, vp, i64, i64, i32, i32, vp, vp, vp, vp]
-        lib.orc_cluster.argtypes = [i64, vp, vp, vp, ctypes.c_int32, ctypes.c_int32, dbl, vp]
+        lib.orc_cluster.argtypes = [i64, vp, vp, vp, ctypes.c_int32, ctypes.c_int32, dbl, i32, vp]
         lib.orc_kth_sqdist.argtypes = [vp, i32, i64, i32, vp, i64, i32, i32, vp]
         lib.orc_threads.argtypes = [i32]
+        lib.orc_tree_run.argtypes = [vp, i32, i64, i32, i32, vp, ctypes.c_int32, i32, vp, vp, vp]
+        lib.orc_tree_batch.argtypes = [vp, i32, ctypes.c_int32, vp, vp, vp, i32, vp, ctypes.c_int32, i32,
+                                       vp, vp, vp]
+        lib.orc_tree_run.restype = ctypes.c_int
+        lib.orc_tree_batch.restype = ctypes.c_int
         for f in (lib.orc_density, lib.orc_dependent, lib.orc_dependent_at, lib.orc_cluster,
                   lib.orc_kth_sqdist, lib.orc_threads):
             f.restype = ctypes.c_int
@@ -148,7 +157,7 @@ def dependent_at(pts, d_cut: float, idx, max_checks: int = 64, variant: int = 0,
     return lam, delta, rho, status.astype(bool)
 
 
-def cluster(rho, lam, delta, rho_noise: int, rho_min: int, delta_min: float) -> np.ndarray:
+def cluster(rho, lam, delta, rho_noise: int, rho_min: int, delta_min: float, variant: int = 0) -> np.ndarray:
     """Labels (Definitions 4-5 and the assignment rule)."""
     rho = np.ascontiguousarray(rho, dtype=np.int32)
     lam = np.ascontiguousarray(lam, dtype=np.int32)
@@ -158,7 +167,7 @@ def cluster(rho, lam, delta, rho_noise: int, rho_min: int, delta_min: float) -> 
     if n == 0:
         return out
     rc = _load().orc_cluster(n, _ptr(rho), _ptr(lam), _ptr(delta), int(rho_noise), int(rho_min),
-                             float(delta_min), _ptr(out))
+                             float(delta_min), int(variant), _ptr(out))
     if rc:
         raise RuntimeError("orc_cluster: dependent pointers do not form a valid forest (%d)" % rc)
     return out
@@ -273,6 +282,58 @@ def kth_sqdist(pts, idx, k: int, nthreads: int = 0) -> np.ndarray:
     if rc:
         raise RuntimeError("orc_kth_sqdist failed: %d" % rc)
     return out
+
+
+def tree_run(pts, d_cuts, rho_skip: int = 0, dependent: bool = True, nthreads: int = 0):
+    """rho, lambda, delta of every point of one set for every cutoff in
+    ``d_cuts``, from the kd-tree oracle (``dpc_oracle_tree.c``: the same
+    definitions as ``density``/``dependent``, searched on the paper's priority
+    search kd-tree).  Returns arrays of shape (len(d_cuts), n); with
+    ``dependent=False`` only rho."""
+    pts, dtype, n, d = _points(pts)
+    cuts = np.ascontiguousarray(np.atleast_1d(np.asarray(d_cuts, dtype=np.float64)))
+    nc = cuts.shape[0]
+    rho = np.zeros((nc, n), dtype=np.int32)
+    lam = np.zeros((nc, n), dtype=np.int32) if dependent else None
+    delta = np.zeros((nc, n), dtype=np.float64) if dependent else None
+    if n:
+        rc = _load().orc_tree_run(_ptr(pts), dtype, n, d, nc, _ptr(cuts), int(rho_skip), nthreads, _ptr(rho),
+                                  _ptr(lam), _ptr(delta))
+        if rc:
+            raise RuntimeError("orc_tree_run failed: %d" % rc)
+    return {"rho": rho, "lam": lam, "delta": delta}
+
+
+def tree_batch(flat, pt_offset, coord_offset, dims, d_cuts, rho_skip: int = 0, nthreads: int = 0):
+    """The kd-tree oracle over a batch of independent point sets packed back to
+    back (``flat``: int32 or float32 coordinates; instance i has
+    ``pt_offset[i+1] - pt_offset[i]`` points of ``dims[i]`` coordinates from
+    element ``coord_offset[i]``), ``d_cuts[i]`` its cutoffs (the same number for
+    every instance).  Returns rho, lam (instance-local ids), delta of shape
+    (ncut, N), one thread per instance."""
+    flat = np.ascontiguousarray(flat)
+    if flat.dtype == np.int32:
+        dtype = I32
+    elif flat.dtype == np.float32:
+        dtype = F32
+    else:
+        raise TypeError("points must be int32 or float32, got %s" % flat.dtype)
+    po = np.ascontiguousarray(pt_offset, dtype=np.int64)
+    co = np.ascontiguousarray(coord_offset, dtype=np.int64)
+    dm = np.ascontiguousarray(dims, dtype=np.int32)
+    cuts = np.ascontiguousarray(np.asarray(d_cuts, dtype=np.float64))
+    ni = dm.shape[0]
+    assert po.shape == (ni + 1,) and co.shape == (ni,) and cuts.ndim == 2 and cuts.shape[0] == ni
+    nc = cuts.shape[1]
+    N = int(po[-1])
+    rho = np.zeros((nc, N), dtype=np.int32)
+    lam = np.zeros((nc, N), dtype=np.int32)
+    delta = np.zeros((nc, N), dtype=np.float64)
+    rc = _load().orc_tree_batch(_ptr(flat), dtype, ni, _ptr(po), _ptr(co), _ptr(dm), nc, _ptr(cuts),
+                                int(rho_skip), nthreads, _ptr(rho), _ptr(lam), _ptr(delta))
+    if rc:
+        raise RuntimeError("orc_tree_batch failed: %d" % rc)
+    return {"rho": rho, "lam": lam, "delta": delta}
 
 
 def run(pts, d_cut: float, rho_noise: int, rho_min: int, delta_min: float, rho_skip: int = 0,

@@ -58,7 +58,8 @@ enum {
   ORC_VAR_TIE_LARGER_ID = 4,    /* rho ties: larger id is higher          */
   ORC_VAR_DIST_TIE_LARGER = 8,  /* distance ties: larger id wins          */
   ORC_VAR_SQRT_COMPARE = 16,    /* sqrt(s) <= d_cut instead of s <= dc2   */
-  ORC_VAR_DROP_LAST_DIM = 32    /* distance ignores the last coordinate   */
+  ORC_VAR_DROP_LAST_DIM = 32,   /* distance ignores the last coordinate   */
+  ORC_VAR_CENTER_NO_RHO_MIN = 64 /* labels: centers skip rho >= rho_min   */
 };
 
 typedef struct {
@@ -412,13 +413,16 @@ int orc_dependent_at(const void* pts, int dtype, int64_t n, int d, double d_cut,
  * leaves the point set, reaches a noise point or does not end within n steps.
  */
 int orc_cluster(int64_t n, const int32_t* rho, const int32_t* lambda, const double* delta,
-                int32_t rho_noise, int32_t rho_min, double delta_min, int32_t* label_out) {
+                int32_t rho_noise, int32_t rho_min, double delta_min, int variant,
+                int32_t* label_out) {
   if (n < 0 || !rho || !lambda || !delta || !label_out) return -1;
+  const int check_rho_min = !(variant & ORC_VAR_CENTER_NO_RHO_MIN);
   /* -3 = not yet known */
   for (int64_t i = 0; i < n; ++i) {
     if (rho[i] < rho_noise)
       label_out[i] = -1;                                  /* Definition 4 */
-    else if (lambda[i] < 0 || (rho[i] >= rho_min && delta[i] >= delta_min))
+    else if (lambda[i] < 0 ||
+             ((!check_rho_min || rho[i] >= rho_min) && delta[i] >= delta_min))
       label_out[i] = (int32_t)i;                          /* Definition 5 */
     else
       label_out[i] = -3;

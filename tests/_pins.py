@@ -44,7 +44,8 @@ def pin_hand_examples(variant=0):
             lam, delta = oracle.dependent(pts, rho, variant=variant)
             assert np.array_equal(lam, g["lambda"]), (name, dtype, lam)
             assert np.array_equal(delta, _golden_delta(g["delta"]) * scale), (name, dtype, delta)
-            lab = oracle.cluster(rho, lam, delta, g["rho_noise"], g["rho_min"], g["delta_min"] * scale)
+            lab = oracle.cluster(rho, lam, delta, g["rho_noise"], g["rho_min"], g["delta_min"] * scale,
+                                 variant=variant)
             assert np.array_equal(lab, g["label"]), (name, dtype, lab)
 
 
@@ -203,7 +204,7 @@ def pin_labels_forest(variant=0):
     pts = w.pts[:3000]
     rho = oracle.density(pts, w.d_cut[0], variant=variant)
     lam, delta = oracle.dependent(pts, rho, variant=variant)
-    lab = oracle.cluster(rho, lam, delta, w.rho_noise[0], w.rho_min[0], w.delta_min[0])
+    lab = oracle.cluster(rho, lam, delta, w.rho_noise[0], w.rho_min[0], w.delta_min[0], variant=variant)
     n = pts.shape[0]
     ids = np.arange(n)
     noise = rho < w.rho_noise[0]
@@ -222,6 +223,28 @@ def pin_labels_forest(variant=0):
     assert np.all(hi)
 
 
+def pin_labels_split_thresholds(variant=0):
+    """The hand-worked split-threshold example (tests/golden): a non-noise point
+    with rho_noise <= rho < rho_min and delta >= delta_min is not a center
+    (Definitions 4-5 read with two thresholds); with one threshold it is."""
+    with open(os.path.join(GOLDEN, "labels_split_thresholds.json")) as f:
+        g = json.load(f)
+    base = np.array(g["points"], dtype=np.int64)
+    for dtype, scale in ((np.int32, 1.0), (np.float32, 0.25)):
+        pts = _as_dtype(base * scale, dtype)
+        rho = oracle.density(pts, g["d_cut"] * scale, variant=variant)
+        assert rho.tolist() == g["rho"]
+        lam, delta = oracle.dependent(pts, rho, variant=variant)
+        assert lam.tolist() == g["lambda"]
+        assert np.array_equal(delta, _golden_delta(g["delta"]) * scale)
+        lab = oracle.cluster(rho, lam, delta, g["rho_noise"], g["rho_min"], g["delta_min"] * scale,
+                             variant=variant)
+        assert lab.tolist() == g["label"]
+        one = oracle.cluster(rho, lam, delta, g["rho_noise"], g["rho_noise"], g["delta_min"] * scale,
+                             variant=variant)
+        assert one.tolist() == g["label_single_threshold"]
+
+
 ALL_PINS = [pin_hand_examples, pin_lattice_2d, pin_lattice_3d, pin_all_equal, pin_line,
             pin_rho_vs_kdtree, pin_rho_parity_and_monotone, pin_zero_cut_prefix_nn,
-            pin_dependent_vs_sorted_prefix, pin_labels_forest]
+            pin_dependent_vs_sorted_prefix, pin_labels_forest, pin_labels_split_thresholds]

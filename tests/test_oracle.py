@@ -23,7 +23,16 @@ def test_pin_holds(pin):
 
 
 PLANTED = [oracle.VAR_EXCLUSIVE, oracle.VAR_NO_SELF, oracle.VAR_TIE_LARGER_ID,
-           oracle.VAR_DIST_TIE_LARGER, oracle.VAR_DROP_LAST_DIM]
+           oracle.VAR_DIST_TIE_LARGER, oracle.VAR_DROP_LAST_DIM, oracle.VAR_CENTER_NO_RHO_MIN]
+
+
+def test_center_threshold_mistake_caught_by_hand_example():
+    """Dropping rho >= rho_min from the center rule is caught by the
+    hand-worked split-threshold example itself, not only by a restatement."""
+    from _pins import pin_labels_split_thresholds
+    pin_labels_split_thresholds(0)
+    with pytest.raises(AssertionError):
+        pin_labels_split_thresholds(oracle.VAR_CENTER_NO_RHO_MIN)
 
 
 @pytest.mark.parametrize("variant", PLANTED)
