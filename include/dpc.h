@@ -353,6 +353,28 @@ int dpc_get_phase_times(void* stream, dpc_phase_times* out);
 /* Device-side status of the last call on `stream` (synchronizes it). */
 int dpc_last_status(void* stream);
 
+/* The float32 certification band of one cutoff.  Host arithmetic only (no
+ * device is touched), so it can be checked without a GPU.  A float32 squared
+ * distance s32 evaluated the way the density and dependent kernels do it
+ * (t_k = x_ik - x_jk rounded to float32, s32 = fmaf(t_k, t_k, s32) over the
+ * coordinates in increasing k, from s32 = 0) and the canonical binary64 value
+ * s64 of the same pair satisfy
+ *     s32 <= t_in   =>  s64 <= fl64(d_cut * d_cut)
+ *     s32 >  t_out  =>  s64 >  fl64(d_cut * d_cut)
+ * and, for two pairs a and b from the same query,
+ *     s32_b > s32_a * band_mul + band_add  =>  s64_b > s64_a,
+ * for float32 coordinates whose squares stay in the normal float32 range
+ * (the entry points' |x| <= 2^60 rule).  Pairs between t_in and t_out are
+ * recounted in binary64; ambiguous dependent candidates are re-ranked in
+ * binary64.  The bound is the standard one for a sum of m = dp + 2 rounded
+ * operations (gamma_m = m u / (1 - m u), u = 2^-24 and 2^-53, dp = 2, 4 or 8
+ * the padded dimension of `dim`), rounded outwards to float32.
+ *   dim  1..8
+ *   out  host, float[4]: t_in, t_out, band_mul, band_add
+ * Returns DPC_OK, or DPC_ERR_ARG for a bad dim, a negative or non-finite
+ * d_cut, or a NULL out. */
+int dpc_cut_band(double d_cut, int32_t dim, float* out);
+
 /* Short description of a status code (static storage). */
 const char* dpc_strerror(int status);
 

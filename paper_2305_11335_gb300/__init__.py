@@ -44,7 +44,7 @@ DPC_FLAG_SYNC_CHECK = 1 << 8
 EXPORTS = ["dpc_density", "dpc_dependent", "dpc_cluster", "dpc_decision_graph", "dpc_priority_range", "dpc_run",
            "dpc_run_host", "dpc_density_static",
            "dpc_get_stats", "dpc_get_phase_times", "dpc_last_status", "dpc_strerror", "dpc_version",
-           "dpc_release"]
+           "dpc_release", "dpc_cut_band"]
 DPC_STATIC_MAX_POINTS = 65536
 
 
@@ -137,6 +137,8 @@ def load(path: str = LIB_PATH):
     lib.dpc_strerror.restype = ctypes.c_char_p
     lib.dpc_version.restype = ctypes.c_char_p
     lib.dpc_release.restype = None
+    lib.dpc_cut_band.argtypes = [ctypes.c_double, i32, vp]
+    lib.dpc_cut_band.restype = ctypes.c_int
     for f in ("dpc_density", "dpc_dependent", "dpc_cluster", "dpc_run", "dpc_run_host", "dpc_get_stats",
               "dpc_last_status"):
         getattr(lib, f).restype = ctypes.c_int
@@ -153,6 +155,16 @@ def strerror(code: int) -> str:
 
 def version() -> str:
     return load().dpc_version().decode()
+
+
+def cut_band(d_cut: float, dim: int):
+    """(t_in, t_out, band_mul, band_add) of one cutoff: the float32
+    certification band (dpc_cut_band; host arithmetic, no device)."""
+    out = (ctypes.c_float * 4)()
+    rc = load().dpc_cut_band(float(d_cut), int(dim), ctypes.cast(out, ctypes.c_void_p))
+    if rc:
+        raise DpcError(rc, "dpc_cut_band")
+    return tuple(float(v) for v in out)
 
 
 def release() -> None:

@@ -998,7 +998,17 @@ using namespace dpc;
 
 extern "C" {
 
-const char* dpc_version(void) { return "0.2.0"; }
+const char* dpc_version(void) { return "0.3.0"; }
+
+int dpc_cut_band(double d_cut, int32_t dim, float* out) {
+  if (!out || dim < 1 || dim > kMaxDim || !std::isfinite(d_cut) || d_cut < 0.0) return DPC_ERR_ARG;
+  const CutHost h = make_cut_host(d_cut, dp_of(dim));
+  out[0] = h.t_in;
+  out[1] = h.t_out;
+  out[2] = h.band_mul;
+  out[3] = h.band_add;
+  return DPC_OK;
+}
 
 const char* dpc_strerror(int status) {
   switch (status) {
