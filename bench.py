@@ -1,8 +1,12 @@
 #!/usr/bin/env python
 """Exact-DPC throughput on GB300: points/s for rho + lambda/delta + labels.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1|c4|c5]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3|c2|c1|c4|c5]
                     [--precision fp32|fp64] [--impl ours|reference]
+
+The default workload is c3: 1e7 points in 3-D (the seed-spreader set), the
+size at which the float32-certified path is compared with the plain binary64
+path.
 
 One step is one ``dpc_run`` call: binning, density, dependent points and
 labels for every cutoff of the workload, inputs resident in HBM, timed with
@@ -13,11 +17,15 @@ the method has no cross-point-set exchange, so N > 1 is replicas only).
 
 Extra keys: ``fp64_path`` (same workload with every distance in binary64),
 ``e2e`` (dpc_run_host: pinned host buffers, copies inside the timed region),
-``roofline`` (the dominant kernel), ``cpu_baseline`` (the CPU oracle on a
-bounded sample of the same workload), ``clocks``, ``phases_ms``.
+``roofline`` (the dominant kernel, against the FFMA rate measured in the same
+run), ``peaks`` (measured FFMA and DFMA rates), ``cpu_baseline`` (the exact
+kd-tree CPU oracle on the same workload, all host cores), ``clocks``,
+``phases_ms``.
 
 ``--impl reference`` times the CPU oracle alone (the paper publishes no code
-that runs here; the oracle is the reference arm), on rank 0.
+that runs here; the oracle is the reference arm), on rank 0: each step is one
+full run of the kd-tree oracle on the workload (rho, lambda, delta at every
+cutoff, labels omitted), as many steps as fit in about two minutes.
 """
 from __future__ import annotations
 
@@ -43,9 +51,8 @@ METRIC = "exact-DPC points/s (rho+delta+labels), FP32-certified vs FP64 path, 1 
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
 
-# FP32 issue peak derived from unit counts and clocks: 152 SMs x 128 FP32
-# lanes x 2 flops per FMA x max SM clock.
-SMS = 152
+# FP32 issue peak derived from unit counts and clocks, for comparison with
+# the measured one: SMs x 128 FP32 lanes x 2 flops per FMA x max SM clock.
 FP32_LANES = 128
 
 
@@ -54,11 +61,12 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "c5"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fast", action="store_true", help="skip the fp64, e2e and CPU legs (profiling runs)")
-    ap.add_argument("--cpu-sample", type=int, default=4096)
+    ap.add_argument("--cpu-instances", type=int, default=96,
+                    help="batched workload: instances the CPU oracle baseline runs (a seeded sample)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default grid-level rule")
     ap.add_argument("--no-graph", action="store_true", help="time plain calls instead of graph replays")
     ap.add_argument("--layout", default="auto", choices=["auto", "union", "segment", "tree", "tensor", "pairs"],
@@ -182,25 +190,32 @@ class ClockSampler:
 # the CPU oracle on a bounded sample
 
 
-def cpu_oracle_sample(job, m, seed):
-    """rho, lambda and delta of m seeded sample points of the full workload
-    (drawn over all points, so instances in proportion to their size), every
-    cutoff, evaluated from the definitions by the oracle.  Returns (points x
-    cutoffs / s, seconds, threads, sample size)."""
+def cpu_oracle_run(job, max_instances, seed):
+    """The exact kd-tree CPU oracle (oracle.tree_run / tree_batch: rho, lambda
+    and delta of every point at every cutoff; labels omitted, they are O(n))
+    on the workload, all host cores.  A single point set runs whole; a batch
+    runs a seeded sample of ``max_instances`` instances.  Returns (points x
+    cutoffs / s, seconds, threads, description of the sample)."""
     import oracle
-    rng = np.random.default_rng(seed)
-    m = min(m, job.N)
-    glob = np.sort(rng.choice(job.N, size=m, replace=False)).astype(np.int64)
-    inst = np.searchsorted(np.asarray(job.pt_offset), glob, side="right") - 1
     t0 = time.perf_counter()
-    for i in np.unique(inst):
-        pts = job.instance(int(i))
-        idx = glob[inst == i] - job.pt_offset[int(i)]
-        for dc in job.d_cut[int(i)]:
-            oracle.density(pts, dc, idx=idx)
-            oracle.dependent_at(pts, dc, idx, max_checks=256)
+    if len(job.sizes) == 1:
+        oracle.tree_run(job.instance(0), job.d_cut[0])
+        units = job.N * job.n_dcut
+        what = "the whole %s (%d points x %d cutoffs)" % (job.name, job.N, job.n_dcut)
+    else:
+        rng = np.random.default_rng(seed)
+        ids = np.sort(rng.choice(len(job.sizes), size=min(max_instances, len(job.sizes)), replace=False))
+        parts = [job.instance(int(i)).reshape(-1) for i in ids]
+        flat = np.concatenate(parts)
+        po = np.concatenate([[0], np.cumsum([job.sizes[int(i)] for i in ids])]).astype(np.int64)
+        co = np.concatenate([[0], np.cumsum([p.size for p in parts])[:-1]]).astype(np.int64)
+        t0 = time.perf_counter()
+        oracle.tree_batch(flat, po, co, [job.dims[int(i)] for i in ids], [job.d_cut[int(i)] for i in ids])
+        units = int(po[-1]) * job.n_dcut
+        what = "%d seeded instances of %s (%d points) x %d cutoffs" % (len(ids), job.name, int(po[-1]),
+                                                                       job.n_dcut)
     dt = time.perf_counter() - t0
-    return m * job.n_dcut / dt, dt, oracle.threads(), m
+    return units / dt, dt, oracle.threads(), what
 
 
 # ---------------------------------------------------------------------------
@@ -365,6 +380,9 @@ def run_ours(args, rank, world, dev):
         torch.distributed.barrier()
     clocks = sampler.stop() if sampler else None
     stats = dpc.dpc_get_stats(stream)
+    # roofline denominators, measured on this GPU right after the timed steps
+    fp32_peak = dpc.probe_peak("fp32", stream=stream)
+    fp64_peak = dpc.probe_peak("fp64", stream=stream)
     # phase breakdown: a separate pass of plain (non-graph) calls with events
     # around every phase on the same stream
     k_ph = max(1, min(args.steps, 5))
@@ -420,12 +438,16 @@ def run_ours(args, rank, world, dev):
     per_launch_ms = step_ms / launches
     achieved = work / (step_ms / 1e3) / 1e12
     clk = pk.get("sm_max_mhz", 2070.0)
-    peak = SMS * FP32_LANES * 2 * clk * 1e6 / 1e12
+    derived = torch.cuda.get_device_properties(dev).multi_processor_count * FP32_LANES * 2 * clk * 1e6 / 1e12
+    peak = fp32_peak / 1e12
+    res["peaks"] = {"fp32_tflops": fp32_peak / 1e12, "fp64_tflops": fp64_peak / 1e12,
+                    "source": "measured in this run (dpc_probe_peak: FFMA / DFMA loops, CUDA events, clocks as "
+                              "found)", "fp32_tflops_derived": derived}
     res["roofline"] = {
         "bound": "alu", "kernel": kernels[model_phase], "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
         "frac": achieved / peak, "traffic": load_traffic(kernels[model_phase], job.name),
-        "peak_source": "derived (no FP32 figure is measured): 152 SMs x 128 FP32 lanes x 2 flops x "
-                       "%.0f MHz max SM clock" % clk,
+        "peak_source": "measured: FFMA loop in this run (dpc_probe_peak), %.1f TFLOP/s; derived from unit "
+                       "counts and the %.0f MHz max clock: %.1f" % (peak, clk, derived),
         "work": ("%.4g flops per step over %d launches: the %d (query, candidate) pairs the density step "
                  "scanned x 3d flops (d > 3: the ideal-grid count rho x 3^d / V_d overestimates clustered "
                  "data)" % (work, launches, int(stats.get("density_pairs", 0)))) if high_d else
@@ -473,12 +495,11 @@ def run_ours(args, rank, world, dev):
                       "ms_per_step": statistics.mean(te), "h2d_bytes_per_step": int(job.flat.nbytes),
                       "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in hout.values())),
                       "api": "dpc_run_host"}
-        # CPU oracle on a bounded sample
-        v, dt, th, m = cpu_oracle_sample(job, args.cpu_sample, 99)
+        # the exact CPU oracle on the same workload
+        v, dt, th, what = cpu_oracle_run(job, args.cpu_instances, 99)
         res["cpu_baseline"] = {"value": v, "unit": "points/s", "cores": th, "kind": "oracle",
-                               "sample": "rho, lambda, delta of %d seeded sample points of the full %s at "
-                                         "each of its %d cutoffs (O(n) each from the definitions, labels "
-                                         "omitted), %.1f s wall" % (m, job.name, job.n_dcut, dt)}
+                               "sample": "kd-tree oracle (rho, lambda, delta from the definitions; labels "
+                                         "omitted) on %s, %.1f s wall" % (what, dt)}
     res["clocks"] = clocks
     return res
 
@@ -651,26 +672,32 @@ def run_next(args, dev, dpc, torch, stream, flush, steps):
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the exact kd-tree CPU oracle on this workload, one
+    full run per step (a batch: the seeded instance sample), as many timed
+    steps as fit in about two minutes after one warm-up run."""
     if rank != 0:
         return None
     job = Job(load_workload(args.workload))
-    m = max(16, 512 // job.n_dcut)
-    for s in range(args.warmup):
-        cpu_oracle_sample(job, 16, 1000 + s)
-    secs = []
-    th = 1
-    for s in range(args.steps):
-        _, dt, th, m = cpu_oracle_sample(job, m, 2000 + s)
+    warm = min(1, args.warmup)
+    for s in range(warm):
+        cpu_oracle_run(job, args.cpu_instances, 99)
+    secs, vals = [], []
+    th, what = 1, ""
+    budget = 120.0
+    while len(secs) < args.steps and (not secs or sum(secs) + secs[-1] <= budget):
+        v, dt, th, what = cpu_oracle_run(job, args.cpu_instances, 99)
         secs.append(dt)
-    value = m * job.n_dcut * len(secs) / sum(secs)
+        vals.append(v)
+    units = vals[0] * secs[0]
+    value = units * len(secs) / sum(secs)
     ms = 1e3 * sum(secs) / len(secs)
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": len(secs), "steps_requested": args.steps, "warmup": warm, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": job.config(),
             "cpu_baseline": {"kind": "oracle", "cores": th, "value": value,
-                             "sample": "%d seeded sample points of %s per step, every cutoff (rho, lambda, "
-                                       "delta from the definitions; labels omitted)" % (m, job.name)},
+                             "sample": "kd-tree oracle on %s per step (rho, lambda, delta from the definitions; "
+                                       "labels omitted); steps capped at about %d s in total" % (what, budget)},
             "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

@@ -48,6 +48,20 @@
  *     that status; otherwise dpc_last_status() returns it later.
  *   - There is no CPU fallback: without a usable CUDA device every compute
  *     entry point returns DPC_ERR_CUDA.
+ *   - Every wait inside a kernel (the radix sort's look-back over earlier
+ *     tiles, the tensor-core density's wait for its MMA) is bounded; when the
+ *     bound runs out the kernel records DPC_ERR_TIMEOUT and finishes.  The
+ *     sort then counts the earlier tiles' digits itself, so its result stays
+ *     exact; the tensor-core density leaves the pieces it did not finish at
+ *     density 0.  Either way no later kernel reads or writes out of bounds.
+ *   - Environment variables, read at every call:
+ *       DPC_WORKSPACE_LIMIT_BYTES  the largest single device allocation the
+ *         library may make; a call that needs more fails with DPC_ERR_OOM
+ *         before any work is queued (unset: no limit).
+ *       DPC_TEST_WAIT_LIMIT  for tests: polls before a bounded wait gives up
+ *         (only lowers the built-in limit; 0 makes every such wait give up at
+ *         once).  A call captured with DPC_FLAG_GRAPH keeps the value it was
+ *         captured with.
  */
 #ifndef DPC_H
 #define DPC_H
@@ -374,6 +388,17 @@ int dpc_last_status(void* stream);
  * Returns DPC_OK, or DPC_ERR_ARG for a bad dim, a negative or non-finite
  * d_cut, or a NULL out. */
 int dpc_cut_band(double d_cut, int32_t dim, float* out);
+
+/* Measured arithmetic peak of this GPU, for the rooflines of the distance
+ * kernels; the paper has no counterpart.  kind 0: float32 fused multiply-add
+ * (FFMA), kind 1: binary64 (DFMA).  *flops_per_s = 2 flops per FMA x the FMAs
+ * of a multiply-add loop (8 independent chains per thread, 4 CTAs of 512
+ * threads per SM) / the median time of 5 launches timed with CUDA events on
+ * `stream`, at whatever clocks the GPU runs (nothing is changed).
+ * Synchronizes the stream; allocates and frees a buffer of 8 KB per SM.
+ * Returns DPC_OK, DPC_ERR_ARG (bad kind or NULL), DPC_ERR_OOM or
+ * DPC_ERR_CUDA. */
+int dpc_probe_peak(int kind, double* flops_per_s, void* stream);
 
 /* Short description of a status code (static storage). */
 const char* dpc_strerror(int status);

@@ -44,7 +44,7 @@ DPC_FLAG_SYNC_CHECK = 1 << 8
 EXPORTS = ["dpc_density", "dpc_dependent", "dpc_cluster", "dpc_decision_graph", "dpc_priority_range", "dpc_run",
            "dpc_run_host", "dpc_density_static",
            "dpc_get_stats", "dpc_get_phase_times", "dpc_last_status", "dpc_strerror", "dpc_version",
-           "dpc_release", "dpc_cut_band"]
+           "dpc_release", "dpc_cut_band", "dpc_probe_peak"]
 DPC_STATIC_MAX_POINTS = 65536
 
 
@@ -139,6 +139,8 @@ def load(path: str = LIB_PATH):
     lib.dpc_release.restype = None
     lib.dpc_cut_band.argtypes = [ctypes.c_double, i32, vp]
     lib.dpc_cut_band.restype = ctypes.c_int
+    lib.dpc_probe_peak.argtypes = [ctypes.c_int, vp, vp]
+    lib.dpc_probe_peak.restype = ctypes.c_int
     for f in ("dpc_density", "dpc_dependent", "dpc_cluster", "dpc_run", "dpc_run_host", "dpc_get_stats",
               "dpc_last_status"):
         getattr(lib, f).restype = ctypes.c_int
@@ -165,6 +167,15 @@ def cut_band(d_cut: float, dim: int):
     if rc:
         raise DpcError(rc, "dpc_cut_band")
     return tuple(float(v) for v in out)
+
+
+def probe_peak(kind: str = "fp32", stream=None) -> float:
+    """Measured FMA throughput of this GPU in flop/s (dpc_probe_peak): "fp32"
+    (FFMA) or "fp64" (DFMA)."""
+    v = ctypes.c_double(0.0)
+    _check(load().dpc_probe_peak({"fp32": 0, "fp64": 1}[kind], ctypes.cast(ctypes.pointer(v), ctypes.c_void_p),
+                                 _stream(stream)), "dpc_probe_peak")
+    return float(v.value)
 
 
 def release() -> None:

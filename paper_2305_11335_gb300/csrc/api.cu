@@ -33,6 +33,31 @@ namespace dpc {
 
 long long g_kernel_launches = 0;
 
+uint32_t wait_limit(uint32_t dflt) {
+  const char* e = std::getenv("DPC_TEST_WAIT_LIMIT");
+  if (!e || !*e) return dflt;
+  char* end = nullptr;
+  const unsigned long long v = std::strtoull(e, &end, 10);
+  if (end == e) return dflt;
+  return v < dflt ? (uint32_t)v : dflt;
+}
+
+bool dev_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  const char* e = std::getenv("DPC_WORKSPACE_LIMIT_BYTES");
+  if (e && *e) {
+    char* end = nullptr;
+    const unsigned long long cap = std::strtoull(e, &end, 10);
+    if (end != e && bytes > cap) return false;
+  }
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return false;
+  }
+  return true;
+}
+
 unsigned sm_count() {
   constexpr int kDevs = 64;
   static int cached[kDevs] = {};
@@ -360,8 +385,7 @@ struct Workspace {
     const size_t o_qpos = take(4 * N), o_qs1 = take(4 * N), o_qs1d = take(8 * N);
     const size_t o_qpos2 = take(4 * N), o_qs1_2 = take(4 * N), o_qs1d2 = take(8 * N);
     void* p = nullptr;
-    if (cudaMalloc(&p, off) != cudaSuccess) {
-      cudaGetLastError();
+    if (!dev_alloc(&p, off)) {
       cap_n = 0;
       cap_inst = 0;
       return DPC_ERR_OOM;
@@ -433,11 +457,7 @@ struct Workspace {
       up_dev = up_host = nullptr;
       up_bytes = 0;
     }
-    if (cudaMalloc(&up_dev, b) != cudaSuccess) {
-      cudaGetLastError();
-      up_dev = nullptr;
-      return DPC_ERR_OOM;
-    }
+    if (!dev_alloc(&up_dev, b)) return DPC_ERR_OOM;
     if (cudaMallocHost(&up_host, b) != cudaSuccess) {
       cudaGetLastError();
       cudaFree(up_dev);
@@ -456,9 +476,7 @@ struct Workspace {
       cudaFree(*p);
       *p = nullptr;
     }
-    if (cudaMalloc(p, b) != cudaSuccess) {
-      cudaGetLastError();
-      *p = nullptr;
+    if (!dev_alloc(p, b)) {
       *have = 0;
       return DPC_ERR_OOM;
     }
@@ -473,8 +491,7 @@ struct Workspace {
       cudaFree(io);
       io = nullptr;
     }
-    if (cudaMalloc(&io, b) != cudaSuccess) {
-      cudaGetLastError();
+    if (!dev_alloc(&io, b)) {
       io_bytes = 0;
       return DPC_ERR_OOM;
     }

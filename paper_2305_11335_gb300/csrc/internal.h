@@ -15,6 +15,16 @@ namespace dpc {
 // of it); queried once per device.
 unsigned sm_count();
 
+// Polls a bounded device-side wait makes before it gives up: `dflt`, or the
+// smaller value in the environment variable DPC_TEST_WAIT_LIMIT (tests use 0
+// to make every such wait give up at once and check the recovery path).
+uint32_t wait_limit(uint32_t dflt);
+
+// Largest single device allocation the library may make (the environment
+// variable DPC_WORKSPACE_LIMIT_BYTES, unset = no limit).  dev_alloc fails
+// without calling cudaMalloc when a request is larger.
+bool dev_alloc(void** p, size_t bytes);
+
 // Kernels enqueued by the current call (the entry points hold the library
 // lock while enqueueing, so a plain counter suffices).
 extern long long g_kernel_launches;

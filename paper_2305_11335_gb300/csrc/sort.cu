@@ -34,7 +34,7 @@ static_assert(kRsTile == (int)kSortTile, "tile size of the scratch formula");
 constexpr unsigned long long kFlagAgg = 1ull << 62;     // the tile's own counts
 constexpr unsigned long long kFlagPrefix = 2ull << 62;  // counts of this and every earlier tile
 constexpr unsigned long long kFlagMask = 3ull << 62;
-constexpr uint32_t kSpinLimit = 1u << 20;  // ld.acquire polls of one earlier tile
+constexpr uint32_t kSpinLimit = 1u << 20;  // ld.acquire polls of earlier tiles before giving up
 
 // The sort's scratch: status[ntiles][256] (u64, reused by every pass), the
 // digit counts and starts of every pass [kMaxPasses][256], a tile counter per
@@ -113,7 +113,7 @@ struct ScatterSmem {
 __global__ void __launch_bounds__(kRsThreads)
 k_rs_onesweep(const unsigned long long* __restrict__ kin, const uint32_t* __restrict__ vin,
               unsigned long long* __restrict__ kout, uint32_t* __restrict__ vout, uint32_t n,
-              int pass, const ClassGeom* __restrict__ cls, SortScratch z) {
+              int pass, const ClassGeom* __restrict__ cls, SortScratch z, uint32_t spin_limit) {
   if (pass >= sort_passes(cls->S, cls->ib)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ScatterSmem& S = *reinterpret_cast<ScatterSmem*>(smem_raw);
@@ -176,8 +176,15 @@ k_rs_onesweep(const unsigned long long* __restrict__ kin, const uint32_t* __rest
         const unsigned long long v = ld_acquire(z.status + (size_t)t * 256u + d);
         const unsigned long long f = v & kFlagMask;
         if (f == 0ull) {
-          if (++spins > kSpinLimit) {  // an earlier tile never published: give up
+          if (spins++ >= spin_limit) {
+            // an earlier tile has not published in time: record it, and count
+            // this digit over every earlier tile's items directly (slow but
+            // exact, so the sort and everything after it stay well formed)
             set_status(cls->status, kStatusTimeout);
+            before = 0;
+            const uint32_t upto = tile * (uint32_t)kRsTile;  // < n: this tile exists
+            for (uint32_t i = 0; i < upto; ++i)
+              before += ((uint32_t)(kin[i] >> shift) & 255u) == (uint32_t)d ? 1u : 0u;
             break;
           }
           continue;
@@ -252,6 +259,7 @@ void launch_sort(unsigned long long* codes_a, unsigned long long* codes_b, uint3
   const uint32_t nt = tiles_for(n);
   sort_init();
   const SortScratch z = sort_scratch(hist, nt);
+  const uint32_t spin = wait_limit(kSpinLimit);
   // counts, starts and tile counters of every pass
   cudaMemsetAsync(z.count, 0, sizeof(uint32_t) * (2 * kMaxPasses * 256 + kMaxPasses), st);
   unsigned hb = nt < sm_count() * 4u ? nt : sm_count() * 4u;
@@ -263,7 +271,7 @@ void launch_sort(unsigned long long* codes_a, unsigned long long* codes_b, uint3
     const int i = pass & 1, o = (pass + 1) & 1;
     cudaMemsetAsync(z.status, 0, sizeof(unsigned long long) * 256u * nt, st);
     k_rs_onesweep<<<nt, kRsThreads, sizeof(ScatterSmem), st>>>(kb[i], vb[i], kb[o], vb[o], n, pass,
-                                                               cls, z);
+                                                               cls, z, spin);
   }
   count_launches(2 + kMaxPasses);
 }

@@ -101,8 +101,8 @@ __device__ __forceinline__ void put_row(float (*ops)[ROWS * kTcK], int r, const 
   }
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
-  for (uint32_t it = 0; it < kTcWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                  " selp.b32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(addr), "r"(parity) : "memory");
@@ -131,8 +131,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 
 // The piece list: (hash slot, first point) of every 128-point piece of every
 // occupied cell, from a scan of the hash table (one atomic per warp).
+// Also gives every point the order key of density 0 (and rho 0) first: a
+// CTA that gives up on a wait (the MMA did not complete in time) leaves its
+// pieces unwritten, and the dependent phase must still see one valid key,
+// with the point's own id, at every position.
 __global__ void k_tc_pieces(HashInfo* hi, const unsigned long long* __restrict__ hkeys,
-                            const uint2* __restrict__ hvals, uint32_t n, uint2* __restrict__ pieces) {
+                            const uint2* __restrict__ hvals, uint32_t n, uint2* __restrict__ pieces,
+                            const uint32_t* __restrict__ sid, int32_t* __restrict__ rho_out,
+                            unsigned long long* __restrict__ skey) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const uint32_t id = sid[q];
+    rho_out[id] = 0;
+    skey[q] = order_key(0, id);
+  }
   const uint32_t T = hi->hmask + 1;
   const int lane = threadIdx.x & 31;
   const uint32_t T_pad = (T + 31) & ~31u;
@@ -160,7 +171,7 @@ k_density_tc(const float* __restrict__ spts, const uint32_t* __restrict__ sid, C
              const CutGeom* __restrict__ cuts, HashInfo* hi,
              const unsigned long long* __restrict__ hkeys, const uint2* __restrict__ hvals,
              const uint2* __restrict__ pieces, int32_t* __restrict__ rho_out,
-             unsigned long long* __restrict__ skey, Counters* ctr) {
+             unsigned long long* __restrict__ skey, Counters* ctr, uint32_t poll_limit) {
   constexpr int DP = 8;
   extern __shared__ __align__(128) unsigned char tc_smem_raw[];
   TcSmem& sm = *reinterpret_cast<TcSmem*>(tc_smem_raw);
@@ -318,11 +329,13 @@ k_density_tc(const float* __restrict__ spts, const uint32_t* __restrict__ sid, C
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                        :: "r"(mbar) : "memory");
         }
-        const bool ok = mbar_wait(mbar, phase);
+        const bool ok = mbar_wait(mbar, phase, poll_limit);
         phase ^= 1u;
         if (__syncthreads_or(!ok)) {  // the MMA did not finish in time: record and stop
           if (tid == 0) set_status(cv.cls->status, kStatusTimeout);
-          mbar_wait(mbar, phase ^ 1u);  // give an MMA still in flight a last chance
+          // let the MMA in flight finish (the full limit, whatever poll_limit
+          // was) before tensor memory is freed and the CTA exits
+          mbar_wait(mbar, phase ^ 1u, kTcWaitLimit);
           stop = true;
           break;
         }
@@ -407,14 +420,15 @@ void launch_density_tc(int g, const float* spts, const uint32_t* sid, const Clas
   }
   cudaMemsetAsync(&hi->work, 0, sizeof(uint32_t), st);
   cudaMemsetAsync(&hi->npieces, 0, sizeof(uint32_t), st);
-  k_tc_pieces<<<sm_count() * 8u, 256, 0, st>>>(hi, hkeys, hvals, cv.N, pieces);
+  k_tc_pieces<<<sm_count() * 8u, 256, 0, st>>>(hi, hkeys, hvals, cv.N, pieces, sid, rho_out, skey);
   const unsigned grid = sm_count() * 2u;  // two resident CTAs per SM take the pieces one by one
+  const uint32_t poll = wait_limit(kTcWaitLimit);
   if (g == 3)
     k_density_tc<3><<<grid, kTcThreads, kTcSmemBytes, st>>>(spts, sid, cv, cuts, hi, hkeys, hvals,
-                                                            pieces, rho_out, skey, ctr);
+                                                            pieces, rho_out, skey, ctr, poll);
   else
     k_density_tc<4><<<grid, kTcThreads, kTcSmemBytes, st>>>(spts, sid, cv, cuts, hi, hkeys, hvals,
-                                                            pieces, rho_out, skey, ctr);
+                                                            pieces, rho_out, skey, ctr, poll);
   count_launches(2);
 }
 

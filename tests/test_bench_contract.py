@@ -1,5 +1,5 @@
 """The benchmark's host-side contract, without a GPU: the reference arm (the
-CPU oracle timed on a bounded sample) prints one well-formed JSON line, and
+kd-tree CPU oracle timed on the workload) prints one well-formed JSON line, and
 the byte models of the streaming-phase rooflines are the documented ones."""
 import json
 import os
@@ -13,8 +13,8 @@ sys.path.insert(0, ROOT)
 
 
 def test_reference_arm_json_line():
-    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "c2",
+                        "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.strip()]
     assert len(lines) == 1
@@ -27,6 +27,7 @@ def test_reference_arm_json_line():
     assert res["cpu_baseline"]["value"] == res["value"]
     assert res["e2e"]["h2d_bytes_per_step"] == 0 and res["e2e"]["d2h_bytes_per_step"] == 0
     assert res["config"]["workload"].startswith("c2_")
+    assert 1 <= res["steps"] <= 2 and res["steps_requested"] == 2
 
 
 def test_phase_roofline_byte_model():

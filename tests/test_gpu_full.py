@@ -1,16 +1,25 @@
-"""GPU parity at the full workload sizes (1e6 to 1e7 points).
+"""GPU parity at the full workload sizes, element by element.
 
-The oracle cannot evaluate every point of these sets (O(n^2)), so each test
-  * compares seeded sample points one by one with the oracle's per-point
-    forms (density from the definition; dependent point by walking candidates
-    in distance order with densities computed from scratch), bit for bit;
-  * checks properties that hold at any size on every point: delta is the
-    canonical binary64 distance to lambda, lambda is higher in the order, one
-    top point per cutoff, labels form the forest the definitions describe;
-  * checks that the float32-certified and the plain binary64 paths agree
-    byte for byte.
+Every point of the 1e6-point 2-D set, the 1e7-point 3-D set and the 2e6-point
+7-D set at all four of its cutoffs is compared with the kd-tree oracle
+(oracle.tree_run: the same definitions as the brute-force oracle, which it
+is pinned against in test_oracle_tree.py): rho, lambda and labels equal,
+delta identical to the last bit.  The float32-certified and the plain binary64
+paths must also agree byte for byte.
+
+The 4096-instance batch (1.6e8 points, 8 cutoffs each) is compared instance
+by instance with digests of the oracle's results (tests/golden/
+c4_oracle_digest.json, written by tests/golden/derive_c4_digest.py from the
+oracle alone), after checking that this machine draws the same inputs; any
+instance whose digest differs is recomputed with the oracle here to report the
+differing elements.  A seeded sample of instances is also recomputed with the
+oracle live, every cutoff, element by element.
+
 The launch configuration is the one bench.py times (dpc_run, all cutoffs).
 """
+import json
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -18,8 +27,12 @@ import torch
 import oracle
 import paper_2305_11335_gb300 as dpc
 import workloads as W
+from _digest import batch_input_digest, instance_digest
+from _gpu_util import assert_same
 
 pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -37,58 +50,25 @@ def run(w, precision):
     return {k: v.cpu().numpy() for k, v in out.items()}
 
 
-def canonical_s64(pts, i, j):
-    """The binary64 squared distance, coordinates in increasing order, numpy
-    elementwise (round to nearest, no contraction)."""
-    x = pts.astype(np.float64)
-    s = np.zeros(len(i), np.float64)
-    for k in range(pts.shape[1]):
-        t = x[i, k] - x[j, k]
-        s = s + t * t
-    return s
+def oracle_full(w):
+    """The oracle's rho, lambda, delta and labels of every point at every
+    cutoff of a single-set workload."""
+    r = oracle.tree_run(w.pts, w.d_cut)
+    r["label"] = np.stack([oracle.cluster(r["rho"][c], r["lam"][c], r["delta"][c], w.rho_noise[c], w.rho_min[c],
+                                          w.delta_min[c]) for c in range(len(w.d_cut))])
+    return r
 
 
-def check_properties(w, out, c):
-    rho, lam, delta, lab = out["rho"][c], out["lam"][c], out["delta"][c], out["label"][c]
-    n = w.n
-    ids = np.arange(n)
-    assert rho.min() >= 1
-    assert (int(rho.sum()) - n) % 2 == 0
-    root = np.flatnonzero(lam < 0)
-    assert len(root) == 1, "exactly one point without a dependent point"
-    r = root[0]
-    assert np.isinf(delta[r]) and rho[r] == rho.max() and r == np.flatnonzero(rho == rho.max()).min()
-    nr = lam >= 0
-    hi = (rho[lam[nr]] > rho[nr]) | ((rho[lam[nr]] == rho[nr]) & (lam[nr] < ids[nr]))
-    assert hi.all(), "dependent points are higher in the order"
-    s = canonical_s64(w.pts, ids[nr], lam[nr])
-    assert np.array_equal(np.sqrt(s).view(np.int64), delta[nr].view(np.int64)), "delta = D(x, lambda)"
-    noise = rho < w.rho_noise[c]
-    center = ~noise & ((lam < 0) | ((rho >= w.rho_min[c]) & (delta >= w.delta_min[c])))
-    assert np.array_equal(lab == -1, noise)
-    assert np.array_equal(lab[center], ids[center])
-    rest = ~noise & ~center
-    assert np.array_equal(lab[rest], lab[lam[rest]])
-
-
-def check_samples(w, out, c, m, extra_ids, seed, min_resolved=0.8, max_checks=48):
-    rng = np.random.default_rng(seed)
-    idx = np.unique(np.concatenate([rng.choice(w.n, m, replace=False), extra_ids])).astype(np.int64)
-    rho_o = oracle.density(w.pts, w.d_cut[c], idx=idx)
-    assert np.array_equal(out["rho"][c][idx], rho_o), "sampled densities"
-    lam_o, delta_o, rho2, ok = oracle.dependent_at(w.pts, w.d_cut[c], idx, max_checks=max_checks)
-    assert np.array_equal(rho2, rho_o)
-    assert ok.mean() >= min_resolved, ok.mean()
-    assert np.array_equal(out["lam"][c][idx[ok]], lam_o[ok]), "sampled dependent points"
-    assert np.array_equal(out["delta"][c][idx[ok]].view(np.int64), delta_o[ok].view(np.int64))
-    return int(ok.sum())
+def compare_all_cutoffs(w, got, ref):
+    for c in range(len(w.d_cut)):
+        assert_same({k: v[c] for k, v in got.items()}, {k: v[c] for k, v in ref.items()},
+                    "%s cut %d (d_cut %r)" % (w.name, c, w.d_cut[c]))
 
 
 def test_c2_full():
     w = W.c2()
     f32 = run(w, "fp32")
-    check_properties(w, f32, 0)
-    check_samples(w, f32, 0, 256, w.noise_ids[:32], 21)
+    compare_all_cutoffs(w, f32, oracle_full(w))
     f64 = run(w, "fp64")
     for k in f32:
         assert np.array_equal(f32[k].view(np.uint8), f64[k].view(np.uint8)), k
@@ -96,55 +76,78 @@ def test_c2_full():
 
 def test_c3_full():
     w = W.c3()
-    out = run(w, "fp32")
-    check_properties(w, out, 0)
-    check_samples(w, out, 0, 96, w.noise_ids[:16], 31, max_checks=24)
+    f32 = run(w, "fp32")
+    compare_all_cutoffs(w, f32, oracle_full(w))
+    f64 = run(w, "fp64")
+    for k in f32:
+        assert np.array_equal(f32[k].view(np.uint8), f64[k].view(np.uint8)), k
 
 
 def test_c5_full_sweep():
     w = W.c5()
     out = run(w, "fp32")
-    for c in range(len(w.d_cut)):
-        check_properties(w, out, c)
-        assert np.all(out["rho"][c] >= out["rho"][c - 1]) if c else True  # rho grows with d_cut
-    check_samples(w, out, 0, 96, w.noise_ids[:16], 51, max_checks=24)
-    check_samples(w, out, 3, 48, w.noise_ids[16:24], 52, max_checks=24)
+    compare_all_cutoffs(w, out, oracle_full(w))
 
 
-def test_c4_full_batch():
-    """The 4096-instance batch with 8 cutoffs each, in one dpc_run (the call
-    bench.py times).  The 8 smallest instances are compared with the oracle in
-    full for every cutoff; 40 random instances get the whole-instance
-    properties and sampled oracle checks at the first and last cutoff."""
-    from types import SimpleNamespace
-    from _gpu_util import assert_same
+# ---------------------------------------------------------------------------
+# the batched workload
 
-    w = W.c4()
+
+def c4_run(w):
     batch = dpc.Batch([0] + list(np.cumsum(w.sizes)), w.dims, w.d_cut, coord_offset=w.coord_offset)
     params = dpc.make_params(batch, w.rho_noise, w.rho_min, w.delta_min)
     out = dpc.dpc_run(torch.from_numpy(w.flat).cuda(), batch, params, sync=True)
+    return batch, out
+
+
+def c4_oracle(w, ids):
+    """Oracle outputs of the instances ``ids`` (all cutoffs), per instance."""
+    parts = [w.instance(int(i)).reshape(-1) for i in ids]
+    flat = np.concatenate(parts)
+    po = np.concatenate([[0], np.cumsum([w.sizes[int(i)] for i in ids])]).astype(np.int64)
+    co = np.concatenate([[0], np.cumsum([p.size for p in parts])[:-1]]).astype(np.int64)
+    r = oracle.tree_batch(flat, po, co, [w.dims[int(i)] for i in ids], [w.d_cut[int(i)] for i in ids])
+    ncut = len(w.d_cut[0])
+    res = {}
+    for t, i in enumerate(ids):
+        lo, hi = po[t], po[t + 1]
+        one = {k: v[:, lo:hi] for k, v in r.items()}
+        one["label"] = np.stack([oracle.cluster(one["rho"][c], one["lam"][c], one["delta"][c],
+                                                w.rho_noise[int(i) * ncut + c], w.rho_min[int(i) * ncut + c],
+                                                w.delta_min[int(i) * ncut + c]) for c in range(ncut)])
+        res[int(i)] = one
+    return res
+
+
+def test_c4_full_batch():
+    """Every instance at every cutoff: the GPU's per-instance digests against
+    the oracle's, plus 64 seeded instances (and the 8 smallest) recomputed
+    with the oracle element by element."""
+    w = W.c4()
+    with open(os.path.join(GOLDEN, "c4_oracle_digest.json")) as f:
+        ref = json.load(f)
+    assert batch_input_digest(w) == ref["input_sha256"], \
+        "this machine draws different c4 inputs than the ones the stored oracle digests describe"
+    batch, out = c4_run(w)
     po = batch.pt_offset
     ncut = batch.n_dcut
-
-    def inst_out(i):
-        return {k: v[:, po[i]:po[i + 1]].cpu().numpy() for k, v in out.items()}
-
-    order = np.argsort(w.sizes, kind="stable")
-    for i in order[:8]:
-        got = inst_out(i)
-        pts = w.instance(i)
-        for c in range(ncut):
-            j = i * ncut + c
-            ref = oracle.run(pts, w.d_cut[i][c], w.rho_noise[j], w.rho_min[j], w.delta_min[j])
-            assert_same({k: v[c] for k, v in got.items()}, ref, "instance %d cut %d" % (i, c))
+    bad = []
+    group = 256
+    for g0 in range(0, w.n_inst, group):
+        lo, hi = po[g0], po[min(w.n_inst, g0 + group)]
+        part = {k: v[:, lo:hi].cpu().numpy() for k, v in out.items()}
+        for i in range(g0, min(w.n_inst, g0 + group)):
+            dg = instance_digest(part["rho"], part["lam"], part["delta"], part["label"], po[i] - lo,
+                                 po[i + 1] - lo)
+            if dg != ref["instances"][i]:
+                bad.append(i)
     rng = np.random.default_rng(41)
-    for i in rng.choice(len(w.sizes), 40, replace=False):
-        got = inst_out(i)
-        view = SimpleNamespace(pts=w.instance(i), n=w.sizes[i], d_cut=w.d_cut[i],
-                               rho_noise=w.rho_noise[i * ncut:(i + 1) * ncut],
-                               rho_min=w.rho_min[i * ncut:(i + 1) * ncut],
-                               delta_min=w.delta_min[i * ncut:(i + 1) * ncut])
-        for c in (0, ncut - 1):
-            check_properties(view, got, c)
-            check_samples(view, got, c, 12, np.zeros(0, np.int64), 4100 + int(i), min_resolved=0.5,
-                          max_checks=32)
+    live = sorted(set(rng.choice(w.n_inst, 64, replace=False).tolist()) |
+                  set(np.argsort(w.sizes, kind="stable")[:8].tolist()) | set(bad[:16]))
+    want = c4_oracle(w, live)
+    for i in live:
+        got = {k: v[:, po[i]:po[i + 1]].cpu().numpy() for k, v in out.items()}
+        for c in range(ncut):
+            assert_same({k: v[c] for k, v in got.items()}, {k: v[c] for k, v in want[i].items()},
+                        "instance %d (n=%d, d=%d) cut %d" % (i, w.sizes[i], w.dims[i], c))
+    assert not bad, "%d instances differ from the oracle's digests, first %s" % (len(bad), bad[:10])
