@@ -54,6 +54,7 @@ TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
 # FP32 issue peak derived from unit counts and clocks, for comparison with
 # the measured one: SMs x 128 FP32 lanes x 2 flops per FMA x max SM clock.
 FP32_LANES = 128
+LAYOUT_NAMES = ["?", "union", "segment", "tree", "tensor", "pairs", "cell"]
 
 
 def parse():
@@ -69,7 +70,7 @@ def parse():
                     help="batched workload: instances the CPU oracle baseline runs (a seeded sample)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default grid-level rule")
     ap.add_argument("--no-graph", action="store_true", help="time plain calls instead of graph replays")
-    ap.add_argument("--layout", default="auto", choices=["auto", "union", "segment", "tree", "tensor", "pairs"],
+    ap.add_argument("--layout", default="auto", choices=["auto", "union", "segment", "tree", "tensor", "pairs", "cell"],
                     help="fixed kernel layout (auto: the autotuned choice)")
     ap.add_argument("--near-shift", type=int, default=-1, choices=[-1, 0, 1, 2],
                     help="fixed near-phase grid level below the density's (-1: the autotuned choice)")
@@ -396,8 +397,8 @@ def run_ours(args, rank, world, dev):
                    "grid_level": "autotuned in the first warm-up call" if not args.no_autotune else "default rule",
                    "block_radius": int(stats.get("block_radius", 0)),
                    "near_shift": int(stats.get("near_shift", 0)),
-                   "layouts": {"density": ["?", "union", "segment", "tree", "tensor", "pairs"][int(stats.get("density_layout", 0))],
-                               "near": ["?", "union", "segment", "tree", "tensor", "pairs"][int(stats.get("near_layout", 0))]},
+                   "layouts": {"density": LAYOUT_NAMES[int(stats.get("density_layout", 0))],
+                               "near": LAYOUT_NAMES[int(stats.get("near_layout", 0))]},
                    "parallelism": "replicas" if world > 1 else "1 GPU"})
     res = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -418,9 +419,10 @@ def run_ours(args, rank, world, dev):
     pk, pk_kind = peaks()
     single = {p: v for p, v in phases.items() if p in ("density", "near", "far", "tree", "maxkey")}
     dom = max(single, key=lambda p: single[p][0]) if single else None
-    kernels = {"density": {2: "k_density_seg", 4: "k_density_tc", 5: "k_density_pairs"}.get(
+    kernels = {"density": {2: "k_density_seg", 4: "k_density_tc", 5: "k_density_pairs", 6: "k_density_cell"}.get(
         stats.get("density_layout"), "k_density"),
-               "near": {2: "k_dep_near_seg", 3: "k_near_to_far"}.get(stats.get("near_layout"), "k_dep_near")}
+               "near": {2: "k_dep_near_seg", 3: "k_near_to_far", 6: "k_dep_near_cell"}.get(stats.get("near_layout"),
+                                                                                          "k_dep_near")}
     model_phase = dom if dom in kernels else max(("density", "near"), key=lambda p: phases[p][0])
     work, mean_rho = block_work(job, out["rho"])
     high_d = max(job.dims) > 3

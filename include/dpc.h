@@ -125,7 +125,10 @@ enum {
  * dimensions with DPC_PREC_FP32_CERT: distance tiles on the tensor cores with a
  * certified error band; other cases use segment), 5 = pairs (density only:
  * the segment layout evaluating every unordered pair once and counting it for
- * both points).  Results do not depend on it. */
+ * both points), 6 = cell (density and near phase: one warp per occupied cell,
+ * the cell's block staged in shared memory, every lane one query -- or a share
+ * of one query's candidates in cells of fewer than 32 points -- against all of
+ * it).  Results do not depend on it. */
 #define DPC_FLAG_LAYOUT(v) ((uint32_t)(v) << 16)
 #define DPC_FLAG_LAYOUT_MASK (0x7u << 16)
 /* dpc_run only: capture the call's kernels into a CUDA graph the first time a

@@ -94,7 +94,7 @@ def DPC_FLAG_RADIUS(r: int) -> int:
     return (int(r) & 7) << 12
 
 
-LAYOUTS = {"auto": 0, "union": 1, "segment": 2, "tree": 3, "tensor": 4, "pairs": 5}
+LAYOUTS = {"auto": 0, "union": 1, "segment": 2, "tree": 3, "tensor": 4, "pairs": 5, "cell": 6}
 
 
 def DPC_FLAG_LAYOUT(layout: str) -> int:

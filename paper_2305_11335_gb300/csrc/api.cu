@@ -140,7 +140,7 @@ int check_flags(uint32_t flags) {
   if (prec != DPC_PREC_FP64 && prec != DPC_PREC_FP32_CERT) return DPC_ERR_UNSUPPORTED;
   if (flags & ~kKnownFlags) return DPC_ERR_ARG;
   if (((flags & DPC_FLAG_RADIUS_MASK) >> 12) > 5) return DPC_ERR_ARG;
-  if (((flags & DPC_FLAG_LAYOUT_MASK) >> 16) > 5) return DPC_ERR_ARG;
+  if (((flags & DPC_FLAG_LAYOUT_MASK) >> 16) > 6) return DPC_ERR_ARG;
   if (((flags & DPC_FLAG_NEAR_SHIFT_MASK) >> 20) > 3) return DPC_ERR_ARG;
   return DPC_OK;
 }

@@ -556,6 +556,11 @@ void launch_density(int dp, int g, bool fp64, int layout, const float* spts,
     }
     layout = kLayoutSegment;
   }
+  if (layout == kLayoutCell) {
+    launch_density_cell(dp, g, fp64, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr,
+                        st);
+    return;
+  }
   if (g == 1) density_dg<2, 1>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, seg_cells, st);
   else if (g == 2) density_dg<2, 2>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, seg_cells, st);
   else if (g == 3) density_dg<4, 3>(fp64, layout, spts, scode, sid, cv, cuts, hi, hkeys, hvals, rho_out, skey, ctr, seg_cells, st);

@@ -1113,6 +1113,11 @@ void launch_dep_near(int dp, int g, bool fp64, int layout, const float* spts,
   if (cv.N == 0) return;
   cudaMemsetAsync(&ctr->queue_n, 0, sizeof(unsigned int), st);
   cudaMemsetAsync(&ctr->queue2_n, 0, sizeof(unsigned int), st);
+  if (layout == kLayoutCell) {
+    launch_dep_near_cell(dp, g, fp64, spts, scode, skey, cv, rho_skip, pts, dtype, cuts, hi, hkeys,
+                         hvals, lambda, delta, q, ctr, st);
+    return;  // counted there
+  }
   if (layout == kLayoutTree) {
     k_near_to_far<<<grid_for((uint64_t)cv.nchunk * 32u, 256, sm_count() * 16u), 256, 0, st>>>(
         skey, cv, cuts, rho_skip, lambda, delta, q, ctr);

@@ -118,7 +118,12 @@ void launch_tree_maxkey(const unsigned long long* skey, const float* spts, int d
 // seg_cells (segment layouts): a segment may span several consecutive cells
 // while their bounding box grown by R holds at most seg_cells cells (0: one
 // cell per segment)
-enum { kLayoutUnion = 1, kLayoutSegment = 2, kLayoutTree = 3, kLayoutTensor = 4, kLayoutPairs = 5 };
+//   cell     one warp per occupied cell: the block's points staged in shared
+//            memory, every lane one query (or a share of one query's
+//            candidates for cells below 32 points) against all of them
+//            (cell_tile.cu)
+enum { kLayoutUnion = 1, kLayoutSegment = 2, kLayoutTree = 3, kLayoutTensor = 4, kLayoutPairs = 5,
+       kLayoutCell = 6 };
 
 // ---- density (density.cu) -------------------------------------------------------
 // rho of every point for one cutoff (cuts: [ninst]); rho_out is indexed by
@@ -135,6 +140,12 @@ void launch_density_tc(int g, const float* spts, const uint32_t* sid, const Clas
                        const CutGeom* cuts, HashInfo* hi, const unsigned long long* hkeys,
                        const uint2* hvals, uint2* pieces, int32_t* rho_out,
                        unsigned long long* skey, Counters* ctr, cudaStream_t st);
+// the cell layout of the density step (cell_tile.cu)
+void launch_density_cell(int dp, int g, bool fp64, const float* spts,
+                         const unsigned long long* scode, const uint32_t* sid, const ClassView& cv,
+                         const CutGeom* cuts, const HashInfo* hi, const unsigned long long* hkeys,
+                         const uint2* hvals, int32_t* rho_out, unsigned long long* skey,
+                         Counters* ctr, cudaStream_t st);
 // order keys of sorted points from densities given by output index
 void launch_keys_from_rho(const int32_t* rho, const uint32_t* sid, uint32_t n,
                           unsigned long long* skey, cudaStream_t st);
@@ -157,6 +168,13 @@ void launch_dep_near(int dp, int g, bool fp64, int layout, const float* spts,
                      const uint2* hvals, int32_t* lambda, double* delta, FarQueue q, Counters* ctr,
                      cudaStream_t st,
                      int seg_cells = 0);
+// the cell layout of the near phase (cell_tile.cu)
+void launch_dep_near_cell(int dp, int g, bool fp64, const float* spts,
+                          const unsigned long long* scode, const unsigned long long* skey,
+                          const ClassView& cv, int32_t rho_skip, const void* pts, int dtype,
+                          const CutGeom* cuts, const HashInfo* hi,
+                          const unsigned long long* hkeys, const uint2* hvals, int32_t* lambda,
+                          double* delta, FarQueue q, Counters* ctr, cudaStream_t st);
 void launch_dep_far(int dp, bool fp64, const float* spts, const unsigned long long* scode,
                     const unsigned long long* skey, const ClassView& cv, const CutGeom* cuts,
                     const Node* nodes, const float* nbox, const uint32_t* root, FarQueue q,

@@ -73,13 +73,14 @@ def check_run(sizes, dims, insts, cuts, dtype, precision, seed, layout="auto", s
 @pytest.mark.parametrize("precision,layout", [("fp32", "auto"), ("fp64", "auto"), ("fp32", "union"),
                                               ("fp32", "segment"), ("fp64", "segment"), ("fp32", "tree"),
                                               ("fp64", "tree"), ("fp32", "tensor"), ("fp64", "tensor"),
-                                              ("fp32", "pairs"), ("fp64", "pairs")])
+                                              ("fp32", "pairs"), ("fp64", "pairs"), ("fp32", "cell"),
+                                              ("fp64", "cell")])
 def test_batch_mixed_dims_float(precision, layout):
     sizes, dims, insts, cuts = make_batch(1, 48, [2, 3, 5, 1, 4, 7, 8, 2, 3, 5])
     check_run(sizes, dims, insts, cuts, np.float32, precision, 11, layout)
 
 
-@pytest.mark.parametrize("layout", ["union", "segment", "tree", "tensor", "pairs"])
+@pytest.mark.parametrize("layout", ["union", "segment", "tree", "tensor", "pairs", "cell"])
 def test_batch_int_ties(layout):
     sizes, dims, insts, cuts = make_batch(2, 30, [2, 3], dtype=np.int32, max_n=1500)
     check_run(sizes, dims, insts, cuts, np.int32, "fp32", 12, layout)
@@ -96,7 +97,8 @@ def test_batch_one_class_many_instances():
     check_run(sizes, dims, insts, cuts, np.float32, "fp32", 13)
 
 
-@pytest.mark.parametrize("layout,graph", [("auto", False), ("tree", False), ("segment", False), ("auto", True)])
+@pytest.mark.parametrize("layout,graph", [("auto", False), ("tree", False), ("segment", False), ("cell", False),
+                                          ("auto", True)])
 def test_batch_skip_noise(layout, graph):
     """Noise points skip the dependent search (lambda -1, delta NaN); every
     instance and cutoff has its own noise threshold."""

@@ -222,7 +222,7 @@ def test_stats():
     assert 0 < s["far_queries"] < 20000
 
 
-@pytest.mark.parametrize("layout", ["union", "segment", "tree", "tensor", "pairs"])
+@pytest.mark.parametrize("layout", ["union", "segment", "tree", "tensor", "pairs", "cell"])
 @pytest.mark.parametrize("radius", [1, 2, 3, 5])
 def test_block_radius_does_not_change_results(radius, layout):
     """Every block radius (grid level) and both kernel layouts give the
@@ -239,7 +239,7 @@ def test_block_radius_does_not_change_results(radius, layout):
         assert 1 <= st["block_radius"] <= (5 if d <= 2 else (2 if d == 3 else 1))
 
 
-@pytest.mark.parametrize("layout", ["union", "segment"])
+@pytest.mark.parametrize("layout", ["union", "segment", "cell"])
 @pytest.mark.parametrize("shift", [0, 1, 2])
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_near_shift_does_not_change_results(shift, layout, precision):
@@ -341,5 +341,30 @@ def test_tensor_density_dense_blocks(d, dtype):
             got = dpc.dpc_density(t, dpc.Batch.single(len(pts), d, [c]), precision=prec, sync=True,
                                   layout="tensor")
             assert np.array_equal(got[0].cpu().numpy(), ref), (d, c, prec)
-    st = dpc.dpc_get_stats()
-    assert st["density_layout"] in (2, 4)
+            # the tensor cores ran the float32 call; binary64 falls back to segments
+            assert dpc.dpc_get_stats()["density_layout"] == (4 if prec == "fp32" else 2), prec
+
+
+@pytest.mark.parametrize("d,dtype", [(1, np.int32), (2, np.float32), (2, np.int32), (3, np.float32),
+                                     (3, np.int32), (4, np.float32), (6, np.float32)])
+def test_cell_layout_large_cells(d, dtype):
+    """The cell layout where cells hold more queries than a warp has lanes
+    (several queries per lane, several passes) and blocks hold more candidates
+    than one shared-memory window (several windows), with exact integer ties
+    at the cutoff, in both precision modes."""
+    rng = np.random.default_rng(400 + d)
+    if dtype == np.int32:
+        side = {1: 4000, 2: 60, 3: 16}.get(d, 8)
+        pts = rng.integers(0, side, (20000, d)).astype(np.int32)
+        cuts = [2.0, 3.0] if d > 1 else [5.0, 40.0]
+    else:
+        pts = W.random_blobs(20000, d, 410 + d, n_blobs=2, dup_frac=0.01)
+        cuts = [0.05 * d ** 0.5, 0.1 * d ** 0.5]
+    refs = [oracle.run(pts, c, 2, 3, 0.1) for c in cuts]
+    t = torch.from_numpy(pts).cuda()
+    for prec in ("fp32", "fp64"):
+        out = dpc.run(t, cuts, 2, 3, 0.1, layout="cell", precision=prec)
+        st = dpc.dpc_get_stats()
+        assert st["density_layout"] == 6 and st["near_layout"] == 6
+        for c, ref in enumerate(refs):
+            assert_same({k: v[c].cpu().numpy() for k, v in out.items()}, ref, "%s d=%d cut %d" % (prec, d, c))
