@@ -62,7 +62,11 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "c5", "spreader"],
+                    help="spreader: the seed-spreader family of c3 at --n points in --d dimensions "
+                         "(reduced cases for profiling)")
+    ap.add_argument("--n", type=int, default=4_000_000, help="points of --workload spreader")
+    ap.add_argument("--d", type=int, default=3, help="dimension of --workload spreader")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fast", action="store_true", help="skip the fp64, e2e and CPU legs (profiling runs)")
@@ -81,7 +85,9 @@ def parse():
     return ap.parse_args()
 
 
-def load_workload(name):
+def load_workload(name, n=4_000_000, d=3):
+    if name == "spreader":
+        return W.spreader(n, d)
     return {"c1": W.c1, "c2": W.c2, "c3": W.c3, "c4": W.c4, "c5": W.c5}[name]()
 
 
@@ -319,7 +325,7 @@ def run_ours(args, rank, world, dev):
         _build.build()
     if world > 1:
         torch.distributed.barrier()
-    job = Job(load_workload(args.workload))
+    job = Job(load_workload(args.workload, args.n, args.d))
     batch = dpc.Batch(job.pt_offset, job.dims, job.d_cut, coord_offset=job.coord_offset)
     params = dpc.make_params(batch, job.rho_noise, job.rho_min, job.delta_min)
     # one stream for every call (the library keeps one workspace, autotuning
@@ -679,7 +685,7 @@ def run_reference(args, rank, world):
     steps as fit in about two minutes after one warm-up run."""
     if rank != 0:
         return None
-    job = Job(load_workload(args.workload))
+    job = Job(load_workload(args.workload, args.n, args.d))
     warm = min(1, args.warmup)
     for s in range(warm):
         cpu_oracle_run(job, args.cpu_instances, 99)

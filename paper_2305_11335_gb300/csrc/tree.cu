@@ -184,6 +184,17 @@ inline unsigned grid_for(uint64_t n) {
   return (unsigned)b;
 }
 
+// One thread per node for the bottom-up walks: a thread that strode over
+// several nodes would run their walks one after another, each a chain of
+// dependent loads; with one node per thread every walk starts at once and
+// the blocks are scheduled as earlier ones retire.
+inline unsigned grid_all(uint64_t n) {
+  uint64_t b = (n + kThreads - 1) / kThreads;
+  if (b < 1) b = 1;
+  if (b > 0x7fffffffull) b = 0x7fffffffull;
+  return (unsigned)b;
+}
+
 }  // namespace
 
 void launch_tree_build(const unsigned long long* scode, const ClassView& cv, Node* nodes,
@@ -201,9 +212,9 @@ void tree_up_dp(const unsigned long long* skey, const float* spts, uint32_t n, N
                 cudaStream_t st) {
   (void)leaf_parent;
   if (boxes)
-    k_tree_up<DP, true><<<grid_for(n - 1), kThreads, 0, st>>>(skey, spts, n, nodes, visit, nbox);
+    k_tree_up<DP, true><<<grid_all(n - 1), kThreads, 0, st>>>(skey, spts, n, nodes, visit, nbox);
   else
-    k_tree_up<DP, false><<<grid_for(n - 1), kThreads, 0, st>>>(skey, spts, n, nodes, visit, nbox);
+    k_tree_up<DP, false><<<grid_all(n - 1), kThreads, 0, st>>>(skey, spts, n, nodes, visit, nbox);
 }
 
 void launch_tree_maxkey(const unsigned long long* skey, const float* spts, int dp, uint32_t n,
