@@ -741,6 +741,10 @@ void cells_step(Workspace* w, const ClassPlan& c, const ClassView& cv, const Cut
 void density_step(Workspace* w, const ClassPlan& c, const ClassView& cv, const CutGeom* cuts,
                   bool fp64, int layout, int seg_cells, int32_t* rho) {
   Phase ph(w, DPC_PHASE_DENSITY);
+  // the tensor layout exists for 5-8 dimensions with the float32 filter;
+  // other cases run in segments, and the statistics report what ran
+  if (layout == kLayoutTensor && !(c.dp == 8 && !fp64)) layout = kLayoutSegment;
+  w->last_choice.dlay = layout;
   launch_density(c.dp, c.g, fp64, layout, w->spts, w->scode, w->sid, cv, cuts, w->hinfo, w->hkeys,
                  w->hvals, w->pieces, rho, w->skey, w->ctr, w->stream, seg_cells);
 }
