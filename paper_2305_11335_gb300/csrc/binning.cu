@@ -278,10 +278,13 @@ __global__ void k_codes(const T* __restrict__ pts, ClassView cv,
     uint32_t c[G];
 #pragma unroll
     for (int a = 0; a < G; ++a) {
-      double x = (double)(float)row[a];
-      double v = (x - geom->org[a]) * inv_f;
-      v = fmin(fmax(v, 0.0), (double)cmax);
-      c[a] = (uint32_t)v;
+      const double x = (double)(float)row[a];
+      const double v = (x - geom->org[a]) * inv_f;
+      // float-to-integer conversion clamps to [0, 2^32 - 1] (NaN to 0), so
+      // only the upper clamp is left, in integer arithmetic (binary64 is
+      // the slow pipe on this chip)
+      const uint32_t ci = __double2uint_rz(v);
+      c[a] = ci < cmax ? ci : cmax;
     }
     codes[p] = (ib ? ((unsigned long long)i << S) : 0ull) | morton<G>(c);
     ids[p] = p;

@@ -369,6 +369,7 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
                const HashInfo* __restrict__ hi, const unsigned long long* __restrict__ hkeys,
                const uint2* __restrict__ hvals, int32_t* __restrict__ lambda,
                double* __restrict__ delta, FarQueue q, Counters* ctr, int seg_cells) {
+  constexpr int ND = real_dims<DP, G>();  // coordinates that can be nonzero
   constexpr int V = near_seg_v<DP>();
   constexpr uint32_t W = 32u * V;
   __shared__ RunTable s_rt[kNearWarps];
@@ -455,8 +456,8 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
 #pragma unroll
               for (int v = 0; v < V; ++v) {
                 if (v >= vn) break;
-                if (ck[v] > Ka) ea.add(dist64<DP>(xa, cand[v]), key_id(ck[v]));
-                if (ck[v] > Kb) eb.add(dist64<DP>(xb, cand[v]), key_id(ck[v]));
+                if (ck[v] > Ka) ea.add(dist64<DP, ND>(xa, cand[v]), key_id(ck[v]));
+                if (ck[v] > Kb) eb.add(dist64<DP, ND>(xb, cand[v]), key_id(ck[v]));
               }
               ea.merge_warp();
               eb.merge_warp();
@@ -469,8 +470,8 @@ k_dep_near_seg(const float* __restrict__ spts, const unsigned long long* __restr
 #pragma unroll
               for (int v = 0; v < V; ++v) {
                 if (v >= vn) break;
-                const float da = dist32<DP>(xa, cand[v]);
-                const float db = dist32<DP>(xb, cand[v]);
+                const float da = dist32<DP, ND>(xa, cand[v]);
+                const float db = dist32<DP, ND>(xb, cand[v]);
                 const uint32_t id = key_id(ck[v]);
                 ma.add(ck[v] > Ka ? da : INFINITY, id);
                 mb.add(ck[v] > Kb ? db : INFINITY, id);

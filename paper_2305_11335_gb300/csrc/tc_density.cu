@@ -6,22 +6,26 @@
 // points (k_tc_pieces); a CTA of 4 warps takes pieces one by one from a global
 // work counter.  The 128 rows of the MMA are the piece's queries, the columns
 // the candidates of the cell's block, 256 per MMA.  With the augmented rows
-//     a = [q_0 .. q_7, |q|^2, 1, 0 ..]            (query, M = 128 rows)
-//     b = [-2 c_0 .. -2 c_7, 1, |c|^2, 0 ..]      (candidate, N = 256 rows)
-// one product a . b = |q|^2 + |c|^2 - 2 q . c is the squared distance.  Every
-// operand is split into a TF32 high part and a TF32 remainder and the three
-// products hi.hi + hi.lo + lo.hi are accumulated (measured error ~2^-22
-// relative to |a||b|); coordinates are taken relative to the segment's first
+//     a = [q_0 .. q_7, (1 + e) |q|^2, 1, 0 ..]                 (query, M = 128)
+//     b = [-2 c_0 .. -2 c_7, 1, (1 + e) |c|^2 - (1 - e) t_in, 0 ..] (N = 256)
+// (e = 2^-14) one product a . b = s + E - t_in: the squared distance s, plus
+// the error allowance E = e (|q|^2 + |c|^2 + t_in), minus the float32 filter's
+// inner threshold, so the epilogue only compares the accumulator with 0.
+// Every operand is split into a TF32 high part and a TF32 remainder and the
+// three products hi.hi + hi.lo + lo.hi are accumulated (measured error ~2^-22
+// relative to |a||b|); coordinates are taken relative to the piece's first
 // query so the norms stay small.  Thread t owns accumulator row t (its query)
-// and counts the 256 columns of each tile with its own thresholds.
+// and counts the 256 columns of each tile.
 //
-// Exactness: with E = 2^-14 (|q|^2 + |c|^2) per pair, far above the split-TF32
-// error and the float32 norm rounding, s_tc + E <= t_in proves
-// s64 <= d_cut^2 and s_tc - E > t_out proves the opposite (t_in, t_out as in
-// the float32 filter); pairs in between are recounted with the canonical
-// binary64 distance from the original coordinates, so rho is exactly the
-// binary64 count.  Dense blocks only: the autotuner picks this layout where
-// it is faster than the float32 layouts.
+// Exactness: E is far above the split-TF32 error, the FP32 accumulation error
+// (at most about 2^-16.4 times the same sum of norms and t_in) and the
+// float32 norm rounding, so acc <= 0 proves s <= t_in, hence s64 <= d_cut^2
+// (t_in, t_out as in the float32 filter); acc > W, with W = (t_out - t_in) +
+// 1.25 e (2 max norm + t_in) over the tile's queries and candidates (rounded
+// up), proves s > t_out, hence s64 > d_cut^2.  Pairs in between are recounted
+// with the canonical binary64 distance from the original coordinates, so rho
+// is exactly the binary64 count.  Dense blocks only: the autotuner picks this
+// layout where it is faster than the float32 layouts.
 #include <cstdint>
 
 #include "block.cuh"
@@ -78,8 +82,8 @@ struct TcSmem {
   float a[2][kTcM * kTcK];      // query rows, TF32 high part / remainder
   float b[2][kTcN * kTcK];      // candidate rows
   float c[kTcN * 8];            // candidate coordinates (original)
-  float tin[kTcN];              // t_in - 2^-14 |c|^2 per candidate (-inf: padding)
-  float tout[kTcN];             // t_out + 2^-14 |c|^2 per candidate (-inf: padding)
+  float qmax[kTcThreads / 32];  // per warp: largest |q'|^2 of the piece's queries
+  float cmax[kTcThreads / 32];  // per warp: largest |c'|^2 of the tile's candidates
   int cnt[kTcM];                // per query: the two column halves' counts
   RunTable rt;
   unsigned long long mbar;
@@ -255,14 +259,18 @@ k_density_tc(const float* __restrict__ spts, const uint32_t* __restrict__ sid, C
           row[a] = t;
           nq = fmaf(t, t, nq);
         }
-        row[8] = nq;
+        row[8] = nq * (1.f + kTcErr);
         row[9] = 1.f;
 #pragma unroll
         for (int a = 10; a < kTcK; ++a) row[a] = 0.f;
         if (chalf == 0) put_row<kTcM>(sm.a, qrow, row);
       }
+      {
+        float m = inq ? nq : 0.f;
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+        if (lane == 0) sm.qmax[warp] = m;
+      }
       if (tid < kTcM) sm.cnt[tid] = 0;
-      const float eq = kTcErr * nq;
       int32_t cnt = 0;
       for (uint32_t w0 = 0; w0 < total && !stop; w0 += kTcN) {
         // candidate rows: one per thread
@@ -272,6 +280,7 @@ k_density_tc(const float* __restrict__ spts, const uint32_t* __restrict__ sid, C
           const uint32_t e = w0 + (uint32_t)r;
           float row[kTcK];
           Pt<DP> x;
+          float ncr = 0.f;
           if (e < total) {
             int lo = 0, hi2 = nr - 1;
             while (lo < hi2) {
@@ -288,16 +297,19 @@ k_density_tc(const float* __restrict__ spts, const uint32_t* __restrict__ sid, C
               nc = fmaf(t, t, nc);
             }
             row[8] = 1.f;
-            row[9] = nc;
-            sm.tin[r] = t_in - kTcErr * nc;
-            sm.tout[r] = t_out + kTcErr * nc;
+            // the threshold folded in: the product is s + E - t_in
+            row[9] = nc * (1.f + kTcErr) - t_in * (1.f - kTcErr);
+            ncr = nc;
           } else {
 #pragma unroll
             for (int a = 0; a < DP; ++a) { x.x[a] = 0.f; row[a] = 0.f; }
             row[8] = 0.f;
             row[9] = kTcFar;
-            sm.tin[r] = -INFINITY;
-            sm.tout[r] = -INFINITY;
+          }
+          {
+            float m = ncr;
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+            if (lane == 0) sm.cmax[warp] = m;
           }
 #pragma unroll
           for (int a = 10; a < kTcK; ++a) row[a] = 0.f;
@@ -341,32 +353,36 @@ k_density_tc(const float* __restrict__ spts, const uint32_t* __restrict__ sid, C
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int ncol = (int)min((uint32_t)kTcN, total - w0);
+        // Above this the pair is certainly farther than t_out: the band of the
+        // tile, (t_out - t_in) plus 1.25 E at the tile's largest norms
+        // (rounded up), so that acc > W implies s > t_out for every pair.
+        float nmax = 0.f;
+#pragma unroll
+        for (int w = 0; w < kTcThreads / 32; ++w) nmax = fmaxf(nmax, fmaxf(sm.qmax[w], sm.cmax[w]));
+        const float W = __fadd_ru(
+            __fsub_ru(t_out, t_in),
+            __fmul_ru(1.25f * kTcErr, __fadd_ru(__fadd_ru(nmax, nmax), t_in)));
         for (int cl = 0; cl < kTcN / 2; cl += 32) {
           const int cb = chalf * (kTcN / 2) + cl;  // first column of this load
           if (cb >= ncol) break;  // warp-uniform
           float v[32];
           tmem_ld32(trow + (uint32_t)cl, v);
           if (inq) {
-            unsigned ci = 0, co = 0;
+            unsigned ci = 0, bm = 0;  // bm: columns of this load in the band
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-              ci += v[j] + eq <= sm.tin[cb + j] ? 1u : 0u;
-              co += v[j] - eq <= sm.tout[cb + j] ? 1u : 0u;
+              ci += v[j] <= 0.f ? 1u : 0u;
+              bm |= (v[j] > 0.f && v[j] <= W) ? (1u << j) : 0u;
             }
             cnt += (int32_t)ci;
-            if (co != ci) {  // band pairs: the canonical binary64 distance decides
-#pragma unroll 1
-              for (int j = 0; j < 32; ++j) {
-                const bool in = v[j] + eq <= sm.tin[cb + j];
-                const bool maybe = v[j] - eq <= sm.tout[cb + j];
-                if (maybe && !in) {
-                  Pt<DP> x;
+            while (bm) {  // band pairs: the canonical binary64 distance decides
+              const int j = __ffs((int)bm) - 1;
+              bm &= bm - 1u;
+              Pt<DP> x;
 #pragma unroll
-                  for (int a = 0; a < DP; ++a) x.x[a] = sm.c[(cb + j) * DP + a];
-                  ++band;
-                  cnt += dist64<DP>(me, x) <= dc2 ? 1 : 0;
-                }
-              }
+              for (int a = 0; a < DP; ++a) x.x[a] = sm.c[(cb + j) * DP + a];
+              ++band;
+              cnt += dist64<DP>(me, x) <= dc2 ? 1 : 0;
             }
           }
         }
