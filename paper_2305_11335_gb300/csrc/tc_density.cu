@@ -21,8 +21,8 @@
 // (at most about 2^-16.4 times the same sum of norms and t_in) and the
 // float32 norm rounding, so acc <= 0 proves s <= t_in, hence s64 <= d_cut^2
 // (t_in, t_out as in the float32 filter); acc > W, with W = (t_out - t_in) +
-// 1.25 e (2 max norm + t_in) over the tile's queries and candidates (rounded
-// up), proves s > t_out, hence s64 > d_cut^2.  Pairs in between are recounted
+// 1.25 e (|q|^2 + the largest |c|^2 of the 32 columns + t_in) (rounded up),
+// proves s > t_out, hence s64 > d_cut^2.  Pairs in between are recounted
 // with the canonical binary64 distance from the original coordinates, so rho
 // is exactly the binary64 count.  Dense blocks only: the autotuner picks this
 // layout where it is faster than the float32 layouts.
@@ -40,6 +40,8 @@ constexpr int kTcM = 128;            // queries per MMA (rows)
 constexpr int kTcN = 256;            // candidates per MMA (columns)
 constexpr int kTcK = 16;             // augmented row length: two K = 8 steps
 constexpr float kTcErr = 0x1p-14f;
+// one candidate row per thread: warp w stages columns 32w .. 32w + 31
+static_assert(kTcN == kTcThreads, "candidate rows per thread");
 constexpr float kTcFar = 1e30f;      // |c|^2 of a padding candidate: never counted
 constexpr uint32_t kTcWaitLimit = 1u << 26;  // mbarrier polls before giving up
 
@@ -82,8 +84,7 @@ struct TcSmem {
   float a[2][kTcM * kTcK];      // query rows, TF32 high part / remainder
   float b[2][kTcN * kTcK];      // candidate rows
   float c[kTcN * 8];            // candidate coordinates (original)
-  float qmax[kTcThreads / 32];  // per warp: largest |q'|^2 of the piece's queries
-  float cmax[kTcThreads / 32];  // per warp: largest |c'|^2 of the tile's candidates
+  float cmax[kTcN / 32];        // per 32 columns (the rows one warp stages): largest |c'|^2
   int cnt[kTcM];                // per query: the two column halves' counts
   RunTable rt;
   unsigned long long mbar;
@@ -265,11 +266,6 @@ k_density_tc(const float* __restrict__ spts, const uint32_t* __restrict__ sid, C
         for (int a = 10; a < kTcK; ++a) row[a] = 0.f;
         if (chalf == 0) put_row<kTcM>(sm.a, qrow, row);
       }
-      {
-        float m = inq ? nq : 0.f;
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
-        if (lane == 0) sm.qmax[warp] = m;
-      }
       if (tid < kTcM) sm.cnt[tid] = 0;
       int32_t cnt = 0;
       for (uint32_t w0 = 0; w0 < total && !stop; w0 += kTcN) {
@@ -353,26 +349,29 @@ k_density_tc(const float* __restrict__ spts, const uint32_t* __restrict__ sid, C
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int ncol = (int)min((uint32_t)kTcN, total - w0);
-        // Above this the pair is certainly farther than t_out: the band of the
-        // tile, (t_out - t_in) plus 1.25 E at the tile's largest norms
-        // (rounded up), so that acc > W implies s > t_out for every pair.
-        float nmax = 0.f;
-#pragma unroll
-        for (int w = 0; w < kTcThreads / 32; ++w) nmax = fmaxf(nmax, fmaxf(sm.qmax[w], sm.cmax[w]));
-        const float W = __fadd_ru(
-            __fsub_ru(t_out, t_in),
-            __fmul_ru(1.25f * kTcErr, __fadd_ru(__fadd_ru(nmax, nmax), t_in)));
+        const float tw = __fsub_ru(t_out, t_in);
         for (int cl = 0; cl < kTcN / 2; cl += 32) {
           const int cb = chalf * (kTcN / 2) + cl;  // first column of this load
           if (cb >= ncol) break;  // warp-uniform
           float v[32];
           tmem_ld32(trow + (uint32_t)cl, v);
+          // Above W the pair is certainly farther than t_out: (t_out - t_in)
+          // plus 1.25 E at this query's norm and the largest candidate norm
+          // of these 32 columns (warp cb / 32 staged them), rounded up, so
+          // that acc > W implies s > t_out.
+          const float W = __fadd_ru(
+              tw, __fmul_ru(1.25f * kTcErr, __fadd_ru(__fadd_ru(nq, sm.cmax[cb >> 5]), t_in)));
+          const uint32_t wbits = __float_as_uint(W);
           if (inq) {
+            // On the bit patterns: a negative accumulator (sign bit set,
+            // -0 included) is counted; one in [+0, W] (an unsigned compare,
+            // W >= 0) goes to the binary64 recount, +0 included.
             unsigned ci = 0, bm = 0;  // bm: columns of this load in the band
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-              ci += v[j] <= 0.f ? 1u : 0u;
-              bm |= (v[j] > 0.f && v[j] <= W) ? (1u << j) : 0u;
+              const uint32_t b = __float_as_uint(v[j]);
+              ci += b >> 31;
+              bm |= (b <= wbits) ? (1u << j) : 0u;
             }
             cnt += (int32_t)ci;
             while (bm) {  // band pairs: the canonical binary64 distance decides
