@@ -268,6 +268,26 @@ k_density_tc(const float* __restrict__ spts, const uint32_t* __restrict__ sid, C
       }
       if (tid < kTcM) sm.cnt[tid] = 0;
       int32_t cnt = 0;
+      // This thread's candidate of the tile starting at w (row tid), loaded
+      // one tile ahead: the next tile's load is issued right after this
+      // tile's MMA, so it is in flight during the MMA and the epilogue.
+      auto fetch = [&](uint32_t w) {
+        Pt<DP> x;
+#pragma unroll
+        for (int a = 0; a < DP; ++a) x.x[a] = 0.f;
+        const uint32_t e = w + (uint32_t)tid;
+        if (e < total) {
+          int lo = 0, hi2 = nr - 1;
+          while (lo < hi2) {
+            const int mid = (lo + hi2 + 1) >> 1;
+            if (sm.rt.pre[mid] <= e) lo = mid;
+            else hi2 = mid - 1;
+          }
+          x = load_pt<DP>(spts, sm.rt.start[lo] + (e - sm.rt.pre[lo]));
+        }
+        return x;
+      };
+      Pt<DP> xnext = fetch(0);
       for (uint32_t w0 = 0; w0 < total && !stop; w0 += kTcN) {
         // candidate rows: one per thread
 #pragma unroll
@@ -278,13 +298,7 @@ k_density_tc(const float* __restrict__ spts, const uint32_t* __restrict__ sid, C
           Pt<DP> x;
           float ncr = 0.f;
           if (e < total) {
-            int lo = 0, hi2 = nr - 1;
-            while (lo < hi2) {
-              const int mid = (lo + hi2 + 1) >> 1;
-              if (sm.rt.pre[mid] <= e) lo = mid;
-              else hi2 = mid - 1;
-            }
-            x = load_pt<DP>(spts, sm.rt.start[lo] + (e - sm.rt.pre[lo]));
+            x = xnext;
             float nc = 0.f;
 #pragma unroll
             for (int a = 0; a < DP; ++a) {
@@ -337,6 +351,7 @@ k_density_tc(const float* __restrict__ spts, const uint32_t* __restrict__ sid, C
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                        :: "r"(mbar) : "memory");
         }
+        if (w0 + kTcN < total) xnext = fetch(w0 + kTcN);
         const bool ok = mbar_wait(mbar, phase, poll_limit);
         phase ^= 1u;
         if (__syncthreads_or(!ok)) {  // the MMA did not finish in time: record and stop
