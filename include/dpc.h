@@ -121,9 +121,10 @@ enum {
  * their blocks streamed as broadcast reads), 2 = segment (the block of one
  * cell spread over the lanes, the cell's queries one at a time), 3 = tree
  * (near phase only, density keeps its default: no block scan, every query goes
- * to the tree search of the far phase), 4 = tensor (density only, 5-8
- * dimensions with DPC_PREC_FP32_CERT: distance tiles on the tensor cores with a
- * certified error band; other cases use segment), 5 = pairs (density only:
+ * to the tree search of the far phase), 4 = tensor (density and near phase,
+ * 5-8 dimensions with DPC_PREC_FP32_CERT: distance tiles on the tensor cores
+ * with a certified error band; other cases use segment for the density and
+ * union for the near phase), 5 = pairs (density only:
  * the segment layout evaluating every unordered pair once and counting it for
  * both points), 6 = cell (density and near phase: one warp per occupied cell,
  * the cell's block staged in shared memory, every lane one query -- or a share

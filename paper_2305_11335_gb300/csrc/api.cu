@@ -147,9 +147,11 @@ int check_flags(uint32_t flags) {
 
 int status_to_code(int s) {
   if (s == 0) return DPC_OK;
-  if (s & (kStatusBadCoord | kStatusCycle | kStatusQuery)) return DPC_ERR_DATA;
-  if (s & kStatusStack) return DPC_ERR_UNSUPPORTED;
+  if (s & kStatusBadCoord) return DPC_ERR_DATA;
+  // a wait that gave up leaves later results unreliable: report it first
   if (s & kStatusTimeout) return DPC_ERR_TIMEOUT;
+  if (s & (kStatusCycle | kStatusQuery)) return DPC_ERR_DATA;
+  if (s & kStatusStack) return DPC_ERR_UNSUPPORTED;
   return DPC_ERR_CUDA;
 }
 
@@ -279,7 +281,7 @@ struct Workspace {
 
   // autotuned radius and layouts per (class shape, cutoff), see choose()
   std::map<std::string, Choice> tuned;
-  cudaEvent_t tune_ev[20] = {};
+  cudaEvent_t tune_ev[24] = {};
 
   // for dpc_get_stats: the last class and cutoff that ran
   Choice last_choice;
@@ -765,9 +767,17 @@ void dependent_step(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGe
   }
   {
     Phase ph(w, DPC_PHASE_NEAR);
-    launch_dep_near(c.dp, c.g, fp64, layout, w->spts, w->scode, w->skey, cv, rho_skip, pts, dtype,
-                    cuts, w->hinfo, w->hkeys, w->hvals, lambda, delta, queue_of(w), w->ctr, st,
-                    seg_cells);
+    if (layout == kLayoutTensor && c.dp == 8 && !fp64) {
+      launch_dep_near_tc(c.g, w->spts, w->sid, w->skey, cv, rho_skip, pts, dtype, cuts, w->hinfo,
+                         w->hkeys, w->hvals, w->pieces, lambda, delta, queue_of(w), w->ctr, st);
+    } else {
+      // the tensor layout exists for 5-8 dimensions with the float32 filter
+      if (layout == kLayoutTensor) layout = kLayoutUnion;
+      launch_dep_near(c.dp, c.g, fp64, layout, w->spts, w->scode, w->skey, cv, rho_skip, pts, dtype,
+                      cuts, w->hinfo, w->hkeys, w->hvals, lambda, delta, queue_of(w), w->ctr, st,
+                      seg_cells);
+    }
+    w->last_choice.nlay = layout;
   }
   {
     Phase ph(w, DPC_PHASE_FAR);
@@ -849,8 +859,7 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
   const int forced = (int)((flags & DPC_FLAG_LAYOUT_MASK) >> 16);
   const int forced_ns = (int)((flags & DPC_FLAG_NEAR_SHIFT_MASK) >> 20);
   ch.dlay = (forced && forced != kLayoutTree) ? forced : default_dlayout(c.g);
-  ch.nlay = (forced && forced != kLayoutTensor && forced != kLayoutPairs) ? forced
-                                                                          : default_nlayout(c.g);
+  ch.nlay = (forced && forced != kLayoutPairs) ? forced : default_nlayout(c.g);
   ch.ns = forced_ns ? forced_ns - 1 : 0;
   ch.sc = default_seg_cells(c.g);
   const std::string key = (near ? "R/" : "D/") + tune_key(c, b, cut);
@@ -864,13 +873,16 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
     // the tensor layout exists for 5-8 dimensions with the float32 filter
     const int ndl = (c.dp == 8 && !fp64) ? 4 : 3;
     const int dlays[4] = {kLayoutUnion, kLayoutSegment, kLayoutPairs, kLayoutTensor};
-    const int nlays[3] = {kLayoutUnion, kLayoutSegment, kLayoutTree};
+    // the tensor layouts exist for 5-8 dimensions with the float32 filter
+    const int nnl = (c.dp == 8 && !fp64) ? 4 : 3;
+    const int nlays[4] = {kLayoutUnion, kLayoutSegment, kLayoutTree, kLayoutTensor};
     constexpr int kShifts = 3;  // near phase 0, 1 or 2 levels below the density's
+    constexpr int kNL = 4;      // near layout slots per shift
     // events: 0 start, 1 after cells, 2-5 after each density layout, 6 after
-    // the subtree keys; per near shift s, 7 + 4s after its level change and
-    // cells, then one after each near layout (each followed by the far search,
-    // which finishes what the near phase leaves; the tree layout, which uses
-    // no cells, only at s = 0)
+    // the subtree keys; per near shift s, 7 + (kNL + 1) s after its level
+    // change and cells, then one after each near layout (each followed by the
+    // far search, which finishes what the near phase leaves; the tree layout,
+    // which uses no cells, only at s = 0)
     auto trial = [&](int r, bool timed) {
       if (timed) cudaEventRecord(w->tune_ev[0], st);
       launch_set_radius(cv, cuts, r, st);
@@ -894,16 +906,22 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
           launch_near_level(cv, cuts, sh, st);
           launch_cells(w->scode, cv, c.g, cuts, w->hinfo, w->hkeys, w->hvals, w->hcap, st);
         }
-        if (timed) cudaEventRecord(w->tune_ev[7 + 4 * sh], st);
-        for (int l = 0; l < 3; ++l) {
-          if (sh == 0 || nlays[l] != kLayoutTree) {
-            launch_dep_near(c.dp, c.g, fp64, nlays[l], w->spts, w->scode, w->skey, cv, 0, near->pts,
-                            near->dtype, cuts, w->hinfo, w->hkeys, w->hvals, near->lambda,
-                            near->delta, queue_of(w), w->ctr, st, default_seg_cells(c.g));
+        if (timed) cudaEventRecord(w->tune_ev[7 + (kNL + 1) * sh], st);
+        for (int l = 0; l < kNL; ++l) {
+          if (l < nnl && (sh == 0 || nlays[l] != kLayoutTree)) {
+            if (nlays[l] == kLayoutTensor)
+              launch_dep_near_tc(c.g, w->spts, w->sid, w->skey, cv, 0, near->pts, near->dtype,
+                                 cuts, w->hinfo, w->hkeys, w->hvals, w->pieces, near->lambda,
+                                 near->delta, queue_of(w), w->ctr, st);
+            else
+              launch_dep_near(c.dp, c.g, fp64, nlays[l], w->spts, w->scode, w->skey, cv, 0,
+                              near->pts, near->dtype, cuts, w->hinfo, w->hkeys, w->hvals,
+                              near->lambda, near->delta, queue_of(w), w->ctr, st,
+                              default_seg_cells(c.g));
             launch_dep_far(c.dp, fp64, w->spts, w->scode, w->skey, cv, cuts, w->nodes, w->nbox,
                            w->roots, queue_of(w), near->lambda, near->delta, w->ctr, st);
           }
-          if (timed) cudaEventRecord(w->tune_ev[8 + 4 * sh + l], st);
+          if (timed) cudaEventRecord(w->tune_ev[8 + (kNL + 1) * sh + l], st);
         }
       }
     };
@@ -923,14 +941,15 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
     for (int r = 1; r <= rmax && !failed; ++r) {
       // each phase: the smaller of two timings
       float cl = 1e30f, dt[4] = {1e30f, 1e30f, 1e30f, 1e30f};
-      float nt[kShifts][3], lv[kShifts];
+      float nt[kShifts][kNL], lv[kShifts];
       for (int sh = 0; sh < kShifts; ++sh) {
         lv[sh] = 1e30f;
-        for (int l = 0; l < 3; ++l) nt[sh][l] = 1e30f;
+        for (int l = 0; l < kNL; ++l) nt[sh][l] = 1e30f;
       }
       for (int rep = 0; rep < 2; ++rep) {
         trial(r, true);
-        if (cudaEventSynchronize(w->tune_ev[near ? 7 + 4 * (kShifts - 1) + 3 : 5]) != cudaSuccess) {
+        if (cudaEventSynchronize(w->tune_ev[near ? 8 + (kNL + 1) * (kShifts - 1) + kNL - 1 : 5]) !=
+            cudaSuccess) {
           cudaGetLastError();
           failed = true;
           break;
@@ -940,10 +959,11 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
         if (near)
           for (int sh = 0; sh < kShifts; ++sh) {
             // the level change and cells of a shift count against it
-            lv[sh] = sh == 0 ? 0.f : fminf(lv[sh], span(7 + 4 * (sh - 1) + 3, 7 + 4 * sh));
-            for (int l = 0; l < 3; ++l)
+            lv[sh] = sh == 0 ? 0.f
+                             : fminf(lv[sh], span(8 + (kNL + 1) * (sh - 1) + kNL - 1, 7 + (kNL + 1) * sh));
+            for (int l = 0; l < nnl; ++l)
               if (sh == 0 || nlays[l] != kLayoutTree)
-                nt[sh][l] = fminf(nt[sh][l], span(7 + 4 * sh + l, 8 + 4 * sh + l));
+                nt[sh][l] = fminf(nt[sh][l], span(7 + (kNL + 1) * sh + l, 8 + (kNL + 1) * sh + l));
           }
       }
       if (failed) break;
@@ -960,10 +980,10 @@ Choice choose(Workspace* w, const ClassPlan& c, const ClassView& cv, CutGeom* cu
       int nsi = 0, ni = -1;
       float nms = 0.f;
       if (near) {
-        ni = pick(nt[0], nlays, 3, default_nlayout(c.g));
+        ni = pick(nt[0], nlays, nnl, default_nlayout(c.g));
         nms = nt[0][ni];
         for (int sh = 1; sh < kShifts; ++sh) {
-          const int l = pick(nt[sh], nlays, 3, default_nlayout(c.g));
+          const int l = pick(nt[sh], nlays, nnl, default_nlayout(c.g));
           const float t = lv[sh] + nt[sh][l];
           if (t < 0.97f * nms) {
             nms = t;

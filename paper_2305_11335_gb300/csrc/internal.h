@@ -175,6 +175,14 @@ void launch_dep_near_cell(int dp, int g, bool fp64, const float* spts,
                           const CutGeom* cuts, const HashInfo* hi,
                           const unsigned long long* hkeys, const uint2* hvals, int32_t* lambda,
                           double* delta, FarQueue q, Counters* ctr, cudaStream_t st);
+// the tensor-core form of the near phase (dp = 8, float32 filter only;
+// pieces: scratch as for launch_density_tc)
+void launch_dep_near_tc(int g, const float* spts, const uint32_t* sid,
+                        const unsigned long long* skey, const ClassView& cv, int32_t rho_skip,
+                        const void* pts, int dtype, const CutGeom* cuts, HashInfo* hi,
+                        const unsigned long long* hkeys, const uint2* hvals, uint2* pieces,
+                        int32_t* lambda, double* delta, FarQueue q, Counters* ctr,
+                        cudaStream_t st);
 void launch_dep_far(int dp, bool fp64, const float* spts, const unsigned long long* scode,
                     const unsigned long long* skey, const ClassView& cv, const CutGeom* cuts,
                     const Node* nodes, const float* nbox, const uint32_t* root, FarQueue q,

@@ -23,7 +23,6 @@ __global__ void __launch_bounds__(kProbeThreads) k_fma_loop(T* out, int iters, T
   T a[kChains];
 #pragma unroll
   for (int k = 0; k < kChains; ++k) a[k] = (T)(threadIdx.x + k);
-#pragma unroll 4
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int k = 0; k < kChains; ++k) a[k] = fma(a[k], b, c);
@@ -72,6 +71,6 @@ int probe(int iters, cudaStream_t st, double* flops_per_s) {
 extern "C" int dpc_probe_peak(int kind, double* flops_per_s, void* stream) {
   if (!flops_per_s || (kind != 0 && kind != 1)) return DPC_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  return kind == 0 ? dpc::probe<float>(1 << 16, st, flops_per_s)
+  return kind == 0 ? dpc::probe<float>(1 << 17, st, flops_per_s)
                    : dpc::probe<double>(1 << 12, st, flops_per_s);
 }

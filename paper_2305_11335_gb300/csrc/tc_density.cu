@@ -136,18 +136,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 
 // The piece list: (hash slot, first point) of every 128-point piece of every
 // occupied cell, from a scan of the hash table (one atomic per warp).
-// Also gives every point the order key of density 0 (and rho 0) first: a
-// CTA that gives up on a wait (the MMA did not complete in time) leaves its
-// pieces unwritten, and the dependent phase must still see one valid key,
-// with the point's own id, at every position.
+// Also gives every point the order key of density 0 (and rho 0) first, or,
+// for the near phase, lambda = -1: a CTA that gives up on a wait (the MMA did
+// not complete in time) leaves its pieces unwritten, and the later phases
+// must still see one valid key per position and dependent pointers that form
+// no cycle.
 __global__ void k_tc_pieces(HashInfo* hi, const unsigned long long* __restrict__ hkeys,
                             const uint2* __restrict__ hvals, uint32_t n, uint2* __restrict__ pieces,
                             const uint32_t* __restrict__ sid, int32_t* __restrict__ rho_out,
-                            unsigned long long* __restrict__ skey) {
+                            unsigned long long* __restrict__ skey, bool init_keys,
+                            int32_t* __restrict__ lambda) {
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
     const uint32_t id = sid[q];
-    rho_out[id] = 0;
-    skey[q] = order_key(0, id);
+    if (init_keys) {
+      rho_out[id] = 0;
+      skey[q] = order_key(0, id);
+    }
+    if (lambda) lambda[id] = -1;  // near phase: what a CTA that gave up leaves
   }
   const uint32_t T = hi->hmask + 1;
   const int lane = threadIdx.x & 31;
@@ -433,6 +438,364 @@ k_density_tc(const float* __restrict__ spts, const uint32_t* __restrict__ sid, C
 constexpr size_t kTcSmemBytes = sizeof(TcSmem) > 100 * 1024 ? sizeof(TcSmem) : 100 * 1024;
 static_assert(sizeof(TcSmem) <= 200 * 1024, "shared-memory layout too large");
 
+
+// ---------------------------------------------------------------------------
+// The near phase of the dependent search (Definitions 2-3) on the tensor
+// cores: the same pieces and tiles, with b = [-2 c', 1, |c'|^2] so that the
+// accumulator is s itself, within E = e (|q'|^2 + |c'|^2) of the exact real
+// squared distance.  Per query row, over the candidates whose order key is
+// above the query's, each thread keeps the smallest upper bound acc + E (and
+// its candidate) and the two smallest lower bounds acc - E (with the
+// candidate of the smallest); E is taken per 32 columns at their largest
+// candidate norm.  A query is settled when one candidate's upper bound U is
+// below every other candidate's lower bound by a relative 2^-20 (so it is the
+// unique nearest higher point in binary64 too) and band(U) is below the far
+// bound of the block; lambda is that candidate and delta the square root of
+// its canonical binary64 distance.  Every other query goes to the far phase
+// with band(U) as its bound.
+
+struct TcNearSmem {
+  float a[2][kTcM * kTcK];
+  float b[2][kTcN * kTcK];
+  unsigned long long key[kTcN];  // order key per column (0: padding)
+  float cmax[kTcN / 32];
+  // the second column half's per-row results, merged by the first half
+  float ub[kTcM], l1[kTcM], l2[kTcM];
+  uint32_t ib[kTcM], il[kTcM];
+  RunTable rt;
+  unsigned long long mbar;
+  uint32_t tmem;
+  int nr;
+  uint32_t item;
+};
+
+__device__ __forceinline__ float tc_band(float s, float mul, float add) {
+  return __fadd_ru(__fmul_ru(s, mul), add);
+}
+
+// Coordinates of point `o` of an instance in the caller's input.
+__device__ __forceinline__ Pt<8> tc_caller_pt(const void* __restrict__ pts, int dtype, uint64_t coord,
+                                              int d, uint32_t o) {
+  Pt<8> p;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    float v = 0.f;
+    if (a < d) {
+      const size_t e = coord + (size_t)o * d + a;
+      v = dtype == 0 ? (float)__ldg((const int32_t*)pts + e) : __ldg((const float*)pts + e);
+    }
+    p.x[a] = v;
+  }
+  return p;
+}
+
+// The running bounds of one query (one column half): best upper bound ub and
+// its candidate ib; the two smallest lower bounds l1 (candidate il) and l2.
+struct NearBounds {
+  float ub, l1, l2;
+  uint32_t ib, il;
+  __device__ __forceinline__ void init() {
+    ub = l1 = l2 = INFINITY;
+    ib = il = 0xffffffffu;
+  }
+  __device__ __forceinline__ void add_lower(float l, uint32_t id) {
+    if (l < l1) {
+      l2 = l1;
+      l1 = l;
+      il = id;
+    } else if (l < l2) {
+      l2 = l;
+    }
+  }
+  __device__ __forceinline__ void add(float u, uint32_t idu, float l, float lo_rest) {
+    if (u < ub) {
+      ub = u;
+      ib = idu;
+    }
+    add_lower(l, idu);
+    add_lower(lo_rest, 0xfffffffeu);  // some other candidate of the same columns
+  }
+  __device__ __forceinline__ void merge(const NearBounds& o) {
+    if (o.ub < ub) {
+      ub = o.ub;
+      ib = o.ib;
+    }
+    add_lower(o.l1, o.il);
+    add_lower(o.l2, 0xfffffffeu);
+  }
+};
+
+template <int G>
+__global__ void __launch_bounds__(kTcThreads)
+k_dep_near_tc(const float* __restrict__ spts, const unsigned long long* __restrict__ skey,
+              ClassView cv, int32_t rho_skip, const void* __restrict__ pts, int dtype,
+              const CutGeom* __restrict__ cuts, HashInfo* hi,
+              const unsigned long long* __restrict__ hkeys, const uint2* __restrict__ hvals,
+              const uint2* __restrict__ pieces, int32_t* __restrict__ lambda,
+              double* __restrict__ delta, FarQueue fq, Counters* ctr, uint32_t poll_limit) {
+  constexpr int DP = 8;
+  extern __shared__ __align__(128) unsigned char tcn_smem_raw[];
+  TcNearSmem& sm = *reinterpret_cast<TcNearSmem*>(tcn_smem_raw);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int S = cv.cls->S, ib = cv.cls->ib;
+  const uint32_t hmask = hi->hmask;
+  const uint32_t npieces = hi->npieces;
+  const uint32_t n = cv.N;
+  const uint32_t mbar = smem_addr(&sm.mbar);
+  const uint32_t lanemask_lt = (1u << lane) - 1u;
+
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar) : "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_addr(&sm.tmem)), "r"(kTcN) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = sm.tmem;
+  const int qrow = (warp & 3) * 32 + lane;
+  const int chalf = warp >> 2;
+  const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(chalf * (kTcN / 2));
+  uint32_t phase = 0;
+  bool stop = false;
+
+  while (!stop) {
+    if (tid == 0) sm.item = atomicAdd(&hi->work, 1u);
+    __syncthreads();
+    const uint32_t item = sm.item;
+    __syncthreads();
+    if (item >= npieces) break;
+    const uint2 pc = pieces[item];
+    const uint32_t slot = pc.x & hmask;
+    const unsigned long long hkey = hkeys[slot];
+    const uint2 run = clip_run(hvals[slot], n);
+    uint32_t inst = key_inst(hkey, S, ib);
+    if (inst >= cv.ninst) inst = 0;
+    const unsigned long long code = key_code(hkey, S, ib);
+    const CutGeom& C = cuts[inst];
+    const InstDev I = cv.instance(inst);
+    const int R = C.R;
+    const int cmax = (1 << (cv.geom[inst].B - C.k)) - 1;
+    const float bmul = C.band_mul, badd = C.band_add, far32 = C.far32;
+    const int32_t skip_below = max(rho_skip, C.skip);
+    const unsigned long long hb = ib ? ((unsigned long long)inst << S) : 0ull;
+    uint32_t c0[G];
+    unmorton<G>(code, c0);
+    if (warp == 0) {
+      Union<G> u;
+      block_union<G>(c0, R, cmax, u);
+      const int nrr = union_runs<G>(u, hkeys, hvals, hmask, hb, n, lane, sm.rt);
+      if (lane == 0) sm.nr = nrr;
+    }
+    __syncthreads();
+    const int nr = sm.nr;
+    const uint32_t total = sm.rt.pre[nr];
+    const uint32_t q0 = pc.y < run.x ? run.x : pc.y;
+    const uint32_t qp = q0 + (uint32_t)qrow;
+    const bool inq = qp < run.y;
+    const Pt<DP> o = load_pt<DP>(spts, q0);
+    Pt<DP> me;
+#pragma unroll
+    for (int a = 0; a < DP; ++a) me.x[a] = 0.f;
+    unsigned long long K = ~0ull;
+    if (inq) {
+      me = load_pt<DP>(spts, qp);
+      K = skey[qp];
+    }
+    const bool act = inq && (int32_t)(K >> 32) >= skip_below;
+    const unsigned long long Kc = act ? K : ~0ull;  // no candidate is above ~0
+    float nq = 0.f;
+    {
+      float row[kTcK];
+#pragma unroll
+      for (int a = 0; a < DP; ++a) {
+        const float t = inq ? me.x[a] - o.x[a] : 0.f;
+        row[a] = t;
+        nq = fmaf(t, t, nq);
+      }
+      row[8] = nq;
+      row[9] = 1.f;
+#pragma unroll
+      for (int a = 10; a < kTcK; ++a) row[a] = 0.f;
+      if (chalf == 0) put_row<kTcM>(sm.a, qrow, row);
+    }
+    NearBounds nb;
+    nb.init();
+    auto fetch = [&](uint32_t w, unsigned long long& kc) {
+      Pt<DP> x;
+#pragma unroll
+      for (int a = 0; a < DP; ++a) x.x[a] = 0.f;
+      kc = 0ull;
+      const uint32_t e = w + (uint32_t)tid;
+      if (e < total) {
+        int lo = 0, hi2 = nr - 1;
+        while (lo < hi2) {
+          const int mid = (lo + hi2 + 1) >> 1;
+          if (sm.rt.pre[mid] <= e) lo = mid;
+          else hi2 = mid - 1;
+        }
+        const uint32_t src = sm.rt.start[lo] + (e - sm.rt.pre[lo]);
+        x = load_pt<DP>(spts, src);
+        kc = skey[src];
+      }
+      return x;
+    };
+    unsigned long long knext;
+    Pt<DP> xnext = fetch(0, knext);
+    for (uint32_t w0 = 0; w0 < total && !stop; w0 += kTcN) {
+      {
+        const int r = tid;
+        float row[kTcK];
+        float ncr = 0.f;
+        if (w0 + (uint32_t)r < total) {
+          float nc = 0.f;
+#pragma unroll
+          for (int a = 0; a < DP; ++a) {
+            const float t = xnext.x[a] - o.x[a];
+            row[a] = -2.f * t;
+            nc = fmaf(t, t, nc);
+          }
+          row[8] = 1.f;
+          row[9] = nc;
+          ncr = nc;
+          sm.key[r] = knext;
+        } else {
+#pragma unroll
+          for (int a = 0; a < DP; ++a) row[a] = 0.f;
+          row[8] = 0.f;
+          row[9] = kTcFar;
+          sm.key[r] = 0ull;
+        }
+        float m = ncr;
+        for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, off));
+        if (lane == 0) sm.cmax[warp] = m;
+#pragma unroll
+        for (int a = 10; a < kTcK; ++a) row[a] = 0.f;
+        put_row<kTcN>(sm.b, r, row);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (tid == 0) {
+        const uint32_t ab = smem_addr(sm.a[0]), al = smem_addr(sm.a[1]);
+        const uint32_t bb = smem_addr(sm.b[0]), bl = smem_addr(sm.b[1]);
+        const uint32_t as[3] = {ab, ab, al}, bs[3] = {bb, bl, bb};
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+#pragma unroll
+          for (int sp = 0; sp < 3; ++sp) {
+            const uint64_t ad = smem_desc(as[sp] + ks * (kTcM * 32));
+            const uint64_t bd = smem_desc(bs[sp] + ks * (kTcN * 32));
+            const uint32_t accum = (ks | sp) ? 1u : 0u;
+            asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+                         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n}\n"
+                         :: "r"(tmem), "l"(ad), "l"(bd), "r"(kTcIdesc), "r"(accum) : "memory");
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     :: "r"(mbar) : "memory");
+      }
+      if (w0 + kTcN < total) xnext = fetch(w0 + kTcN, knext);
+      const bool ok = mbar_wait(mbar, phase, poll_limit);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {  // the MMA did not finish in time: record and stop
+        if (tid == 0) set_status(cv.cls->status, kStatusTimeout);
+        mbar_wait(mbar, phase ^ 1u, kTcWaitLimit);  // the MMA in flight, before TMEM is freed
+        stop = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int ncol = (int)min((uint32_t)kTcN, total - w0);
+      for (int cl = 0; cl < kTcN / 2; cl += 32) {
+        const int cb = chalf * (kTcN / 2) + cl;
+        if (cb >= ncol) break;  // warp-uniform
+        float v[32];
+        tmem_ld32(trow + (uint32_t)cl, v);
+        if (act) {
+          // the two smallest accumulators among the higher candidates of
+          // these 32 columns, and the candidate at the smallest
+          float a1 = INFINITY, a2 = INFINITY;
+          uint32_t i1 = 0xffffffffu;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const unsigned long long kc = sm.key[cb + j];
+            const float x = kc > Kc ? v[j] : INFINITY;
+            a2 = fminf(a2, fmaxf(a1, x));
+            i1 = x < a1 ? key_id(kc) : i1;
+            a1 = fminf(a1, x);
+          }
+          if (i1 != 0xffffffffu) {
+            const float E = __fmul_ru(kTcErr, __fadd_ru(nq, sm.cmax[cb >> 5]));
+            nb.add(__fadd_ru(a1, E), i1, __fsub_rd(a1, E), __fsub_rd(a2, E));
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+    }
+    // the two column halves of each query, then settle it or queue it
+    if (chalf == 1) {
+      sm.ub[qrow] = nb.ub;
+      sm.l1[qrow] = nb.l1;
+      sm.l2[qrow] = nb.l2;
+      sm.ib[qrow] = nb.ib;
+      sm.il[qrow] = nb.il;
+    }
+    __syncthreads();
+    bool push = false;
+    float s_hand = INFINITY;
+    if (chalf == 0 && inq && !stop) {
+      NearBounds other;
+      other.ub = sm.ub[qrow];
+      other.l1 = sm.l1[qrow];
+      other.l2 = sm.l2[qrow];
+      other.ib = sm.ib[qrow];
+      other.il = sm.il[qrow];
+      nb.merge(other);
+      const uint32_t id = key_id(K);
+      if (!act) {
+        lambda[id] = -1;
+        delta[id] = __longlong_as_double(0x7ff8000000000000ll);  // NaN: skipped
+      } else {
+        bool settled = false;
+        if (nb.ib != 0xffffffffu) {
+          const float rest = nb.il == nb.ib ? nb.l2 : nb.l1;
+          settled = tc_band(nb.ub, bmul, badd) < far32 && rest > __fmul_ru(nb.ub, 1.f + 0x1p-20f);
+          s_hand = tc_band(nb.ub, bmul, badd);
+        }
+        if (settled) {
+          const uint32_t ol = nb.ib - (uint32_t)I.out;
+          lambda[id] = (int32_t)ol;
+          delta[id] = sqrt(dist64<DP>(me, tc_caller_pt(pts, dtype, I.coord, I.d, ol)));
+        } else {
+          push = true;
+        }
+      }
+    }
+    const unsigned pm = __ballot_sync(kFull, push);
+    uint32_t base = 0;
+    if (lane == 0 && pm) base = atomicAdd(&ctr->queue_n, (unsigned)__popc(pm));
+    base = __shfl_sync(kFull, base, 0);
+    if (push) {
+      const uint32_t slot2 = base + __popc(pm & lanemask_lt);
+      fq.pos[slot2] = qp;
+      fq.s1[slot2] = s_hand;
+    }
+    __syncthreads();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcN) : "memory");
+}
+
+constexpr size_t kTcNearSmemBytes =
+    sizeof(TcNearSmem) > 100 * 1024 ? sizeof(TcNearSmem) : 100 * 1024;
+static_assert(sizeof(TcNearSmem) <= 200 * 1024, "shared-memory layout too large");
+
 }  // namespace
 
 void launch_density_tc(int g, const float* spts, const uint32_t* sid, const ClassView& cv,
@@ -450,7 +813,8 @@ void launch_density_tc(int g, const float* spts, const uint32_t* sid, const Clas
   }
   cudaMemsetAsync(&hi->work, 0, sizeof(uint32_t), st);
   cudaMemsetAsync(&hi->npieces, 0, sizeof(uint32_t), st);
-  k_tc_pieces<<<sm_count() * 8u, 256, 0, st>>>(hi, hkeys, hvals, cv.N, pieces, sid, rho_out, skey);
+  k_tc_pieces<<<sm_count() * 8u, 256, 0, st>>>(hi, hkeys, hvals, cv.N, pieces, sid, rho_out, skey,
+                                                true, nullptr);
   const unsigned grid = sm_count() * 2u;  // two resident CTAs per SM take the pieces one by one
   const uint32_t poll = wait_limit(kTcWaitLimit);
   if (g == 3)
@@ -459,6 +823,41 @@ void launch_density_tc(int g, const float* spts, const uint32_t* sid, const Clas
   else
     k_density_tc<4><<<grid, kTcThreads, kTcSmemBytes, st>>>(spts, sid, cv, cuts, hi, hkeys, hvals,
                                                             pieces, rho_out, skey, ctr, poll);
+  count_launches(2);
+}
+
+
+void launch_dep_near_tc(int g, const float* spts, const uint32_t* sid,
+                        const unsigned long long* skey, const ClassView& cv, int32_t rho_skip,
+                        const void* pts, int dtype, const CutGeom* cuts, HashInfo* hi,
+                        const unsigned long long* hkeys, const uint2* hvals, uint2* pieces,
+                        int32_t* lambda, double* delta, FarQueue q, Counters* ctr,
+                        cudaStream_t st) {
+  if (cv.N == 0) return;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_dep_near_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kTcNearSmemBytes);
+    cudaFuncSetAttribute(k_dep_near_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kTcNearSmemBytes);
+    attr = true;
+  }
+  cudaMemsetAsync(&ctr->queue_n, 0, sizeof(unsigned int), st);
+  cudaMemsetAsync(&ctr->queue2_n, 0, sizeof(unsigned int), st);
+  cudaMemsetAsync(&hi->work, 0, sizeof(uint32_t), st);
+  cudaMemsetAsync(&hi->npieces, 0, sizeof(uint32_t), st);
+  k_tc_pieces<<<sm_count() * 8u, 256, 0, st>>>(hi, hkeys, hvals, cv.N, pieces, sid, nullptr,
+                                                nullptr, false, lambda);
+  const unsigned grid = sm_count() * 2u;
+  const uint32_t poll = wait_limit(kTcWaitLimit);
+  if (g == 3)
+    k_dep_near_tc<3><<<grid, kTcThreads, kTcNearSmemBytes, st>>>(spts, skey, cv, rho_skip, pts, dtype,
+                                                                 cuts, hi, hkeys, hvals, pieces,
+                                                                 lambda, delta, q, ctr, poll);
+  else
+    k_dep_near_tc<4><<<grid, kTcThreads, kTcNearSmemBytes, st>>>(spts, skey, cv, rho_skip, pts, dtype,
+                                                                 cuts, hi, hkeys, hvals, pieces,
+                                                                 lambda, delta, q, ctr, poll);
   count_launches(2);
 }
 

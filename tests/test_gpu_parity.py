@@ -345,6 +345,30 @@ def test_tensor_density_dense_blocks(d, dtype):
             assert dpc.dpc_get_stats()["density_layout"] == (4 if prec == "fp32" else 2), prec
 
 
+@pytest.mark.parametrize("d,dtype", [(5, np.float32), (7, np.float32), (8, np.float32), (5, np.int32),
+                                     (6, np.int32)])
+def test_tensor_near_phase(d, dtype):
+    """The tensor-core near phase (and density) in 5-8 dimensions: dense blocks
+    of many 256-candidate tiles, and for integer coordinates many exactly equal
+    distances (candidates no bound separates go to the far phase, which ranks
+    them in binary64); every output against the oracle, and the near phase
+    checked to have run on the tensor cores."""
+    rng = np.random.default_rng(500 + d)
+    if dtype == np.int32:
+        pts = rng.integers(0, 9, (8000, d)).astype(np.int32)
+        cuts = [2.0, 3.0]
+    else:
+        pts = W.random_blobs(10000, d, 510 + d, n_blobs=3, dup_frac=0.01)
+        cuts = [0.12, 0.2]
+    refs = [oracle.run(pts, c, 2, 3, 0.1) for c in cuts]
+    t = torch.from_numpy(pts).cuda()
+    out = dpc.run(t, cuts, 2, 3, 0.1, layout="tensor")
+    st = dpc.dpc_get_stats()
+    assert st["near_layout"] == 4 and st["density_layout"] == 4
+    for c, ref in enumerate(refs):
+        assert_same({k: v[c].cpu().numpy() for k, v in out.items()}, ref, "d=%d cut %d" % (d, c))
+
+
 @pytest.mark.parametrize("d,dtype", [(1, np.int32), (2, np.float32), (2, np.int32), (3, np.float32),
                                      (3, np.int32), (4, np.float32), (6, np.float32)])
 def test_cell_layout_large_cells(d, dtype):
