@@ -157,12 +157,57 @@ k_density(const float* __restrict__ spts, const unsigned long long* __restrict__
 // compares its V candidates with the query (read as a broadcast) and one warp
 // reduction gives the query's count.  No lane evaluates a candidate outside
 // the query's block, so the work is exactly the block's pairs.
+// In float32 the lane holds its candidates negated, two per packed register,
+// and evaluates dist32 for both at once (packed add / mul / fma: the same
+// rounding as the scalar sequence, so the certified band is unchanged); a
+// pair counts when s - up(t_in) is negative (its sign bit), and one unsigned
+// minimum per lane over the bit patterns of s finds band pairs, which are
+// recounted in binary64 after the window.  Small V (4 slots in 3-D) keeps the
+// kernel at 80 registers, 6 blocks per SM: the loop is latency-bound, and more
+// resident warps pay more than longer windows.
+
+// Exact count of the band pairs of queries qa and qb (sorted positions) among
+// this lane's candidates of window w0 (rare path: a warp takes it only for the
+// query pairs of a window that met a band pair, after the window's passes).
+// The candidates are loaded again one slot at a time, so neither the hot loop
+// nor this pass holds a window's copy.  Returns (binary64 counts of a | b << 16,
+// band pairs seen of a | b << 16), summed over the warp.
+template <int DP, int V, int ND>
+__device__ __forceinline__ uint2 seg_band_recount(const RunTable& rt, int nr, uint32_t w0,
+                                                  uint32_t total, const float* __restrict__ spts,
+                                                  int lane, uint32_t qa, uint32_t qb, float t_in,
+                                                  float t_out, double dc2) {
+  const Pt<DP> xa = load_pt<DP>(spts, qa);
+  const Pt<DP> xb = load_pt<DP>(spts, qb);
+  unsigned in = 0, seen = 0;
+#pragma unroll 1
+  for (uint32_t e = w0 + lane; e < total && e < w0 + 32u * V; e += 32u) {
+    int lo = 0, hi = nr - 1;  // the run holding candidate e
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (rt.pre[mid] <= e) lo = mid;
+      else hi = mid - 1;
+    }
+    const Pt<DP> x = load_pt<DP>(spts, rt.start[lo] + (e - rt.pre[lo]));
+    const float sa = dist32<DP, ND>(xa, x);
+    const float sb = dist32<DP, ND>(xb, x);
+    if (sa > t_in && sa <= t_out) {
+      ++seen;
+      in += dist64<DP, ND>(xa, x) <= dc2 ? 1u : 0u;
+    }
+    if (sb > t_in && sb <= t_out) {
+      seen += 0x10000u;
+      in += dist64<DP, ND>(xb, x) <= dc2 ? 0x10000u : 0u;
+    }
+  }
+  return make_uint2(__reduce_add_sync(kFull, in), __reduce_add_sync(kFull, seen));
+}
 
 template <int DP>
-constexpr int seg_v() { return DP == 2 ? 16 : (DP == 4 ? 8 : 4); }
+constexpr int seg_v() { return DP == 2 ? 8 : (DP == 4 ? 4 : 2); }
 
 template <int DP, int G, bool F64>
-__global__ void __launch_bounds__(kThreads, 5)
+__global__ void __launch_bounds__(kThreads, (F64 || G >= 4) ? 5 : 6)
 k_density_seg(const float* __restrict__ spts, const unsigned long long* __restrict__ scode,
               const uint32_t* __restrict__ sid, ClassView cv, const CutGeom* __restrict__ cuts,
               const HashInfo* __restrict__ hi, const unsigned long long* __restrict__ hkeys,
@@ -190,6 +235,9 @@ k_density_seg(const float* __restrict__ spts, const unsigned long long* __restri
     const int cmax = (1 << (cv.geom[inst].B - k)) - 1;
     const double dc2 = C.dc2;
     const float t_in = C.t_in, t_out = C.t_out;
+    const BandBits bb = band_bits(t_in, t_out);
+    // s <= t_in  <=>  s - up(t_in) < 0, with up(t_in) the next float above
+    const f32x2 ntin2 = pack2(-next_up(t_in), -next_up(t_in));
     const unsigned long long hb = ib ? ((unsigned long long)inst << S) : 0ull;
     const uint32_t p = p0 + lane;
     const bool valid = p < end;
@@ -208,15 +256,11 @@ k_density_seg(const float* __restrict__ spts, const unsigned long long* __restri
         load_window<DP, V>(rt, nr, w0, total, spts, lane, cand);
         // slots of this window that hold candidates (warp-uniform)
         const int vn = (int)min((uint32_t)V, (total - w0 + 31u) / 32u);
-        // two queries per pass over the lane's candidates (independent
-        // chains); their per-lane counts (at most V each) share one 32-bit
-        // word per reduction
-        for (int j = s; j < e; j += 2) {
-          const bool two = j + 1 < e;
-          const Pt<DP> xa = load_pt<DP>(spts, p0 + j);
-          const Pt<DP> xb = load_pt<DP>(spts, p0 + (two ? j + 1 : j));
-          int32_t cnt_a, cnt_b;
-          if constexpr (F64) {
+        if constexpr (F64) {
+          for (int j = s; j < e; j += 2) {
+            const bool two = j + 1 < e;
+            const Pt<DP> xa = load_pt<DP>(spts, p0 + j);
+            const Pt<DP> xb = load_pt<DP>(spts, p0 + (two ? j + 1 : j));
             unsigned c = 0;
 #pragma unroll
             for (int v = 0; v < V; ++v) {
@@ -225,47 +269,71 @@ k_density_seg(const float* __restrict__ spts, const unsigned long long* __restri
               c += (dist64<DP, ND>(xb, cand[v]) <= dc2) ? 0x10000u : 0u;
             }
             c = __reduce_add_sync(kFull, c);
-            cnt_a = (int32_t)(c & 0xffffu);
-            cnt_b = (int32_t)(c >> 16);
-          } else {
-            unsigned ci = 0, co = 0;
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-              if (v >= vn) break;
-              const float sa = dist32<DP, ND>(xa, cand[v]);
-              const float sb = dist32<DP, ND>(xb, cand[v]);
-              ci += (sa <= t_in ? 1u : 0u) + (sb <= t_in ? 0x10000u : 0u);
-              co += (sa <= t_out ? 1u : 0u) + (sb <= t_out ? 0x10000u : 0u);
-            }
-            ci = __reduce_add_sync(kFull, ci);
-            co = __reduce_add_sync(kFull, co);
-            cnt_a = (int32_t)(ci & 0xffffu);
-            cnt_b = (int32_t)(ci >> 16);
-            if (co != ci) {  // band pairs: recount them in binary64
-              unsigned in = 0, seen = 0;
-#pragma unroll
-              for (int v = 0; v < V; ++v) {
-                if (v >= vn) break;
-                const float sa = dist32<DP, ND>(xa, cand[v]);
-                const float sb = dist32<DP, ND>(xb, cand[v]);
-                if (sa > t_in && sa <= t_out) {
-                  ++seen;
-                  in += dist64<DP, ND>(xa, cand[v]) <= dc2 ? 1u : 0u;
-                }
-                if (sb > t_in && sb <= t_out) {
-                  seen += 0x10000u;
-                  in += dist64<DP, ND>(xb, cand[v]) <= dc2 ? 0x10000u : 0u;
-                }
-              }
-              in = __reduce_add_sync(kFull, in);
-              seen = __reduce_add_sync(kFull, seen);
-              cnt_a += (int32_t)(in & 0xffffu);
-              cnt_b += (int32_t)(in >> 16);
-              if (lane == 0) band += (seen & 0xffffu) + (two ? (seen >> 16) : 0u);
-            }
+            if (lane == j) acc += (int32_t)(c & 0xffffu);
+            if (two && lane == j + 1) acc += (int32_t)(c >> 16);
           }
-          if (lane == j) acc += cnt_a;
-          if (two && lane == j + 1) acc += cnt_b;
+        } else {
+          // the lane's candidates negated, two slots per packed register; a
+          // slot past the window's end holds +inf (distance +inf: never
+          // counted, never in the band)
+          f32x2 nc[V / 2][ND];
+#pragma unroll
+          for (int i = 0; i < V / 2; ++i) {
+            const bool ok0 = w0 + (uint32_t)lane + 64u * i < total;
+            const bool ok1 = w0 + (uint32_t)lane + 64u * i + 32u < total;
+#pragma unroll
+            for (int k = 0; k < ND; ++k)
+              nc[i][k] = pack2(ok0 ? -cand[2 * i].x[k] : INFINITY, ok1 ? -cand[2 * i + 1].x[k] : INFINITY);
+          }
+          // two queries per pass over the lane's candidate pairs (independent
+          // chains); their per-lane counts (at most V each) share one 32-bit
+          // word per reduction, and one unsigned minimum per lane tells
+          // whether any of its pairs fell in the band
+          uint32_t bandq = 0;  // bit j: queries j and j + 1 met a band pair
+          auto passes = [&](auto full_window) {
+            constexpr bool kFullWindow = decltype(full_window)::value;
+            const int vp = (vn + 1) >> 1;
+            for (int j = s; j < e; j += 2) {
+              const bool two = j + 1 < e;
+              const Pt<DP> xa = load_pt<DP>(spts, p0 + j);
+              const Pt<DP> xb = load_pt<DP>(spts, p0 + (two ? j + 1 : j));
+              f32x2 qa[ND], qb[ND];
+#pragma unroll
+              for (int k = 0; k < ND; ++k) {
+                qa[k] = pack2(xa.x[k], xa.x[k]);
+                qb[k] = pack2(xb.x[k], xb.x[k]);
+              }
+              uint32_t na = 0, nb = 0, mband = 0xffffffffu;
+#pragma unroll
+              for (int i = 0; i < V / 2; ++i) {
+                if (!kFullWindow && i >= vp) break;
+                const f32x2 sa = dist32x2<ND>(qa, nc[i]);
+                const f32x2 sb = dist32x2<ND>(qb, nc[i]);
+                na += sign_count2(add2(sa, ntin2));
+                nb += sign_count2(add2(sb, ntin2));
+                mband = min(mband, band_min2(sa, bb.lo));
+                mband = min(mband, band_min2(sb, bb.lo));
+              }
+              unsigned c = na + (nb << 16);
+              c = __reduce_add_sync(kFull, c);
+              // band pairs: recounted in binary64 after the window's passes
+              if (__any_sync(kFull, mband < bb.width)) bandq |= 1u << j;
+              if (lane == j) acc += (int32_t)(c & 0xffffu);
+              if (two && lane == j + 1) acc += (int32_t)(c >> 16);
+            }
+          };
+          if (vn == V) passes(std::true_type{});
+          else passes(std::false_type{});
+          while (bandq) {
+            const int j = __ffs(bandq) - 1;
+            bandq &= bandq - 1u;
+            const bool two = j + 1 < e;
+            const uint2 r = seg_band_recount<DP, V, ND>(rt, nr, w0, total, spts, lane, p0 + j,
+                                                        p0 + (two ? j + 1 : j), t_in, t_out, dc2);
+            if (lane == j) acc += (int32_t)(r.x & 0xffffu);
+            if (two && lane == j + 1) acc += (int32_t)(r.x >> 16);
+            if (lane == 0) band += (r.y & 0xffffu) + (two ? (r.y >> 16) : 0u);
+          }
         }
       }
       s = e;

@@ -357,6 +357,93 @@ __device__ __forceinline__ double dist64(const Pt<DP>& a, const Pt<DP>& b) {
   return s;
 }
 
+// ---------------------------------------------------------------------------
+// Packed float32 pairs: add / mul / fma on the two float32 halves of a 64-bit
+// register in one instruction (sm_100 and later), each half rounded to nearest
+// exactly as the scalar operation, subnormals kept.  The segment kernels
+// evaluate dist32 for two candidates at once with them -- the same value bit
+// for bit, in half the issue slots.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pack2(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float lo2(f32x2 v) {
+  float lo;
+  asm("mov.b64 {%0, _}, %1;" : "=f"(lo) : "l"(v));
+  return lo;
+}
+__device__ __forceinline__ float hi2(f32x2 v) {
+  float hi;
+  asm("mov.b64 {_, %0}, %1;" : "=f"(hi) : "l"(v));
+  return hi;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// dist32 of a query against two candidates at once.  q2[k] holds the query's
+// coordinate k in both halves, nc[k] the two candidates' coordinate k negated:
+// t = q + (-c) rounds exactly as q - c, and s = t0*t0 (= fma(t0, t0, 0)), then
+// s = fma(t_k, t_k, s) in increasing k: dist32's sequence in each half.
+template <int ND>
+__device__ __forceinline__ f32x2 dist32x2(const f32x2* q2, const f32x2* nc) {
+  f32x2 t = add2(q2[0], nc[0]);
+  f32x2 s = mul2(t, t);
+#pragma unroll
+  for (int k = 1; k < ND; ++k) {
+    t = add2(q2[k], nc[k]);
+    s = fma2(t, t, s);
+  }
+  return s;
+}
+
+// The next float above x (finite x): s <= x  <=>  s < next_up(x) for floats.
+__device__ __forceinline__ float next_up(float x) {
+  const uint32_t b = __float_as_uint(x);
+  if (b == 0x80000000u) return __uint_as_float(1u);  // -0: the least positive subnormal
+  return __uint_as_float((b >> 31) ? b - 1u : b + 1u);
+}
+
+// Number of negative halves of a packed pair (sign bits: fl(s - t) is
+// negative exactly when s < t, for s, t not NaN).
+__device__ __forceinline__ uint32_t sign_count2(f32x2 u) {
+  return (__float_as_uint(lo2(u)) >> 31) + (__float_as_uint(hi2(u)) >> 31);
+}
+
+// The float32 filter band t_in < s <= t_out as one unsigned test on the bit
+// pattern of s >= +0 (non-negative floats order like their bit patterns):
+// (bits(s) - lo) < width.  A negative (or -0) t_in takes every s from +0 on
+// (a superset: the band pass rechecks each pair exactly); NaN and values above
+// t_out fall outside.
+struct BandBits {
+  uint32_t lo, width;
+};
+__device__ __forceinline__ BandBits band_bits(float t_in, float t_out) {
+  const uint32_t bi = __float_as_uint(t_in);
+  const uint32_t lo = (bi >> 31) ? 0u : bi + 1u;
+  return BandBits{lo, __float_as_uint(t_out) + 1u - lo};
+}
+// min over both halves of s of bits(s) - lo: below BandBits::width iff a half
+// lies in the band.
+__device__ __forceinline__ uint32_t band_min2(f32x2 s, uint32_t lo) {
+  return min(__float_as_uint(lo2(s)) - lo, __float_as_uint(hi2(s)) - lo);
+}
+
 // Order key: larger = higher in the total order (density, then smaller id).
 __device__ __forceinline__ unsigned long long order_key(int32_t rho, uint32_t id) {
   return ((unsigned long long)(uint32_t)rho << 32) | (unsigned long long)(0xffffffffu - id);
