@@ -124,6 +124,95 @@ __device__ __forceinline__ int union_runs(const Union<G>& u,
   return nr;
 }
 
+// Run table of a union of at most 64 cells around the queries of one
+// segment, ordered by offset class for a multi-pass search over blocks of
+// radius 1.  A cell's class is the least number of axes on which it differs
+// from the cell of a segment query whose 3^G block contains it (0: a query's
+// own cell, 1: a face neighbour, 2: an edge neighbour, ...); cells in no
+// query's block get class G + 1 and are left out (no hash lookup either).
+// segc holds the segment's nseg distinct query cells.  cend[k] is one past
+// the last run of class <= k; returns the number of runs.
+template <int G>
+__device__ __forceinline__ int union_runs_classed(const Union<G>& u,
+                                                  const unsigned long long* __restrict__ hkeys,
+                                                  const uint2* __restrict__ hvals, uint32_t hmask,
+                                                  unsigned long long hb, uint32_t n, int lane,
+                                                  RunTable& rt, const uint32_t (*segc)[G], int nseg,
+                                                  int* cend) {
+  const uint32_t lanemask_lt = (1u << lane) - 1u;
+  uint32_t st[2], len[2], rel[2];
+  int cl[2];
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    const int o = 32 * b + lane;
+    st[b] = len[b] = rel[b] = 0u;
+    cl[b] = G + 1;
+    if (o < u.ncell) {
+      int rem = o;
+      uint32_t c[G];
+#pragma unroll
+      for (int a = 0; a < G; ++a) {
+        const int q = div_small(rem, u.inv[a]);
+        const uint32_t r = (uint32_t)(rem - q * u.w[a]);
+        c[a] = (uint32_t)u.lo[a] + r;
+        rel[b] |= r << (7 * a);
+        rem = q;
+      }
+      for (int t = 0; t < nseg; ++t) {
+        int nnz = 0;
+        bool inb = true;
+#pragma unroll
+        for (int a = 0; a < G; ++a) {
+          const int dl = (int)c[a] - (int)segc[t][a];
+          inb &= dl >= -1 && dl <= 1;
+          nnz += dl != 0;
+        }
+        if (inb) cl[b] = min(cl[b], nnz);
+      }
+      if (cl[b] <= G) {
+        const uint2 run = clip_run(hash_find(hkeys, hvals, hmask, hb | morton<G>(c)), n);
+        st[b] = run.x;
+        len[b] = run.y - run.x;
+      }
+    }
+  }
+  // slots: by class, then by round and lane; lengths first, offsets below
+  int nr = 0;
+#pragma unroll
+  for (int k = 0; k <= G; ++k) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const bool mine = len[b] > 0 && cl[b] == k;
+      const unsigned m = __ballot_sync(kFull, mine);
+      if (mine) {
+        const int slot = nr + __popc(m & lanemask_lt);
+        rt.start[slot] = st[b];
+        rt.cell[slot] = rel[b];
+        rt.pre[slot] = len[b];
+      }
+      nr += __popc(m);
+    }
+    cend[k] = nr;
+  }
+  __syncwarp();
+  uint32_t carry = 0;
+  for (int base = 0; base < nr; base += 32) {
+    const int sl = base + lane;
+    const uint32_t v = sl < nr ? rt.pre[sl] : 0u;
+    uint32_t incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t t = __shfl_up_sync(kFull, incl, d);
+      if (lane >= d) incl += t;
+    }
+    if (sl < nr) rt.pre[sl] = carry + incl - v;
+    carry += __shfl_sync(kFull, incl, 31);
+  }
+  if (lane == 0) rt.pre[nr] = carry;
+  __syncwarp();
+  return nr;
+}
+
 // Copy candidates [w0, w1) of the concatenated list into the window: lane l
 // copies candidates w0 + l, w0 + l + 32, ...; all loads of a window are
 // independent, so the warp keeps many of them in flight.
