@@ -288,8 +288,13 @@ int dpc_run(const void* pts, int dtype, const dpc_batch* b, const dpc_params* pa
             void* stream);
 
 /* dpc_run on HOST buffers: copies the points to the device, runs, copies the
- * four results back and synchronizes `stream` before returning.  Host buffers
- * that are page-locked copy faster.  Same layouts as dpc_run. */
+ * four results back and synchronizes `stream` before returning.  Each result
+ * is copied back on a stream the library owns as soon as the phase that
+ * writes it has finished (rho after the density, lambda and delta after the
+ * dependent search, the labels last), overlapping the phases still to run;
+ * every copy has finished when the call returns, also on error.  Host buffers
+ * that are page-locked copy faster (and only those overlap).  Same layouts as
+ * dpc_run. */
 int dpc_run_host(const void* pts_host, int dtype, const dpc_batch* b, const dpc_params* params,
                  int32_t* rho_host, int32_t* lambda_host, double* delta_host,
                  int32_t* label_host, uint32_t flags, void* stream);
@@ -337,9 +342,11 @@ typedef struct {
   int64_t far_nodes_max;  /* most nodes expanded by a single far query       */
   int32_t block_radius;   /* block radius R of the last cutoff (cells per side
                              of the (2R+1)^g block around a query's cell)     */
-  int32_t density_layout; /* layout of the last density launch: 1 union,
-                             2 segment (see DPC_FLAG_LAYOUT)                  */
-  int32_t near_layout;    /* layout of the last near-dependent launch (3 = tree) */
+  int32_t density_layout; /* layout the last density launch ran: 1 union,
+                             2 segment, 4 tensor, 5 pairs, 6 cell
+                             (see DPC_FLAG_LAYOUT)                            */
+  int32_t near_layout;    /* layout of the last near-dependent launch: 1 union,
+                             2 segment, 3 tree, 4 tensor, 6 cell              */
   int32_t near_shift;     /* grid levels the near phase ran below the density's */
   int64_t density_pairs;  /* (query, candidate) pairs the density step scanned
                              (every cutoff and instance of the last call)    */

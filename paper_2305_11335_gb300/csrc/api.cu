@@ -20,6 +20,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <string>
 #include <mutex>
@@ -259,9 +260,12 @@ struct Workspace {
   size_t up_bytes = 0;
   cudaEvent_t up_done = nullptr;  // the last copy out of up_host has finished
 
-  // host-buffer entry point staging
+  // host-buffer entry point staging; its copies to the host run on a stream
+  // of their own, each behind the event of the phase that finished its output
   void* io = nullptr;
   size_t io_bytes = 0;
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> out_ev;
 
   // priority range search: per-query arrays (scr) and the match keys (scr2)
   void* scr = nullptr;
@@ -332,6 +336,10 @@ struct Workspace {
     if (up_dev) cudaFree(up_dev);
     if (up_host) cudaFreeHost(up_host);
     if (up_done) cudaEventDestroy(up_done);
+    for (cudaEvent_t e : out_ev) cudaEventDestroy(e);
+    out_ev.clear();
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+    copy_stream = nullptr;
     for (auto& e : tune_ev) {
       if (e) cudaEventDestroy(e);
       e = nullptr;
@@ -1154,12 +1162,19 @@ int dpc_cluster(const dpc_batch* b, int32_t dcut_index, const dpc_params* params
 }
 
 // The kernels of every class and cutoff (the part of dpc_run a graph holds).
+// A phase of one cutoff finished for every class: stage 0 after the density
+// (rho), 1 after the dependent search (lambda, delta), 2 after the labels.
+using StageDone = std::function<void(int stage, int cut)>;
+
 static void run_classes(Workspace* w, const CallPlan& P, const void* pts, int dtype,
                         const dpc_batch* b, const std::vector<Inst>& insts, uint64_t N,
                         const dpc_params* params, int32_t* rho, int32_t* lambda, double* delta,
-                        int32_t* label, uint32_t flags) {
+                        int32_t* label, uint32_t flags, const StageDone* done = nullptr) {
   const bool fp64 = (flags & DPC_PREC_MASK) == DPC_PREC_FP64;
   for (const ClassPlan& c : P.classes) {
+    // classes run one after another on the stream, so a phase of the last
+    // class finishes that phase's output of every class
+    const bool last = &c == &P.classes.back();
     const ClassView cv = view_of(w, c, insts);
     bin_class(w, pts, dtype, P, c, cv, b, insts);
     tree_step(w, cv);
@@ -1170,10 +1185,13 @@ static void run_classes(Workspace* w, const CallPlan& P, const void* pts, int dt
       const Choice ch = choose(w, c, cv, cuts, b, k, fp64, rho + o, flags, &nt);
       cells_step(w, c, cv, cuts);
       density_step(w, c, cv, cuts, fp64, ch.dlay, ch.sc, rho + o);
+      if (last && done) (*done)(0, k);
       dependent_step(w, c, cv, cuts, pts, dtype, 0, fp64, ch.nlay, ch.ns, ch.sc, lambda + o,
                      delta + o);
+      if (last && done) (*done)(1, k);
       labels_step(w, c, cv, k, one_params(params, c, P.ncut_all, k), rho + o, lambda + o,
                   delta + o, label + o);
+      if (last && done) (*done)(2, k);
     }
   }
 }
@@ -1323,11 +1341,11 @@ int dpc_priority_range(const void* pts, int dtype, const dpc_batch* b, const int
 static int run_device(Workspace* w, const void* pts, int dtype, const dpc_batch* b,
                       const std::vector<Inst>& insts, uint64_t N, const dpc_params* params,
                       int32_t* rho, int32_t* lambda, double* delta, int32_t* label,
-                      uint32_t flags) {
+                      uint32_t flags, const StageDone* done = nullptr) {
   CallPlan P = make_plan(b, insts, 0, b->n_dcut, false);
   int rc = prepare(w, P, b, insts, params, flags);
   if (rc) return rc;
-  run_classes(w, P, pts, dtype, b, insts, N, params, rho, lambda, delta, label, flags);
+  run_classes(w, P, pts, dtype, b, insts, N, params, rho, lambda, delta, label, flags, done);
   return cudaGetLastError() == cudaSuccess ? DPC_OK : DPC_ERR_CUDA;
 }
 
@@ -1456,17 +1474,46 @@ int dpc_run_host(const void* pts_host, int dtype, const dpc_batch* b, const dpc_
   if ((rc = w->reserve_io(total ? total : kAlign))) return rc;
   char* io = (char*)w->io;
   cudaStream_t st = w->stream;
+  // each output goes back as soon as its phase has finished (a copy stream
+  // behind an event), overlapping the phases still to run
+  if (!w->copy_stream && cudaStreamCreateWithFlags(&w->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    w->copy_stream = nullptr;
+    return DPC_ERR_CUDA;
+  }
+  const size_t nev = 3u * (size_t)b->n_dcut;
+  while (w->out_ev.size() < nev) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return DPC_ERR_CUDA;
+    }
+    w->out_ev.push_back(e);
+  }
+  cudaStream_t cs = w->copy_stream;
+  const StageDone done = [&](int stage, int k) {
+    const size_t o = (size_t)k * N;
+    cudaEvent_t ev = w->out_ev[3u * (size_t)k + (size_t)stage];
+    cudaEventRecord(ev, st);
+    cudaStreamWaitEvent(cs, ev, 0);
+    if (N == 0) return;
+    if (stage == 0) {
+      cudaMemcpyAsync(rho_host + o, io + o_rho + 4 * o, 4 * N, cudaMemcpyDeviceToHost, cs);
+    } else if (stage == 1) {
+      cudaMemcpyAsync(lambda_host + o, io + o_lam + 4 * o, 4 * N, cudaMemcpyDeviceToHost, cs);
+      cudaMemcpyAsync(delta_host + o, io + o_del + 8 * o, 8 * N, cudaMemcpyDeviceToHost, cs);
+    } else {
+      cudaMemcpyAsync(label_host + o, io + o_lab + 4 * o, 4 * N, cudaMemcpyDeviceToHost, cs);
+    }
+  };
   if (elems) cudaMemcpyAsync(io + o_pts, pts_host, 4 * elems, cudaMemcpyHostToDevice, st);
   rc = run_device(w, io + o_pts, dtype, b, insts, N, params, (int32_t*)(io + o_rho),
-                  (int32_t*)(io + o_lam), (double*)(io + o_del), (int32_t*)(io + o_lab), flags);
+                  (int32_t*)(io + o_lam), (double*)(io + o_del), (int32_t*)(io + o_lab), flags,
+                  &done);
+  // no copy into the caller's buffers may outlive the call, whatever happened
+  const cudaError_t ec = cudaStreamSynchronize(cs);
   if (rc) return rc;
-  if (R) {
-    cudaMemcpyAsync(rho_host, io + o_rho, 4 * R, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(lambda_host, io + o_lam, 4 * R, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(delta_host, io + o_del, 8 * R, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(label_host, io + o_lab, 4 * R, cudaMemcpyDeviceToHost, st);
-  }
-  if (cudaStreamSynchronize(st) != cudaSuccess) {
+  if (ec != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
     return DPC_ERR_CUDA;
   }

@@ -214,6 +214,29 @@ def test_run_host_matches_device():
         assert np.array_equal(host[k].numpy().view(np.uint8), dev[k].cpu().numpy().view(np.uint8))
 
 
+def test_run_host_batch_matches_oracle():
+    """The host-buffer entry point copies each output back as soon as its
+    phase has finished for the last dimension class; a batch of several
+    classes and two cutoffs checks that every per-cutoff copy holds the
+    finished values (against the oracle), twice in a row."""
+    sizes = [700, 0, 2100, 900, 1300]
+    dims = [2, 3, 3, 5, 1]
+    insts = [W.random_blobs(n, d, 300 + i) if n else np.zeros((0, d), np.float32)
+             for i, (n, d) in enumerate(zip(sizes, dims))]
+    cuts = [[0.02 * (1 + 0.5 * (d - 1)), 0.04 * (1 + 0.5 * (d - 1))] for d in dims]
+    batch = dpc.Batch.packed(sizes, dims, cuts)
+    flat = torch.from_numpy(np.concatenate([q.reshape(-1) for q in insts]).astype(np.float32))
+    params = dpc.make_params(batch, 2, 3, [0.1] * (len(sizes) * 2))
+    for _ in range(2):
+        out = dpc.dpc_run_host(flat.pin_memory(), batch, params)
+        out = {k: v.numpy() for k, v in out.items()}
+        for i, q in enumerate(insts):
+            lo, hi = batch.pt_offset[i], batch.pt_offset[i + 1]
+            for c in range(2):
+                ref = oracle.run(q, cuts[i][c], 2, 3, 0.1)
+                assert_same({k: v[c, lo:hi] for k, v in out.items()}, ref, "inst %d cut %d" % (i, c))
+
+
 def test_stats():
     pts = W.random_blobs(20000, 2, 67)
     gpu_run(pts, [0.01], 2, 4, 0.1)
