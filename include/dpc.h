@@ -278,9 +278,10 @@ int dpc_priority_range(const void* pts, int dtype, const dpc_batch* b, const int
 
 /* The whole pipeline for every cutoff: one binning per instance, then for each
  * cutoff density, dependent points and labels.  The instances of a batch are
- * processed together in at most four groups of equal padded dimension
- * (d = 1; d = 2; d = 3..4; d = 5..8), each kernel launched once per group, so
- * the launch count does not grow with the number of instances.
+ * processed together in at most five groups of equal padded dimension and
+ * gridded axes (d = 1; d = 2; d = 3; d = 4; d = 5..8), each kernel launched
+ * once per group, so the launch count does not grow with the number of
+ * instances.
  *   params                   host, [n_inst * n_dcut] thresholds
  *   rho, lambda, delta, label  device, [n_dcut][N] each (cutoff-major) */
 int dpc_run(const void* pts, int dtype, const dpc_batch* b, const dpc_params* params,
