@@ -241,7 +241,7 @@ struct Workspace {
   uint2* hvals = nullptr;
   uint32_t hcap = 0;
   Node* nodes = nullptr;
-  float* nbox = nullptr;    // per-node bounding boxes, [lo(dp) | hi(dp)]
+  float* nbox = nullptr;    // per-node child records of the radix tree (dpc_device.cuh)
   bool boxes_ready = false; // nbox matches the current binning
   uint32_t* leaf_parent = nullptr;
   uint32_t* visit = nullptr;
@@ -389,7 +389,7 @@ struct Workspace {
     const size_t o_skey = take(8 * N);
     const size_t o_hk = take(8 * (size_t)hc), o_hv = take(8 * (size_t)hc);
     const size_t o_nodes = take(sizeof(Node) * N);
-    const size_t o_nbox = take(4 * 16 * N);
+    const size_t o_nbox = take(4 * (size_t)kRecWordsMax * N);
     const size_t o_lp = take(4 * N), o_visit = take(4 * N);
     const size_t o_pieces = take(8 * N);
     const size_t o_qpos = take(4 * N), o_qs1 = take(4 * N), o_qs1d = take(8 * N);

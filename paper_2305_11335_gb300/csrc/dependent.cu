@@ -720,29 +720,31 @@ __global__ void k_near_to_far(const unsigned long long* __restrict__ skey, Class
 // 1e-5 down so that it stays below the float32 distance of every point inside
 // despite the rounding of this evaluation and of dist32.
 template <int DP>
-__device__ __forceinline__ float box_lb2(const float* __restrict__ nbox, uint32_t node,
-                                         const Pt<DP>& x) {
-  const float4* b = reinterpret_cast<const float4*>(nbox) + (size_t)node * (DP / 2);
-  float v[2 * DP];
-#pragma unroll
-  for (int k = 0; k < DP / 2; ++k) {
-    const float4 q = __ldg(b + k);
-    v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
-  }
+__device__ __forceinline__ float rec_lb2(const ChildRec<DP>& r, int s, const Pt<DP>& x) {
   float lb2 = 0.f;
 #pragma unroll
   for (int a = 0; a < DP; ++a) {
-    const float l = fmaxf(fmaxf(v[a] - x.x[a], x.x[a] - v[DP + a]), 0.f);
+    const float l = fmaxf(fmaxf(r.lo[s][a] - x.x[a], x.x[a] - r.hi[s][a]), 0.f);
     lb2 = fmaf(l, l, lb2);
   }
   return lb2 * (1.f - 1e-5f);
+}
+
+// A leaf child's point, from its record (its box is the point itself).
+template <int DP>
+__device__ __forceinline__ Pt<DP> rec_point(const ChildRec<DP>& r, int s) {
+  Pt<DP> p;
+#pragma unroll
+  for (int a = 0; a < DP; ++a) p.x[a] = r.lo[s][a];
+  return p;
 }
 
 enum { kWalkDone = 0, kWalkBudget = 1, kWalkBad = -1 };
 
 // One thread's depth-first search below internal node `start`, nearer child
 // first: every leaf with key > K not excluded by `prune` is passed to
-// visit(t, kt).  Stops with kWalkBudget after `budget` node expansions, and
+// visit(t, kt, point).  Expanding a node reads its child record alone (the
+// children's indices, keys and boxes).  Stops with kWalkBudget after `budget` node expansions, and
 // with kWalkBad on a malformed tree or stack overflow (neither happens for a
 // tree built by tree.cu: its depth is at most 64 + 32).
 template <int DP, typename Prune, typename Visit>
@@ -765,21 +767,19 @@ __device__ __noinline__ int tree_walk_from(const Node* __restrict__ nodes,
     if (ni + 1 >= n) return kWalkBad;
     if (expanded >= budget) return kWalkBudget;
     ++expanded;
-    const uint32_t ch[2] = {nodes[ni].left, nodes[ni].right};
+    const ChildRec<DP> r = load_rec<DP>(nbox, ni);
     uint32_t keep[2];
     float keepl[2];
     int nk = 0;
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-      const uint32_t c = ch[s];
+      const uint32_t c = r.child[s];
+      if (r.key[s] <= K) continue;  // nothing of higher key below
       if (c & kLeafBit) {
-        const uint32_t t = c & ~kLeafBit;
-        if (t >= n) return kWalkBad;
-        const unsigned long long kt = skey[t];
-        if (kt > K) visit(t, kt);
+        if ((c & ~kLeafBit) >= n) return kWalkBad;
+        visit(c & ~kLeafBit, r.key[s], rec_point<DP>(r, s));
       } else {
-        if (nodes[c].maxkey <= K) continue;
-        const float lbs = box_lb2<DP>(nbox, c, xq);
+        const float lbs = rec_lb2<DP>(r, s, xq);
         if (prune(lbs)) continue;
         keep[nk] = c;
         keepl[nk] = lbs;
@@ -859,8 +859,8 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
         const int r = tree_walk_from<DP>(
             nodes, nbox, n, skey, fq.K, fq.xq, fq.root, kFarBudget, expanded,
             [&](float lbs) { return (double)lbs > fmin(best.s1, s_init); },
-            [&](uint32_t t, unsigned long long kt) {
-              best.add(dist64<DP>(fq.xq, load_pt<DP>(spts, t)), key_id(kt), t);
+            [&](uint32_t t, unsigned long long kt, const Pt<DP>& x) {
+              best.add(dist64<DP>(fq.xq, x), key_id(kt), t);
             });
         bad |= r == kWalkBad;
         if (r == kWalkBudget) {
@@ -880,8 +880,8 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
         const int r = tree_walk_from<DP>(
             nodes, nbox, n, skey, fq.K, fq.xq, fq.root, kFarBudget, expanded,
             [&](float lbs) { return beyond(lbs, band_of(fminf(best.s1, s_init), bmul, badd)); },
-            [&](uint32_t t, unsigned long long kt) {
-              best.add(dist32<DP>(fq.xq, load_pt<DP>(spts, t)), key_id(kt), t);
+            [&](uint32_t t, unsigned long long kt, const Pt<DP>& x) {
+              best.add(dist32<DP>(fq.xq, x), key_id(kt), t);
             });
         bad |= r == kWalkBad;
         if (r == kWalkBudget) {
@@ -900,8 +900,7 @@ k_dep_far(const float* __restrict__ spts, const unsigned long long* __restrict__
             bad |= tree_walk_from<DP>(
                        nodes, nbox, n, skey, fq.K, fq.xq, fq.root, 0xffffffffu, more,
                        [&](float lbs) { return beyond(lbs, b); },
-                       [&](uint32_t t, unsigned long long kt) {
-                         const Pt<DP> x = load_pt<DP>(spts, t);
+                       [&](uint32_t t, unsigned long long kt, const Pt<DP>& x) {
                          if (dist32<DP>(fq.xq, x) <= b) ex.add(dist64<DP>(fq.xq, x), key_id(kt));
                        }) != kWalkDone;
             expanded += more;
@@ -995,21 +994,19 @@ k_dep_far_wide(const float* __restrict__ spts, const unsigned long long* __restr
               bad = true;
             } else {
               ++expanded;
-              const uint32_t ch[2] = {nodes[ni].left, nodes[ni].right};
+              const ChildRec<DP> r = load_rec<DP>(nbox, ni);
 #pragma unroll
               for (int s = 0; s < 2; ++s) {
-                const uint32_t c = ch[s];
+                const uint32_t c = r.child[s];
+                if (r.key[s] <= fq.K) continue;  // nothing of higher key below
                 if (c & kLeafBit) {
-                  const uint32_t t = c & ~kLeafBit;
-                  if (t >= n) {
+                  if ((c & ~kLeafBit) >= n) {
                     bad = true;
                     continue;
                   }
-                  const unsigned long long kt = skey[t];
-                  if (kt > fq.K) visit(t, kt);
+                  visit(c & ~kLeafBit, r.key[s], rec_point<DP>(r, s));
                 } else {
-                  if (nodes[c].maxkey <= fq.K) continue;
-                  const float l = box_lb2<DP>(nbox, c, fq.xq);
+                  const float l = rec_lb2<DP>(r, s, fq.xq);
                   if (prune(l)) continue;
                   keep[nk] = c;
                   keepl[nk] = l;
@@ -1059,8 +1056,8 @@ k_dep_far_wide(const float* __restrict__ spts, const unsigned long long* __restr
             wbest = fmin(m, s_init);
           },
           [&](float lbs) { return (double)lbs > fmin(best.s1, wbest); },
-          [&](uint32_t t, unsigned long long kt) {
-            best.add(dist64<DP>(fq.xq, load_pt<DP>(spts, t)), key_id(kt), t);
+          [&](uint32_t t, unsigned long long kt, const Pt<DP>& x) {
+            best.add(dist64<DP>(fq.xq, x), key_id(kt), t);
           });
       best.merge_warp();
       if (lane == 0) {
@@ -1085,8 +1082,8 @@ k_dep_far_wide(const float* __restrict__ spts, const unsigned long long* __restr
             wbest = fminf(m, s_init);
           },
           [&](float lbs) { return beyond(lbs, band_of(fminf(best.s1, wbest), bmul, badd)); },
-          [&](uint32_t t, unsigned long long kt) {
-            best.add(dist32<DP>(fq.xq, load_pt<DP>(spts, t)), key_id(kt), t);
+          [&](uint32_t t, unsigned long long kt, const Pt<DP>& x) {
+            best.add(dist32<DP>(fq.xq, x), key_id(kt), t);
           });
       best.merge_warp();
       if (best.t1 == 0xffffffffu) {
@@ -1101,8 +1098,7 @@ k_dep_far_wide(const float* __restrict__ spts, const unsigned long long* __restr
         if (best.s2 <= b) {  // near tie: re-rank the band in binary64
           ++rescans;
           search([] {}, [&](float lbs) { return beyond(lbs, b); },
-                 [&](uint32_t t, unsigned long long kt) {
-                   const Pt<DP> x = load_pt<DP>(spts, t);
+                 [&](uint32_t t, unsigned long long kt, const Pt<DP>& x) {
                    if (dist32<DP>(fq.xq, x) <= b) ex.add(dist64<DP>(fq.xq, x), key_id(kt));
                  });
           ex.merge_warp();

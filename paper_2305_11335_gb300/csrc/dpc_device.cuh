@@ -182,10 +182,55 @@ struct Counters {
 // One internal node of the binary radix tree over the sorted keys.
 struct __align__(8) Node {
   uint32_t left, right;   // child index; kLeafBit marks a leaf (sorted point)
-  unsigned long long maxkey;  // largest order key in the subtree (per cutoff)
+  unsigned long long maxkey;  // unused (the keys live in the parent's child record)
   uint32_t parent;        // parent internal node (root: itself)
   uint32_t pad;
 };
+
+// Child records of the radix tree (tree.cu): internal node i keeps in one
+// 16-byte-aligned record of rec_words<DP>() words what a search needs about
+// both its children -- their indices, their largest order keys and their
+// bounding boxes (a leaf's box is its point) -- so that expanding a node is
+// one load instead of a chain of dependent ones.
+//   words 0, 1                 left, right child (kLeafBit: a sorted point)
+//   words 4..5, 6..7           largest order key below the left, right child
+//   words 8 .. 8+2DP           box of the left child [lo(DP) | hi(DP)]
+//   words 8+2DP .. 8+4DP       box of the right child
+template <int DP>
+constexpr int rec_words() { return 8 + 4 * DP; }
+constexpr int kRecWordsMax = 8 + 4 * 8;
+
+template <int DP>
+struct ChildRec {
+  uint32_t child[2];
+  unsigned long long key[2];
+  float lo[2][DP], hi[2][DP];
+};
+
+template <int DP>
+__device__ __forceinline__ ChildRec<DP> load_rec(const float* __restrict__ nrec, uint32_t node) {
+  constexpr int W = rec_words<DP>();
+  const float4* r = reinterpret_cast<const float4*>(nrec) + (size_t)node * (W / 4);
+  float v[W];
+#pragma unroll
+  for (int k = 0; k < W / 4; ++k) {
+    const float4 q = __ldg(r + k);
+    v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
+  }
+  ChildRec<DP> c;
+  c.child[0] = __float_as_uint(v[0]);
+  c.child[1] = __float_as_uint(v[1]);
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    c.key[s] = ((unsigned long long)__float_as_uint(v[5 + 2 * s]) << 32) | __float_as_uint(v[4 + 2 * s]);
+#pragma unroll
+    for (int a = 0; a < DP; ++a) {
+      c.lo[s][a] = v[8 + 2 * DP * s + a];
+      c.hi[s][a] = v[8 + 2 * DP * s + DP + a];
+    }
+  }
+  return c;
+}
 
 // ---------------------------------------------------------------------------
 // Morton codes: axis a's bit b sits at position g*b + a.

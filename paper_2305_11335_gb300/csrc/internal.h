@@ -95,11 +95,12 @@ void launch_sort(unsigned long long* codes_a, unsigned long long* codes_b, uint3
 // are exactly instance i (kNoNode for an instance of one point).
 void launch_tree_build(const unsigned long long* scode, const ClassView& cv, Node* nodes,
                        uint32_t* leaf_parent, uint32_t* root, cudaStream_t st);
-// Largest order key of every subtree; with `boxes`, also every node's
-// bounding box over all dp coordinates into nbox ([lo(dp) | hi(dp)] floats per
-// node; the box depends only on the points, so once per binning suffices).
+// Every internal node's child record (dpc_device.cuh: the children's
+// indices, their largest order keys and, with `boxes`, their bounding boxes
+// over all dp coordinates) into nrec, kRecWordsMax words per node at most;
+// the boxes depend only on the points, so once per binning suffices.
 void launch_tree_maxkey(const unsigned long long* skey, const float* spts, int dp, uint32_t n,
-                        Node* nodes, const uint32_t* leaf_parent, uint32_t* visit, float* nbox,
+                        Node* nodes, const uint32_t* leaf_parent, uint32_t* visit, float* nrec,
                         bool boxes, cudaStream_t st);
 
 // Work layouts of the density and near-dependent kernels:

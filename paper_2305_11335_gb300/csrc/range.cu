@@ -40,26 +40,6 @@ struct PrQuery {
 };
 
 template <int DP>
-__device__ __forceinline__ bool box_meets(const float* __restrict__ nbox, uint32_t node,
-                                          const PrQuery<DP>& Q) {
-  const float4* b = reinterpret_cast<const float4*>(nbox) + (size_t)node * (DP / 2);
-  float v[2 * DP];
-#pragma unroll
-  for (int k = 0; k < DP / 2; ++k) {
-    const float4 q = __ldg(b + k);
-    v[4 * k] = q.x;
-    v[4 * k + 1] = q.y;
-    v[4 * k + 2] = q.z;
-    v[4 * k + 3] = q.w;
-  }
-  bool ok = true;
-#pragma unroll
-  for (int a = 0; a < DP; ++a)
-    if (a < Q.d) ok &= (double)v[DP + a] >= Q.lo[a] && (double)v[a] <= Q.hi[a];
-  return ok;
-}
-
-template <int DP>
 __device__ __forceinline__ bool point_in(const float* __restrict__ spts, uint32_t t,
                                          const PrQuery<DP>& Q) {
   const Pt<DP> p = load_pt<DP>(spts, t);
@@ -72,11 +52,16 @@ __device__ __forceinline__ bool point_in(const float* __restrict__ spts, uint32_
 
 __device__ __forceinline__ int32_t key_rho(unsigned long long k) { return (int32_t)(k >> 32); }
 
-// Internal node test: some key below is above the threshold, and the box meets.
+// Child test from its parent's record: some key below is above the
+// threshold, and the box meets.
 template <int DP>
-__device__ __forceinline__ bool node_ok(const Node* __restrict__ nodes, const float* __restrict__ nbox,
-                                        uint32_t c, const PrQuery<DP>& Q) {
-  return key_rho(nodes[c].maxkey) > Q.rq && box_meets<DP>(nbox, c, Q);
+__device__ __forceinline__ bool child_ok(const ChildRec<DP>& r, int s, const PrQuery<DP>& Q) {
+  if (key_rho(r.key[s]) <= Q.rq) return false;
+  bool ok = true;
+#pragma unroll
+  for (int a = 0; a < DP; ++a)
+    if (a < Q.d) ok &= (double)r.hi[s][a] >= Q.lo[a] && (double)r.lo[s][a] <= Q.hi[a];
+  return ok;
 }
 
 // Leaf test; a match goes to `hit(t)`.
@@ -106,14 +91,15 @@ __device__ bool walk_alone(const Node* __restrict__ nodes, const float* __restri
       return false;
     }
     if (down) {
-      const uint32_t l = nodes[cur].left, rr = nodes[cur].right;
+      const ChildRec<DP> rc = load_rec<DP>(nbox, cur);
+      const uint32_t l = rc.child[0], rr = rc.child[1];
       if (l & kLeafBit) leaf<DP>(spts, skey, l & ~kLeafBit, n, Q, bad, hit);
       if (rr & kLeafBit) leaf<DP>(spts, skey, rr & ~kLeafBit, n, Q, bad, hit);
-      if (!(l & kLeafBit) && node_ok<DP>(nodes, nbox, l, Q)) {
+      if (!(l & kLeafBit) && child_ok<DP>(rc, 0, Q)) {
         cur = l;
         continue;
       }
-      if (!(rr & kLeafBit) && node_ok<DP>(nodes, nbox, rr, Q)) {
+      if (!(rr & kLeafBit) && child_ok<DP>(rc, 1, Q)) {
         cur = rr;
         continue;
       }
@@ -126,8 +112,9 @@ __device__ bool walk_alone(const Node* __restrict__ nodes, const float* __restri
       bad = true;
       return false;
     }
-    const uint32_t pr = nodes[p].right;
-    if (nodes[p].left == cur && !(pr & kLeafBit) && node_ok<DP>(nodes, nbox, pr, Q)) {
+    const ChildRec<DP> rp = load_rec<DP>(nbox, p);
+    const uint32_t pr = rp.child[1];
+    if (rp.child[0] == cur && !(pr & kLeafBit) && child_ok<DP>(rp, 1, Q)) {
       cur = pr;
       down = true;
       continue;
@@ -197,7 +184,7 @@ k_prange(const float* __restrict__ spts, const uint32_t* __restrict__ sid,
       if (root + 1 >= n) {
         bad = true;
       } else {
-        go = node_ok<DP>(nodes, nbox, root, Q);
+        go = true;  // the root's own key and box live in its parent's record: test its children
       }
       if (lane == 0 && go) stk[0] = root;
       int sp = go ? 1 : 0;
@@ -212,15 +199,15 @@ k_prange(const float* __restrict__ spts, const uint32_t* __restrict__ sid,
           if (ni + 1 >= n) {
             bad = true;
           } else {
-            const uint32_t ch[2] = {nodes[ni].left, nodes[ni].right};
+            const ChildRec<DP> rc = load_rec<DP>(nbox, ni);
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
-              const uint32_t c = ch[s];
+              const uint32_t c = rc.child[s];
               if (c & kLeafBit) {
                 leaf<DP>(spts, skey, c & ~kLeafBit, n, Q, bad, hit);
               } else if (c + 1 >= n) {
                 bad = true;
-              } else if (node_ok<DP>(nodes, nbox, c, Q)) {
+              } else if (child_ok<DP>(rc, s, Q)) {
                 keep[nk++] = c;
               }
             }

@@ -77,16 +77,39 @@ __global__ void k_root_parent(Node* nodes) { nodes[0].parent = 0u; }
 
 // Bottom-up pass: the second child to arrive at a node computes its largest
 // key and, on the first pass after a binning, its bounding box over all DP
-// coordinates (layout [lo(DP) | hi(DP)] per node; a leaf's box is its point).
-template <int DP>
-__device__ __forceinline__ void child_box(uint32_t c, const float* __restrict__ spts,
-                                          const float* nbox, float* lo, float* hi) {
-  if (c & kLeafBit) {
-    const Pt<DP> p = load_pt<DP>(spts, c & ~kLeafBit);
+// coordinates, and writes both into its parent's child record (dpc_device.cuh;
+// a leaf's key is its point's and its box the point itself).
+
+// Writes the summary of child `side` of node `node` into its record.
+template <int DP, bool BOX>
+__device__ __forceinline__ void put_child(float* nrec, uint32_t node, int side, unsigned long long key,
+                                          const float* lo, const float* hi) {
+  constexpr int W = rec_words<DP>();
+  float* r = nrec + (size_t)node * W;
+  __stcg(reinterpret_cast<unsigned long long*>(r + 4 + 2 * side), key);
+  if constexpr (BOX) {
+    float4* b = reinterpret_cast<float4*>(r + 8 + 2 * DP * side);
 #pragma unroll
-    for (int a = 0; a < DP; ++a) lo[a] = hi[a] = p.x[a];
-  } else {
-    const float4* b = reinterpret_cast<const float4*>(nbox) + (size_t)c * (DP / 2);
+    for (int k = 0; k < DP / 2; ++k) {
+      const float v0 = (4 * k < DP) ? lo[4 * k] : hi[4 * k - DP];
+      const float v1 = (4 * k + 1 < DP) ? lo[4 * k + 1] : hi[4 * k + 1 - DP];
+      const float v2 = (4 * k + 2 < DP) ? lo[4 * k + 2] : hi[4 * k + 2 - DP];
+      const float v3 = (4 * k + 3 < DP) ? lo[4 * k + 3] : hi[4 * k + 3 - DP];
+      __stcg(b + k, make_float4(v0, v1, v2, v3));
+    }
+  }
+}
+
+// Reads the summary of child `side` of node `node` back from its record
+// (written by another thread's walk before its release).
+template <int DP, bool BOX>
+__device__ __forceinline__ void get_child(const float* nrec, uint32_t node, int side,
+                                          unsigned long long& key, float* lo, float* hi) {
+  constexpr int W = rec_words<DP>();
+  const float* r = nrec + (size_t)node * W;
+  key = __ldcg(reinterpret_cast<const unsigned long long*>(r + 4 + 2 * side));
+  if constexpr (BOX) {
+    const float4* b = reinterpret_cast<const float4*>(r + 8 + 2 * DP * side);
     float v[2 * DP];
 #pragma unroll
     for (int k = 0; k < DP / 2; ++k) {
@@ -98,6 +121,20 @@ __device__ __forceinline__ void child_box(uint32_t c, const float* __restrict__ 
       lo[a] = v[a];
       hi[a] = v[DP + a];
     }
+  }
+}
+
+// A leaf's summary: its point's key, and (BOX) the point as its box.
+template <int DP, bool BOX>
+__device__ __forceinline__ void leaf_summary(uint32_t c, const unsigned long long* __restrict__ skey,
+                                             const float* __restrict__ spts, unsigned long long& key,
+                                             float* lo, float* hi) {
+  const uint32_t t = c & ~kLeafBit;
+  key = skey[t];
+  if constexpr (BOX) {
+    const Pt<DP> p = load_pt<DP>(spts, t);
+#pragma unroll
+    for (int a = 0; a < DP; ++a) lo[a] = hi[a] = p.x[a];
   }
 }
 
@@ -115,11 +152,13 @@ __device__ __forceinline__ uint32_t arrive(uint32_t* counter) {
 // walks up, carrying the node's results in registers.  A parent whose other
 // child is a leaf is computed at once; only at a parent with two internal
 // children do the two walks meet, and the second to arrive (an acq_rel atomic
-// counter) continues with the first's published results.
+// counter) continues with the first's published results.  Every node's
+// record gets its children's indices, keys and (BOX) boxes on the way.
 template <int DP, bool BOX>
 __global__ void k_tree_up(const unsigned long long* __restrict__ skey,
                           const float* __restrict__ spts, uint32_t n, Node* nodes,
-                          uint32_t* visit, float* nbox) {
+                          uint32_t* visit, float* nrec) {
+  constexpr int W = rec_words<DP>();
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t + 1 < n; t += gridDim.x * blockDim.x) {
     uint32_t node = t;
     const uint32_t l0 = nodes[node].left, r0 = nodes[node].right;
@@ -128,12 +167,15 @@ __global__ void k_tree_up(const unsigned long long* __restrict__ skey,
     unsigned long long key;
     float lo[DP], hi[DP];
     {
-      const unsigned long long kl = skey[l0 & ~kLeafBit], kr = skey[r0 & ~kLeafBit];
-      key = kl > kr ? kl : kr;
+      unsigned long long kr;
+      float lo2[DP], hi2[DP];
+      leaf_summary<DP, BOX>(l0, skey, spts, key, lo, hi);
+      leaf_summary<DP, BOX>(r0, skey, spts, kr, lo2, hi2);
+      __stcg(reinterpret_cast<uint2*>(nrec + (size_t)node * W), make_uint2(l0, r0));
+      put_child<DP, BOX>(nrec, node, 0, key, lo, hi);
+      put_child<DP, BOX>(nrec, node, 1, kr, lo2, hi2);
+      key = key > kr ? key : kr;
       if constexpr (BOX) {
-        float lo2[DP], hi2[DP];
-        child_box<DP>(l0, spts, nbox, lo, hi);
-        child_box<DP>(r0, spts, nbox, lo2, hi2);
 #pragma unroll
         for (int a = 0; a < DP; ++a) {
           lo[a] = fminf(lo[a], lo2[a]);
@@ -142,30 +184,26 @@ __global__ void k_tree_up(const unsigned long long* __restrict__ skey,
       }
     }
     for (uint32_t depth = 0; depth < 2u * n + 64u; ++depth) {
-      __stcg(&nodes[node].maxkey, key);
-      if constexpr (BOX) {
-        float4* b = reinterpret_cast<float4*>(nbox) + (size_t)node * (DP / 2);
-#pragma unroll
-        for (int k = 0; k < DP / 2; ++k) {
-          const float v0 = (4 * k < DP) ? lo[4 * k] : hi[4 * k - DP];
-          const float v1 = (4 * k + 1 < DP) ? lo[4 * k + 1] : hi[4 * k + 1 - DP];
-          const float v2 = (4 * k + 2 < DP) ? lo[4 * k + 2] : hi[4 * k + 2 - DP];
-          const float v3 = (4 * k + 3 < DP) ? lo[4 * k + 3] : hi[4 * k + 3 - DP];
-          __stcg(b + k, make_float4(v0, v1, v2, v3));
-        }
-      }
       if (node == 0u) break;
       const uint32_t par = nodes[node].parent;
       const uint32_t pl = nodes[par].left, pr = nodes[par].right;
-      const uint32_t sib = (pl == node) ? pr : pl;
+      const int side = pl == node ? 0 : 1;
+      const uint32_t sib = side == 0 ? pr : pl;
+      // this node's summary into the parent's record, before the release
+      put_child<DP, BOX>(nrec, par, side, key, lo, hi);
       if (!(sib & kLeafBit) && arrive(&visit[par]) == 0u) break;  // the sibling's walk continues
       // the parent from this node (registers) and its sibling
-      const unsigned long long ks =
-          (sib & kLeafBit) ? skey[sib & ~kLeafBit] : __ldcg(&nodes[sib].maxkey);
+      __stcg(reinterpret_cast<uint2*>(nrec + (size_t)par * W), make_uint2(pl, pr));
+      unsigned long long ks;
+      float lo2[DP], hi2[DP];
+      if (sib & kLeafBit) {
+        leaf_summary<DP, BOX>(sib, skey, spts, ks, lo2, hi2);
+        put_child<DP, BOX>(nrec, par, 1 - side, ks, lo2, hi2);
+      } else {
+        get_child<DP, BOX>(nrec, par, 1 - side, ks, lo2, hi2);
+      }
       key = key > ks ? key : ks;
       if constexpr (BOX) {
-        float lo2[DP], hi2[DP];
-        child_box<DP>(sib, spts, nbox, lo2, hi2);
 #pragma unroll
         for (int a = 0; a < DP; ++a) {
           lo[a] = fminf(lo[a], lo2[a]);
@@ -218,13 +256,13 @@ void tree_up_dp(const unsigned long long* skey, const float* spts, uint32_t n, N
 }
 
 void launch_tree_maxkey(const unsigned long long* skey, const float* spts, int dp, uint32_t n,
-                        Node* nodes, const uint32_t* leaf_parent, uint32_t* visit, float* nbox,
+                        Node* nodes, const uint32_t* leaf_parent, uint32_t* visit, float* nrec,
                         bool boxes, cudaStream_t st) {
   if (n < 2) return;
   cudaMemsetAsync(visit, 0, sizeof(uint32_t) * (n - 1), st);
-  if (dp == 2) tree_up_dp<2>(skey, spts, n, nodes, leaf_parent, visit, nbox, boxes, st);
-  else if (dp == 4) tree_up_dp<4>(skey, spts, n, nodes, leaf_parent, visit, nbox, boxes, st);
-  else tree_up_dp<8>(skey, spts, n, nodes, leaf_parent, visit, nbox, boxes, st);
+  if (dp == 2) tree_up_dp<2>(skey, spts, n, nodes, leaf_parent, visit, nrec, boxes, st);
+  else if (dp == 4) tree_up_dp<4>(skey, spts, n, nodes, leaf_parent, visit, nrec, boxes, st);
+  else tree_up_dp<8>(skey, spts, n, nodes, leaf_parent, visit, nrec, boxes, st);
   count_launches(1);
 }
 
