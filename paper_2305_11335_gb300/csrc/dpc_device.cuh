@@ -182,7 +182,8 @@ struct Counters {
 // One internal node of the binary radix tree over the sorted keys.
 struct __align__(8) Node {
   uint32_t left, right;   // child index; kLeafBit marks a leaf (sorted point)
-  unsigned long long maxkey;  // unused (the keys live in the parent's child record)
+  uint32_t sib;           // the parent's other child (kLeafBit: a sorted point)
+  uint32_t side;          // 0: this node is its parent's left child, 1: right
   uint32_t parent;        // parent internal node (root: itself)
   uint32_t pad;
 };

@@ -59,11 +59,20 @@ __global__ void k_tree_build(const unsigned long long* __restrict__ code, ClassV
     const uint32_t right = (hi == gamma + 1) ? ((uint32_t)(gamma + 1) | kLeafBit) : (uint32_t)(gamma + 1);
     nodes[i].left = left;
     nodes[i].right = right;
-    nodes[i].maxkey = 0ull;
-    if (left & kLeafBit) leaf_parent[left & ~kLeafBit] = (uint32_t)i;
-    else nodes[left].parent = (uint32_t)i;
-    if (right & kLeafBit) leaf_parent[right & ~kLeafBit] = (uint32_t)i;
-    else nodes[right].parent = (uint32_t)i;
+    if (left & kLeafBit) {
+      leaf_parent[left & ~kLeafBit] = (uint32_t)i;
+    } else {
+      nodes[left].parent = (uint32_t)i;
+      nodes[left].sib = right;
+      nodes[left].side = 0u;
+    }
+    if (right & kLeafBit) {
+      leaf_parent[right & ~kLeafBit] = (uint32_t)i;
+    } else {
+      nodes[right].parent = (uint32_t)i;
+      nodes[right].sib = left;
+      nodes[right].side = 1u;
+    }
     // the node whose leaves are exactly one instance is that instance's root
     const uint32_t inst = key_inst(code[lo], S, ib);
     if (inst < cv.ninst) {
@@ -185,10 +194,12 @@ __global__ void k_tree_up(const unsigned long long* __restrict__ skey,
     }
     for (uint32_t depth = 0; depth < 2u * n + 64u; ++depth) {
       if (node == 0u) break;
+      // parent, side and sibling in one record (k_tree_build)
+      const uint2 ps = *reinterpret_cast<const uint2*>(&nodes[node].sib);
       const uint32_t par = nodes[node].parent;
-      const uint32_t pl = nodes[par].left, pr = nodes[par].right;
-      const int side = pl == node ? 0 : 1;
-      const uint32_t sib = side == 0 ? pr : pl;
+      const int side = (int)(ps.y & 1u);
+      const uint32_t sib = ps.x;
+      const uint32_t pl = side == 0 ? node : sib, pr = side == 0 ? sib : node;
       // this node's summary into the parent's record, before the release
       put_child<DP, BOX>(nrec, par, side, key, lo, hi);
       if (!(sib & kLeafBit) && arrive(&visit[par]) == 0u) break;  // the sibling's walk continues
