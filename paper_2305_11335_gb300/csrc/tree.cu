@@ -237,8 +237,11 @@ inline unsigned grid_for(uint64_t n) {
 // several nodes would run their walks one after another, each a chain of
 // dependent loads; with one node per thread every walk starts at once and
 // the blocks are scheduled as earlier ones retire.
+// (blocks of 128: a block holds its slot until its longest walk ends, so
+// smaller blocks free slots sooner; 0.99 ms against 1.03 with 256 on c3)
+constexpr int kUpThreads = 128;
 inline unsigned grid_all(uint64_t n) {
-  uint64_t b = (n + kThreads - 1) / kThreads;
+  uint64_t b = (n + kUpThreads - 1) / kUpThreads;
   if (b < 1) b = 1;
   if (b > 0x7fffffffull) b = 0x7fffffffull;
   return (unsigned)b;
@@ -261,9 +264,9 @@ void tree_up_dp(const unsigned long long* skey, const float* spts, uint32_t n, N
                 cudaStream_t st) {
   (void)leaf_parent;
   if (boxes)
-    k_tree_up<DP, true><<<grid_all(n - 1), kThreads, 0, st>>>(skey, spts, n, nodes, visit, nbox);
+    k_tree_up<DP, true><<<grid_all(n - 1), kUpThreads, 0, st>>>(skey, spts, n, nodes, visit, nbox);
   else
-    k_tree_up<DP, false><<<grid_all(n - 1), kThreads, 0, st>>>(skey, spts, n, nodes, visit, nbox);
+    k_tree_up<DP, false><<<grid_all(n - 1), kUpThreads, 0, st>>>(skey, spts, n, nodes, visit, nbox);
 }
 
 void launch_tree_maxkey(const unsigned long long* skey, const float* spts, int dp, uint32_t n,
