@@ -185,7 +185,7 @@ struct __align__(8) Node {
   uint32_t sib;           // the parent's other child (kLeafBit: a sorted point)
   uint32_t side;          // 0: this node is its parent's left child, 1: right
   uint32_t parent;        // parent internal node (root: itself)
-  uint32_t pad;
+  uint32_t pend;          // the parent's number is one end of its leaf range; this is the other
 };
 
 // Child records of the radix tree (tree.cu): internal node i keeps in one

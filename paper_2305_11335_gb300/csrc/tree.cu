@@ -63,6 +63,7 @@ __global__ void k_tree_build(const unsigned long long* __restrict__ code, ClassV
       leaf_parent[left & ~kLeafBit] = (uint32_t)i;
     } else {
       nodes[left].parent = (uint32_t)i;
+      nodes[left].pend = (uint32_t)j;
       nodes[left].sib = right;
       nodes[left].side = 0u;
     }
@@ -70,6 +71,7 @@ __global__ void k_tree_build(const unsigned long long* __restrict__ code, ClassV
       leaf_parent[right & ~kLeafBit] = (uint32_t)i;
     } else {
       nodes[right].parent = (uint32_t)i;
+      nodes[right].pend = (uint32_t)j;
       nodes[right].sib = left;
       nodes[right].side = 1u;
     }
@@ -156,73 +158,133 @@ __device__ __forceinline__ uint32_t arrive(uint32_t* counter) {
   return old;
 }
 
+// One thread per node for the bottom-up walks: a thread that strode over
+// several nodes would run their walks one after another, each a chain of
+// dependent loads; with one node per thread every walk starts at once and
+// the blocks are scheduled as earlier ones retire.
+// (blocks of 128: a block holds its slot until its longest walk ends, so
+// smaller blocks free slots sooner; 0.99 ms against 1.03 with 256 on c3)
+constexpr int kUpThreads = 128;
+
+// Arrival counter in shared memory, acquire-release at block scope.
+__device__ __forceinline__ uint32_t arrive_cta(uint32_t* counter) {
+  uint32_t old;
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(counter);
+  asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], 1;" : "=r"(old) : "r"(a) : "memory");
+  return old;
+}
+
 // One thread per internal node whose two children are both leaves (the
 // bottom of the tree: about a third of the nodes).  It computes that node and
 // walks up, carrying the node's results in registers.  A parent whose other
 // child is a leaf is computed at once; only at a parent with two internal
-// children do the two walks meet, and the second to arrive (an acq_rel atomic
-// counter) continues with the first's published results.  Every node's
-// record gets its children's indices, keys and (BOX) boxes on the way.
+// children do the two walks meet, and the second to arrive continues with
+// the first's results.  The internal nodes below a node with leaf range
+// [lo, hi] are numbered within [lo, hi], so when that range lies inside the
+// block's own 128 node numbers both walks run in this block: they meet
+// through a shared-memory counter and summary slots (block-scope ordering),
+// and only nodes whose range crosses a block boundary (a few percent) take
+// the global acq_rel counter.  Every node's record gets its children's
+// indices, keys and (BOX) boxes on the way.
 template <int DP, bool BOX>
-__global__ void k_tree_up(const unsigned long long* __restrict__ skey,
-                          const float* __restrict__ spts, uint32_t n, Node* nodes,
-                          uint32_t* visit, float* nrec) {
+__global__ void __launch_bounds__(kUpThreads) k_tree_up(const unsigned long long* __restrict__ skey,
+                                                        const float* __restrict__ spts, uint32_t n,
+                                                        const Node* __restrict__ nodes,
+                                                        uint32_t* visit, float* nrec) {
   constexpr int W = rec_words<DP>();
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t + 1 < n; t += gridDim.x * blockDim.x) {
-    uint32_t node = t;
-    const uint32_t l0 = nodes[node].left, r0 = nodes[node].right;
-    if (!((l0 & kLeafBit) && (r0 & kLeafBit))) continue;
-    // this node from its two leaves
-    unsigned long long key;
-    float lo[DP], hi[DP];
-    {
-      unsigned long long kr;
-      float lo2[DP], hi2[DP];
-      leaf_summary<DP, BOX>(l0, skey, spts, key, lo, hi);
-      leaf_summary<DP, BOX>(r0, skey, spts, kr, lo2, hi2);
-      __stcg(reinterpret_cast<uint2*>(nrec + (size_t)node * W), make_uint2(l0, r0));
-      put_child<DP, BOX>(nrec, node, 0, key, lo, hi);
-      put_child<DP, BOX>(nrec, node, 1, kr, lo2, hi2);
-      key = key > kr ? key : kr;
-      if constexpr (BOX) {
+  constexpr int SB = BOX ? 2 * DP : 1;
+  __shared__ uint32_t s_cnt[kUpThreads];
+  __shared__ unsigned long long s_key[2 * kUpThreads];  // [node - base][side]
+  __shared__ float s_box[2 * kUpThreads * SB];          // [node - base][side][lo | hi]
+  const uint32_t base = blockIdx.x * kUpThreads;
+  s_cnt[threadIdx.x] = 0u;
+  __syncthreads();
+  // the launch has one thread per internal node (grid_all)
+  const uint32_t t = base + threadIdx.x;
+  if (t + 1 >= n) return;
+  uint32_t node = t;
+  const uint32_t l0 = nodes[node].left, r0 = nodes[node].right;
+  if (!((l0 & kLeafBit) && (r0 & kLeafBit))) return;
+  // this node from its two leaves
+  unsigned long long key;
+  float lo[DP], hi[DP];
+  {
+    unsigned long long kr;
+    float lo2[DP], hi2[DP];
+    leaf_summary<DP, BOX>(l0, skey, spts, key, lo, hi);
+    leaf_summary<DP, BOX>(r0, skey, spts, kr, lo2, hi2);
+    __stcg(reinterpret_cast<uint2*>(nrec + (size_t)node * W), make_uint2(l0, r0));
+    put_child<DP, BOX>(nrec, node, 0, key, lo, hi);
+    put_child<DP, BOX>(nrec, node, 1, kr, lo2, hi2);
+    key = key > kr ? key : kr;
+    if constexpr (BOX) {
 #pragma unroll
-        for (int a = 0; a < DP; ++a) {
-          lo[a] = fminf(lo[a], lo2[a]);
-          hi[a] = fmaxf(hi[a], hi2[a]);
-        }
+      for (int a = 0; a < DP; ++a) {
+        lo[a] = fminf(lo[a], lo2[a]);
+        hi[a] = fmaxf(hi[a], hi2[a]);
       }
     }
-    for (uint32_t depth = 0; depth < 2u * n + 64u; ++depth) {
-      if (node == 0u) break;
-      // parent, side and sibling in one record (k_tree_build)
-      const uint2 ps = *reinterpret_cast<const uint2*>(&nodes[node].sib);
-      const uint32_t par = nodes[node].parent;
-      const int side = (int)(ps.y & 1u);
-      const uint32_t sib = ps.x;
-      const uint32_t pl = side == 0 ? node : sib, pr = side == 0 ? sib : node;
-      // this node's summary into the parent's record, before the release
+  }
+  for (uint32_t depth = 0; depth < 2u * n + 64u; ++depth) {
+    if (node == 0u) break;
+    // sibling, side, parent and the far end of the parent's leaf range
+    // (k_tree_build)
+    const uint2 ps = *reinterpret_cast<const uint2*>(&nodes[node].sib);
+    const uint2 pp = *reinterpret_cast<const uint2*>(&nodes[node].parent);
+    const uint32_t par = pp.x;
+    const int side = (int)(ps.y & 1u);
+    const uint32_t sib = ps.x;
+    const uint32_t pl = side == 0 ? node : sib, pr = side == 0 ? sib : node;
+    unsigned long long ks;
+    float lo2[DP], hi2[DP];
+    if (sib & kLeafBit) {
       put_child<DP, BOX>(nrec, par, side, key, lo, hi);
-      if (!(sib & kLeafBit) && arrive(&visit[par]) == 0u) break;  // the sibling's walk continues
-      // the parent from this node (registers) and its sibling
-      __stcg(reinterpret_cast<uint2*>(nrec + (size_t)par * W), make_uint2(pl, pr));
-      unsigned long long ks;
-      float lo2[DP], hi2[DP];
-      if (sib & kLeafBit) {
-        leaf_summary<DP, BOX>(sib, skey, spts, ks, lo2, hi2);
-        put_child<DP, BOX>(nrec, par, 1 - side, ks, lo2, hi2);
+      leaf_summary<DP, BOX>(sib, skey, spts, ks, lo2, hi2);
+      put_child<DP, BOX>(nrec, par, 1 - side, ks, lo2, hi2);
+    } else {
+      const uint32_t plo = par < pp.y ? par : pp.y, phi = par < pp.y ? pp.y : par;
+      if (plo >= base && phi < base + kUpThreads) {
+        // both walks in this block: the summary into this side's slot, then
+        // the block-scope arrival; the record in global memory is written
+        // after it (read only by later launches)
+        const uint32_t k = par - base;
+        s_key[2 * k + side] = key;
+        if constexpr (BOX) {
+#pragma unroll
+          for (int a = 0; a < DP; ++a) {
+            s_box[(2 * k + side) * SB + a] = lo[a];
+            s_box[(2 * k + side) * SB + DP + a] = hi[a];
+          }
+        }
+        const uint32_t old = arrive_cta(&s_cnt[k]);
+        put_child<DP, BOX>(nrec, par, side, key, lo, hi);
+        if (old == 0u) break;  // the sibling's walk continues
+        ks = s_key[2 * k + 1 - side];
+        if constexpr (BOX) {
+#pragma unroll
+          for (int a = 0; a < DP; ++a) {
+            lo2[a] = s_box[(2 * k + 1 - side) * SB + a];
+            hi2[a] = s_box[(2 * k + 1 - side) * SB + DP + a];
+          }
+        }
       } else {
+        // this node's summary into the parent's record, before the release
+        put_child<DP, BOX>(nrec, par, side, key, lo, hi);
+        if (arrive(&visit[par]) == 0u) break;  // the sibling's walk continues
         get_child<DP, BOX>(nrec, par, 1 - side, ks, lo2, hi2);
       }
-      key = key > ks ? key : ks;
-      if constexpr (BOX) {
-#pragma unroll
-        for (int a = 0; a < DP; ++a) {
-          lo[a] = fminf(lo[a], lo2[a]);
-          hi[a] = fmaxf(hi[a], hi2[a]);
-        }
-      }
-      node = par;
     }
+    // the parent from this node (registers) and its sibling
+    __stcg(reinterpret_cast<uint2*>(nrec + (size_t)par * W), make_uint2(pl, pr));
+    key = key > ks ? key : ks;
+    if constexpr (BOX) {
+#pragma unroll
+      for (int a = 0; a < DP; ++a) {
+        lo[a] = fminf(lo[a], lo2[a]);
+        hi[a] = fmaxf(hi[a], hi2[a]);
+      }
+    }
+    node = par;
   }
 }
 
@@ -233,13 +295,6 @@ inline unsigned grid_for(uint64_t n) {
   return (unsigned)b;
 }
 
-// One thread per node for the bottom-up walks: a thread that strode over
-// several nodes would run their walks one after another, each a chain of
-// dependent loads; with one node per thread every walk starts at once and
-// the blocks are scheduled as earlier ones retire.
-// (blocks of 128: a block holds its slot until its longest walk ends, so
-// smaller blocks free slots sooner; 0.99 ms against 1.03 with 256 on c3)
-constexpr int kUpThreads = 128;
 inline unsigned grid_all(uint64_t n) {
   uint64_t b = (n + kUpThreads - 1) / kUpThreads;
   if (b < 1) b = 1;
