@@ -206,8 +206,9 @@ int dpc_dependent(const void* pts, int dtype, const dpc_batch* b, int32_t dcut_i
  *   rho, lambda, delta  device, [N], as produced by the two calls above
  *   label   device, int32 [N]: instance-local id of the cluster center, or -1
  * lambda must form a forest within each instance (as dpc_dependent writes
- * it); pointers that still move after the fixed number of pointer-jumping
- * rounds (enough for any forest) reveal a cycle, reported as DPC_ERR_DATA. */
+ * it); a pointer that has not reached a root (a center or a noise point)
+ * after the fixed number of pointer-jumping rounds (enough for any forest)
+ * reveals a cycle, reported as DPC_ERR_DATA. */
 int dpc_cluster(const dpc_batch* b, int32_t dcut_index, const dpc_params* params,
                 const int32_t* rho, const int32_t* lambda, const double* delta, int32_t* label,
                 uint32_t flags, void* stream);

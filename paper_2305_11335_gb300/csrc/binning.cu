@@ -45,11 +45,75 @@ __global__ void k_class_init(ClassView cv, int g, int ib, int bcap, int* status)
 }
 
 // Bounding box of the gridded axes of every instance, and the coordinate
-// range check.  Each warp takes a contiguous range of chunks and keeps a
-// running box while the instance stays the same, so most instances see one
-// atomic per warp and axis.
+// range check.  In a batch each warp takes a contiguous range of chunks and
+// keeps a running box while the instance stays the same, so most instances
+// see one atomic per warp and axis.
+template <typename T>
+__device__ __forceinline__ float bbox_value(T v, int& bad) {
+  if constexpr (std::is_integral<T>::value) {
+    bad |= (v > (1 << 24)) | (v < -(1 << 24));
+    return (float)v;
+  } else {
+    const float x = (float)v;
+    bad |= !(fabsf(x) <= 1.152921504606846976e18f);  // 2^60; false for NaN
+    return x;
+  }
+}
+
 template <typename T>
 __global__ void k_bbox(const T* __restrict__ pts, ClassView cv, int g) {
+  if (!cv.chunk_inst) {
+    // One instance: the coordinates are one array of N*d values.  A stride
+    // that is a multiple of d gives every thread one axis, the loads are
+    // coalesced and four are in flight per thread; the block's box is
+    // reduced in shared memory, one atomic per block and gridded axis.
+    __shared__ uint32_t s_lo[kMaxGrid], s_hi[kMaxGrid];
+    if (threadIdx.x < kMaxGrid) {
+      s_lo[threadIdx.x] = 0xffffffffu;
+      s_hi[threadIdx.x] = 0u;
+    }
+    __syncthreads();
+    const InstDev I = cv.one;
+    const uint64_t d = (uint64_t)I.d;
+    const uint64_t nv = (uint64_t)cv.N * d;
+    const uint64_t all = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t stride = all - all % d;
+    const uint64_t t0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float mn = FLT_MAX, mx = -FLT_MAX;
+    int bad = 0;
+    if (t0 < stride) {
+      const T* __restrict__ src = pts + I.coord;
+      uint64_t v = t0;
+      for (; v + 3 * stride < nv; v += 4 * stride) {
+        T q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) q[u] = src[v + u * stride];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float x = bbox_value<T>(q[u], bad);
+          mn = fminf(mn, x);
+          mx = fmaxf(mx, x);
+        }
+      }
+      for (; v < nv; v += stride) {
+        const float x = bbox_value<T>(src[v], bad);
+        mn = fminf(mn, x);
+        mx = fmaxf(mx, x);
+      }
+      const int a = (int)(t0 % d);
+      if (a < g && mn <= mx) {
+        atomicMin(&s_lo[a], float_ord(mn));
+        atomicMax(&s_hi[a], float_ord(mx));
+      }
+    }
+    const int any_bad = __syncthreads_or(bad);
+    if (threadIdx.x < (unsigned)g && s_lo[threadIdx.x] != 0xffffffffu) {
+      atomicMin(&cv.geom[0].bbox_ord[threadIdx.x], s_lo[threadIdx.x]);
+      atomicMax(&cv.geom[0].bbox_ord[kMaxGrid + threadIdx.x], s_hi[threadIdx.x]);
+    }
+    if (any_bad && threadIdx.x == 0) set_status(cv.cls->status, kStatusBadCoord);
+    return;
+  }
   const int lane = threadIdx.x & 31;
   const uint32_t nw = gridDim.x * (blockDim.x >> 5);
   const uint32_t w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -86,15 +150,7 @@ __global__ void k_bbox(const T* __restrict__ pts, ClassView cv, int g) {
     if (p < end) {
       const T* row = pts + I.coord + (size_t)(p - I.start) * I.d;
       for (int a = 0; a < I.d; ++a) {
-        const T v = row[a];
-        float x;
-        if constexpr (std::is_integral<T>::value) {
-          bad |= (v > (1 << 24)) | (v < -(1 << 24));
-          x = (float)v;
-        } else {
-          x = (float)v;
-          bad |= !(fabsf(x) <= 1.152921504606846976e18f);  // 2^60; false for NaN
-        }
+        const float x = bbox_value<T>(row[a], bad);
         if (a < kMaxGrid) {
 #pragma unroll
           for (int k = 0; k < kMaxGrid; ++k)

@@ -7,9 +7,10 @@
 // pointer jumping instead: each round makes every pointer jump several times
 // towards its root (see k_label_jump for the rate).  Rounds are launched a
 // fixed number of times (label_rounds: enough for any forest of n points);
-// a round that sees no change in the previous one returns at once, so the
-// launch sequence does not depend on the data.  A pointer still moving after
-// the last round means the input was not a forest, recorded as kStatusCycle.
+// a round after one in which every pointer reached its root returns at once,
+// so the launch sequence does not depend on the data.  A pointer still short
+// of a root after the last round means the input was not a forest, recorded
+// as kStatusCycle.
 #include "internal.h"
 
 namespace dpc {
@@ -61,30 +62,37 @@ __global__ void k_label_init(const int32_t* __restrict__ rho, const int32_t* __r
 // ever move towards the root, so concurrent updates by other threads are
 // harmless.  If every pointer covered at least L steps before a round, the
 // first jump covers 2L and each further one at least L more, so a round
-// multiplies the covered distance by at least kJumps + 1.
+// multiplies the covered distance by at least kJumps + 1.  A pointer that
+// reached a root (a center, which points to itself, or noise) is final; the
+// next round runs only if some pointer has not (flags[r]).  Only thread i
+// writes par[i], and never i itself: a walk that comes back to its own point
+// is on a cycle, and writing it as its own parent would make a root of it,
+// so the points of a cycle (and those leading into it) never reach a root
+// and the flag of the last round reports it.
 constexpr int kJumps = 32;
 __global__ void k_label_jump(int32_t* par, ClassView cv, int32_t* flags, int r) {
-  if (flags[r - 1] == 0) return;  // the previous round changed nothing
-  int changed = 0;
+  if (flags[r - 1] == 0) return;  // every pointer reached its root before
+  int open = 0;
   for_class_points(cv, [&](uint32_t, int32_t i, const InstDev&) {
     int32_t p = par[i];
     if (p < 0 || p == i) return;
     const int32_t p0 = p;
+    bool root = false;
 #pragma unroll 1
     for (int j = 0; j < kJumps; ++j) {
       const int32_t pp = par[p];
       if (pp == p || pp < 0) {
         if (pp < 0) p = pp;
+        root = true;
         break;
       }
       p = pp;
+      if (p == i) break;  // back at itself: a cycle, never written as a root
     }
-    if (p != p0) {
-      par[i] = p;
-      changed = 1;
-    }
+    if (p != p0 && p != i) par[i] = p;
+    if (!root) open = 1;
   });
-  if (__syncthreads_or(changed) && threadIdx.x == 0) flags[r] = 1;
+  if (__syncthreads_or(open) && threadIdx.x == 0) flags[r] = 1;
 }
 
 // Output indices of the centers back to instance-local ids.
@@ -108,8 +116,10 @@ inline unsigned grid_for(uint64_t n) {
 
 }  // namespace
 
-// Rounds until every chain (at most n - 1 long) has reached its root, plus
-// one that sees no change: the smallest r with (kJumps + 1)^r >= n, plus 2.
+// Rounds until every chain (at most n - 1 long) has reached its root (the
+// smallest r with (kJumps + 1)^r >= n), one in which a pointer that landed on
+// its root with its last jump sees it, and one more whose flag the check
+// reads (0 for a forest): r + 2.
 int label_rounds(uint32_t n) {
   int r = 0;
   unsigned long long reach = 1;

@@ -181,6 +181,31 @@ def test_cluster_on_generated_forest():
     assert np.array_equal(got.cpu().numpy(), ref)
 
 
+def test_cluster_reports_cycles():
+    """Dependent pointers that do not form a forest (a three-cycle, with a long
+    chain leading into it) are reported as DPC_ERR_DATA, and a forest
+    afterwards is labelled exactly."""
+    n = 5000
+    rho = np.full(n, 10, np.int32)
+    lam = (np.arange(n) - 1).astype(np.int32)   # i depends on i - 1
+    lam[0] = -1
+    delta = np.full(n, 1.0)
+    delta[0] = np.inf
+    batch = dpc.Batch.single(n, 2, [1.0])
+    params = dpc.make_params(batch, 1, 5, 5.0)
+    ref = oracle.cluster(rho, lam, delta, 1, 5, 5.0)
+    cyc = lam.copy()
+    cyc[10], cyc[11], cyc[12] = 12, 10, 11      # 10 -> 12 -> 11 -> 10; 13.. lead into it
+    with pytest.raises(dpc.DpcError) as e:
+        dpc.dpc_cluster(batch, 0, params, torch.from_numpy(rho).cuda(), torch.from_numpy(cyc).cuda(),
+                        torch.from_numpy(delta).cuda(), sync=True)
+    assert e.value.code == dpc.DPC_ERR_DATA
+    got = dpc.dpc_cluster(batch, 0, params, torch.from_numpy(rho).cuda(), torch.from_numpy(lam).cuda(),
+                          torch.from_numpy(delta).cuda(), sync=True)
+    assert np.array_equal(got.cpu().numpy(), ref)
+    assert np.all(ref == 0)
+
+
 def test_bad_coordinates_reported():
     pts = W.random_blobs(100, 2, 4)
     pts[17, 1] = np.nan
