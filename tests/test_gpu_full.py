@@ -1,7 +1,8 @@
 """GPU parity at the full workload sizes, element by element.
 
-Every point of the 1e6-point 2-D set, the 1e7-point 3-D set and the 2e6-point
-7-D set at all four of its cutoffs is compared with the kd-tree oracle
+Every point of the 1e6-point 2-D set, the 1e7-point 3-D set, the 2e6-point
+7-D set at all four of its cutoffs and the seed-spreader family of the
+scaling study (2-D up to 1e6 points, 3-D at 4e6) is compared with the kd-tree oracle
 (oracle.tree_run: the same definitions as the brute-force oracle, which it
 is pinned against in test_oracle_tree.py): rho, lambda and labels equal,
 delta identical to the last bit.  The float32-certified and the plain binary64
@@ -81,6 +82,15 @@ def test_c3_full():
     f64 = run(w, "fp64")
     for k in f32:
         assert np.array_equal(f32[k].view(np.uint8), f64[k].view(np.uint8)), k
+
+
+@pytest.mark.parametrize("n,d", [(1000, 2), (100_000, 2), (1_000_000, 2), (4_000_000, 3)])
+def test_spreader_family(n, d):
+    """The seed-spreader family of the scaling study (2-D, the simden stand-in,
+    at 1e3..1e6 points) and the 4e6-point 3-D case the kernel profiles use,
+    every point against the oracle."""
+    w = W.spreader(n, d)
+    compare_all_cutoffs(w, run(w, "fp32"), oracle_full(w))
 
 
 def test_c5_full_sweep():
